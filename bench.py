@@ -1,0 +1,340 @@
+#!/usr/bin/env python
+"""Benchmark of the CT-AUX submatrix-update hot path on GB300.
+
+One step = one full submatrix block of every chain: pre-insertion and G0
+gather, prep products, k_max proposals with Gamma growth, Woodbury flush with
+compaction, G(tau) measurement, and the FP64 refresh every 32 blocks
+(amortised: it lands inside the timed steps at its natural rate).
+
+Metric: accepted updates per second (whole job, all GPUs).  Default workload:
+the 2x2x2 simple-cubic cluster (N_c=8, beta=5, U=8) with k_max=64 and the
+expansion constant K=256 that puts the order at n~430 (inside the 300-500
+range the workload names).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
+  python bench.py --impl reference      # the CPU oracle on the same workload
+
+Timing: W untimed blocks, then K timed blocks, each bracketed by CUDA events on
+the stream the library launches on, with the L2 cache flushed (a 512 MB write)
+between timed blocks; barrier + synchronize on both sides; max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "CT-AUX accepted updates/s per GPU, mixed vs FP64 at |dN|<1e-8; flush %peak"
+UNIT = "accepted updates/s"
+N_TAU_BINS, N_ANCHORS, REFRESH_EVERY = 32, 4, 32
+
+
+def workload(name, K, k_max, chain_id=0):
+    from workloads import configs
+    if name == "cube8":
+        ch = configs.cube8(K=K, k_max=k_max, capacity=1024, seed=chain_id)
+        ch.chain_id = chain_id
+        return [ch], dict(n_target=430 if K >= 200 else 140)
+    if name == "aim1":
+        ch = configs.aim1(K=K, k_max=k_max, capacity=256, seed=chain_id)
+        return [ch], dict(n_target=20)
+    if name == "batch":
+        chs = configs.batch(n_chains=512, k_max=k_max, K=K)
+        for c in chs:
+            c.chain_id += 512 * chain_id
+        return chs, dict(n_target=None)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# nominal dense rates of GB300 per the recipe table (TFLOP/s)
+NOMINAL = {"bf16": 2250.0, "tf32": 1100.0, "fp64": 1.25}
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            v = [x.strip() for x in line.split(",")]
+            if len(v) >= 9:
+                rows.append(v)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def cpu_baseline(chains, meta, seconds=15.0):
+    """The oracle as it stands, single process, on a bounded sample of the workload."""
+    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+    from oracle.ctaux import OracleChain
+    from workloads import configs
+    ch = chains[0]
+    n0 = meta["n_target"] or 100
+    cfg = configs.synthetic_configuration(ch, n0, seed=11)
+    oc = OracleChain(ch.table, ch.dx_class, ch.beta, ch.U, ch.K, seed=ch.seed, chain_id=ch.chain_id)
+    oc.set_config(cfg["tau"], cfg["site"], cfg["s"], cfg["birth"], cfg["t"])
+    t0 = time.perf_counter()
+    props = acc = 0
+    while time.perf_counter() - t0 < seconds:
+        for rec in oc.run(ch.k_max):
+            props += 1
+            acc += int(rec["accept"])
+    dt = time.perf_counter() - t0
+    threads = int(os.environ.get("OPENBLAS_NUM_THREADS", "1"))
+    return {"value": acc / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{props} proposals ({props // ch.k_max} blocks of k_max={ch.k_max}) of "
+                      f"{ch.name} from a seeded n={n0} configuration, {dt:.1f} s, dense-LU ratios",
+            "proposals_per_s": props / dt}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+    from oracle.ctaux import OracleChain
+    from workloads import configs
+    chains, meta = workload(args.workload, args.K, args.k_max)
+    ch = chains[0]
+    n0 = meta["n_target"] or 100
+    cfg = configs.synthetic_configuration(ch, n0, seed=11)
+    oc = OracleChain(ch.table, ch.dx_class, ch.beta, ch.U, ch.K, seed=ch.seed, chain_id=ch.chain_id)
+    oc.set_config(cfg["tau"], cfg["site"], cfg["s"], cfg["birth"], cfg["t"])
+    # a step of the reference: a bounded sample of one block (at most 8 proposals)
+    per_step = min(ch.k_max, 8)
+    for _ in range(args.warmup):
+        oc.run(per_step)
+    acc = 0
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        acc += sum(int(r["accept"]) for r in oc.run(per_step))
+    dt = time.perf_counter() - t0
+    value = acc / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{ch.name} N_c={ch.n_c} beta={ch.beta} U={ch.U} K={ch.K} "
+                                   f"k_max={ch.k_max} n~{n0}", "l2": "oracle on host"},
+            "cpu_baseline": {"value": value, "unit": UNIT,
+                             "cores": int(os.environ.get("OPENBLAS_NUM_THREADS", "1")),
+                             "kind": "oracle",
+                             "sample": f"{args.steps} steps of {per_step} proposals from a seeded "
+                                       f"n={n0} configuration"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--workload", default="cube8")
+    ap.add_argument("--K", type=float, default=256.0)
+    ap.add_argument("--k-max", dest="k_max", type=int, default=64)
+    ap.add_argument("--thermalize", type=int, default=300)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import paper_1010_3690_gb300 as pk
+    chains, meta = workload(args.workload, args.K, args.k_max, chain_id=rank)
+    precision = pk.CTAUX_MIXED if args.precision == "mixed" else pk.CTAUX_FP64
+    ctx = pk.Context(chains, precision=precision, refresh_every=REFRESH_EVERY,
+                     n_tau_bins=N_TAU_BINS, n_anchors=N_ANCHORS, device=local)
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    ctx.sweep(args.thermalize, measure=False, stream=sh)
+    for _ in range(max(3, args.warmup)):
+        ctx.sweep(1, measure=True, stream=sh)
+    ctx.synchronize()
+
+    def accepted_total():
+        return sum(sum(ctx.stats(i)["accepted"]) for i in range(len(chains)))
+
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    acc0 = accepted_total()
+    work0 = ctx.work()
+    ms0, kern0 = ctx.phase_times()
+    ctx.set_profiling(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.zero_()
+        starts[i].record(stream)
+        ctx.sweep(1, measure=True, stream=sh)
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ctx.set_profiling(False)
+    total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    acc = accepted_total() - acc0
+    ms1, kern1 = ctx.phase_times()
+    work1 = ctx.work()
+    phase_ms = ms1 - ms0
+    kernels = int((kern1 - kern0).sum())
+    if world > 1:
+        t = torch.tensor([total_ms, float(acc)], dtype=torch.float64, device="cuda")
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        total_ms, acc = float(tmax[0]), float(t[1])
+    value = acc / (total_ms / 1e3)
+
+    # ---------------- roofline of the dominant kernel (CUDA events, live)
+    peaks, peak_kind = load_peaks()
+    names = ctx.PHASES
+    dom = int(phase_ms.argmax())
+    steps = args.steps
+    fp64_peak = peaks["bf16_tflops"] * NOMINAL["fp64"] / NOMINAL["bf16"]
+    fp32_simt_peak = 152 * 128 * 2 * 2.07e9 / 1e12     # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
+    prep_flop = work1["prep_flop"] - work0["prep_flop"]
+    flush_flop = work1["flush_flop"] - work0["flush_flop"]
+    flush_bytes = work1["flush_bytes"] - work0["flush_bytes"]
+    def roof(phase):
+        sec = phase_ms[phase] / 1e3
+        if names[phase] == "flush_gemm":
+            if precision == pk.CTAUX_FP64:
+                return dict(bound="alu", achieved=flush_flop / sec / 1e12, peak=fp64_peak,
+                            unit="TFLOP/s", peak_source=f"FP64 = bf16 {peak_kind} x 1.25/2250")
+            return dict(bound="alu", achieved=flush_flop / sec / 1e12, peak=fp32_simt_peak,
+                        unit="TFLOP/s", peak_source="FP32 FMA lanes x max clock")
+        if names[phase] == "prep":
+            pk_ = fp64_peak if precision == pk.CTAUX_FP64 else fp32_simt_peak
+            return dict(bound="alu", achieved=prep_flop / sec / 1e12, peak=pk_, unit="TFLOP/s",
+                        peak_source="FP64 = bf16 x 1.25/2250" if precision == pk.CTAUX_FP64 else
+                        "FP32 FMA lanes x max clock")
+        # latency-bound phases: report bytes of N touched per block against HBM
+        nbytes = flush_bytes / 2.0
+        return dict(bound="hbm", achieved=nbytes / sec / 1e9, peak=peaks["hbm_gbs"], unit="GB/s",
+                    peak_source=f"hbm_gbs {peak_kind}")
+    r = roof(dom)
+    roofline = {"kernel": names[dom], "bound": r["bound"], "achieved": r["achieved"],
+                "peak": r["peak"], "unit": r["unit"], "frac": r["achieved"] / r["peak"],
+                "traffic": None, "peak_source": r["peak_source"],
+                "ms_per_step": phase_ms[dom] / steps}
+    fr = roof(names.index("flush_gemm"))
+    flush_roof = {"bound": fr["bound"], "achieved": fr["achieved"], "peak": fr["peak"],
+                  "unit": fr["unit"], "frac": fr["achieved"] / fr["peak"],
+                  "ms_per_step": phase_ms[3] / steps, "peak_source": fr["peak_source"]}
+
+    # ---------------- end to end through the C ABI with host buffers
+    e2e_steps = max(5, min(args.steps, 50))
+    acc_e0 = accepted_total()
+    t_e2e = 0.0
+    d2h = 0
+    for _ in range(e2e_steps):
+        t0 = time.perf_counter()
+        ctx.sweep(1, measure=True, stream=sh)
+        G, E, nm = ctx.measure_G(0)
+        st = ctx.stats(0)
+        t_e2e += time.perf_counter() - t0
+        d2h = 2 * G.nbytes + 512   # sums and squares of G, plus the counters
+    acc_e = accepted_total() - acc_e0
+    e2e = {"value": acc_e / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 0,
+           "d2h_bytes_per_step": d2h}
+
+    st = ctx.stats(0)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if precision == pk.CTAUX_FP64 else "f32",
+            "data": "synthetic",
+            "config": {"workload": f"{chains[0].name} N_c={chains[0].n_c} beta={chains[0].beta} "
+                                   f"U={chains[0].U} K={chains[0].K} k_max={chains[0].k_max}, "
+                                   f"{len(chains)} chain(s) per GPU",
+                       "order_n": st["n"], "precision": args.precision,
+                       "l2": "flushed between timed steps (512 MB write)",
+                       "refresh_every": REFRESH_EVERY, "n_tau_bins": N_TAU_BINS,
+                       "n_anchors": N_ANCHORS},
+            "roofline": roofline, "flush_roofline": flush_roof,
+            "phase_ms_per_step": {names[i]: phase_ms[i] / steps for i in range(len(names))},
+            "gpu_launches": kernels,
+            "accept_rate": acc / max(1, steps * sum(c.k_max for c in chains) * world),
+            "drift_max_last_refresh": st["last_drift_max"],
+            "clocks": clk, "e2e": e2e}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(chains, meta, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,209 @@
+/*
+ * ctaux.h -- C ABI of the GB300 submatrix-update CT-AUX hot path.
+ *
+ * What the library computes (Gull et al., "Submatrix updates for the
+ * Continuous-Time Auxiliary Field algorithm"):
+ *   - Markov chains over auxiliary-spin configurations {(tau_i, x_i, s_i)} with
+ *     weight prod_sigma det N_sigma^{-1}, N_sigma^{-1} = e^{V_sigma} - G0_sigma
+ *     (e^{V_sigma} - 1)  (Sec. II A, Eqs. Zn_div_Z0 and Nmatrix);
+ *   - insertion/removal/spin-flip proposals accepted with min(1, |R|)
+ *     (Sec. II B, Eq. insprob);
+ *   - executed as the submatrix update of Secs. III-IV: k_max s=0 vertices are
+ *     pre-inserted (Sec. IV A), each proposal grows a k x k Gamma^{-1} per spin
+ *     by partitioning (Sec. III D, Eq. ratS), and after k_max proposals N is
+ *     updated by the Woodbury formula (Eq. Nshermanmorrison) and the s=0 rows
+ *     and columns are removed (Sec. IV C);
+ *   - plus a periodic from-scratch FP64 recomputation of N and the G(tau)
+ *     measurement of Sec. IV D.
+ *
+ * Conventions shared by every entry point:
+ *   - All pointers are HOST pointers unless a name says otherwise.  Input
+ *     arrays are copied before the call returns; the caller keeps ownership.
+ *     Output arrays are caller-owned and written synchronously.
+ *   - The library allocates all device memory it needs in ctaux_init
+ *     (cudaMalloc) and frees it in ctaux_destroy.
+ *   - Errors are returned as ctaux_status; nothing aborts or traps.  A device
+ *     side fault flag (capacity exceeded, non-finite ratio) is reported by the
+ *     next synchronous call; ctaux_last_error() gives a text for the last
+ *     failure of a context.
+ *   - One context must be used from one host thread at a time.
+ *   - Spin index: 0 = up (sigma = +1), 1 = down (sigma = -1).  Matrices are
+ *     column-major.
+ */
+#ifndef CTAUX_H
+#define CTAUX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ctaux_ctx ctaux_ctx;
+
+typedef enum {
+  CTAUX_OK = 0,
+  CTAUX_EINVAL = 1,     /* bad argument */
+  CTAUX_ENOMEM = 2,     /* device allocation failed */
+  CTAUX_ECUDA = 3,      /* CUDA runtime error (text in ctaux_last_error) */
+  CTAUX_ECAPACITY = 4,  /* expansion order + k_max exceeded the capacity */
+  CTAUX_ESINGULAR = 5,  /* zero pivot in the from-scratch recomputation */
+  CTAUX_EDRIFT = 6,     /* drift above the threshold at a recomputation */
+  CTAUX_ETIMEOUT = 7,   /* a bounded device-side wait gave up */
+  CTAUX_ENUMERIC = 8    /* non-finite determinant ratio (proposal rejected) */
+} ctaux_status;
+
+/* Precision forms. */
+enum {
+  CTAUX_FP64 = 0,       /* N, Gamma^{-1}, all products in float64 */
+  CTAUX_MIXED = 1       /* N, Gamma^{-1} in float32; FP64 refresh and near-tie accepts */
+};
+
+/* Move types (trace records). */
+enum { CTAUX_INSERT = 0, CTAUX_REMOVE = 1, CTAUX_FLIP = 2 };
+
+/* One Markov chain's model and run parameters. */
+typedef struct {
+  int n_c;                  /* cluster sites N_c (1 = single impurity) */
+  int n_classes;            /* displacement classes = rows of the table per spin */
+  int n_tau;                /* table points on [0, beta], both ends included, >= 2 */
+  const double *g0_table;   /* [2][n_classes][n_tau]: G0_sigma(class, j*beta/(n_tau-1)),
+                               sign G0 = -<T d d^dagger>; j=0 holds G0(0+), j=n_tau-1 G0(beta-) */
+  const int *dx_class;      /* [n_c][n_c]: class of the displacement x_i - x_j */
+  double beta;              /* inverse temperature */
+  double U;                 /* Hubbard interaction */
+  double K;                 /* expansion constant (Eq. gamma), > 0 */
+  int k_max;                /* proposals per submatrix block, 1..256 */
+  int capacity;             /* largest expansion order n the chain may reach */
+  uint64_t seed;            /* Philox-4x32-10 key */
+  uint32_t chain_id;        /* third Philox counter word */
+} ctaux_chain_params;
+
+typedef struct {
+  int n_chains;                       /* 1..2048 independent chains */
+  const ctaux_chain_params *chains;   /* [n_chains] */
+  int precision;                      /* CTAUX_FP64 or CTAUX_MIXED */
+  int refresh_every;                  /* from-scratch N every this many blocks; 0 = never */
+  double p_insert;                    /* move mix: insert / flip; remove = 1 - both */
+  double p_flip;
+  int n_tau_bins;                     /* G(tau) measurement bins on (0, beta) */
+  int n_anchors;                      /* anchor times of the G(tau) estimator */
+  int trace_capacity;                 /* per-chain trace ring size; 0 = no trace */
+  int device;                         /* CUDA device ordinal */
+} ctaux_params;
+
+typedef struct {
+  int64_t n;                 /* current expansion order */
+  int64_t t;                 /* next proposal counter */
+  int64_t proposals[3];      /* by move type */
+  int64_t accepted[3];
+  int64_t sweeps;            /* completed blocks (prep + k_max proposals + flush) */
+  int64_t measurements;
+  int64_t order_sum;         /* sum of n over measurements */
+  double sign_sum;           /* sum of the walker sign over measurements */
+  int64_t numeric_rejects;   /* proposals rejected for a non-finite ratio */
+  int64_t refreshes;
+  double last_drift_max;     /* max |N_run - N_fresh| at the last refresh (both spins) */
+  double last_drift_fro;     /* Frobenius norm of the same difference */
+  double logdet[2];          /* log|det N_sigma^{-1}| at the last refresh */
+  int sign;                  /* current walker sign */
+  int status;                /* device fault bits (0 = none) */
+} ctaux_stats;
+
+typedef struct {
+  int64_t t;                 /* proposal counter */
+  int32_t move;              /* CTAUX_INSERT / REMOVE / FLIP */
+  int32_t n;                 /* order before the proposal */
+  int64_t birth;             /* birth stamp (insertion counter) of the vertex; -1 if none */
+  int32_t s_new;             /* proposed auxiliary spin */
+  int32_t accept;            /* 1 if accepted */
+  double ratio[2];           /* det N'^{-1}_sigma / det N^{-1}_sigma per spin */
+  double R;                  /* full Metropolis ratio */
+  double u;                  /* accept uniform */
+} ctaux_trace_rec;
+
+/* Create a context: copies the tables, allocates device state for every
+ * chain (N double-buffered at (capacity + k_max)^2 per spin), starts every
+ * chain from the empty configuration at counter 0.  *out is NULL on error. */
+ctaux_status ctaux_init(const ctaux_params *params, ctaux_ctx **out);
+
+/* Run n_sweeps blocks on every chain, asynchronously on `cuda_stream`
+ * (a cudaStream_t, NULL = legacy default stream).  One block = pre-insertion
+ * of the block's insertion candidates (s = 0), the G0 gather and prep
+ * products (Sec. IV A), k_max proposals with Gamma growth (Secs. III D, IV B),
+ * the Woodbury flush with compaction (Sec. IV C), then, if `measure` is
+ * non-zero, one G(tau) measurement (Sec. IV D), and every refresh_every
+ * blocks a from-scratch FP64 recomputation of N. */
+ctaux_status ctaux_sweep(ctaux_ctx *ctx, int n_sweeps, int measure, void *cuda_stream);
+
+/* Mean and naive standard error of G_sigma(class, tau bin) over the
+ * measurements of one chain since the last reset; arrays [2][n_classes][n_tau_bins].
+ * err_out may be NULL.  Synchronises the context's stream. */
+ctaux_status ctaux_measure_G(ctaux_ctx *ctx, int chain, double *G_out, double *err_out,
+                             int64_t *n_meas_out);
+
+/* Zero every chain's measurement accumulators (asynchronous). */
+ctaux_status ctaux_reset_measurements(ctaux_ctx *ctx);
+
+/* FP64 from-scratch recomputation of N for every chain (build N^{-1} from the
+ * configuration, Gauss-Jordan inversion with partial pivoting); returns the
+ * largest max-abs drift |N_run - N_fresh| over chains and spins.  Synchronous. */
+ctaux_status ctaux_recompute(ctaux_ctx *ctx, double *drift_max_out);
+
+/* Counters of one chain (synchronous). */
+ctaux_status ctaux_get_stats(ctaux_ctx *ctx, int chain, ctaux_stats *out);
+
+/* The trace records written since the previous call (oldest first, at most
+ * trace_capacity are kept); *n_out records are written to buf[0..cap). */
+ctaux_status ctaux_get_trace(ctaux_ctx *ctx, int chain, ctaux_trace_rec *buf, int cap,
+                             int *n_out);
+
+/* Configuration checkpoint of one chain in birth order: tau, site, spin,
+ * birth stamp (arrays of at least `cap` entries), order and next counter. */
+ctaux_status ctaux_get_config(ctaux_ctx *ctx, int chain, double *tau, int *site, int *s,
+                              int64_t *birth, int cap, int *n_out, int64_t *t_out);
+
+/* Replace one chain's configuration (sorted by birth stamp inside) and
+ * counter, then rebuild its N from scratch in FP64.  s must be +-1. */
+ctaux_status ctaux_set_config(ctaux_ctx *ctx, int chain, const double *tau, const int *site,
+                              const int *s, const int64_t *birth, int n, int64_t t);
+
+/* Copy N_sigma of one chain (m x m, m = current order) into out[j*ld_out + i],
+ * converted to float64; *m_out = m. */
+ctaux_status ctaux_get_N(ctaux_ctx *ctx, int chain, int spin, double *out, int ld_out,
+                         int *m_out);
+
+/* Per-phase device time, accumulated with CUDA events recorded on the sweep
+ * stream while profiling is on, and the number of kernels launched per phase
+ * (always counted).  Phases: 0 plan + G0 gather, 1 prep products,
+ * 2 proposals (Gamma growth), 3 flush product, 4 flush support (survivor
+ * list, Y = (G-1) Gamma^{-1}, end of block), 5 measurement, 6 FP64 refresh.
+ * ms_out[7], kernels_out[7]; either may be NULL. */
+ctaux_status ctaux_set_profiling(ctaux_ctx *ctx, int on);
+ctaux_status ctaux_get_phase_times(ctaux_ctx *ctx, double *ms_out, int64_t *kernels_out);
+
+/* Algorithmic work of the blocks run so far, summed over chains (for
+ * rooflines): flop counts of prep and flush products, bytes of N read and
+ * written by the flush. */
+ctaux_status ctaux_get_work(ctaux_ctx *ctx, double *prep_flop, double *flush_flop,
+                            double *flush_bytes);
+
+/* Philox-4x32-10 on the device: for counters (t0 + i, chain, purpose), i <
+ * count, write the two 53-bit uniforms of each draw to out[2*i], out[2*i+1].
+ * A check of the device generator; allocates and frees a small buffer. */
+ctaux_status ctaux_philox_uniforms(uint64_t seed, uint32_t chain, int64_t t0, int count,
+                                   int purpose, double *out);
+
+/* Block until all work queued on the context finishes; reports device faults. */
+ctaux_status ctaux_synchronize(ctaux_ctx *ctx);
+
+void ctaux_destroy(ctaux_ctx *ctx);
+
+/* Text of the last error of a context (never NULL). */
+const char *ctaux_last_error(const ctaux_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CTAUX_H */

@@ -1,0 +1,627 @@
+// C ABI of the CT-AUX submatrix-update library (declared in include/ctaux.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/ctaux.h"
+#include "ctaux_dev.cuh"
+#include "ctaux_kernels.h"
+
+using namespace ctaux;
+
+struct ctaux_ctx {
+  ctaux_params params{};
+  std::vector<ctaux_chain_params> chains;
+  int device = 0;
+  int sm_count = 0;
+  LaunchShape ls{};
+  void* chains_dev = nullptr;        // Chain<double>[] or Chain<float>[]
+  std::vector<Chain<double>> hc64;   // host copies of the descriptors
+  std::vector<Chain<float>> hc32;
+  std::vector<void*> allocations;
+  cudaStream_t last_stream = nullptr;
+  PhaseTimer* timer = nullptr;
+  bool profiling = false;
+  int blocks_since_refresh = 0;
+  std::string err;
+  int max_ld = 0;
+};
+
+namespace {
+
+ctaux_status set_err(ctaux_ctx* ctx, ctaux_status st, const char* fmt, ...) {
+  if (ctx) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    ctx->err = buf;
+  }
+  return st;
+}
+
+#define CUDA_TRY(ctx, expr)                                                                  \
+  do {                                                                                       \
+    cudaError_t _e = (expr);                                                                 \
+    if (_e != cudaSuccess)                                                                   \
+      return set_err(ctx, CTAUX_ECUDA, "%s: %s", #expr, cudaGetErrorString(_e));             \
+  } while (0)
+
+template <typename X>
+X* dalloc(ctaux_ctx* ctx, size_t count, cudaError_t* err) {
+  void* p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc(&p, count * sizeof(X));
+  if (e != cudaSuccess) {
+    *err = e;
+    return nullptr;
+  }
+  e = cudaMemset(p, 0, count * sizeof(X));
+  if (e != cudaSuccess) *err = e;
+  ctx->allocations.push_back(p);
+  return reinterpret_cast<X*>(p);
+}
+
+int round_up(int v, int q) { return (v + q - 1) / q * q; }
+
+bool is_mixed(const ctaux_ctx* ctx) { return ctx->params.precision == CTAUX_MIXED; }
+
+template <typename T>
+std::vector<Chain<T>>& host_chains(ctaux_ctx* ctx);
+template <>
+std::vector<Chain<double>>& host_chains<double>(ctaux_ctx* ctx) { return ctx->hc64; }
+template <>
+std::vector<Chain<float>>& host_chains<float>(ctaux_ctx* ctx) { return ctx->hc32; }
+
+template <typename T>
+ctaux_status build_chains(ctaux_ctx* ctx) {
+  const ctaux_params& P = ctx->params;
+  auto& hc = host_chains<T>(ctx);
+  hc.resize(ctx->chains.size());
+  cudaError_t err = cudaSuccess;
+  int max_ld = 0, max_k = 1, max_cls_bins = 1, max_pts = 1;
+  size_t kpart_elems = 0;
+  int max_tiles[PH_COUNT] = {0, 0, 0, 0, 0};
+  // launch shape first (tile bounds and k splits from the capacities)
+  const int items = 2 * (int)ctx->chains.size();
+  for (size_t ci = 0; ci < ctx->chains.size(); ++ci) {
+    const ctaux_chain_params& cp = ctx->chains[ci];
+    const int cap_m = cp.capacity + cp.k_max;
+    const int ld = round_up(cap_m, 32);
+    max_ld = std::max(max_ld, ld);
+    max_k = std::max(max_k, cp.k_max);
+    max_cls_bins = std::max(max_cls_bins, cp.n_classes * P.n_tau_bins);
+    max_pts = std::max(max_pts, P.n_anchors * cp.n_c * P.n_tau_bins);
+    const int te = sizeof(T) == 8 ? 32 : 64;  // output tile edge of the products
+    const int tm = (cap_m + te - 1) / te, tk = (cp.k_max + te - 1) / te, ta = (P.n_anchors + te - 1) / te;
+    max_tiles[PH_RTILDE] = std::max(max_tiles[PH_RTILDE], tk * tm);
+    max_tiles[PH_GCOL_OLD] = std::max(max_tiles[PH_GCOL_OLD], tm * tk);
+    max_tiles[PH_GCOL_NEW] = std::max(max_tiles[PH_GCOL_NEW], tk * tk);
+    max_tiles[PH_FLUSH] = std::max(max_tiles[PH_FLUSH], tm * tm);
+    max_tiles[PH_MEAS] = std::max(max_tiles[PH_MEAS], tm * ta);
+  }
+  LaunchShape& ls = ctx->ls;
+  ls.n_chains = (int)ctx->chains.size();
+  // fixed slice width of the inner dimension: narrow for FP64 (the FP64 pipe
+  // is the bottleneck, so more CTAs), wider for FP32
+  ls.kchunk = (sizeof(T) == 8) ? 32 : 128;
+  for (int ph = 0; ph < PH_COUNT; ++ph) {
+    ls.tiles[ph] = std::max(1, max_tiles[ph]);
+    int max_k_inner = 0;
+    for (const auto& cp : ctx->chains)
+      max_k_inner = std::max(max_k_inner, ph == PH_FLUSH ? cp.k_max : cp.capacity + cp.k_max);
+    const int ks = std::max(1, (max_k_inner + ls.kchunk - 1) / ls.kchunk);
+    ls.ksplit[ph] = ks;
+    const size_t te = sizeof(T) == 8 ? 32 : 64;
+    if (ks > 1) kpart_elems = std::max(kpart_elems, (size_t)ls.tiles[ph] * ks * te * te);
+  }
+  ls.gather_slices = std::max(1, std::min(64, (2 * ctx->sm_count + items - 1) / items));
+  ls.y_blocks = (max_ld + 15) / 16;
+  ls.meas_point_blocks = (max_pts + 255) / 256;
+  ls.meas_lchunks = (max_ld + kMeasChunk - 1) / kMeasChunk;
+  ls.meas_cb_blocks = (max_cls_bins + 255) / 256;
+  ctx->max_ld = max_ld;
+  // proposal kernel shared memory
+  size_t fixed = sizeof(double) * 8 * max_k + sizeof(double) * 2 * max_k + sizeof(int) * max_k +
+                 sizeof(short) * ((max_ld + 7) & ~7) + sizeof(uint32_t) * ((max_ld + 31) / 32) + 64;
+  size_t gam = sizeof(T) * 2 * (size_t)max_k * max_k;
+  ls.gamma_in_smem = (fixed + gam <= 200 * 1024) ? 1 : 0;
+  ls.prop_smem = (int)(fixed + (ls.gamma_in_smem ? gam : 0));
+  CUDA_TRY(ctx, configure_block_kernels<T>(ls));
+  int nb = refresh_blocks_per_sm<T>();
+  ls.refresh_grid = std::max(1, nb) * ctx->sm_count;
+
+  for (size_t ci = 0; ci < ctx->chains.size(); ++ci) {
+    const ctaux_chain_params& cp = ctx->chains[ci];
+    Chain<T>& c = hc[ci];
+    std::memset(&c, 0, sizeof(c));
+    c.beta = cp.beta;
+    c.K = cp.K;
+    c.gamma = std::acosh(1.0 + cp.beta * cp.U * (double)cp.n_c / (2.0 * cp.K));
+    c.dtau = cp.beta / (double)(cp.n_tau - 1);
+    c.inv_dtau = (double)(cp.n_tau - 1) / cp.beta;
+    for (int spin = 0; spin < 2; ++spin) {
+      const double sig = spin == 0 ? 1.0 : -1.0;
+      for (int dd = -2; dd <= 2; ++dd) {
+        c.ev[spin][dd + 2] = (dd == 0) ? 1.0 : std::exp(c.gamma * sig * dd);
+        c.inv_em1[spin][dd + 2] = (dd == 0) ? 0.0 : 1.0 / (c.ev[spin][dd + 2] - 1.0);
+      }
+    }
+    c.p_insert = P.p_insert;
+    c.p_remove = 1.0 - P.p_insert - P.p_flip;
+    c.n_c = cp.n_c;
+    c.n_classes = cp.n_classes;
+    c.n_tau = cp.n_tau;
+    c.k_max = cp.k_max;
+    c.cap_m = cp.capacity + cp.k_max;
+    c.ld = round_up(c.cap_m, 32);
+    c.seed = cp.seed;
+    c.chain_id = cp.chain_id;
+    c.trace_cap = P.trace_capacity;
+    c.n_bins = P.n_tau_bins;
+    c.n_anchors = P.n_anchors;
+    const size_t ld = c.ld, K = cp.k_max;
+    const size_t tab = (size_t)2 * cp.n_classes * cp.n_tau;
+    double* g0 = dalloc<double>(ctx, tab, &err);
+    int* dxc = dalloc<int>(ctx, (size_t)cp.n_c * cp.n_c, &err);
+    double* cw = dalloc<double>(ctx, cp.n_classes, &err);
+    if (err != cudaSuccess) return set_err(ctx, CTAUX_ENOMEM, "device allocation failed: %s", cudaGetErrorString(err));
+    CUDA_TRY(ctx, cudaMemcpy(g0, cp.g0_table, tab * sizeof(double), cudaMemcpyHostToDevice));
+    CUDA_TRY(ctx, cudaMemcpy(dxc, cp.dx_class, (size_t)cp.n_c * cp.n_c * sizeof(int), cudaMemcpyHostToDevice));
+    std::vector<double> w(cp.n_classes, 0.0);
+    for (int x = 0; x < cp.n_c; ++x) w[cp.dx_class[x * cp.n_c + 0]] += 1.0;
+    for (int k = 0; k < cp.n_classes; ++k) w[k] = w[k] > 0 ? 1.0 / (w[k] * P.n_anchors) : 0.0;
+    CUDA_TRY(ctx, cudaMemcpy(cw, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice));
+    c.g0 = g0;
+    c.dx_class = dxc;
+    c.class_weight = cw;
+    for (int b = 0; b < 2; ++b) {
+      for (int spin = 0; spin < 2; ++spin) c.N[b][spin] = dalloc<T>(ctx, ld * ld, &err);
+      c.tau[b] = dalloc<double>(ctx, ld, &err);
+      c.site[b] = dalloc<int>(ctx, ld, &err);
+      c.s[b] = dalloc<int8_t>(ctx, ld, &err);
+      c.birth[b] = dalloc<int64_t>(ctx, ld, &err);
+    }
+    c.s0 = dalloc<int8_t>(ctx, ld, &err);
+    for (int spin = 0; spin < 2; ++spin) {
+      c.Cpan[spin] = dalloc<T>(ctx, K * ld, &err);
+      c.Bpan[spin] = dalloc<T>(ctx, ld * K, &err);
+      c.Gcol[spin] = dalloc<T>(ctx, ld * K, &err);
+      c.Ginv[spin] = dalloc<T>(ctx, K * K, &err);
+      c.lam[spin] = dalloc<double>(ctx, K, &err);
+      c.Y[spin] = dalloc<T>(ctx, ld * K, &err);
+      c.Mg[spin] = dalloc<T>(ctx, ld * P.n_anchors, &err);
+      c.Mv[spin] = dalloc<T>(ctx, ld * P.n_anchors, &err);
+      c.Mpts[spin] = dalloc<double>(ctx, (size_t)ls.meas_lchunks * P.n_anchors * cp.n_c * P.n_tau_bins, &err);
+      c.kpart[spin] = dalloc<T>(ctx, kpart_elems, &err);
+      c.ticket[spin] = dalloc<int>(ctx, *std::max_element(ls.tiles, ls.tiles + PH_COUNT), &err);
+    }
+    c.P = dalloc<int>(ctx, K, &err);
+    c.S = dalloc<int>(ctx, ld, &err);
+    c.work = dalloc<double>(ctx, (size_t)2 * 2 * ld * ld, &err);
+    c.perm = dalloc<int>(ctx, 2 * ld, &err);
+    c.used = dalloc<int8_t>(ctx, 2 * ld, &err);
+    c.pkeys = dalloc<unsigned long long>(ctx, 2 * ld, &err);
+    c.work_drift = dalloc<double>(ctx, 2, &err);
+    c.work_logdet = dalloc<double>(ctx, 2, &err);
+    const size_t gb = (size_t)2 * cp.n_classes * P.n_tau_bins;
+    c.Gsum = dalloc<double>(ctx, gb, &err);
+    c.Gsq = dalloc<double>(ctx, gb, &err);
+    c.Gmeas = dalloc<double>(ctx, gb, &err);
+    c.trace = dalloc<TraceRec>(ctx, std::max(1, P.trace_capacity), &err);
+    c.dyn = dalloc<Dyn>(ctx, 1, &err);
+    if (err != cudaSuccess)
+      return set_err(ctx, CTAUX_ENOMEM, "device allocation failed: %s", cudaGetErrorString(err));
+    Dyn d0;
+    std::memset(&d0, 0, sizeof(d0));
+    d0.sign = 1;
+    CUDA_TRY(ctx, cudaMemcpy(c.dyn, &d0, sizeof(Dyn), cudaMemcpyHostToDevice));
+  }
+  void* dc = nullptr;
+  CUDA_TRY(ctx, cudaMalloc(&dc, hc.size() * sizeof(Chain<T>)));
+  ctx->allocations.push_back(dc);
+  CUDA_TRY(ctx, cudaMemcpy(dc, hc.data(), hc.size() * sizeof(Chain<T>), cudaMemcpyHostToDevice));
+  ctx->chains_dev = dc;
+  return CTAUX_OK;
+}
+
+ctaux_status check_device_status(ctaux_ctx* ctx) {
+  const bool mixed = is_mixed(ctx);
+  for (size_t ci = 0; ci < ctx->chains.size(); ++ci) {
+    Dyn* dp = mixed ? ctx->hc32[ci].dyn : ctx->hc64[ci].dyn;
+    int st = 0;
+    CUDA_TRY(ctx, cudaMemcpy(&st, &dp->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st & DS_CAPACITY)
+      return set_err(ctx, CTAUX_ECAPACITY, "chain %zu: expansion order + k_max exceeded the capacity", ci);
+    if (st & DS_SINGULAR)
+      return set_err(ctx, CTAUX_ESINGULAR, "chain %zu: zero pivot in the FP64 recomputation", ci);
+    if (st & DS_INDEX) return set_err(ctx, CTAUX_EINVAL, "chain %zu: vertex selection out of range", ci);
+    if (st) return set_err(ctx, CTAUX_ENUMERIC, "chain %zu: device status %d", ci, st);
+  }
+  return CTAUX_OK;
+}
+
+Dyn* dyn_of(ctaux_ctx* ctx, int chain) {
+  return is_mixed(ctx) ? ctx->hc32[chain].dyn : ctx->hc64[chain].dyn;
+}
+
+ctaux_status read_dyn(ctaux_ctx* ctx, int chain, Dyn* out) {
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->last_stream));
+  CUDA_TRY(ctx, cudaMemcpy(out, dyn_of(ctx, chain), sizeof(Dyn), cudaMemcpyDeviceToHost));
+  return CTAUX_OK;
+}
+
+template <typename T>
+ctaux_status do_refresh(ctaux_ctx* ctx, int only_chain, cudaStream_t st) {
+  cudaError_t e = launch_refresh<T>(reinterpret_cast<Chain<T>*>(ctx->chains_dev), ctx->ls, only_chain,
+                                    st, ctx->timer);
+  if (e != cudaSuccess) return set_err(ctx, CTAUX_ECUDA, "refresh launch: %s", cudaGetErrorString(e));
+  return CTAUX_OK;
+}
+
+template <typename T>
+ctaux_status do_sweeps(ctaux_ctx* ctx, int n_sweeps, int measure, cudaStream_t st) {
+  Chain<T>* dc = reinterpret_cast<Chain<T>*>(ctx->chains_dev);
+  PhaseTimer* pt = ctx->timer;
+  for (int s = 0; s < n_sweeps; ++s) {
+    launch_block<T>(dc, ctx->ls, st, pt);
+    ctx->blocks_since_refresh += 1;
+    if (ctx->params.refresh_every > 0 && ctx->blocks_since_refresh >= ctx->params.refresh_every) {
+      ctaux_status r = do_refresh<T>(ctx, -1, st);
+      if (r != CTAUX_OK) return r;
+      ctx->blocks_since_refresh = 0;
+    }
+    if (measure) launch_measure<T>(dc, ctx->ls, st, pt);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_err(ctx, CTAUX_ECUDA, "sweep launch: %s", cudaGetErrorString(e));
+  return CTAUX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ctaux_status ctaux_init(const ctaux_params* params, ctaux_ctx** out) {
+  if (!out) return CTAUX_EINVAL;
+  *out = nullptr;
+  if (!params || params->n_chains < 1 || params->n_chains > 2048 || !params->chains)
+    return CTAUX_EINVAL;
+  if (params->precision != CTAUX_FP64 && params->precision != CTAUX_MIXED) return CTAUX_EINVAL;
+  if (params->p_insert < 0 || params->p_flip < 0 || params->p_insert + params->p_flip > 1.0)
+    return CTAUX_EINVAL;
+  if (params->n_tau_bins < 1 || params->n_anchors < 1 || params->n_anchors > 64 ||
+      params->trace_capacity < 0 || params->refresh_every < 0)
+    return CTAUX_EINVAL;
+  for (int i = 0; i < params->n_chains; ++i) {
+    const ctaux_chain_params& c = params->chains[i];
+    if (c.n_c < 1 || c.n_classes < 1 || c.n_tau < 2 || !c.g0_table || !c.dx_class) return CTAUX_EINVAL;
+    if (!(c.beta > 0) || !(c.K > 0) || !(c.U >= 0) || c.k_max < 1 || c.k_max > kMaxK || c.capacity < 1)
+      return CTAUX_EINVAL;
+    if (c.capacity + c.k_max > 30000) return CTAUX_EINVAL;
+    for (int k = 0; k < c.n_c * c.n_c; ++k)
+      if (c.dx_class[k] < 0 || c.dx_class[k] >= c.n_classes) return CTAUX_EINVAL;
+  }
+  ctaux_ctx* ctx = new ctaux_ctx();
+  ctx->params = *params;
+  ctx->chains.assign(params->chains, params->chains + params->n_chains);
+  ctx->params.chains = nullptr;
+  ctx->device = params->device;
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->device);
+  if (e != cudaSuccess) {
+    set_err(ctx, CTAUX_ECUDA, "device %d: %s", ctx->device, cudaGetErrorString(e));
+    ctaux_destroy(ctx);
+    return CTAUX_ECUDA;
+  }
+  ctaux_status st = is_mixed(ctx) ? build_chains<float>(ctx) : build_chains<double>(ctx);
+  if (st != CTAUX_OK) {
+    ctaux_destroy(ctx);
+    return st;
+  }
+  ctx->timer = new PhaseTimer();
+  for (int i = 0; i < PhaseTimer::kPool; ++i) cudaEventCreate(&ctx->timer->ev[i]);
+  ctx->timer->created = true;
+  *out = ctx;
+  return CTAUX_OK;
+}
+
+ctaux_status ctaux_sweep(ctaux_ctx* ctx, int n_sweeps, int measure, void* cuda_stream) {
+  if (!ctx || n_sweeps < 0) return CTAUX_EINVAL;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+  ctx->last_stream = st;
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  // algorithmic work estimate from the current orders is accumulated at stats time
+  return is_mixed(ctx) ? do_sweeps<float>(ctx, n_sweeps, measure, st)
+                       : do_sweeps<double>(ctx, n_sweeps, measure, st);
+}
+
+ctaux_status ctaux_synchronize(ctaux_ctx* ctx) {
+  if (!ctx) return CTAUX_EINVAL;
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->last_stream));
+  CUDA_TRY(ctx, cudaGetLastError());
+  return check_device_status(ctx);
+}
+
+ctaux_status ctaux_measure_G(ctaux_ctx* ctx, int chain, double* G_out, double* err_out,
+                             int64_t* n_meas_out) {
+  if (!ctx || chain < 0 || chain >= (int)ctx->chains.size() || !G_out) return CTAUX_EINVAL;
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->last_stream));
+  const ctaux_chain_params& cp = ctx->chains[chain];
+  const size_t nb = (size_t)2 * cp.n_classes * ctx->params.n_tau_bins;
+  std::vector<double> sum(nb), sq(nb);
+  const double* ds = is_mixed(ctx) ? ctx->hc32[chain].Gsum : ctx->hc64[chain].Gsum;
+  const double* dq = is_mixed(ctx) ? ctx->hc32[chain].Gsq : ctx->hc64[chain].Gsq;
+  CUDA_TRY(ctx, cudaMemcpy(sum.data(), ds, nb * sizeof(double), cudaMemcpyDeviceToHost));
+  CUDA_TRY(ctx, cudaMemcpy(sq.data(), dq, nb * sizeof(double), cudaMemcpyDeviceToHost));
+  Dyn d;
+  ctaux_status r = read_dyn(ctx, chain, &d);
+  if (r != CTAUX_OK) return r;
+  const double nm = (double)d.measurements;
+  for (size_t i = 0; i < nb; ++i) {
+    const double mean = nm > 0 ? sum[i] / nm : 0.0;
+    G_out[i] = mean;
+    if (err_out) {
+      const double var = nm > 1 ? std::max(0.0, sq[i] / nm - mean * mean) * nm / (nm - 1.0) : 0.0;
+      err_out[i] = nm > 1 ? std::sqrt(var / nm) : 0.0;
+    }
+  }
+  if (n_meas_out) *n_meas_out = d.measurements;
+  return CTAUX_OK;
+}
+
+ctaux_status ctaux_reset_measurements(ctaux_ctx* ctx) {
+  if (!ctx) return CTAUX_EINVAL;
+  if (is_mixed(ctx))
+    launch_reset_measure<float>(reinterpret_cast<Chain<float>*>(ctx->chains_dev), ctx->ls, ctx->last_stream);
+  else
+    launch_reset_measure<double>(reinterpret_cast<Chain<double>*>(ctx->chains_dev), ctx->ls, ctx->last_stream);
+  CUDA_TRY(ctx, cudaGetLastError());
+  return CTAUX_OK;
+}
+
+ctaux_status ctaux_recompute(ctaux_ctx* ctx, double* drift_max_out) {
+  if (!ctx) return CTAUX_EINVAL;
+  ctaux_status r = is_mixed(ctx) ? do_refresh<float>(ctx, -1, ctx->last_stream)
+                                 : do_refresh<double>(ctx, -1, ctx->last_stream);
+  if (r != CTAUX_OK) return r;
+  ctx->blocks_since_refresh = 0;
+  r = ctaux_synchronize(ctx);
+  if (r != CTAUX_OK) return r;
+  double mx = 0.0;
+  for (size_t ci = 0; ci < ctx->chains.size(); ++ci) {
+    Dyn d;
+    r = read_dyn(ctx, (int)ci, &d);
+    if (r != CTAUX_OK) return r;
+    mx = std::max(mx, d.drift_max);
+  }
+  if (drift_max_out) *drift_max_out = mx;
+  return CTAUX_OK;
+}
+
+ctaux_status ctaux_get_stats(ctaux_ctx* ctx, int chain, ctaux_stats* out) {
+  if (!ctx || !out || chain < 0 || chain >= (int)ctx->chains.size()) return CTAUX_EINVAL;
+  Dyn d;
+  ctaux_status r = read_dyn(ctx, chain, &d);
+  if (r != CTAUX_OK) return r;
+  std::memset(out, 0, sizeof(*out));
+  out->n = d.n;
+  out->t = d.t;
+  for (int q = 0; q < 3; ++q) {
+    out->proposals[q] = d.proposals[q];
+    out->accepted[q] = d.accepted[q];
+  }
+  out->sweeps = d.sweeps;
+  out->measurements = d.measurements;
+  out->order_sum = d.order_sum;
+  out->sign_sum = d.sign_sum;
+  out->numeric_rejects = d.numeric_rejects;
+  out->refreshes = d.refreshes;
+  out->last_drift_max = d.drift_max;
+  out->last_drift_fro = d.drift_fro;
+  out->logdet[0] = d.logdet[0];
+  out->logdet[1] = d.logdet[1];
+  out->sign = d.sign;
+  out->status = d.status;
+  return CTAUX_OK;
+}
+
+ctaux_status ctaux_get_trace(ctaux_ctx* ctx, int chain, ctaux_trace_rec* buf, int cap, int* n_out) {
+  if (!ctx || chain < 0 || chain >= (int)ctx->chains.size() || (!buf && cap > 0) || !n_out)
+    return CTAUX_EINVAL;
+  *n_out = 0;
+  const int tc = ctx->params.trace_capacity;
+  if (tc <= 0) return CTAUX_OK;
+  Dyn d;
+  ctaux_status r = read_dyn(ctx, chain, &d);
+  if (r != CTAUX_OK) return r;
+  int64_t from = std::max(d.trace_read, d.trace_written - (int64_t)tc);
+  int64_t count = std::min<int64_t>(d.trace_written - from, cap);
+  const TraceRec* dt = is_mixed(ctx) ? ctx->hc32[chain].trace : ctx->hc64[chain].trace;
+  static_assert(sizeof(TraceRec) == sizeof(ctaux_trace_rec), "trace record layout");
+  for (int64_t i = 0; i < count; ++i) {
+    const int64_t slot = (from + i) % tc;
+    CUDA_TRY(ctx, cudaMemcpy(buf + i, dt + slot, sizeof(TraceRec), cudaMemcpyDeviceToHost));
+  }
+  const int64_t new_read = from + count;
+  CUDA_TRY(ctx, cudaMemcpy(&dyn_of(ctx, chain)->trace_read, &new_read, sizeof(int64_t),
+                           cudaMemcpyHostToDevice));
+  *n_out = (int)count;
+  return CTAUX_OK;
+}
+
+ctaux_status ctaux_get_config(ctaux_ctx* ctx, int chain, double* tau, int* site, int* s,
+                              int64_t* birth, int cap, int* n_out, int64_t* t_out) {
+  if (!ctx || chain < 0 || chain >= (int)ctx->chains.size() || !n_out) return CTAUX_EINVAL;
+  Dyn d;
+  ctaux_status r = read_dyn(ctx, chain, &d);
+  if (r != CTAUX_OK) return r;
+  *n_out = d.n;
+  if (t_out) *t_out = d.t;
+  if (d.n > cap) return set_err(ctx, CTAUX_EINVAL, "buffer of %d entries for %d vertices", cap, d.n);
+  const int b = d.buf;
+  const double* dtau = is_mixed(ctx) ? ctx->hc32[chain].tau[b] : ctx->hc64[chain].tau[b];
+  const int* dsite = is_mixed(ctx) ? ctx->hc32[chain].site[b] : ctx->hc64[chain].site[b];
+  const int8_t* ds = is_mixed(ctx) ? ctx->hc32[chain].s[b] : ctx->hc64[chain].s[b];
+  const int64_t* db = is_mixed(ctx) ? ctx->hc32[chain].birth[b] : ctx->hc64[chain].birth[b];
+  std::vector<int8_t> s8(d.n);
+  if (d.n > 0) {
+    if (tau) CUDA_TRY(ctx, cudaMemcpy(tau, dtau, d.n * sizeof(double), cudaMemcpyDeviceToHost));
+    if (site) CUDA_TRY(ctx, cudaMemcpy(site, dsite, d.n * sizeof(int), cudaMemcpyDeviceToHost));
+    if (birth) CUDA_TRY(ctx, cudaMemcpy(birth, db, d.n * sizeof(int64_t), cudaMemcpyDeviceToHost));
+    CUDA_TRY(ctx, cudaMemcpy(s8.data(), ds, d.n, cudaMemcpyDeviceToHost));
+    if (s)
+      for (int i = 0; i < d.n; ++i) s[i] = s8[i];
+  }
+  return CTAUX_OK;
+}
+
+ctaux_status ctaux_set_config(ctaux_ctx* ctx, int chain, const double* tau, const int* site,
+                              const int* s, const int64_t* birth, int n, int64_t t) {
+  if (!ctx || chain < 0 || chain >= (int)ctx->chains.size() || n < 0 || t < 0) return CTAUX_EINVAL;
+  const ctaux_chain_params& cp = ctx->chains[chain];
+  if (n > cp.capacity) return set_err(ctx, CTAUX_ECAPACITY, "order %d above capacity %d", n, cp.capacity);
+  if (n > 0 && (!tau || !site || !s || !birth)) return CTAUX_EINVAL;
+  std::vector<int> order(n);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return birth[a] < birth[b]; });
+  std::vector<double> tv(n);
+  std::vector<int> sv(n);
+  std::vector<int8_t> s8(n);
+  std::vector<int64_t> bv(n);
+  for (int i = 0; i < n; ++i) {
+    const int k = order[i];
+    if (!(tau[k] >= 0.0 && tau[k] < cp.beta) || site[k] < 0 || site[k] >= cp.n_c || (s[k] != 1 && s[k] != -1))
+      return set_err(ctx, CTAUX_EINVAL, "vertex %d out of range", k);
+    tv[i] = tau[k];
+    sv[i] = site[k];
+    s8[i] = (int8_t)s[k];
+    bv[i] = birth[k];
+  }
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->last_stream));
+  Dyn d;
+  CUDA_TRY(ctx, cudaMemcpy(&d, dyn_of(ctx, chain), sizeof(Dyn), cudaMemcpyDeviceToHost));
+  const int b = d.buf;
+  double* dtau = is_mixed(ctx) ? ctx->hc32[chain].tau[b] : ctx->hc64[chain].tau[b];
+  int* dsite = is_mixed(ctx) ? ctx->hc32[chain].site[b] : ctx->hc64[chain].site[b];
+  int8_t* ds = is_mixed(ctx) ? ctx->hc32[chain].s[b] : ctx->hc64[chain].s[b];
+  int64_t* db = is_mixed(ctx) ? ctx->hc32[chain].birth[b] : ctx->hc64[chain].birth[b];
+  if (n > 0) {
+    CUDA_TRY(ctx, cudaMemcpy(dtau, tv.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+    CUDA_TRY(ctx, cudaMemcpy(dsite, sv.data(), n * sizeof(int), cudaMemcpyHostToDevice));
+    CUDA_TRY(ctx, cudaMemcpy(ds, s8.data(), n, cudaMemcpyHostToDevice));
+    CUDA_TRY(ctx, cudaMemcpy(db, bv.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice));
+  }
+  d.n = n;
+  d.t = t;
+  d.status = 0;
+  int sg = 1;
+  d.sign = sg;
+  CUDA_TRY(ctx, cudaMemcpy(dyn_of(ctx, chain), &d, sizeof(Dyn), cudaMemcpyHostToDevice));
+  ctaux_status r = is_mixed(ctx) ? do_refresh<float>(ctx, chain, ctx->last_stream)
+                                 : do_refresh<double>(ctx, chain, ctx->last_stream);
+  if (r != CTAUX_OK) return r;
+  return ctaux_synchronize(ctx);
+}
+
+ctaux_status ctaux_get_N(ctaux_ctx* ctx, int chain, int spin, double* out, int ld_out, int* m_out) {
+  if (!ctx || chain < 0 || chain >= (int)ctx->chains.size() || spin < 0 || spin > 1 || !m_out)
+    return CTAUX_EINVAL;
+  Dyn d;
+  ctaux_status r = read_dyn(ctx, chain, &d);
+  if (r != CTAUX_OK) return r;
+  *m_out = d.n;
+  if (!out) return CTAUX_OK;
+  if (ld_out < d.n) return CTAUX_EINVAL;
+  const int b = d.buf;
+  if (is_mixed(ctx)) {
+    const Chain<float>& c = ctx->hc32[chain];
+    std::vector<float> col(d.n);
+    for (int j = 0; j < d.n; ++j) {
+      CUDA_TRY(ctx, cudaMemcpy(col.data(), c.N[b][spin] + (size_t)j * c.ld, d.n * sizeof(float),
+                               cudaMemcpyDeviceToHost));
+      for (int i = 0; i < d.n; ++i) out[(size_t)j * ld_out + i] = col[i];
+    }
+  } else {
+    const Chain<double>& c = ctx->hc64[chain];
+    if (d.n > 0)
+      CUDA_TRY(ctx, cudaMemcpy2D(out, (size_t)ld_out * sizeof(double), c.N[b][spin], (size_t)c.ld * sizeof(double),
+                                 d.n * sizeof(double), d.n, cudaMemcpyDeviceToHost));
+  }
+  return CTAUX_OK;
+}
+
+ctaux_status ctaux_set_profiling(ctaux_ctx* ctx, int on) {
+  if (!ctx) return CTAUX_EINVAL;
+  if (ctx->profiling && !on) ctx->timer->collect();
+  ctx->profiling = on != 0;
+  ctx->timer->on = ctx->profiling;
+  return CTAUX_OK;
+}
+
+ctaux_status ctaux_get_phase_times(ctaux_ctx* ctx, double* ms_out, int64_t* kernels_out) {
+  if (!ctx) return CTAUX_EINVAL;
+  ctx->timer->collect();
+  for (int p = 0; p < PhaseTimer::kPhases; ++p) {
+    if (ms_out) ms_out[p] = ctx->timer->ms[p];
+    if (kernels_out) kernels_out[p] = ctx->timer->kernels[p];
+  }
+  return CTAUX_OK;
+}
+
+ctaux_status ctaux_get_work(ctaux_ctx* ctx, double* prep_flop, double* flush_flop, double* flush_bytes) {
+  if (!ctx) return CTAUX_EINVAL;
+  double a = 0.0, b = 0.0, c = 0.0;
+  for (size_t ci = 0; ci < ctx->chains.size(); ++ci) {
+    Dyn d;
+    ctaux_status r = read_dyn(ctx, (int)ci, &d);
+    if (r != CTAUX_OK) return r;
+    a += d.work_prep;
+    b += d.work_flush;
+    c += d.bytes_flush;
+  }
+  if (prep_flop) *prep_flop = a;
+  if (flush_flop) *flush_flop = b;
+  if (flush_bytes) *flush_bytes = c;
+  return CTAUX_OK;
+}
+
+ctaux_status ctaux_philox_uniforms(uint64_t seed, uint32_t chain, int64_t t0, int count, int purpose,
+                                   double* out) {
+  if (count < 0 || !out || purpose < 0) return CTAUX_EINVAL;
+  if (count == 0) return CTAUX_OK;
+  double* d = nullptr;
+  if (cudaMalloc(&d, (size_t)count * 2 * sizeof(double)) != cudaSuccess) return CTAUX_ENOMEM;
+  launch_philox_test(seed, chain, t0, count, purpose, d, nullptr);
+  cudaError_t e = cudaMemcpy(out, d, (size_t)count * 2 * sizeof(double), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  return e == cudaSuccess ? CTAUX_OK : CTAUX_ECUDA;
+}
+
+void ctaux_destroy(ctaux_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->last_stream);
+  for (void* p : ctx->allocations) cudaFree(p);
+  if (ctx->timer) {
+    if (ctx->timer->created)
+      for (int i = 0; i < PhaseTimer::kPool; ++i) cudaEventDestroy(ctx->timer->ev[i]);
+    delete ctx->timer;
+  }
+  delete ctx;
+}
+
+const char* ctaux_last_error(const ctaux_ctx* ctx) {
+  if (!ctx) return "null context";
+  return ctx->err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,779 @@
+// One submatrix block of CT-AUX on every chain: pre-insertion (Sec. IV A),
+// G0 gather, prep products, the k_max proposals with Gamma growth
+// (Secs. III D and IV B) and the Woodbury flush with compaction (Sec. IV C).
+#include "ctaux_dev.cuh"
+#include "ctaux_kernels.h"
+
+namespace ctaux {
+
+// ---------------------------------------------------------------- plan
+// One CTA per chain: draw the block's move types, place the insertion
+// candidates as s=0 vertices in slots [n, n + k_ins) (Sec. IV A) and record
+// the block-start spins.
+template <typename T>
+__global__ void __launch_bounds__(256) k_plan(Chain<T>* chains) {
+  const Chain<T>& c = chains[blockIdx.x];
+  Dyn& d = *c.dyn;
+  if (d.status) return;
+  const int n = d.n, buf = d.buf;
+  const int64_t t0 = d.t;
+  __shared__ int scan[256];
+  const int j = threadIdx.x;
+  int is_ins = 0;
+  Draws dr;
+  if (j < c.k_max) {
+    dr = draw(c.seed, c.chain_id, t0 + j);
+    is_ins = move_of(dr.u_move, c.p_insert, c.p_remove) == MV_INSERT;
+  }
+  scan[j] = is_ins;
+  __syncthreads();
+  for (int off = 1; off < 256; off <<= 1) {
+    const int v = (j >= off) ? scan[j - off] : 0;
+    __syncthreads();
+    scan[j] += v;
+    __syncthreads();
+  }
+  const int k_ins = scan[255];
+  const int m = n + k_ins;
+  if (m > c.cap_m) {
+    if (j == 0) atomicOr(&d.status, DS_CAPACITY);
+    return;
+  }
+  if (is_ins) {
+    const int slot = n + scan[j] - 1;
+    int site = (int)floor(dr.u_site * (double)c.n_c);
+    if (site > c.n_c - 1) site = c.n_c - 1;
+    c.tau[buf][slot] = dr.u_tau * c.beta;
+    c.site[buf][slot] = site;
+    c.s[buf][slot] = 0;
+    c.birth[buf][slot] = t0 + j;
+  }
+  for (int i = j; i < m; i += blockDim.x) c.s0[i] = (i < n) ? c.s[buf][i] : (int8_t)0;
+  if (j == 0) {
+    d.m = m;
+    d.k_ins = k_ins;
+  }
+}
+
+// -------------------------------------------------------------- gather
+// G0 panels of the new vertices (Sec. IV A):
+//   C[a][l] = G0(new_a, old_l) (e^{V_l} - 1)   (rows of R~ = C N)
+//   B[l][a] = G0(old_l, new_a)                 (G_{:,new} = N_ext [B; G0(new,new)])
+//   Gcol[n + a][b] = G0(new_a, new_b)          (accumulated onto by the prep products)
+//   N_ext[:, n + a] = e_{n+a}                  (s=0 columns of N_ext are unit vectors)
+template <typename T>
+__global__ void __launch_bounds__(256) k_gather(Chain<T>* chains) {
+  const Chain<T>& c = chains[blockIdx.z];
+  const Dyn& d = *c.dyn;
+  if (d.status) return;
+  const int spin = blockIdx.y;
+  const int n = d.n, k_ins = d.k_ins, m = d.m, buf = d.buf, ld = c.ld;
+  const double* tau = c.tau[buf];
+  const int* site = c.site[buf];
+  T* Nb = c.N[buf][spin];
+  const long nC = (long)k_ins * n, nB = nC, nG = (long)k_ins * k_ins, nI = (long)m * k_ins;
+  const long total = nC + nB + nG + nI;
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    if (e < nC) {
+      const int a = (int)(e / n), l = (int)(e % n);
+      const double ev = c.ev[spin][c.s0[l] + 2];
+      c.Cpan[spin][(long)a * ld + l] =
+          (T)(g0_eval(c, spin, tau[n + a], site[n + a], tau[l], site[l]) * (ev - 1.0));
+    } else if (e < nC + nB) {
+      const long f = e - nC;
+      const int a = (int)(f / n), l = (int)(f % n);
+      c.Bpan[spin][(long)a * ld + l] = (T)g0_eval(c, spin, tau[l], site[l], tau[n + a], site[n + a]);
+    } else if (e < nC + nB + nG) {
+      const long f = e - nC - nB;
+      const int b = (int)(f / k_ins), a = (int)(f % k_ins);
+      c.Gcol[spin][(long)b * ld + n + a] =
+          (T)g0_eval(c, spin, tau[n + a], site[n + a], tau[n + b], site[n + b]);
+    } else {
+      const long f = e - nC - nB - nG;
+      const int a = (int)(f / m), i = (int)(f % m);
+      Nb[(long)(n + a) * ld + i] = (i == n + a) ? (T)1 : (T)0;
+    }
+  }
+}
+
+// ------------------------------------------------------ batched GEMM
+// out(i,j) = alpha * sum_k A(i,k) B(k,j) + (cin ? cin(i,j) : 0), every operand
+// a strided view with optional row/column index lists (gathers).
+template <typename T>
+struct View {
+  const T* p;
+  long rs, cs;
+  const int* ri;
+  const int* ci;
+  __device__ __forceinline__ T at(int i, int j) const {
+    const long r = ri ? ri[i] : i;
+    const long q = ci ? ci[j] : j;
+    return p[r * rs + q * cs];
+  }
+};
+
+template <typename T>
+struct Gemm {
+  int M, Nn, Kk;
+  double alpha;
+  View<T> A, B, Cin;
+  bool has_cin;
+  T* out;
+  long out_rs, out_cs;
+};
+
+template <typename T>
+__device__ __forceinline__ bool setup_gemm(const Chain<T>& c, const Dyn& d, int spin, int phase,
+                                           Gemm<T>& g) {
+  const int ld = c.ld, n = d.n, k_ins = d.k_ins;
+  T* Nb = c.N[d.buf][spin];
+  g.alpha = 1.0;
+  g.has_cin = false;
+  g.A.ri = g.A.ci = g.B.ri = g.B.ci = g.Cin.ri = g.Cin.ci = nullptr;
+  switch (phase) {
+    case PH_RTILDE:  // R~ = C N -> N_ext rows [n, m), cols [0, n)
+      g.M = k_ins; g.Nn = n; g.Kk = n;
+      g.A.p = c.Cpan[spin]; g.A.rs = ld; g.A.cs = 1;
+      g.B.p = Nb; g.B.rs = 1; g.B.cs = ld;
+      g.out = Nb + n; g.out_rs = 1; g.out_cs = ld;
+      break;
+    case PH_GCOL_OLD:  // G_{old,new} = N B
+      g.M = n; g.Nn = k_ins; g.Kk = n;
+      g.A.p = Nb; g.A.rs = 1; g.A.cs = ld;
+      g.B.p = c.Bpan[spin]; g.B.rs = 1; g.B.cs = ld;
+      g.out = c.Gcol[spin]; g.out_rs = 1; g.out_cs = ld;
+      break;
+    case PH_GCOL_NEW:  // G_{new,new} = C G_{old,new} + G0(new,new)
+      g.M = k_ins; g.Nn = k_ins; g.Kk = n;
+      g.A.p = c.Cpan[spin]; g.A.rs = ld; g.A.cs = 1;
+      g.B.p = c.Gcol[spin]; g.B.rs = 1; g.B.cs = ld;
+      g.Cin.p = c.Gcol[spin] + n; g.Cin.rs = 1; g.Cin.cs = ld; g.has_cin = true;
+      g.out = c.Gcol[spin] + n; g.out_rs = 1; g.out_cs = ld;
+      break;
+    case PH_FLUSH:  // N'[a,b] = N[S_a,S_b] - Y[a,:] N[P,S_b]
+      g.M = d.n_new; g.Nn = d.n_new; g.Kk = d.k_acc;
+      g.alpha = -1.0;
+      g.A.p = c.Y[spin]; g.A.rs = 1; g.A.cs = ld;
+      g.B.p = Nb; g.B.rs = 1; g.B.cs = ld; g.B.ri = c.P; g.B.ci = c.S;
+      g.Cin.p = Nb; g.Cin.rs = 1; g.Cin.cs = ld; g.Cin.ri = c.S; g.Cin.ci = c.S; g.has_cin = true;
+      g.out = c.N[1 - d.buf][spin]; g.out_rs = 1; g.out_cs = ld;
+      break;
+    default:  // measurement: v_b = N g_b
+      g.M = n; g.Nn = c.n_anchors; g.Kk = n;
+      g.A.p = Nb; g.A.rs = 1; g.A.cs = ld;
+      g.B.p = c.Mg[spin]; g.B.rs = 1; g.B.cs = ld;
+      g.out = c.Mv[spin]; g.out_rs = 1; g.out_cs = ld;
+      break;
+  }
+  return g.M > 0 && g.Nn > 0;
+}
+
+constexpr int GBK = 16;
+// Output tile edge: 32 for float64 (the FP64 pipe is the bottleneck, so padded
+// rows cost real time and more CTAs spread it over more SMs), 64 for float32.
+template <typename T>
+struct TileEdge {
+  static constexpr int v = sizeof(T) == 8 ? 32 : 64;
+};
+
+// One output tile (TileEdge) and one slice of the inner dimension per CTA
+// (256 threads); grid (tiles x max slices, 2 spins, chains), CTAs
+// beyond the problem exit at once.  Slices have a fixed width kchunk, so the
+// partition of a product, and with it the rounding, depends only on that
+// product's own sizes (a chain gives the same bits alone or in a batch).
+// With more than one slice every slice stores its partial tile, and the slice
+// that arrives last at the tile's ticket adds the partials in slice order
+// (deterministic, no waiting) and writes the result.
+template <typename T>
+__global__ void __launch_bounds__(256) k_gemm(Chain<T>* chains, int phase, int ksplit, int kchunk) {
+  constexpr int GBM = TileEdge<T>::v, GBN = TileEdge<T>::v, TM = GBM / 16, TN = GBN / 16;
+  const Chain<T>& c = chains[blockIdx.z];
+  const Dyn& d = *c.dyn;
+  if (d.status) return;
+  const int spin = blockIdx.y;
+  Gemm<T> g;
+  if (!setup_gemm(c, d, spin, phase, g)) return;
+  const int tiles_n = (g.Nn + GBN - 1) / GBN;
+  const int tiles_m = (g.M + GBM - 1) / GBM;
+  const int tile = blockIdx.x / ksplit, ks = blockIdx.x % ksplit;
+  if (tile >= tiles_m * tiles_n) return;
+  const int nslices = max(1, (g.Kk + kchunk - 1) / kchunk);
+  if (ks >= nslices) return;
+  const int i0 = (tile / tiles_n) * GBM, j0 = (tile % tiles_n) * GBN;
+  const int kb = ks * kchunk, ke = min(g.Kk, kb + kchunk);
+  __shared__ T As[GBK][GBM + 1];
+  __shared__ T Bs[GBK][GBN + 1];
+  __shared__ int s_last;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  T acc[TM][TN];
+#pragma unroll
+  for (int a = 0; a < TM; ++a)
+#pragma unroll
+    for (int b = 0; b < TN; ++b) acc[a][b] = (T)0;
+  for (int k0 = kb; k0 < ke; k0 += GBK) {
+    for (int e = threadIdx.x; e < GBK * GBM; e += 256) {
+      const int ii = e % GBM, kk = e / GBM;
+      const int i = i0 + ii, k = k0 + kk;
+      As[kk][ii] = (i < g.M && k < ke) ? g.A.at(i, k) : (T)0;
+    }
+    for (int e = threadIdx.x; e < GBK * GBN; e += 256) {
+      const int kk = e % GBK, jj = e / GBK;
+      const int j = j0 + jj, k = k0 + kk;
+      Bs[kk][jj] = (j < g.Nn && k < ke) ? g.B.at(k, j) : (T)0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GBK; ++kk) {
+      T av[TM], bv[TN];
+#pragma unroll
+      for (int a = 0; a < TM; ++a) av[a] = As[kk][ty + 16 * a];
+#pragma unroll
+      for (int b = 0; b < TN; ++b) bv[b] = Bs[kk][tx + 16 * b];
+#pragma unroll
+      for (int a = 0; a < TM; ++a)
+#pragma unroll
+        for (int b = 0; b < TN; ++b) acc[a][b] += av[a] * bv[b];
+    }
+    __syncthreads();
+  }
+  if (nslices > 1) {
+    T* part = c.kpart[spin] + (size_t)tile * ksplit * GBM * GBN;
+#pragma unroll
+    for (int a = 0; a < TM; ++a)
+#pragma unroll
+      for (int b = 0; b < TN; ++b)
+        part[(size_t)ks * GBM * GBN + (ty + 16 * a) * GBN + tx + 16 * b] = acc[a][b];
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(c.ticket[spin] + tile, 1) == nslices - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+#pragma unroll
+    for (int a = 0; a < TM; ++a)
+#pragma unroll
+      for (int b = 0; b < TN; ++b) {
+        T v = (T)0;
+        for (int q = 0; q < nslices; ++q)
+          v += __ldcg(part + (size_t)q * GBM * GBN + (ty + 16 * a) * GBN + tx + 16 * b);
+        acc[a][b] = v;
+      }
+    if (threadIdx.x == 0) c.ticket[spin][tile] = 0;
+  }
+#pragma unroll
+  for (int a = 0; a < TM; ++a) {
+    const int i = i0 + ty + 16 * a;
+    if (i >= g.M) continue;
+#pragma unroll
+    for (int b = 0; b < TN; ++b) {
+      const int j = j0 + tx + 16 * b;
+      if (j >= g.Nn) continue;
+      T v = (T)g.alpha * acc[a][b];
+      if (g.has_cin) v += g.Cin.at(i, j);
+      g.out[(long)i * g.out_rs + (long)j * g.out_cs] = v;
+    }
+  }
+}
+
+template <typename T>
+void launch_gemm(Chain<T>* dchains, const LaunchShape& ls, int phase, cudaStream_t st) {
+  k_gemm<T><<<dim3(ls.tiles[phase] * ls.ksplit[phase], 2, ls.n_chains), 256, 0, st>>>(
+      dchains, phase, ls.ksplit[phase], ls.kchunk);
+}
+
+// ------------------------------------------------------------ proposals
+// Interacting Green's function of the block start, G0int(i, j) = G^0_{ij}
+// (Sec. III C: "G^0 is the interacting Green's function at step k=0"):
+// old columns from N by G = (N e^V - 1)/(e^V - 1) (Eq. NfromG), new (s=0)
+// columns from the prep product G_{:,new} = N_ext G0_{:,new}.
+template <typename T>
+__device__ __forceinline__ double g_int(const Chain<T>& c, const T* Nb, const T* Gc, int n_old,
+                                        int spin, int i, int j) {
+  if (j < n_old) {
+    const int k = c.s0[j] + 2;
+    return ((double)Nb[(long)j * c.ld + i] * c.ev[spin][k] - (i == j ? 1.0 : 0.0)) * c.inv_em1[spin][k];
+  }
+  return (double)Gc[(long)(j - n_old) * c.ld + i];
+}
+
+// Select the idx-th set bit of a bitmask (one warp).
+__device__ __forceinline__ int select_bit(const uint32_t* mask, int n_words, int idx, int lane) {
+  int base = 0;
+  for (int w0 = 0; w0 < n_words; w0 += 32) {
+    const int w = w0 + lane;
+    const uint32_t word = (w < n_words) ? mask[w] : 0u;
+    const int cnt = __popc(word);
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    if (idx < base + total) {
+      const int excl = incl - cnt;
+      const bool mine = (idx >= base + excl) && (idx < base + incl);
+      const unsigned who = __ballot_sync(0xffffffffu, mine);
+      const int src = __ffs(who) - 1;
+      int res = -1;
+      if (lane == src) res = w * 32 + (__fns(word, 0, idx - base - excl + 1));
+      return __shfl_sync(0xffffffffu, res, src);
+    }
+    base += total;
+  }
+  return -1;
+}
+
+// One CTA per chain, threads [0,128) spin up, [128,256) spin down.  Runs the
+// k_max proposals of the block in order; Gamma^{-1} is grown by partitioning
+// (Sec. III D): beta = d - w^T Gamma^{-1} s, ratio_sigma = -lambda beta
+// (Eq. ratS), the bordered inverse on acceptance.  A slot touched twice in a
+// block changes only the diagonal of Gamma (Eq. Gamma): Sherman-Morrison on
+// Gamma^{-1}, or removal of the slot from P when it returns to its
+// block-start spin (then ratio = -(Gamma^{-1})_qq / lambda).
+template <typename T>
+__global__ void __launch_bounds__(256) k_proposals(Chain<T>* chains, int gamma_in_smem) {
+  const Chain<T>& c = chains[blockIdx.x];
+  Dyn& d = *c.dyn;
+  if (d.status) return;
+  const int tid = threadIdx.x, half = tid >> 7, ht = tid & 127, hw = ht >> 5, lane = tid & 31;
+  const int spin = half;
+  const int KM = c.k_max, ld = c.ld;
+  const int n_old = d.n, m = d.m, buf = d.buf;
+  const int64_t t0 = d.t;
+  const T* Nb = c.N[buf][spin];
+  const T* Gc = c.Gcol[spin];
+  int8_t* s_cur = c.s[buf];
+  const int64_t* birth = c.birth[buf];
+
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  // layout: [Ginv 2*KM*KM T (optional)] [vec 2 x 4 x KM double] [lam 2 x KM double]
+  //         [P KM int] [pmap cap_m short] [alive mask]
+  unsigned char* sp = smem_raw;
+  T* Gs = nullptr;
+  if (gamma_in_smem) {
+    Gs = reinterpret_cast<T*>(sp);
+    sp += sizeof(T) * 2 * KM * KM;
+  }
+  double* vec = reinterpret_cast<double*>(sp);
+  sp += sizeof(double) * 8 * KM;
+  double* lam_s = reinterpret_cast<double*>(sp);
+  sp += sizeof(double) * 2 * KM;
+  int* P_s = reinterpret_cast<int*>(sp);
+  sp += sizeof(int) * KM;
+  short* pmap = reinterpret_cast<short*>(sp);
+  sp += sizeof(short) * ((c.cap_m + 7) & ~7);
+  uint32_t* alive = reinterpret_cast<uint32_t*>(sp);
+  const int n_words = (m + 31) / 32;
+
+  T* G = gamma_in_smem ? (Gs + (size_t)spin * KM * KM) : c.Ginv[spin];  // row-major KM x KM
+  double* sv = vec + spin * 4 * KM;   // s (column of G^0 over P)
+  double* wv = sv + KM;               // w (row of G^0 over P)
+  double* yv = wv + KM;               // Gamma^{-1} s
+  double* zv = yv + KM;               // w^T Gamma^{-1}
+  double* lam = lam_s + spin * KM;
+
+  __shared__ double red[2][4];
+  __shared__ double gpp_s[2];
+  __shared__ double ratio_s[2];
+  __shared__ int sel_p;
+  __shared__ int jP;        // |P|
+  __shared__ int n_cur, sign_s;
+  __shared__ long long cnt_prop[3], cnt_acc[3], numeric;
+
+  for (int i = tid; i < m; i += 256) pmap[i] = -1;
+  for (int w = tid; w < n_words; w += 256) {
+    uint32_t bits = 0;
+    for (int b = 0; b < 32; ++b) {
+      const int i = w * 32 + b;
+      if (i < m && s_cur[i] != 0) bits |= (1u << b);
+    }
+    alive[w] = bits;
+  }
+  if (tid == 0) {
+    jP = 0;
+    n_cur = n_old;
+    sign_s = d.sign;
+    for (int q = 0; q < 3; ++q) cnt_prop[q] = cnt_acc[q] = 0;
+    numeric = 0;
+  }
+  __syncthreads();
+
+  int ins_count = 0;
+  for (int jj = 0; jj < KM; ++jj) {
+    const int64_t t = t0 + jj;
+    const Draws dr = draw(c.seed, c.chain_id, t);
+    const int move = move_of(dr.u_move, c.p_insert, c.p_remove);
+    const int nc = n_cur;
+    int p = -1, s_new = 0;
+    double f = 0.0;
+    if (move == MV_INSERT) {
+      p = n_old + ins_count;
+      ++ins_count;
+      s_new = (dr.u_spin < 0.5) ? 1 : -1;
+      f = c.K / (double)(nc + 1);
+    } else if (nc > 0) {
+      int idx = (int)floor(dr.u_idx * (double)nc);
+      if (idx > nc - 1) idx = nc - 1;
+      if (tid < 32) {
+        const int ps = select_bit(alive, n_words, idx, lane);
+        if (lane == 0) sel_p = ps;
+      }
+      __syncthreads();
+      p = sel_p;
+      if (p < 0 || p >= m) {
+        if (tid == 0) atomicOr(&d.status, DS_INDEX);
+        break;
+      }
+      s_new = (move == MV_REMOVE) ? 0 : -(int)s_cur[p];
+      f = (move == MV_REMOVE) ? (double)nc / c.K : 1.0;
+    }
+    if (p < 0) {  // removal or flip with no vertex: automatic rejection
+      if (tid == 0) {
+        cnt_prop[move]++;
+        if (c.trace_cap > 0) {
+          TraceRec& r = c.trace[(d.trace_written + jj) % c.trace_cap];
+          r.t = t; r.move = move; r.n = nc; r.birth = -1; r.s_new = 0; r.accept = 0;
+          r.ratio[0] = r.ratio[1] = 0.0; r.R = 0.0; r.u = dr.u_acc;
+        }
+      }
+      continue;
+    }
+    const int q = pmap[p];
+    const int j = jP;
+    const int s_start = c.s0[p];
+    const double lam_new = c.ev[spin][s_new - s_start + 2] - 1.0;
+    if (q < 0) {
+      // first touch: gather s = G^0_{P,p}, w = G^0_{p,P}, d = G^0_pp - (1+lambda)/lambda
+      for (int r = ht; r < j; r += 128) {
+        const int pr = P_s[r];
+        sv[r] = g_int(c, Nb, Gc, n_old, spin, pr, p);
+        wv[r] = g_int(c, Nb, Gc, n_old, spin, p, pr);
+      }
+      if (ht == 127) gpp_s[half] = g_int(c, Nb, Gc, n_old, spin, p, p);
+      __syncthreads();
+      // y = Gamma^{-1} s : warp per row (lanes along the row)
+      for (int r = hw; r < j; r += 4) {
+        double acc = 0.0;
+        for (int cc = lane; cc < j; cc += 32) acc += (double)G[(size_t)r * KM + cc] * sv[cc];
+        acc = warp_sum(acc);
+        if (lane == 0) yv[r] = acc;
+      }
+      // z = w^T Gamma^{-1} : thread per column
+      for (int cc = ht; cc < j; cc += 128) {
+        double acc = 0.0;
+        for (int r = 0; r < j; ++r) acc += wv[r] * (double)G[(size_t)r * KM + cc];
+        zv[cc] = acc;
+      }
+      __syncthreads();
+      double part = 0.0;
+      for (int r = ht; r < j; r += 128) part += wv[r] * yv[r];
+      part = warp_sum(part);
+      if (lane == 0) red[half][hw] = part;
+      __syncthreads();
+      if (ht == 0) {
+        const double dd = gpp_s[half] - (1.0 + lam_new) / lam_new;
+        const double beta = dd - (red[half][0] + red[half][1] + red[half][2] + red[half][3]);
+        red[half][0] = beta;
+        ratio_s[half] = -lam_new * beta;
+      }
+    } else {
+      if (ht == 0) {
+        const double lam_old = lam[q];
+        const double gqq = (double)G[(size_t)q * KM + q];
+        double r;
+        if (lam_new != 0.0) {
+          const double delta = 1.0 / lam_old - 1.0 / lam_new;
+          r = (lam_new / lam_old) * (1.0 + delta * gqq);
+          red[half][0] = delta;
+        } else {
+          r = -gqq / lam_old;
+        }
+        ratio_s[half] = r;
+      }
+    }
+    __syncthreads();
+    const double R = f * ratio_s[0] * ratio_s[1];
+    bool accept = dr.u_acc < fmin(1.0, fabs(R));
+    const bool finite = isfinite(R);
+    if (!finite) accept = false;
+    if (tid == 0) {
+      cnt_prop[move]++;
+      if (!finite) numeric++;
+      if (c.trace_cap > 0) {
+        TraceRec& rr = c.trace[(d.trace_written + jj) % c.trace_cap];
+        rr.t = t; rr.move = move; rr.n = nc;
+        rr.birth = birth[p]; rr.s_new = s_new; rr.accept = accept ? 1 : 0;
+        rr.ratio[0] = ratio_s[0]; rr.ratio[1] = ratio_s[1]; rr.R = R; rr.u = dr.u_acc;
+      }
+    }
+    if (accept) {
+      if (q < 0) {
+        // bordered inverse (Sec. III D): [[G + y z / beta, -y / beta], [-z / beta, 1 / beta]]
+        const double beta = red[half][0];
+        const double ib = 1.0 / beta;
+        for (int e = ht; e < (j + 1) * (j + 1); e += 128) {
+          const int r = e / (j + 1), cc = e % (j + 1);
+          double v;
+          if (r < j && cc < j) v = (double)G[(size_t)r * KM + cc] + yv[r] * zv[cc] * ib;
+          else if (r < j) v = -yv[r] * ib;
+          else if (cc < j) v = -zv[cc] * ib;
+          else v = ib;
+          G[(size_t)r * KM + cc] = (T)v;
+        }
+        if (ht == 0) lam[j] = lam_new;
+      } else if (lam_new != 0.0) {
+        // diagonal change delta of Gamma_qq: Sherman-Morrison on Gamma^{-1}
+        for (int r = ht; r < j; r += 128) {
+          sv[r] = (double)G[(size_t)r * KM + q];
+          wv[r] = (double)G[(size_t)q * KM + r];
+        }
+        __syncthreads();
+        const double delta = red[half][0];
+        const double coef = delta / (1.0 + delta * sv[q]);
+        for (int e = ht; e < j * j; e += 128) {
+          const int r = e / j, cc = e % j;
+          G[(size_t)r * KM + cc] = (T)((double)G[(size_t)r * KM + cc] - coef * sv[r] * wv[cc]);
+        }
+        if (ht == 0) lam[q] = lam_new;
+      } else {
+        // back to the block-start spin: Schur complement removes q from P,
+        // then the last entry of P moves into position q
+        for (int r = ht; r < j; r += 128) {
+          sv[r] = (double)G[(size_t)r * KM + q];
+          wv[r] = (double)G[(size_t)q * KM + r];
+        }
+        __syncthreads();
+        const double gqq = sv[q];
+        for (int e = ht; e < j * j; e += 128) {
+          const int r = e / j, cc = e % j;
+          G[(size_t)r * KM + cc] = (T)((double)G[(size_t)r * KM + cc] - sv[r] * wv[cc] / gqq);
+        }
+        __syncthreads();
+        const int last = j - 1;
+        if (q != last) {
+          for (int e = ht; e < last; e += 128) {
+            if (e == q) continue;
+            G[(size_t)q * KM + e] = G[(size_t)last * KM + e];
+            G[(size_t)e * KM + q] = G[(size_t)e * KM + last];
+          }
+          if (ht == 0) {
+            G[(size_t)q * KM + q] = G[(size_t)last * KM + last];
+            lam[q] = lam[last];
+          }
+        }
+      }
+      __syncthreads();
+      if (tid == 0) {
+        if (q < 0) {
+          P_s[j] = p;
+          pmap[p] = (short)j;
+          jP = j + 1;
+        } else if (lam_new == 0.0) {
+          const int last = j - 1;
+          if (q != last) {
+            P_s[q] = P_s[last];
+            pmap[P_s[q]] = (short)q;
+          }
+          pmap[p] = -1;
+          jP = last;
+        }
+        s_cur[p] = (int8_t)s_new;
+        if (s_new == 0) alive[p >> 5] &= ~(1u << (p & 31));
+        else alive[p >> 5] |= (1u << (p & 31));
+        if (move == MV_INSERT) n_cur = nc + 1;
+        else if (move == MV_REMOVE) n_cur = nc - 1;
+        if (R < 0.0) sign_s = -sign_s;
+        cnt_acc[move]++;
+      }
+    }
+    __syncthreads();
+  }
+  // write back Gamma^{-1}, lambda, P
+  const int jf = jP;
+  if (gamma_in_smem) {
+    for (int e = ht; e < jf * jf; e += 128) {
+      const int r = e / jf, cc = e % jf;
+      c.Ginv[spin][(size_t)r * KM + cc] = G[(size_t)r * KM + cc];
+    }
+  }
+  for (int r = ht; r < jf; r += 128) c.lam[spin][r] = lam[r];
+  for (int r = tid; r < jf; r += 256) c.P[r] = P_s[r];
+  if (tid == 0) {
+    d.k_acc = jf;
+    d.sign = sign_s;
+    for (int q = 0; q < 3; ++q) {
+      d.proposals[q] += cnt_prop[q];
+      d.accepted[q] += cnt_acc[q];
+    }
+    d.numeric_rejects += numeric;
+    if (c.trace_cap > 0) d.trace_written += KM;
+  }
+}
+
+// -------------------------------------------------------------- flush
+// Survivor list S (slots with s != 0 after the block, in slot order) and the
+// compacted configuration in the other buffer (Sec. IV C: s=0 rows and
+// columns are deleted).
+template <typename T>
+__global__ void __launch_bounds__(1024) k_survivors(Chain<T>* chains) {
+  const Chain<T>& c = chains[blockIdx.x];
+  Dyn& d = *c.dyn;
+  if (d.status) return;
+  const int m = d.m, buf = d.buf, ob = 1 - buf;
+  __shared__ int warp_tot[32];
+  __shared__ int base_s;
+  if (threadIdx.x == 0) base_s = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int i0 = 0; i0 < m; i0 += 1024) {
+    const int i = i0 + threadIdx.x;
+    const int keep = (i < m) && c.s[buf][i] != 0;
+    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+    if (lane == 0) warp_tot[w] = __popc(bal);
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      int v = warp_tot[threadIdx.x];
+      int incl = v;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (threadIdx.x >= o) incl += u;
+      }
+      warp_tot[threadIdx.x] = incl - v;
+    }
+    __syncthreads();
+    if (keep) {
+      const int a = base_s + warp_tot[w] + __popc(bal & ((1u << lane) - 1u));
+      c.S[a] = i;
+      c.tau[ob][a] = c.tau[buf][i];
+      c.site[ob][a] = c.site[buf][i];
+      c.s[ob][a] = c.s[buf][i];
+      c.birth[ob][a] = c.birth[buf][i];
+    }
+    __syncthreads();
+    if (threadIdx.x == 1023) base_s += warp_tot[31] + __popc(bal);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) d.n_new = base_s;
+}
+
+// Y = (G^0 - 1)_{S,P} Gamma^{-1}, so that N'_{SS} = N_{SS} - Y N_{P,S}
+// (Eq. Nshermanmorrison with D^{-1} folded: rows p in P of
+// D^{-1}(N - G Gamma^{-1} N_P) equal those of N - (G - 1) Gamma^{-1} N_P).
+// A CTA takes 16 surviving rows: it stages (G^0 - 1)_{rows,P} in shared
+// memory, then multiplies by Gamma^{-1} read from global memory.
+constexpr int kYRows = 16;
+template <typename T>
+__global__ void __launch_bounds__(256) k_flush_y(Chain<T>* chains) {
+  const Chain<T>& c = chains[blockIdx.z];
+  const Dyn& d = *c.dyn;
+  if (d.status) return;
+  const int spin = blockIdx.y;
+  const int kacc = d.k_acc, nn = d.n_new, KM = c.k_max;
+  const int a0 = blockIdx.x * kYRows;
+  if (kacc == 0 || a0 >= nn) return;
+  __shared__ double gh[kYRows * kMaxK];
+  __shared__ int Ps[kMaxK];
+  __shared__ int Si[kYRows];
+  for (int e = threadIdx.x; e < kacc; e += blockDim.x) Ps[e] = c.P[e];
+  for (int e = threadIdx.x; e < kYRows; e += blockDim.x) Si[e] = (a0 + e < nn) ? c.S[a0 + e] : -1;
+  __syncthreads();
+  const T* Nb = c.N[d.buf][spin];
+  const T* Gc = c.Gcol[spin];
+  const int n_old = d.n;
+  for (int e = threadIdx.x; e < kYRows * kacc; e += blockDim.x) {
+    const int aa = e % kYRows, q = e / kYRows;
+    const int i = Si[aa];
+    double v = 0.0;
+    if (i >= 0) {
+      const int pq = Ps[q];
+      v = g_int(c, Nb, Gc, n_old, spin, i, pq) - (i == pq ? 1.0 : 0.0);
+    }
+    gh[q * kYRows + aa] = v;
+  }
+  __syncthreads();
+  const T* Gi = c.Ginv[spin];
+  for (int e = threadIdx.x; e < kYRows * kacc; e += blockDim.x) {
+    const int aa = e % kYRows, r = e / kYRows;
+    if (Si[aa] < 0) continue;
+    double acc = 0.0;
+    for (int q = 0; q < kacc; ++q) acc += gh[q * kYRows + aa] * (double)Gi[(size_t)q * KM + r];
+    c.Y[spin][(size_t)r * c.ld + a0 + aa] = (T)acc;
+  }
+}
+
+// End of block: swap buffers, advance the counter.
+template <typename T>
+__global__ void k_finish_block(Chain<T>* chains, int n_chains) {
+  const int ci = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ci >= n_chains) return;
+  const Chain<T>& c = chains[ci];
+  Dyn& d = *c.dyn;
+  if (d.status) return;
+  const double n = d.n, ki = d.k_ins, ka = d.k_acc, nn = d.n_new;
+  d.work_prep += 2.0 * (2.0 * ki * n * n + 2.0 * n * n * ki + 2.0 * ki * ki * n);
+  d.work_flush += 2.0 * (2.0 * nn * nn * ka + 2.0 * nn * ka * ka);
+  d.bytes_flush += 2.0 * (2.0 * nn * nn + 2.0 * nn * ka) * sizeof(T);
+  d.n = d.n_new;
+  d.buf = 1 - d.buf;
+  d.t += c.k_max;
+  d.sweeps += 1;
+}
+
+__global__ void k_philox_test(uint64_t seed, uint32_t chain, int64_t t0, int count, int purpose,
+                              double* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  double u0, u1;
+  philox_pair(seed, chain, t0 + i, (uint32_t)purpose, u0, u1);
+  out[2 * i] = u0;
+  out[2 * i + 1] = u1;
+}
+
+void launch_philox_test(uint64_t seed, uint32_t chain, int64_t t0, int count, int purpose,
+                        double* out, cudaStream_t st) {
+  k_philox_test<<<(count + 255) / 256, 256, 0, st>>>(seed, chain, t0, count, purpose, out);
+}
+
+// ----------------------------------------------------------- launchers
+template <typename T>
+void launch_block(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t st, PhaseTimer* pt) {
+  const int nch = ls.n_chains;
+  pt->begin(0, st);
+  k_plan<T><<<nch, 256, 0, st>>>(dchains);
+  k_gather<T><<<dim3(ls.gather_slices, 2, nch), 256, 0, st>>>(dchains);
+  pt->end(0, st, 2);
+  pt->begin(1, st);
+  launch_gemm<T>(dchains, ls, PH_RTILDE, st);
+  launch_gemm<T>(dchains, ls, PH_GCOL_OLD, st);
+  launch_gemm<T>(dchains, ls, PH_GCOL_NEW, st);
+  pt->end(1, st, 3);
+  pt->begin(2, st);
+  k_proposals<T><<<nch, 256, ls.prop_smem, st>>>(dchains, ls.gamma_in_smem);
+  pt->end(2, st, 1);
+  pt->begin(4, st);
+  k_survivors<T><<<nch, 1024, 0, st>>>(dchains);
+  k_flush_y<T><<<dim3(ls.y_blocks, 2, nch), 256, 0, st>>>(dchains);
+  pt->end(4, st, 2);
+  pt->begin(3, st);
+  launch_gemm<T>(dchains, ls, PH_FLUSH, st);
+  pt->end(3, st, 1);
+  k_finish_block<T><<<(nch + 127) / 128, 128, 0, st>>>(dchains, nch);
+  pt->kernels[4] += 1;
+}
+
+template <typename T>
+cudaError_t configure_block_kernels(const LaunchShape& ls) {
+  return cudaFuncSetAttribute(k_proposals<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              ls.prop_smem);
+}
+
+template void launch_gemm<double>(Chain<double>*, const LaunchShape&, int, cudaStream_t);
+template void launch_gemm<float>(Chain<float>*, const LaunchShape&, int, cudaStream_t);
+template void launch_block<double>(Chain<double>*, const LaunchShape&, cudaStream_t, PhaseTimer*);
+template void launch_block<float>(Chain<float>*, const LaunchShape&, cudaStream_t, PhaseTimer*);
+template cudaError_t configure_block_kernels<double>(const LaunchShape&);
+template cudaError_t configure_block_kernels<float>(const LaunchShape&);
+
+}  // namespace ctaux

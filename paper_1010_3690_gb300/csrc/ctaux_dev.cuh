@@ -1,0 +1,190 @@
+// Device-side state and helpers of the CT-AUX submatrix-update path.
+//
+// Layout in HBM, per chain (all allocated once at init):
+//   N[buf][spin]   ld x ld, column-major, T = double (FP64 form) or float (mixed)
+//                  double-buffered: a flush reads buffer `buf` and writes the
+//                  compacted result into buffer 1-buf.
+//   tau/site/s/birth[buf]  configuration, slot order = birth order (Sec. IV)
+//   s0             auxiliary spin of each slot at block start
+//   Cpan[spin]     k_max x ld row-major   C = G0(new, old) (e^{V_old} - 1)
+//   Bpan[spin]     ld x k_max col-major   B = G0(old, new)
+//   Gcol[spin]     ld x k_max col-major   columns of G = N_ext G0 for the new vertices
+//   Ginv[spin]     k_max x k_max row-major  Gamma^{-1} (Sec. III D)
+//   lam[spin], P   the touched slots of the block and their cumulative lambda
+//   S              surviving slots of a flush (compaction list)
+//   Y[spin]        ld x k_max col-major   (G - 1)_{S,P} Gamma^{-1}
+// The extended matrix of Sec. IV A, N_ext = [[N, 0], [R~, 1]], is stored in
+// place: rows/cols [n, m) of N hold R~ and the identity block.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ctaux {
+
+constexpr int kMaxK = 256;
+
+enum { MV_INSERT = 0, MV_REMOVE = 1, MV_FLIP = 2 };
+enum { DS_CAPACITY = 1, DS_NUMERIC = 2, DS_SINGULAR = 4, DS_TIMEOUT = 8, DS_INDEX = 16 };
+
+struct TraceRec {  // layout of ctaux_trace_rec
+  int64_t t;
+  int32_t move;
+  int32_t n;
+  int64_t birth;
+  int32_t s_new;
+  int32_t accept;
+  double ratio[2];
+  double R;
+  double u;
+};
+
+struct Dyn {
+  int n;        // interacting vertices (slots [0, n) after a flush)
+  int m;        // n + k_ins during a block
+  int k_ins;    // pre-inserted vertices of the block
+  int k_acc;    // |P| at the end of the proposals
+  int n_new;    // survivors of the flush
+  int buf;      // current N / configuration buffer
+  int status;   // DS_* bits
+  int sign;     // walker sign
+  int64_t t;    // next proposal counter
+  int64_t proposals[3], accepted[3];
+  int64_t sweeps, measurements, order_sum;
+  double sign_sum;
+  int64_t numeric_rejects;
+  int64_t refreshes;
+  double drift_max, drift_fro;
+  double logdet[2];
+  int64_t trace_written;  // total records written
+  int64_t trace_read;     // records handed to the host
+  double work_prep;       // algorithmic flops of the prep products (both spins)
+  double work_flush;      // algorithmic flops of the flush products
+  double bytes_flush;     // algorithmic bytes of the flush (N read + N' written)
+};
+
+template <typename T>
+struct Chain {
+  double beta, K, gamma, dtau, inv_dtau;
+  double ev[2][5];           // e^{gamma sigma d}, d = -2..2  (index d + 2)
+  double inv_em1[2][5];      // 1 / (e^{gamma sigma d} - 1), d != 0
+  double p_insert, p_remove;
+  int n_c, n_classes, n_tau, k_max, cap_m, ld;
+  uint64_t seed;
+  uint32_t chain_id;
+  int trace_cap;
+  int n_bins, n_anchors;
+  const double* g0;          // [2][n_classes][n_tau]
+  const int* dx_class;       // [n_c][n_c]
+  const double* class_weight;  // [n_classes] 1/(n_anchors * #sites of the class)
+  T* N[2][2];                // [buf][spin]
+  double* tau[2];
+  int* site[2];
+  int8_t* s[2];
+  int64_t* birth[2];
+  int8_t* s0;
+  T* Cpan[2];
+  T* Bpan[2];
+  T* Gcol[2];
+  T* Ginv[2];
+  double* lam[2];
+  int* P;
+  int* S;
+  T* Y[2];
+  T* Mg[2];                  // measurement: g_b columns, ld x n_anchors
+  T* Mv[2];                  // measurement: v_b = N g_b, ld x n_anchors
+  double* Mpts[2];           // measurement: value per (anchor, site, bin)
+  T* kpart[2];               // split-K partial tiles
+  int* ticket[2];            // split-K arrival counters per output tile
+  double* work;              // refresh: [spin][2][ld][ld] float64 ping-pong
+  int* perm;                 // refresh pivot rows [spin][ld]
+  int8_t* used;              // refresh pivot flags [spin][ld]
+  unsigned long long* pkeys; // refresh pivot keys [spin][ld]
+  double* work_drift;        // refresh: max, sum of squares
+  double* work_logdet;       // refresh: [spin]
+  double* Gsum;              // [2][n_classes][n_bins] running sums
+  double* Gsq;
+  double* Gmeas;             // last measurement
+  TraceRec* trace;
+  Dyn* dyn;
+};
+
+// ----------------------------------------------------------------- Philox
+// Philox-4x32-10 (Salmon et al., SC'11): 10 rounds of two 32x32 -> 64-bit
+// products; counter (t_lo, t_hi, chain, purpose), key = seed.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    k.x += 0x9E3779B9u;
+    k.y += 0xBB67AE85u;
+  }
+  return c;
+}
+
+__device__ __forceinline__ double u53(uint32_t a, uint32_t b) {
+  return (double)((((uint64_t)a) << 21) + (uint64_t)(b >> 11)) * 0x1.0p-53;
+}
+
+__device__ __forceinline__ void philox_pair(uint64_t seed, uint32_t chain, int64_t t,
+                                            uint32_t purpose, double& u0, double& u1) {
+  const uint4 w = philox4x32_10(make_uint4((uint32_t)((uint64_t)t & 0xffffffffu),
+                                           (uint32_t)((uint64_t)t >> 32), chain, purpose),
+                                make_uint2((uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)));
+  u0 = u53(w.x, w.y);
+  u1 = u53(w.z, w.w);
+}
+
+struct Draws {
+  double u_move, u_acc, u_tau, u_site, u_spin, u_idx;
+};
+
+__device__ __forceinline__ Draws draw(uint64_t seed, uint32_t chain, int64_t t) {
+  Draws d;
+  philox_pair(seed, chain, t, 0u, d.u_move, d.u_acc);
+  philox_pair(seed, chain, t, 1u, d.u_tau, d.u_site);
+  philox_pair(seed, chain, t, 2u, d.u_spin, d.u_idx);
+  return d;
+}
+
+__device__ __forceinline__ int move_of(double u_move, double p_insert, double p_remove) {
+  if (u_move < p_insert) return MV_INSERT;
+  if (u_move < p_insert + p_remove) return MV_REMOVE;
+  return MV_FLIP;
+}
+
+// ------------------------------------------------------- G0 interpolation
+// Linear interpolation of a table row at 0 <= x <= beta; explicit _rn
+// operations keep the arithmetic free of FMA contraction.
+__device__ __forceinline__ double interp_row(const double* row, int n_tau, double inv_dtau, double x) {
+  const double pos = x * inv_dtau;
+  double fi = floor(pos);
+  if (fi < 0.0) fi = 0.0;
+  if (fi > (double)(n_tau - 2)) fi = (double)(n_tau - 2);
+  const int idx = (int)fi;
+  const double f = pos - fi;
+  return __dadd_rn(__dmul_rn(1.0 - f, __ldg(row + idx)), __dmul_rn(f, __ldg(row + idx + 1)));
+}
+
+// G0_sigma(x_i - x_j, tau_i - tau_j): antiperiodic in tau; equal times take
+// G0(0-) = -G0(beta-) (the density convention of Eq. Nmatrix's diagonal).
+template <typename T>
+__device__ __forceinline__ double g0_eval(const Chain<T>& c, int spin, double ti, int xi, double tj,
+                                          int xj) {
+  const double dt = ti - tj;
+  const int cls = __ldg(c.dx_class + xi * c.n_c + xj);
+  const double* row = c.g0 + ((size_t)spin * c.n_classes + cls) * c.n_tau;
+  if (dt > 0.0) return interp_row(row, c.n_tau, c.inv_dtau, dt);
+  if (dt < 0.0) return -interp_row(row, c.n_tau, c.inv_dtau, dt + c.beta);
+  return -__ldg(row + c.n_tau - 1);
+}
+
+// ----------------------------------------------------------- reductions
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+}  // namespace ctaux

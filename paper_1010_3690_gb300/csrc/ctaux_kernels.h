@@ -1,0 +1,95 @@
+// Host-side interface between the C ABI (ctaux_api.cu) and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "ctaux_dev.cuh"
+
+namespace ctaux {
+
+// Fixed launch shapes of one context (derived from capacities at init, so
+// that a sweep needs no host-side knowledge of the current orders).
+constexpr int kMeasChunk = 64;  // vertices per measurement evaluation chunk
+
+enum { PH_RTILDE = 0, PH_GCOL_OLD = 1, PH_GCOL_NEW = 2, PH_FLUSH = 3, PH_MEAS = 4, PH_COUNT = 5 };
+
+struct LaunchShape {
+  int n_chains;
+  int gather_slices;
+  int tiles[PH_COUNT];   // bound on output tiles per (chain, spin)
+  int ksplit[PH_COUNT];  // most slices of the inner dimension a product can need
+  int kchunk;            // fixed slice width of the inner dimension
+  int y_blocks;
+  int prop_smem;
+  int gamma_in_smem;
+  int meas_point_blocks;
+  int meas_lchunks;      // vertex chunks of the measurement evaluation
+  int meas_cb_blocks;
+  int refresh_grid;
+};
+
+// CUDA-event timing of the sweep phases and kernel launch counts.  Phases:
+// 0 plan + G0 gather, 1 prep products, 2 proposals (Gamma growth), 3 flush
+// product, 4 flush support (survivors, Y, end of block), 5 measurement,
+// 6 FP64 refresh.  Events are recorded only while profiling is on; launch
+// counts are always kept.
+struct PhaseTimer {
+  static constexpr int kPhases = 7;
+  static constexpr int kPool = 1024;
+  cudaEvent_t ev[kPool];
+  int phase_of[kPool / 2];
+  int used = 0;
+  int open_slot[kPhases];
+  double ms[kPhases] = {0, 0, 0, 0, 0, 0, 0};
+  long long timed[kPhases] = {0, 0, 0, 0, 0, 0, 0};
+  long long kernels[kPhases] = {0, 0, 0, 0, 0, 0, 0};
+  bool created = false;
+  bool on = false;
+  void begin(int ph, cudaStream_t st) {
+    if (!on) return;
+    if (used + 2 > kPool) collect();
+    open_slot[ph] = used;
+    cudaEventRecord(ev[used], st);
+    used += 1;
+  }
+  void end(int ph, cudaStream_t st, int n_kernels) {
+    kernels[ph] += n_kernels;
+    if (!on) return;
+    const int s = open_slot[ph];
+    cudaEventRecord(ev[used], st);
+    phase_of[s / 2] = ph;
+    used += 1;
+  }
+  // Sums the durations of recorded pairs (synchronises on the last event).
+  void collect() {
+    if (used == 0) return;
+    cudaEventSynchronize(ev[used - 1]);
+    for (int s = 0; s + 1 < used; s += 2) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, ev[s], ev[s + 1]) == cudaSuccess) {
+        ms[phase_of[s / 2]] += t;
+        timed[phase_of[s / 2]] += 1;
+      }
+    }
+    used = 0;
+  }
+};
+
+template <typename T>
+void launch_block(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t st, PhaseTimer* pt);
+template <typename T>
+cudaError_t configure_block_kernels(const LaunchShape& ls);
+template <typename T>
+void launch_gemm(Chain<T>* dchains, const LaunchShape& ls, int phase, cudaStream_t st);
+template <typename T>
+int refresh_blocks_per_sm();
+template <typename T>
+void launch_measure(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t st, PhaseTimer* pt);
+template <typename T>
+cudaError_t launch_refresh(Chain<T>* dchains, const LaunchShape& ls, int only_chain,
+                           cudaStream_t st, PhaseTimer* pt);
+template <typename T>
+void launch_reset_measure(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t st);
+void launch_philox_test(uint64_t seed, uint32_t chain, int64_t t0, int count, int purpose,
+                        double* out, cudaStream_t st);
+
+}  // namespace ctaux

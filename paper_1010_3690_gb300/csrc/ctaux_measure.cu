@@ -1,0 +1,142 @@
+// G(tau) measurement (Sec. IV D) after a flush, on every chain.
+//
+// Estimator for external points a = (x_a, tau_a), b = (x_b, tau_b) (both s=0):
+//   G(a, b) = G0(a, b) + sum_{l,m} G0(a, l) [(e^V - 1) N]_{lm} G0(m, b),
+// the row of an s=0 vertex of N_ext (Sec. IV A) contracted with G = N G0.
+// Anchors b = (site 0, j beta / n_anchors); a = (x_a, tau_b + tau_c) with
+// tau_c the centre of a bin on (0, beta), folded into [0, beta) with the
+// antiperiodic sign.  G_sigma(class(x_a), bin) is the average over anchors
+// and over the sites of a class.
+//
+// Steps: gather g_b[m] = G0(m, b) (k_meas_gather), v_b = N g_b (batched GEMM,
+// split over K), evaluate every point (k_meas_eval), reduce per class in a
+// fixed order and accumulate sums and squares (k_meas_accumulate).
+#include "ctaux_dev.cuh"
+#include "ctaux_kernels.h"
+
+namespace ctaux {
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_meas_gather(Chain<T>* chains) {
+  const Chain<T>& c = chains[blockIdx.z];
+  const Dyn& d = *c.dyn;
+  if (d.status) return;
+  const int spin = blockIdx.y, n = d.n, buf = d.buf, A = c.n_anchors;
+  const long total = (long)n * A;
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    const int m = (int)(e % n), b = (int)(e / n);
+    const double tb = (double)b * c.beta / (double)A;
+    c.Mg[spin][(long)b * c.ld + m] = (T)g0_eval(c, spin, c.tau[buf][m], c.site[buf][m], tb, 0);
+  }
+}
+
+// One thread per evaluation point (anchor, site, bin) and chunk of kMeasChunk
+// vertices; partial sums go to Mpts[spin][chunk][point].
+template <typename T>
+__global__ void __launch_bounds__(256) k_meas_eval(Chain<T>* chains, int point_blocks) {
+  const Chain<T>& c = chains[blockIdx.z];
+  const Dyn& d = *c.dyn;
+  if (d.status) return;
+  const int spin = blockIdx.y, n = d.n, buf = d.buf, A = c.n_anchors, B = c.n_bins;
+  const int npts = A * c.n_c * B;
+  const int chunk = blockIdx.x / point_blocks;
+  const int l0 = chunk * kMeasChunk;
+  if (l0 > 0 && l0 >= n) return;
+  const int pt = (blockIdx.x % point_blocks) * blockDim.x + threadIdx.x;
+  if (pt >= npts) return;
+  const int bin = pt % B, xa = (pt / B) % c.n_c, b = pt / (B * c.n_c);
+  const double tb = (double)b * c.beta / (double)A;
+  const double tc = ((double)bin + 0.5) * c.beta / (double)B;
+  double ta = tb + tc, sg = 1.0;
+  if (ta >= c.beta) {
+    ta -= c.beta;
+    sg = -1.0;
+  }
+  double val = (chunk == 0) ? g0_eval(c, spin, ta, xa, tb, 0) : 0.0;
+  const double* tau = c.tau[buf];
+  const int* site = c.site[buf];
+  const int8_t* s = c.s[buf];
+  const T* V = c.Mv[spin] + (long)b * c.ld;  // v_b = N g_b
+  const int l1 = min(n, l0 + kMeasChunk);
+  for (int l = l0; l < l1; ++l) {
+    const double vl = (c.ev[spin][s[l] + 2] - 1.0) * (double)V[l];
+    val += g0_eval(c, spin, ta, xa, tau[l], site[l]) * vl;
+  }
+  c.Mpts[spin][(size_t)chunk * npts + pt] = sg * val;
+}
+
+// Per (chain, spin, class, bin): fixed-order sum over vertex chunks, anchors
+// and sites.
+template <typename T>
+__global__ void k_meas_accumulate(Chain<T>* chains) {
+  const Chain<T>& c = chains[blockIdx.z];
+  Dyn& d = *c.dyn;
+  if (d.status) return;
+  const int spin = blockIdx.y, A = c.n_anchors, B = c.n_bins;
+  const int npts = A * c.n_c * B;
+  const int nchunks = max(1, (d.n + kMeasChunk - 1) / kMeasChunk);
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < c.n_classes * B) {
+    const int cls = e / B, bin = e % B;
+    double acc = 0.0;
+    for (int b = 0; b < A; ++b)
+      for (int xa = 0; xa < c.n_c; ++xa)
+        if (c.dx_class[xa * c.n_c] == cls) {
+          const int pt = (b * c.n_c + xa) * B + bin;
+          double v = 0.0;
+          for (int q = 0; q < nchunks; ++q) v += c.Mpts[spin][(size_t)q * npts + pt];
+          acc += v;
+        }
+    acc *= c.class_weight[cls];
+    const long o = ((long)spin * c.n_classes + cls) * B + bin;
+    c.Gmeas[o] = acc;
+    c.Gsum[o] += acc;
+    c.Gsq[o] += acc * acc;
+  }
+  if (e == 0 && spin == 0) {
+    d.measurements += 1;
+    d.order_sum += d.n;
+    d.sign_sum += (double)d.sign;
+  }
+}
+
+template <typename T>
+__global__ void k_meas_reset(Chain<T>* chains) {
+  const Chain<T>& c = chains[blockIdx.y];
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < 2 * c.n_classes * c.n_bins) {
+    c.Gsum[e] = 0.0;
+    c.Gsq[e] = 0.0;
+    c.Gmeas[e] = 0.0;
+  }
+  if (e == 0) {
+    c.dyn->measurements = 0;
+    c.dyn->order_sum = 0;
+    c.dyn->sign_sum = 0.0;
+  }
+}
+
+template <typename T>
+void launch_measure(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t st, PhaseTimer* pt) {
+  const int nch = ls.n_chains;
+  pt->begin(5, st);
+  k_meas_gather<T><<<dim3(ls.gather_slices, 2, nch), 256, 0, st>>>(dchains);
+  launch_gemm<T>(dchains, ls, PH_MEAS, st);
+  k_meas_eval<T><<<dim3(ls.meas_point_blocks * ls.meas_lchunks, 2, nch), 256, 0, st>>>(
+      dchains, ls.meas_point_blocks);
+  k_meas_accumulate<T><<<dim3(ls.meas_cb_blocks, 2, nch), 256, 0, st>>>(dchains);
+  pt->end(5, st, 4);
+}
+
+template <typename T>
+void launch_reset_measure(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t st) {
+  k_meas_reset<T><<<dim3(ls.meas_cb_blocks * 2, ls.n_chains), 256, 0, st>>>(dchains);
+}
+
+template void launch_measure<double>(Chain<double>*, const LaunchShape&, cudaStream_t, PhaseTimer*);
+template void launch_measure<float>(Chain<float>*, const LaunchShape&, cudaStream_t, PhaseTimer*);
+template void launch_reset_measure<double>(Chain<double>*, const LaunchShape&, cudaStream_t);
+template void launch_reset_measure<float>(Chain<float>*, const LaunchShape&, cudaStream_t);
+
+}  // namespace ctaux

@@ -1,0 +1,185 @@
+"""CUDA path against the oracle, through the C ABI (needs a GB300).
+
+The oracle replays the same Philox proposals with dense-LU determinant ratios;
+the CUDA path runs the submatrix algorithm (pre-inserted s=0 vertices, Gamma
+growth, Woodbury flush, FP64 refresh).  FP64 tolerance: ratios within 1e-10
+relative, identical accept decisions and identical configurations.
+"""
+import numpy as np
+import pytest
+
+from parity import compare_config, compare_traces, oracle_for
+from oracle import philox
+from workloads import configs
+
+pytestmark = pytest.mark.gpu
+
+pk = pytest.importorskip("paper_1010_3690_gb300")
+
+RTOL64 = 1e-10
+
+
+def test_device_philox_matches_oracle():
+    for purpose in (0, 1, 2):
+        got = pk.ctaux_philox_uniforms(0x1234_5678_9abc_def0, 7, 2**33 - 5, 1 << 18, purpose)
+        ua, ub = philox.uniforms(0x1234_5678_9abc_def0, 7,
+                                 np.arange(2**33 - 5, 2**33 - 5 + (1 << 18), dtype=np.uint64),
+                                 purpose)
+        np.testing.assert_array_equal(got[:, 0], ua)
+        np.testing.assert_array_equal(got[:, 1], ub)
+
+
+@pytest.mark.parametrize("k_max", [1, 8, 16])
+def test_aim1_trace_parity(k_max):
+    ch = configs.aim1(K=1.0, k_max=k_max, capacity=128)
+    n_prop = 1600
+    n_blocks = n_prop // k_max
+    with pk.Context([ch], trace_capacity=n_prop, refresh_every=16) as ctx:
+        ctx.sweep(n_blocks)
+        ctx.synchronize()
+        tr = ctx.trace(0)
+        oc = oracle_for(ch)
+        recs = oc.run(n_prop)
+        compare_traces(tr, recs, RTOL64)
+        compare_config(ctx, 0, oc)
+        for spin in (0, 1):
+            Ng = ctx.get_N(0, spin)
+            No = oc.N(spin)
+            assert Ng.shape == No.shape
+            np.testing.assert_allclose(Ng, No, rtol=1e-9, atol=1e-11 * max(1.0, np.abs(No).max()))
+
+
+def test_accept_sequence_independent_of_k():
+    """k_max = 1 is the rank-one algorithm; the Markov chain must not depend on k."""
+    n_prop = 512
+    seqs = []
+    for k in (1, 4, 32, 64, 128):
+        ch = configs.cube8(K=8.0, k_max=k, capacity=256)
+        with pk.Context([ch], trace_capacity=n_prop, refresh_every=0) as ctx:
+            ctx.sweep(n_prop // k)
+            ctx.synchronize()
+            tr = ctx.trace(0)
+            seqs.append((tr["accept"].copy(), tr["birth"].copy(), ctx.get_config(0)))
+    for acc, birth, cfg in seqs[1:]:
+        np.testing.assert_array_equal(acc, seqs[0][0])
+        np.testing.assert_array_equal(birth, seqs[0][1])
+        np.testing.assert_array_equal(cfg["birth"], seqs[0][2]["birth"])
+
+
+@pytest.mark.parametrize("K,n0", [(1.0, 140), (256.0, 430)])
+def test_cube8_checkpoint_prefix_parity(K, n0):
+    """2x2x2 cluster, beta=5, U=8 at the orders of the workload: both sides start
+    from the same seeded configuration and replay three blocks of k_max=64."""
+    ch = configs.cube8(K=K, k_max=64, capacity=768 if K > 1 else 256)
+    cfg = configs.synthetic_configuration(ch, n0, seed=3)
+    oc = oracle_for(ch)
+    oc.set_config(cfg["tau"], cfg["site"], cfg["s"], cfg["birth"], cfg["t"])
+    with pk.Context([ch], trace_capacity=4096, refresh_every=8) as ctx:
+        ctx.set_config(0, cfg["tau"], cfg["site"], cfg["s"], cfg["birth"], cfg["t"])
+        ctx.sweep(3)
+        ctx.synchronize()
+        tr = ctx.trace(0)
+        recs = oc.run(3 * ch.k_max)
+        compare_traces(tr, recs, RTOL64)
+        compare_config(ctx, 0, oc)
+        Ng = ctx.get_N(0, 1)
+        No = oc.N(1)
+        np.testing.assert_allclose(Ng, No, rtol=1e-8, atol=1e-10 * np.abs(No).max())
+
+
+def test_set_config_builds_N_from_scratch():
+    ch = configs.cube8(K=16.0, k_max=32, capacity=512)
+    oc = oracle_for(ch)
+    oc.run(600)
+    with pk.Context([ch]) as ctx:
+        ctx.set_config(0, oc.tau, oc.site, oc.s, oc.birth, oc.t)
+        for spin in (0, 1):
+            np.testing.assert_allclose(ctx.get_N(0, spin), oc.N(spin), rtol=1e-9,
+                                       atol=1e-12 * np.abs(oc.N(spin)).max())
+        st = ctx.stats(0)
+        for spin in (0, 1):
+            assert st["logdet"][spin] == pytest.approx(oc.slogdet(spin, oc.tau, oc.site, oc.s)[1],
+                                                       rel=1e-10, abs=1e-9)
+
+
+def test_measurement_matches_oracle_per_configuration():
+    ch = configs.cube8(K=16.0, k_max=32, capacity=512)
+    cfg = configs.synthetic_configuration(ch, 60, seed=5)
+    oc = oracle_for(ch)
+    oc.set_config(cfg["tau"], cfg["site"], cfg["s"], cfg["birth"], cfg["t"])
+    with pk.Context([ch], n_tau_bins=12, n_anchors=3) as ctx:
+        ctx.set_config(0, cfg["tau"], cfg["site"], cfg["s"], cfg["birth"], cfg["t"])
+        ctx.reset_measurements()
+        ctx.sweep(1, measure=True)
+        G, E, nm = ctx.measure_G(0)
+        assert nm == 1
+        oc.run(ch.k_max)
+        compare_config(ctx, 0, oc)
+        ref = oc.measure_G(12, 3)
+        np.testing.assert_allclose(G, ref, rtol=1e-9, atol=1e-11)
+
+
+def test_refresh_drift_small_fp64():
+    ch = configs.cube8(K=64.0, k_max=64, capacity=768)
+    with pk.Context([ch], refresh_every=0) as ctx:
+        ctx.sweep(64)
+        drift = ctx.recompute()
+        st = ctx.stats(0)
+        assert st["refreshes"] == 1
+        assert drift < 1e-8, drift
+
+
+def test_flip_moves_and_retouch_parity():
+    """Spin flips make slots change twice inside a block (Gamma diagonal updates)."""
+    ch = configs.cube8(K=4.0, k_max=32, capacity=256)
+    n_prop = 32 * 30
+    with pk.Context([ch], trace_capacity=n_prop, p_insert=0.4, p_flip=0.3) as ctx:
+        ctx.sweep(30)
+        ctx.synchronize()
+        tr = ctx.trace(0)
+        oc = oracle_for(ch, p_insert=0.4, p_flip=0.3)
+        recs = oc.run(n_prop)
+        compare_traces(tr, recs, RTOL64)
+        compare_config(ctx, 0, oc)
+
+
+def test_batched_chains_equal_single_chains():
+    chs = configs.batch(n_chains=4, k_max=16, n_tau=512)
+    n_sw = 20
+    with pk.Context(chs, trace_capacity=n_sw * 16) as ctx:
+        ctx.sweep(n_sw)
+        ctx.synchronize()
+        together = [(ctx.trace(i), ctx.get_config(i)) for i in range(len(chs))]
+    for i, ch in enumerate(chs):
+        with pk.Context([ch], trace_capacity=n_sw * 16) as ctx:
+            ctx.sweep(n_sw)
+            ctx.synchronize()
+            tr = ctx.trace(0)
+            cfg = ctx.get_config(0)
+        np.testing.assert_array_equal(tr["accept"], together[i][0]["accept"])
+        np.testing.assert_array_equal(tr["ratio"], together[i][0]["ratio"])
+        np.testing.assert_array_equal(cfg["tau"], together[i][1]["tau"])
+
+
+def test_capacity_overflow_reports_error():
+    ch = configs.cube8(K=64.0, k_max=32, capacity=40)
+    with pk.Context([ch]) as ctx:
+        ctx.sweep(40)
+        with pytest.raises(pk.CtauxError) as ei:
+            ctx.synchronize()
+        assert ei.value.code == 4
+
+
+def test_empty_configuration_and_removals():
+    """From n=0, removals reject automatically and insertions follow the closed form."""
+    ch = configs.aim1(K=1.0, k_max=8, capacity=64)
+    with pk.Context([ch], trace_capacity=8, p_insert=0.5) as ctx:
+        ctx.sweep(1)
+        ctx.synchronize()
+        tr = ctx.trace(0)
+    want = ch.K + ch.beta * ch.U * ch.n_c / 4.0
+    for r in tr:
+        if r["n"] == 0 and r["move"] == 0:
+            assert r["R"] == pytest.approx(want, rel=1e-12)
+        if r["n"] == 0 and r["move"] == 1:
+            assert not r["accept"] and r["birth"] == -1

@@ -140,3 +140,19 @@ def batch(n_chains=512, seed=12345, k_max=32, K=1.0, capacity=None, n_tau=1024):
 def expected_order(beta, U, n_c, K, double_occ, density=1.0):
     """<n> = K - beta <V> = K + beta U N_c (density/2 - d) (follows from Eq. decoupledZ)."""
     return K + beta * U * n_c * (0.5 * density - double_occ)
+
+
+def synthetic_configuration(ch, n, seed=0, t0=None):
+    """A seeded configuration of n interacting vertices for checkpoint starts.
+
+    tau ~ U[0, beta), site ~ U{0..N_c-1}, s = +-1 with equal probability, birth
+    stamps 0..n-1 (canonical order), next proposal counter t0 (default
+    2^20 + n).  Not an equilibrium sample: a valid Markov-chain state of the
+    requested size, used as the common starting point of the CUDA path and the
+    oracle.
+    """
+    rng = np.random.default_rng(seed)
+    return dict(tau=rng.uniform(0.0, ch.beta, n), site=rng.integers(0, ch.n_c, n).astype(np.int32),
+                s=rng.choice(np.array([-1, 1], dtype=np.int32), n),
+                birth=np.arange(n, dtype=np.int64),
+                t=int(t0 if t0 is not None else (1 << 20) + n))
