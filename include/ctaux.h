@@ -197,6 +197,36 @@ ctaux_status ctaux_philox_uniforms(uint64_t seed, uint32_t chain, int64_t t0, in
 /* Block until all work queued on the context finishes; reports device faults. */
 ctaux_status ctaux_synchronize(ctaux_ctx *ctx);
 
+/* ---- Inversion without device allocation --------------------------------
+ * The paper has no counterpart to this entry point.  It is for callers that
+ * cannot call cudaMalloc: a host program whose device memory belongs to
+ * another allocator (for example a framework's caching allocator that has
+ * already reserved the GPU), or a steady-state loop that must not call
+ * cudaMalloc because the call can block on, or synchronise, the whole device.
+ *
+ * Inverts the m x m float64 matrix d_a (column-major, leading dimension lda,
+ * device memory) by Gauss-Jordan elimination with partial pivoting -- the
+ * arithmetic of the FP64 recomputation that ctaux_recompute runs -- and
+ * writes the inverse to d_inv (leading dimension ld_inv, device memory) and
+ * log|det d_a| to *d_logdet (device memory, may be NULL).  Asynchronous on
+ * cuda_stream (NULL = legacy default stream).  A singular input gives -inf in
+ * *d_logdet and non-finite entries in d_inv.  The caller owns d_a, d_inv and
+ * d_logdet; no context is needed.
+ *
+ * Scratch: one static device array of CTAUX_NOALLOC_SCRATCH_BYTES, held by
+ * every GPU that loads the library until the process exits.  m is limited to
+ * CTAUX_NOALLOC_MAX_M; a larger m returns CTAUX_ECAPACITY, bad pointers or
+ * leading dimensions CTAUX_EINVAL, a failed launch CTAUX_ECUDA.  The first
+ * call on a device looks up the array's device address and the launch size,
+ * with that device current; make that first call before any stream capture.
+ * Every call uses the same array and clears what must start at zero; calls
+ * that overlap on the GPU (other streams, or other host threads without
+ * ordering) race on it and corrupt each other's results. */
+#define CTAUX_NOALLOC_MAX_M 512
+#define CTAUX_NOALLOC_SCRATCH_BYTES 4202752
+ctaux_status ctaux_invert_noalloc(const double *d_a, int lda, double *d_inv, int ld_inv, int m,
+                                  double *d_logdet, void *cuda_stream);
+
 void ctaux_destroy(ctaux_ctx *ctx);
 
 /* Text of the last error of a context (never NULL). */

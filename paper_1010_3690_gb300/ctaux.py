@@ -90,6 +90,7 @@ def _load():
         "ctaux_philox_uniforms": (C.c_int, [C.c_uint64, C.c_uint32, C.c_int64, C.c_int, C.c_int,
                                             P(C.c_double)]),
         "ctaux_synchronize": (C.c_int, [vp]),
+        "ctaux_invert_noalloc": (C.c_int, [vp, C.c_int, vp, C.c_int, C.c_int, vp, vp]),
         "ctaux_destroy": (None, [vp]),
         "ctaux_last_error": (C.c_char_p, [vp]),
     }
@@ -105,7 +106,7 @@ EXPORTED = ("ctaux_init", "ctaux_sweep", "ctaux_measure_G", "ctaux_reset_measure
             "ctaux_recompute", "ctaux_get_stats", "ctaux_get_trace", "ctaux_get_config",
             "ctaux_set_config", "ctaux_get_N", "ctaux_set_profiling", "ctaux_get_phase_times",
             "ctaux_get_work", "ctaux_philox_uniforms", "ctaux_synchronize", "ctaux_destroy",
-            "ctaux_last_error")
+            "ctaux_last_error", "ctaux_invert_noalloc")
 
 
 class CtauxError(RuntimeError):
@@ -132,6 +133,12 @@ def ctaux_philox_uniforms(seed, chain, t0, count, purpose):
     if r:
         raise CtauxError(r, "philox")
     return out
+
+
+def ctaux_invert_noalloc(d_a, lda, d_inv, ld_inv, m, d_logdet=None, stream=None):
+    """Device pointers (ints) in, status code out; see include/ctaux.h."""
+    return lib.ctaux_invert_noalloc(C.c_void_p(d_a), int(lda), C.c_void_p(d_inv), int(ld_inv),
+                                    int(m), C.c_void_p(d_logdet or 0), C.c_void_p(stream or 0))
 
 
 class Context:
