@@ -185,8 +185,9 @@ struct TileEdge {
 // With more than one slice every slice stores its partial tile, and the slice
 // that arrives last at the tile's ticket adds the partials in slice order
 // (deterministic, no waiting) and writes the result.
-template <typename T>
-__global__ void __launch_bounds__(256) k_gemm(Chain<T>* chains, int phase, int ksplit, int kchunk) {
+template <typename T, int PHASE>
+__global__ void __launch_bounds__(256) k_gemm(Chain<T>* chains, int ksplit, int kchunk) {
+  constexpr int phase = PHASE;
   constexpr int GBM = TileEdge<T>::v, GBN = TileEdge<T>::v, TM = GBM / 16, TN = GBN / 16;
   const Chain<T>& c = chains[blockIdx.z];
   const Dyn& d = *c.dyn;
@@ -278,8 +279,15 @@ __global__ void __launch_bounds__(256) k_gemm(Chain<T>* chains, int phase, int k
 
 template <typename T>
 void launch_gemm(Chain<T>* dchains, const LaunchShape& ls, int phase, cudaStream_t st) {
-  k_gemm<T><<<dim3(ls.tiles[phase] * ls.ksplit[phase], 2, ls.n_chains), 256, 0, st>>>(
-      dchains, phase, ls.ksplit[phase], ls.kchunk);
+  const dim3 grid(ls.tiles[phase] * ls.ksplit[phase], 2, ls.n_chains);
+  const int ks = ls.ksplit[phase], kc = ls.kchunk;
+  switch (phase) {
+    case PH_RTILDE: k_gemm<T, PH_RTILDE><<<grid, 256, 0, st>>>(dchains, ks, kc); break;
+    case PH_GCOL_OLD: k_gemm<T, PH_GCOL_OLD><<<grid, 256, 0, st>>>(dchains, ks, kc); break;
+    case PH_GCOL_NEW: k_gemm<T, PH_GCOL_NEW><<<grid, 256, 0, st>>>(dchains, ks, kc); break;
+    case PH_FLUSH: k_gemm<T, PH_FLUSH><<<grid, 256, 0, st>>>(dchains, ks, kc); break;
+    default: k_gemm<T, PH_MEAS><<<grid, 256, 0, st>>>(dchains, ks, kc); break;
+  }
 }
 
 // ------------------------------------------------------------ proposals

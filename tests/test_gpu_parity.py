@@ -183,3 +183,38 @@ def test_empty_configuration_and_removals():
             assert r["R"] == pytest.approx(want, rel=1e-12)
         if r["n"] == 0 and r["move"] == 1:
             assert not r["accept"] and r["birth"] == -1
+
+
+RTOL_MIXED = 1e-5
+
+
+@pytest.mark.parametrize("maker,K,k,n0", [("aim1", 1.0, 8, 0), ("cube8", 256.0, 64, 430),
+                                         ("cube8", 1.0, 32, 140)])
+def test_mixed_precision_trace_parity(maker, K, k, n0):
+    """Float32 N and Gamma^{-1}: ratios within 1e-5 of the FP64 oracle, same accepts."""
+    ch = configs.aim1(K=K, k_max=k, capacity=128) if maker == "aim1" else \
+        configs.cube8(K=K, k_max=k, capacity=768 if K > 1 else 256)
+    oc = oracle_for(ch)
+    n_blocks = 40 if maker == "aim1" else 3
+    with pk.Context([ch], precision=pk.CTAUX_MIXED, trace_capacity=n_blocks * k,
+                    refresh_every=8) as ctx:
+        if n0:
+            cfg = configs.synthetic_configuration(ch, n0, seed=3)
+            oc.set_config(cfg["tau"], cfg["site"], cfg["s"], cfg["birth"], cfg["t"])
+            ctx.set_config(0, cfg["tau"], cfg["site"], cfg["s"], cfg["birth"], cfg["t"])
+        ctx.sweep(n_blocks)
+        ctx.synchronize()
+        tr = ctx.trace(0)
+        recs = oc.run(n_blocks * k)
+        worst = compare_traces(tr, recs, RTOL_MIXED)
+        compare_config(ctx, 0, oc)
+        print(f"mixed {maker} K={K}: worst relative ratio error {worst:.2e}")
+
+
+def test_mixed_refresh_reports_drift_against_fp64():
+    ch = configs.cube8(K=256.0, k_max=64, capacity=768)
+    with pk.Context([ch], precision=pk.CTAUX_MIXED, refresh_every=0) as ctx:
+        ctx.sweep(48)
+        drift = ctx.recompute()
+        N = ctx.get_N(0, 0)
+        assert 0.0 < drift < 1e-3 * max(1.0, np.abs(N).max()), drift
