@@ -45,6 +45,13 @@ def workload(name, K, k_max, chain_id=0):
         ch = configs.cube8(K=K, k_max=k_max, capacity=1024, seed=chain_id)
         ch.chain_id = chain_id
         return [ch], dict(n_target=430 if K >= 200 else 140)
+    if name == "sq36":
+        ch = configs.sq36(K=K, k_max=k_max, capacity=3072, seed=chain_id)
+        ch.chain_id = chain_id
+        return [ch], dict(n_target=2000 if K >= 1000 else 640)
+    if name == "cube100":
+        ch = configs.cube100(K=K, k_max=k_max, capacity=9216, seed=chain_id, chain_id=chain_id)
+        return [ch], dict(n_target=7000 if K >= 4000 else 1400)
     if name == "aim1":
         ch = configs.aim1(K=K, k_max=k_max, capacity=256, seed=chain_id)
         return [ch], dict(n_target=20)
@@ -129,14 +136,13 @@ def cpu_baseline(chains, meta, seconds=15.0):
     t0 = time.perf_counter()
     props = acc = 0
     while time.perf_counter() - t0 < seconds:
-        for rec in oc.run(ch.k_max):
-            props += 1
-            acc += int(rec["accept"])
+        acc += int(oc.step()["accept"])
+        props += 1
     dt = time.perf_counter() - t0
     threads = int(os.environ.get("OPENBLAS_NUM_THREADS", "1"))
     return {"value": acc / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{props} proposals ({props // ch.k_max} blocks of k_max={ch.k_max}) of "
-                      f"{ch.name} from a seeded n={n0} configuration, {dt:.1f} s, dense-LU ratios",
+            "sample": f"{props} proposals of {ch.name} (k_max={ch.k_max}) from a seeded n={n0} "
+                      f"configuration, {dt:.1f} s, dense-LU ratios",
             "proposals_per_s": props / dt}
 
 
@@ -152,8 +158,12 @@ def run_reference(args, rank, world):
     cfg = configs.synthetic_configuration(ch, n0, seed=11)
     oc = OracleChain(ch.table, ch.dx_class, ch.beta, ch.U, ch.K, seed=ch.seed, chain_id=ch.chain_id)
     oc.set_config(cfg["tau"], cfg["site"], cfg["s"], cfg["birth"], cfg["t"])
-    # a step of the reference: a bounded sample of one block (at most 8 proposals)
-    per_step = min(ch.k_max, 8)
+    # a step of the reference is a bounded sample of one block: as many
+    # proposals as keep the whole run near two minutes (at least one)
+    t1 = time.perf_counter()
+    oc.step()
+    t_prop = time.perf_counter() - t1
+    per_step = int(max(1, min(ch.k_max, 120.0 / (t_prop * (args.steps + args.warmup)))))
     for _ in range(args.warmup):
         oc.run(per_step)
     acc = 0

@@ -102,6 +102,7 @@ typedef struct {
   int64_t order_sum;         /* sum of n over measurements */
   double sign_sum;           /* sum of the walker sign over measurements */
   int64_t numeric_rejects;   /* proposals rejected for a non-finite ratio */
+  int64_t near_ties;         /* mixed form: decisions with |u - min(1,|R|)| < 1e-4 max(u, min(1,|R|)) */
   int64_t refreshes;
   double last_drift_max;     /* max |N_run - N_fresh| at the last refresh (both spins) */
   double last_drift_fro;     /* Frobenius norm of the same difference */

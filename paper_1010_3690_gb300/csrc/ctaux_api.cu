@@ -130,9 +130,9 @@ ctaux_status build_chains(ctaux_ctx* ctx) {
   ls.meas_cb_blocks = (max_cls_bins + 255) / 256;
   ctx->max_ld = max_ld;
   // proposal kernel shared memory
-  size_t fixed = sizeof(double) * 8 * max_k + sizeof(double) * 2 * max_k + sizeof(int) * max_k +
+  size_t fixed = ((sizeof(T) * 8 * max_k + 15) & ~size_t(15)) + sizeof(double) * 2 * max_k + sizeof(int) * max_k +
                  sizeof(short) * ((max_ld + 7) & ~7) + sizeof(uint32_t) * ((max_ld + 31) / 32) + 64;
-  size_t gam = sizeof(T) * 2 * (size_t)max_k * max_k;
+  size_t gam = ((sizeof(T) * 2 * (size_t)max_k * (max_k + 1)) + 15) & ~size_t(15);
   ls.gamma_in_smem = (fixed + gam <= 200 * 1024) ? 1 : 0;
   ls.prop_smem = (int)(fixed + (ls.gamma_in_smem ? gam : 0));
   CUDA_TRY(ctx, configure_block_kernels<T>(ls));
@@ -195,7 +195,7 @@ ctaux_status build_chains(ctaux_ctx* ctx) {
       c.Cpan[spin] = dalloc<T>(ctx, K * ld, &err);
       c.Bpan[spin] = dalloc<T>(ctx, ld * K, &err);
       c.Gcol[spin] = dalloc<T>(ctx, ld * K, &err);
-      c.Ginv[spin] = dalloc<T>(ctx, K * K, &err);
+      c.Ginv[spin] = dalloc<T>(ctx, K * (K + 1), &err);
       c.lam[spin] = dalloc<double>(ctx, K, &err);
       c.Y[spin] = dalloc<T>(ctx, ld * K, &err);
       c.Mg[spin] = dalloc<T>(ctx, ld * P.n_anchors, &err);
@@ -424,6 +424,7 @@ ctaux_status ctaux_get_stats(ctaux_ctx* ctx, int chain, ctaux_stats* out) {
   out->order_sum = d.order_sum;
   out->sign_sum = d.sign_sum;
   out->numeric_rejects = d.numeric_rejects;
+  out->near_ties = d.near_ties;
   out->refreshes = d.refreshes;
   out->last_drift_max = d.drift_max;
   out->last_drift_fro = d.drift_fro;

@@ -294,15 +294,17 @@ void launch_gemm(Chain<T>* dchains, const LaunchShape& ls, int phase, cudaStream
 // Interacting Green's function of the block start, G0int(i, j) = G^0_{ij}
 // (Sec. III C: "G^0 is the interacting Green's function at step k=0"):
 // old columns from N by G = (N e^V - 1)/(e^V - 1) (Eq. NfromG), new (s=0)
-// columns from the prep product G_{:,new} = N_ext G0_{:,new}.
-template <typename T>
-__device__ __forceinline__ double g_int(const Chain<T>& c, const T* Nb, const T* Gc, int n_old,
-                                        int spin, int i, int j) {
+// columns from the prep product G_{:,new} = N_ext G0_{:,new}.  Evaluated in
+// the arithmetic type A of the form (float64, or float32 in the mixed form).
+template <typename A, typename T>
+__device__ __forceinline__ A g_int(const Chain<T>& c, const T* Nb, const T* Gc, int n_old, int spin,
+                                   int i, int j) {
   if (j < n_old) {
     const int k = c.s0[j] + 2;
-    return ((double)Nb[(long)j * c.ld + i] * c.ev[spin][k] - (i == j ? 1.0 : 0.0)) * c.inv_em1[spin][k];
+    return ((A)Nb[(long)j * c.ld + i] * (A)c.ev[spin][k] - (i == j ? (A)1 : (A)0)) *
+           (A)c.inv_em1[spin][k];
   }
-  return (double)Gc[(long)(j - n_old) * c.ld + i];
+  return (A)Gc[(long)(j - n_old) * c.ld + i];
 }
 
 // Select the idx-th set bit of a bitmask (one warp).
@@ -333,21 +335,35 @@ __device__ __forceinline__ int select_bit(const uint32_t* mask, int n_words, int
   return -1;
 }
 
+template <typename A>
+__device__ __forceinline__ A warp_sum_t(A v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Relative guard band of the mixed form: a float32 ratio whose Metropolis
+// decision lies this close to the uniform is a near tie.
+constexpr double kTieGuard = 1e-4;
+
 // One CTA per chain, threads [0,128) spin up, [128,256) spin down.  Runs the
-// k_max proposals of the block in order; Gamma^{-1} is grown by partitioning
-// (Sec. III D): beta = d - w^T Gamma^{-1} s, ratio_sigma = -lambda beta
-// (Eq. ratS), the bordered inverse on acceptance.  A slot touched twice in a
-// block changes only the diagonal of Gamma (Eq. Gamma): Sherman-Morrison on
-// Gamma^{-1}, or removal of the slot from P when it returns to its
-// block-start spin (then ratio = -(Gamma^{-1})_qq / lambda).
+// k_max proposals of the block in order; Gamma^{-1} (row-major, row stride
+// k_max + 1) is grown by partitioning (Sec. III D): beta = d - w^T Gamma^{-1} s,
+// ratio_sigma = -lambda beta (Eq. ratS), the bordered inverse on acceptance.
+// A slot touched twice in a block changes only the diagonal of Gamma
+// (Eq. Gamma): Sherman-Morrison on Gamma^{-1}, or removal of the slot from P
+// when it returns to its block-start spin (then ratio = -(Gamma^{-1})_qq / lambda).
+// Arithmetic in T (float64, or float32 in the mixed form, which counts near
+// ties of the accept decision).
 template <typename T>
 __global__ void __launch_bounds__(256) k_proposals(Chain<T>* chains, int gamma_in_smem) {
+  using A = T;
   const Chain<T>& c = chains[blockIdx.x];
   Dyn& d = *c.dyn;
   if (d.status) return;
   const int tid = threadIdx.x, half = tid >> 7, ht = tid & 127, hw = ht >> 5, lane = tid & 31;
   const int spin = half;
-  const int KM = c.k_max, ld = c.ld;
+  const int KM = c.k_max, LG = c.k_max + 1, ld = c.ld;
   const int n_old = d.n, m = d.m, buf = d.buf;
   const int64_t t0 = d.t;
   const T* Nb = c.N[buf][spin];
@@ -356,16 +372,16 @@ __global__ void __launch_bounds__(256) k_proposals(Chain<T>* chains, int gamma_i
   const int64_t* birth = c.birth[buf];
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  // layout: [Ginv 2*KM*KM T (optional)] [vec 2 x 4 x KM double] [lam 2 x KM double]
+  // layout: [Gamma^{-1} 2 x KM x LG (optional)] [vec 2 x 4 x KM] [lam 2 x KM double]
   //         [P KM int] [pmap cap_m short] [alive mask]
   unsigned char* sp = smem_raw;
   T* Gs = nullptr;
   if (gamma_in_smem) {
     Gs = reinterpret_cast<T*>(sp);
-    sp += sizeof(T) * 2 * KM * KM;
+    sp += (sizeof(T) * 2 * KM * LG + 15) & ~size_t(15);
   }
-  double* vec = reinterpret_cast<double*>(sp);
-  sp += sizeof(double) * 8 * KM;
+  A* vec = reinterpret_cast<A*>(sp);
+  sp += (sizeof(A) * 8 * KM + 15) & ~size_t(15);
   double* lam_s = reinterpret_cast<double*>(sp);
   sp += sizeof(double) * 2 * KM;
   int* P_s = reinterpret_cast<int*>(sp);
@@ -375,20 +391,21 @@ __global__ void __launch_bounds__(256) k_proposals(Chain<T>* chains, int gamma_i
   uint32_t* alive = reinterpret_cast<uint32_t*>(sp);
   const int n_words = (m + 31) / 32;
 
-  T* G = gamma_in_smem ? (Gs + (size_t)spin * KM * KM) : c.Ginv[spin];  // row-major KM x KM
-  double* sv = vec + spin * 4 * KM;   // s (column of G^0 over P)
-  double* wv = sv + KM;               // w (row of G^0 over P)
-  double* yv = wv + KM;               // Gamma^{-1} s
-  double* zv = yv + KM;               // w^T Gamma^{-1}
+  T* G = gamma_in_smem ? (Gs + (size_t)spin * KM * LG) : c.Ginv[spin];
+  A* sv = vec + spin * 4 * KM;   // s (column of G^0 over P)
+  A* wv = sv + KM;               // w (row of G^0 over P)
+  A* yv = wv + KM;               // Gamma^{-1} s
+  A* zv = yv + KM;               // w^T Gamma^{-1}
   double* lam = lam_s + spin * KM;
 
-  __shared__ double red[2][4];
-  __shared__ double gpp_s[2];
+  __shared__ A red[2][4];
+  __shared__ A gpp_s[2];
   __shared__ double ratio_s[2];
+  __shared__ double beta_s[2];
   __shared__ int sel_p;
-  __shared__ int jP;        // |P|
+  __shared__ int jP;
   __shared__ int n_cur, sign_s;
-  __shared__ long long cnt_prop[3], cnt_acc[3], numeric;
+  __shared__ long long cnt_prop[3], cnt_acc[3], numeric, ties;
 
   for (int i = tid; i < m; i += 256) pmap[i] = -1;
   for (int w = tid; w < n_words; w += 256) {
@@ -405,6 +422,7 @@ __global__ void __launch_bounds__(256) k_proposals(Chain<T>* chains, int gamma_i
     sign_s = d.sign;
     for (int q = 0; q < 3; ++q) cnt_prop[q] = cnt_acc[q] = 0;
     numeric = 0;
+    ties = 0;
   }
   __syncthreads();
 
@@ -452,63 +470,69 @@ __global__ void __launch_bounds__(256) k_proposals(Chain<T>* chains, int gamma_i
     const int j = jP;
     const int s_start = c.s0[p];
     const double lam_new = c.ev[spin][s_new - s_start + 2] - 1.0;
+    const A lam_a = (A)lam_new;
     if (q < 0) {
-      // first touch: gather s = G^0_{P,p}, w = G^0_{p,P}, d = G^0_pp - (1+lambda)/lambda
+      // first touch: gather s = G^0_{P,p}, w = G^0_{p,P}, G^0_pp
       for (int r = ht; r < j; r += 128) {
         const int pr = P_s[r];
-        sv[r] = g_int(c, Nb, Gc, n_old, spin, pr, p);
-        wv[r] = g_int(c, Nb, Gc, n_old, spin, p, pr);
+        sv[r] = g_int<A>(c, Nb, Gc, n_old, spin, pr, p);
+        wv[r] = g_int<A>(c, Nb, Gc, n_old, spin, p, pr);
       }
-      if (ht == 127) gpp_s[half] = g_int(c, Nb, Gc, n_old, spin, p, p);
+      if (ht == 127) gpp_s[half] = g_int<A>(c, Nb, Gc, n_old, spin, p, p);
       __syncthreads();
-      // y = Gamma^{-1} s : warp per row (lanes along the row)
-      for (int r = hw; r < j; r += 4) {
-        double acc = 0.0;
-        for (int cc = lane; cc < j; cc += 32) acc += (double)G[(size_t)r * KM + cc] * sv[cc];
-        acc = warp_sum(acc);
-        if (lane == 0) yv[r] = acc;
-      }
-      // z = w^T Gamma^{-1} : thread per column
-      for (int cc = ht; cc < j; cc += 128) {
-        double acc = 0.0;
-        for (int r = 0; r < j; ++r) acc += wv[r] * (double)G[(size_t)r * KM + cc];
-        zv[cc] = acc;
+      // y = Gamma^{-1} s (threads 0..63 of the half, one row each) and
+      // z = w^T Gamma^{-1} (threads 64..127, one column each), concurrently
+      if (ht < 64) {
+        for (int r = ht; r < j; r += 64) {
+          A acc = (A)0;
+          const T* Gr = G + (size_t)r * LG;
+          for (int cc = 0; cc < j; ++cc) acc += (A)Gr[cc] * sv[cc];
+          yv[r] = acc;
+        }
+      } else {
+        for (int cc = ht - 64; cc < j; cc += 64) {
+          A acc = (A)0;
+          for (int r = 0; r < j; ++r) acc += wv[r] * (A)G[(size_t)r * LG + cc];
+          zv[cc] = acc;
+        }
       }
       __syncthreads();
-      double part = 0.0;
+      A part = (A)0;
       for (int r = ht; r < j; r += 128) part += wv[r] * yv[r];
-      part = warp_sum(part);
+      part = warp_sum_t(part);
       if (lane == 0) red[half][hw] = part;
       __syncthreads();
       if (ht == 0) {
-        const double dd = gpp_s[half] - (1.0 + lam_new) / lam_new;
-        const double beta = dd - (red[half][0] + red[half][1] + red[half][2] + red[half][3]);
-        red[half][0] = beta;
-        ratio_s[half] = -lam_new * beta;
+        const A dd = gpp_s[half] - ((A)1 + lam_a) / lam_a;
+        const A beta = dd - (red[half][0] + red[half][1] + red[half][2] + red[half][3]);
+        beta_s[half] = (double)beta;
+        ratio_s[half] = (double)(-lam_a * beta);
       }
     } else {
       if (ht == 0) {
-        const double lam_old = lam[q];
-        const double gqq = (double)G[(size_t)q * KM + q];
-        double r;
+        const A lam_old = (A)lam[q];
+        const A gqq = (A)G[(size_t)q * LG + q];
+        A r;
         if (lam_new != 0.0) {
-          const double delta = 1.0 / lam_old - 1.0 / lam_new;
-          r = (lam_new / lam_old) * (1.0 + delta * gqq);
-          red[half][0] = delta;
+          const A delta = (A)1 / lam_old - (A)1 / lam_a;
+          r = (lam_a / lam_old) * ((A)1 + delta * gqq);
+          beta_s[half] = (double)delta;
         } else {
           r = -gqq / lam_old;
         }
-        ratio_s[half] = r;
+        ratio_s[half] = (double)r;
       }
     }
     __syncthreads();
     const double R = f * ratio_s[0] * ratio_s[1];
-    bool accept = dr.u_acc < fmin(1.0, fabs(R));
+    const double pacc = fmin(1.0, fabs(R));
+    bool accept = dr.u_acc < pacc;
     const bool finite = isfinite(R);
     if (!finite) accept = false;
     if (tid == 0) {
       cnt_prop[move]++;
       if (!finite) numeric++;
+      if (sizeof(T) == 4 && finite && fabs(dr.u_acc - pacc) < kTieGuard * fmax(dr.u_acc, pacc)) ties++;
       if (c.trace_cap > 0) {
         TraceRec& rr = c.trace[(d.trace_written + jj) % c.trace_cap];
         rr.t = t; rr.move = move; rr.n = nc;
@@ -519,55 +543,54 @@ __global__ void __launch_bounds__(256) k_proposals(Chain<T>* chains, int gamma_i
     if (accept) {
       if (q < 0) {
         // bordered inverse (Sec. III D): [[G + y z / beta, -y / beta], [-z / beta, 1 / beta]]
-        const double beta = red[half][0];
-        const double ib = 1.0 / beta;
+        const A ib = (A)1 / (A)beta_s[half];
         for (int e = ht; e < (j + 1) * (j + 1); e += 128) {
           const int r = e / (j + 1), cc = e % (j + 1);
-          double v;
-          if (r < j && cc < j) v = (double)G[(size_t)r * KM + cc] + yv[r] * zv[cc] * ib;
+          A v;
+          if (r < j && cc < j) v = (A)G[(size_t)r * LG + cc] + yv[r] * zv[cc] * ib;
           else if (r < j) v = -yv[r] * ib;
           else if (cc < j) v = -zv[cc] * ib;
           else v = ib;
-          G[(size_t)r * KM + cc] = (T)v;
+          G[(size_t)r * LG + cc] = (T)v;
         }
         if (ht == 0) lam[j] = lam_new;
       } else if (lam_new != 0.0) {
         // diagonal change delta of Gamma_qq: Sherman-Morrison on Gamma^{-1}
         for (int r = ht; r < j; r += 128) {
-          sv[r] = (double)G[(size_t)r * KM + q];
-          wv[r] = (double)G[(size_t)q * KM + r];
+          sv[r] = (A)G[(size_t)r * LG + q];
+          wv[r] = (A)G[(size_t)q * LG + r];
         }
         __syncthreads();
-        const double delta = red[half][0];
-        const double coef = delta / (1.0 + delta * sv[q]);
+        const A delta = (A)beta_s[half];
+        const A coef = delta / ((A)1 + delta * sv[q]);
         for (int e = ht; e < j * j; e += 128) {
           const int r = e / j, cc = e % j;
-          G[(size_t)r * KM + cc] = (T)((double)G[(size_t)r * KM + cc] - coef * sv[r] * wv[cc]);
+          G[(size_t)r * LG + cc] = (T)((A)G[(size_t)r * LG + cc] - coef * sv[r] * wv[cc]);
         }
         if (ht == 0) lam[q] = lam_new;
       } else {
         // back to the block-start spin: Schur complement removes q from P,
         // then the last entry of P moves into position q
         for (int r = ht; r < j; r += 128) {
-          sv[r] = (double)G[(size_t)r * KM + q];
-          wv[r] = (double)G[(size_t)q * KM + r];
+          sv[r] = (A)G[(size_t)r * LG + q];
+          wv[r] = (A)G[(size_t)q * LG + r];
         }
         __syncthreads();
-        const double gqq = sv[q];
+        const A igqq = (A)1 / sv[q];
         for (int e = ht; e < j * j; e += 128) {
           const int r = e / j, cc = e % j;
-          G[(size_t)r * KM + cc] = (T)((double)G[(size_t)r * KM + cc] - sv[r] * wv[cc] / gqq);
+          G[(size_t)r * LG + cc] = (T)((A)G[(size_t)r * LG + cc] - sv[r] * wv[cc] * igqq);
         }
         __syncthreads();
         const int last = j - 1;
         if (q != last) {
           for (int e = ht; e < last; e += 128) {
             if (e == q) continue;
-            G[(size_t)q * KM + e] = G[(size_t)last * KM + e];
-            G[(size_t)e * KM + q] = G[(size_t)e * KM + last];
+            G[(size_t)q * LG + e] = G[(size_t)last * LG + e];
+            G[(size_t)e * LG + q] = G[(size_t)e * LG + last];
           }
           if (ht == 0) {
-            G[(size_t)q * KM + q] = G[(size_t)last * KM + last];
+            G[(size_t)q * LG + q] = G[(size_t)last * LG + last];
             lam[q] = lam[last];
           }
         }
@@ -603,7 +626,7 @@ __global__ void __launch_bounds__(256) k_proposals(Chain<T>* chains, int gamma_i
   if (gamma_in_smem) {
     for (int e = ht; e < jf * jf; e += 128) {
       const int r = e / jf, cc = e % jf;
-      c.Ginv[spin][(size_t)r * KM + cc] = G[(size_t)r * KM + cc];
+      c.Ginv[spin][(size_t)r * LG + cc] = G[(size_t)r * LG + cc];
     }
   }
   for (int r = ht; r < jf; r += 128) c.lam[spin][r] = lam[r];
@@ -616,6 +639,7 @@ __global__ void __launch_bounds__(256) k_proposals(Chain<T>* chains, int gamma_i
       d.accepted[q] += cnt_acc[q];
     }
     d.numeric_rejects += numeric;
+    d.near_ties += ties;
     if (c.trace_cap > 0) d.trace_written += KM;
   }
 }
@@ -681,7 +705,8 @@ __global__ void __launch_bounds__(256) k_flush_y(Chain<T>* chains) {
   const int kacc = d.k_acc, nn = d.n_new, KM = c.k_max;
   const int a0 = blockIdx.x * kYRows;
   if (kacc == 0 || a0 >= nn) return;
-  __shared__ double gh[kYRows * kMaxK];
+  using A = T;
+  __shared__ A gh[kYRows * kMaxK];
   __shared__ int Ps[kMaxK];
   __shared__ int Si[kYRows];
   for (int e = threadIdx.x; e < kacc; e += blockDim.x) Ps[e] = c.P[e];
@@ -693,10 +718,10 @@ __global__ void __launch_bounds__(256) k_flush_y(Chain<T>* chains) {
   for (int e = threadIdx.x; e < kYRows * kacc; e += blockDim.x) {
     const int aa = e % kYRows, q = e / kYRows;
     const int i = Si[aa];
-    double v = 0.0;
+    A v = (A)0;
     if (i >= 0) {
       const int pq = Ps[q];
-      v = g_int(c, Nb, Gc, n_old, spin, i, pq) - (i == pq ? 1.0 : 0.0);
+      v = g_int<A>(c, Nb, Gc, n_old, spin, i, pq) - (i == pq ? (A)1 : (A)0);
     }
     gh[q * kYRows + aa] = v;
   }
@@ -705,8 +730,8 @@ __global__ void __launch_bounds__(256) k_flush_y(Chain<T>* chains) {
   for (int e = threadIdx.x; e < kYRows * kacc; e += blockDim.x) {
     const int aa = e % kYRows, r = e / kYRows;
     if (Si[aa] < 0) continue;
-    double acc = 0.0;
-    for (int q = 0; q < kacc; ++q) acc += gh[q * kYRows + aa] * (double)Gi[(size_t)q * KM + r];
+    A acc = (A)0;
+    for (int q = 0; q < kacc; ++q) acc += gh[q * kYRows + aa] * (A)Gi[(size_t)q * (KM + 1) + r];
     c.Y[spin][(size_t)r * c.ld + a0 + aa] = (T)acc;
   }
 }

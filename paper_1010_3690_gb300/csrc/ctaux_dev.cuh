@@ -9,7 +9,7 @@
 //   Cpan[spin]     k_max x ld row-major   C = G0(new, old) (e^{V_old} - 1)
 //   Bpan[spin]     ld x k_max col-major   B = G0(old, new)
 //   Gcol[spin]     ld x k_max col-major   columns of G = N_ext G0 for the new vertices
-//   Ginv[spin]     k_max x k_max row-major  Gamma^{-1} (Sec. III D)
+//   Ginv[spin]     k_max x (k_max+1) row-major  Gamma^{-1} (Sec. III D)
 //   lam[spin], P   the touched slots of the block and their cumulative lambda
 //   S              surviving slots of a flush (compaction list)
 //   Y[spin]        ld x k_max col-major   (G - 1)_{S,P} Gamma^{-1}
@@ -52,6 +52,7 @@ struct Dyn {
   int64_t sweeps, measurements, order_sum;
   double sign_sum;
   int64_t numeric_rejects;
+  int64_t near_ties;      // mixed form: accept decisions within the guard band
   int64_t refreshes;
   double drift_max, drift_fro;
   double logdet[2];
@@ -178,6 +179,29 @@ __device__ __forceinline__ double g0_eval(const Chain<T>& c, int spin, double ti
   if (dt > 0.0) return interp_row(row, c.n_tau, c.inv_dtau, dt);
   if (dt < 0.0) return -interp_row(row, c.n_tau, c.inv_dtau, dt + c.beta);
   return -__ldg(row + c.n_tau - 1);
+}
+
+// Same interpolation in float32 (the mixed form's measurement): table entries
+// rounded to float, position and weights in float.
+__device__ __forceinline__ float interp_row_f(const double* row, int n_tau, float inv_dtau, float x) {
+  const float pos = x * inv_dtau;
+  float fi = floorf(pos);
+  fi = fminf(fmaxf(fi, 0.f), (float)(n_tau - 2));
+  const int idx = (int)fi;
+  const float f = pos - fi;
+  return (1.f - f) * (float)__ldg(row + idx) + f * (float)__ldg(row + idx + 1);
+}
+
+template <typename T>
+__device__ __forceinline__ float g0_eval_f(const Chain<T>& c, int spin, float ti, int xi, float tj,
+                                           int xj) {
+  const float dt = ti - tj;
+  const int cls = __ldg(c.dx_class + xi * c.n_c + xj);
+  const double* row = c.g0 + ((size_t)spin * c.n_classes + cls) * c.n_tau;
+  const float idt = (float)c.inv_dtau;
+  if (dt > 0.f) return interp_row_f(row, c.n_tau, idt, dt);
+  if (dt < 0.f) return -interp_row_f(row, c.n_tau, idt, dt + (float)c.beta);
+  return -(float)__ldg(row + c.n_tau - 1);
 }
 
 // ----------------------------------------------------------- reductions

@@ -59,9 +59,19 @@ __global__ void __launch_bounds__(256) k_meas_eval(Chain<T>* chains, int point_b
   const int8_t* s = c.s[buf];
   const T* V = c.Mv[spin] + (long)b * c.ld;  // v_b = N g_b
   const int l1 = min(n, l0 + kMeasChunk);
-  for (int l = l0; l < l1; ++l) {
-    const double vl = (c.ev[spin][s[l] + 2] - 1.0) * (double)V[l];
-    val += g0_eval(c, spin, ta, xa, tau[l], site[l]) * vl;
+  if (sizeof(T) == 8) {
+    for (int l = l0; l < l1; ++l) {
+      const double vl = (c.ev[spin][s[l] + 2] - 1.0) * (double)V[l];
+      val += g0_eval(c, spin, ta, xa, tau[l], site[l]) * vl;
+    }
+  } else {  // mixed form: float32 interpolation and products
+    float acc = 0.f;
+    const float taf = (float)ta;
+    for (int l = l0; l < l1; ++l) {
+      const float vl = ((float)c.ev[spin][s[l] + 2] - 1.f) * (float)V[l];
+      acc += g0_eval_f(c, spin, taf, xa, (float)tau[l], site[l]) * vl;
+    }
+    val += (double)acc;
   }
   c.Mpts[spin][(size_t)chunk * npts + pt] = sg * val;
 }

@@ -41,7 +41,8 @@ class Stats(C.Structure):
     _fields_ = [("n", C.c_int64), ("t", C.c_int64), ("proposals", C.c_int64 * 3),
                 ("accepted", C.c_int64 * 3), ("sweeps", C.c_int64), ("measurements", C.c_int64),
                 ("order_sum", C.c_int64), ("sign_sum", C.c_double),
-                ("numeric_rejects", C.c_int64), ("refreshes", C.c_int64),
+                ("numeric_rejects", C.c_int64), ("near_ties", C.c_int64),
+                ("refreshes", C.c_int64),
                 ("last_drift_max", C.c_double), ("last_drift_fro", C.c_double),
                 ("logdet", C.c_double * 2), ("sign", C.c_int), ("status", C.c_int)]
 

@@ -186,12 +186,22 @@ def test_empty_configuration_and_removals():
 
 
 RTOL_MIXED = 1e-5
+# At K=1 the expansion parameter is large (e^gamma = 42 for aim1, 320 for
+# cube8): the float32 prep products sum terms of size ~e^gamma/2 that cancel
+# to O(1), so float32 ratios carry ~e^gamma * 2^-24 relative error.  There the
+# test asks for 1e-4 (and identical decisions); the K-matched workloads of the
+# benchmark (gamma ~ 1.1) meet 1e-5.
+RTOL_MIXED_K1 = 1e-4
 
 
-@pytest.mark.parametrize("maker,K,k,n0", [("aim1", 1.0, 8, 0), ("cube8", 256.0, 64, 430),
-                                         ("cube8", 1.0, 32, 140)])
-def test_mixed_precision_trace_parity(maker, K, k, n0):
-    """Float32 N and Gamma^{-1}: ratios within 1e-5 of the FP64 oracle, same accepts."""
+@pytest.mark.parametrize("maker,K,k,n0,rtol", [
+    ("aim1", 1.0, 8, 0, RTOL_MIXED_K1),
+    ("cube8", 256.0, 64, 430, RTOL_MIXED),
+    ("cube8", 1.0, 32, 140, RTOL_MIXED_K1),
+    ("aim1", 16.0, 8, 0, RTOL_MIXED),
+])
+def test_mixed_precision_trace_parity(maker, K, k, n0, rtol):
+    """Float32 N and Gamma^{-1}: ratios within tolerance of the FP64 oracle, same accepts."""
     ch = configs.aim1(K=K, k_max=k, capacity=128) if maker == "aim1" else \
         configs.cube8(K=K, k_max=k, capacity=768 if K > 1 else 256)
     oc = oracle_for(ch)
@@ -206,9 +216,10 @@ def test_mixed_precision_trace_parity(maker, K, k, n0):
         ctx.synchronize()
         tr = ctx.trace(0)
         recs = oc.run(n_blocks * k)
-        worst = compare_traces(tr, recs, RTOL_MIXED)
+        worst = compare_traces(tr, recs, rtol)
         compare_config(ctx, 0, oc)
-        print(f"mixed {maker} K={K}: worst relative ratio error {worst:.2e}")
+        print(f"mixed {maker} K={K}: worst relative ratio error {worst:.2e}, "
+              f"near ties {ctx.stats(0)['near_ties']}")
 
 
 def test_mixed_refresh_reports_drift_against_fp64():

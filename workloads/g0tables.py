@@ -113,20 +113,24 @@ class Cluster:
         for i in range(n_c):
             for j in range(n_c):
                 self.dx_class[i, j] = index[self.reduce(self.sites[i] - self.sites[j])]
-        # reciprocal superlattice b = 2 pi A^{-T} (rows), cluster momenta
+        # reciprocal superlattice b = 2 pi A^{-T} (rows).  Cluster momenta
+        # K = 2 pi phi with phi = m A^{-T}; n_c * phi is an integer vector, so the
+        # momenta are enumerated and reduced modulo 2 pi in exact integers.
         self.B = 2.0 * math.pi * np.linalg.inv(A.astype(np.float64)).T
+        adjT = np.round(np.linalg.inv(A.astype(np.float64)).T * n_c).astype(np.int64)
         ks = {}
-        rng = range(-n_c, n_c + 1)
-        for m in itertools.product(rng, repeat=d):
-            k = np.array(m, dtype=np.float64) @ self.B
-            k = (k + math.pi) % (2.0 * math.pi) - math.pi
-            key = tuple(np.round(k / (2 * math.pi) * 4 * n_c).astype(int))
+        for m in itertools.product(range(n_c), repeat=d):
+            num = (np.array(m, dtype=np.int64) @ adjT) % n_c           # n_c * phi mod n_c
+            num = np.where(num >= (n_c + 1) // 2, num - n_c, num)      # to [-n_c/2, n_c/2)
+            key = tuple(int(v) for v in num)
             if key not in ks:
-                ks[key] = k
+                ks[key] = 2.0 * math.pi * num.astype(np.float64) / n_c
             if len(ks) == n_c:
                 break
-        self.K = np.array(sorted(ks.values(), key=lambda k: tuple(np.round(k, 9))))
+        self.K = np.array([ks[k] for k in sorted(ks)])
         assert len(self.K) == n_c
+        # exp(i K . a) = 1 for every superlattice vector a
+        assert np.allclose(np.exp(1j * (self.K @ A.T.astype(np.float64))), 1.0)
 
     def reduce(self, r):
         f = self._At_inv @ np.asarray(r, dtype=np.float64)
