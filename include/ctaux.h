@@ -90,6 +90,8 @@ typedef struct {
   int n_anchors;                      /* anchor times of the G(tau) estimator */
   int trace_capacity;                 /* per-chain trace ring size; 0 = no trace */
   int device;                         /* CUDA device ordinal */
+  int mixed_flush_tc;                 /* mixed form: 1 = flush on the tensor cores (tcgen05,
+                                         split 3xTF32), 0 = float32 CUDA-core product */
 } ctaux_params;
 
 typedef struct {

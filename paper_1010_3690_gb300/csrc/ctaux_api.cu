@@ -23,6 +23,7 @@ struct ctaux_ctx {
   int sm_count = 0;
   LaunchShape ls{};
   void* chains_dev = nullptr;        // Chain<double>[] or Chain<float>[]
+  TcMaps* tc_maps_dev = nullptr;     // mixed form: TMA descriptors [chain][spin]
   std::vector<Chain<double>> hc64;   // host copies of the descriptors
   std::vector<Chain<float>> hc32;
   std::vector<void*> allocations;
@@ -136,6 +137,14 @@ ctaux_status build_chains(ctaux_ctx* ctx) {
   ls.gamma_in_smem = (fixed + gam <= 200 * 1024) ? 1 : 0;
   ls.prop_smem = (int)(fixed + (ls.gamma_in_smem ? gam : 0));
   CUDA_TRY(ctx, configure_block_kernels<T>(ls));
+  const bool mixed_tc = (sizeof(T) == 4) && P.mixed_flush_tc != 0;
+  ls.use_tc = mixed_tc ? 1 : 0;
+  int max_rows = 128;
+  for (const auto& cp : ctx->chains) max_rows = std::max(max_rows, round_up(cp.capacity + cp.k_max, 128));
+  ls.tc_tiles = (max_rows / 128) * (max_rows / 128);
+  ls.split_x_blocks = std::max(1, std::min(256, (max_rows + 7) / 8));
+  if (mixed_tc) CUDA_TRY(ctx, configure_flush_tc());
+  std::vector<TcMaps> host_maps(mixed_tc ? 2 * ctx->chains.size() : 0);
   int nb = refresh_blocks_per_sm<T>();
   ls.refresh_grid = std::max(1, nb) * ctx->sm_count;
 
@@ -204,6 +213,22 @@ ctaux_status build_chains(ctaux_ctx* ctx) {
       c.kpart[spin] = dalloc<T>(ctx, kpart_elems, &err);
       c.ticket[spin] = dalloc<int>(ctx, *std::max_element(ls.tiles, ls.tiles + PH_COUNT), &err);
     }
+    c.kp = round_up(cp.k_max, 32);
+    if (mixed_tc) {
+      const int rows = round_up(c.cap_m, 128);
+      for (int spin = 0; spin < 2; ++spin) {
+        c.Yh[spin] = reinterpret_cast<float*>(dalloc<T>(ctx, (size_t)rows * c.kp, &err));
+        c.Yl[spin] = reinterpret_cast<float*>(dalloc<T>(ctx, (size_t)rows * c.kp, &err));
+        c.Xh[spin] = reinterpret_cast<float*>(dalloc<T>(ctx, (size_t)rows * c.kp, &err));
+        c.Xl[spin] = reinterpret_cast<float*>(dalloc<T>(ctx, (size_t)rows * c.kp, &err));
+        if (err != cudaSuccess)
+          return set_err(ctx, CTAUX_ENOMEM, "device allocation failed: %s", cudaGetErrorString(err));
+        cudaError_t me = encode_tc_maps(&host_maps[2 * ci + spin], c.Yh[spin], c.Yl[spin], c.Xh[spin],
+                                        c.Xl[spin], rows, c.kp);
+        if (me != cudaSuccess)
+          return set_err(ctx, CTAUX_ECUDA, "tensor map encoding failed (%s)", cudaGetErrorString(me));
+      }
+    }
     c.P = dalloc<int>(ctx, K, &err);
     c.S = dalloc<int>(ctx, ld, &err);
     c.work = dalloc<double>(ctx, (size_t)2 * 2 * ld * ld, &err);
@@ -224,6 +249,14 @@ ctaux_status build_chains(ctaux_ctx* ctx) {
     std::memset(&d0, 0, sizeof(d0));
     d0.sign = 1;
     CUDA_TRY(ctx, cudaMemcpy(c.dyn, &d0, sizeof(Dyn), cudaMemcpyHostToDevice));
+  }
+  if (mixed_tc) {
+    void* dm = nullptr;
+    CUDA_TRY(ctx, cudaMalloc(&dm, host_maps.size() * sizeof(TcMaps)));
+    ctx->allocations.push_back(dm);
+    CUDA_TRY(ctx, cudaMemcpy(dm, host_maps.data(), host_maps.size() * sizeof(TcMaps),
+                             cudaMemcpyHostToDevice));
+    ctx->tc_maps_dev = reinterpret_cast<TcMaps*>(dm);
   }
   void* dc = nullptr;
   CUDA_TRY(ctx, cudaMalloc(&dc, hc.size() * sizeof(Chain<T>)));
@@ -272,7 +305,7 @@ ctaux_status do_sweeps(ctaux_ctx* ctx, int n_sweeps, int measure, cudaStream_t s
   Chain<T>* dc = reinterpret_cast<Chain<T>*>(ctx->chains_dev);
   PhaseTimer* pt = ctx->timer;
   for (int s = 0; s < n_sweeps; ++s) {
-    launch_block<T>(dc, ctx->ls, st, pt);
+    launch_block<T>(dc, ctx->ls, st, pt, ctx->tc_maps_dev);
     ctx->blocks_since_refresh += 1;
     if (ctx->params.refresh_every > 0 && ctx->blocks_since_refresh >= ctx->params.refresh_every) {
       ctaux_status r = do_refresh<T>(ctx, -1, st);

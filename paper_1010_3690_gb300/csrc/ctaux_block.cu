@@ -1,6 +1,8 @@
 // One submatrix block of CT-AUX on every chain: pre-insertion (Sec. IV A),
 // G0 gather, prep products, the k_max proposals with Gamma growth
 // (Secs. III D and IV B) and the Woodbury flush with compaction (Sec. IV C).
+#include <type_traits>
+
 #include "ctaux_dev.cuh"
 #include "ctaux_kernels.h"
 
@@ -695,8 +697,19 @@ __global__ void __launch_bounds__(1024) k_survivors(Chain<T>* chains) {
 // D^{-1}(N - G Gamma^{-1} N_P) equal those of N - (G - 1) Gamma^{-1} N_P).
 // A CTA takes 16 surviving rows: it stages (G^0 - 1)_{rows,P} in shared
 // memory, then multiplies by Gamma^{-1} read from global memory.
+// With SPLIT (mixed form, tensor-core flush) Y is written instead as K-major
+// tf32 hi/lo rows Yh/Yl[a * kp + r], zero for k_acc <= r < kp.
 constexpr int kYRows = 16;
-template <typename T>
+
+__device__ __forceinline__ void split_tf32_y(float x, float& hi, float& lo) {
+  uint32_t h, l;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+  hi = __uint_as_float(h);
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(x - hi));
+  lo = __uint_as_float(l);
+}
+
+template <typename T, bool SPLIT>
 __global__ void __launch_bounds__(256) k_flush_y(Chain<T>* chains) {
   const Chain<T>& c = chains[blockIdx.z];
   const Dyn& d = *c.dyn;
@@ -704,7 +717,7 @@ __global__ void __launch_bounds__(256) k_flush_y(Chain<T>* chains) {
   const int spin = blockIdx.y;
   const int kacc = d.k_acc, nn = d.n_new, KM = c.k_max;
   const int a0 = blockIdx.x * kYRows;
-  if (kacc == 0 || a0 >= nn) return;
+  if ((!SPLIT && kacc == 0) || a0 >= nn) return;
   using A = T;
   __shared__ A gh[kYRows * kMaxK];
   __shared__ int Ps[kMaxK];
@@ -727,12 +740,29 @@ __global__ void __launch_bounds__(256) k_flush_y(Chain<T>* chains) {
   }
   __syncthreads();
   const T* Gi = c.Ginv[spin];
-  for (int e = threadIdx.x; e < kYRows * kacc; e += blockDim.x) {
-    const int aa = e % kYRows, r = e / kYRows;
-    if (Si[aa] < 0) continue;
-    A acc = (A)0;
-    for (int q = 0; q < kacc; ++q) acc += gh[q * kYRows + aa] * (A)Gi[(size_t)q * (KM + 1) + r];
-    c.Y[spin][(size_t)r * c.ld + a0 + aa] = (T)acc;
+  if constexpr (!SPLIT) {
+    for (int e = threadIdx.x; e < kYRows * kacc; e += blockDim.x) {
+      const int aa = e % kYRows, r = e / kYRows;
+      if (Si[aa] < 0) continue;
+      A acc = (A)0;
+      for (int q = 0; q < kacc; ++q) acc += gh[q * kYRows + aa] * (A)Gi[(size_t)q * (KM + 1) + r];
+      c.Y[spin][(size_t)r * c.ld + a0 + aa] = (T)acc;
+    }
+  } else {
+    const int KP = c.kp;
+    for (int e = threadIdx.x; e < kYRows * KP; e += blockDim.x) {
+      const int r = e % KP, aa = e / KP;
+      if (Si[aa] < 0) continue;
+      float hi = 0.f, lo = 0.f;
+      if (r < kacc) {
+        float acc = 0.f;
+        for (int q = 0; q < kacc; ++q)
+          acc += (float)gh[q * kYRows + aa] * (float)Gi[(size_t)q * (KM + 1) + r];
+        split_tf32_y(acc, hi, lo);
+      }
+      c.Yh[spin][(size_t)(a0 + aa) * KP + r] = hi;
+      c.Yl[spin][(size_t)(a0 + aa) * KP + r] = lo;
+    }
   }
 }
 
@@ -771,7 +801,8 @@ void launch_philox_test(uint64_t seed, uint32_t chain, int64_t t0, int count, in
 
 // ----------------------------------------------------------- launchers
 template <typename T>
-void launch_block(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t st, PhaseTimer* pt) {
+void launch_block(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t st, PhaseTimer* pt,
+                  const TcMaps* maps) {
   const int nch = ls.n_chains;
   pt->begin(0, st);
   k_plan<T><<<nch, 256, 0, st>>>(dchains);
@@ -785,13 +816,25 @@ void launch_block(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t st, Pha
   pt->begin(2, st);
   k_proposals<T><<<nch, 256, ls.prop_smem, st>>>(dchains, ls.gamma_in_smem);
   pt->end(2, st, 1);
+  bool tc = false;
+  if constexpr (std::is_same<T, float>::value) tc = ls.use_tc != 0;
   pt->begin(4, st);
   k_survivors<T><<<nch, 1024, 0, st>>>(dchains);
-  k_flush_y<T><<<dim3(ls.y_blocks, 2, nch), 256, 0, st>>>(dchains);
+  if (tc) {
+    if constexpr (std::is_same<T, float>::value)
+      k_flush_y<float, true><<<dim3(ls.y_blocks, 2, nch), 256, 0, st>>>(dchains);
+  } else {
+    k_flush_y<T, false><<<dim3(ls.y_blocks, 2, nch), 256, 0, st>>>(dchains);
+  }
   pt->end(4, st, 2);
   pt->begin(3, st);
-  launch_gemm<T>(dchains, ls, PH_FLUSH, st);
-  pt->end(3, st, 1);
+  if (tc) {
+    if constexpr (std::is_same<T, float>::value) launch_flush_tc(dchains, maps, ls, st);
+    pt->end(3, st, 2);
+  } else {
+    launch_gemm<T>(dchains, ls, PH_FLUSH, st);
+    pt->end(3, st, 1);
+  }
   k_finish_block<T><<<(nch + 127) / 128, 128, 0, st>>>(dchains, nch);
   pt->kernels[4] += 1;
 }
@@ -804,8 +847,10 @@ cudaError_t configure_block_kernels(const LaunchShape& ls) {
 
 template void launch_gemm<double>(Chain<double>*, const LaunchShape&, int, cudaStream_t);
 template void launch_gemm<float>(Chain<float>*, const LaunchShape&, int, cudaStream_t);
-template void launch_block<double>(Chain<double>*, const LaunchShape&, cudaStream_t, PhaseTimer*);
-template void launch_block<float>(Chain<float>*, const LaunchShape&, cudaStream_t, PhaseTimer*);
+template void launch_block<double>(Chain<double>*, const LaunchShape&, cudaStream_t, PhaseTimer*,
+                                   const TcMaps*);
+template void launch_block<float>(Chain<float>*, const LaunchShape&, cudaStream_t, PhaseTimer*,
+                                  const TcMaps*);
 template cudaError_t configure_block_kernels<double>(const LaunchShape&);
 template cudaError_t configure_block_kernels<float>(const LaunchShape&);
 

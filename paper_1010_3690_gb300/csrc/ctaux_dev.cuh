@@ -74,6 +74,7 @@ struct Chain {
   uint32_t chain_id;
   int trace_cap;
   int n_bins, n_anchors;
+  int kp;                    // mixed form: k_max rounded up to 32 (split operand row length)
   const double* g0;          // [2][n_classes][n_tau]
   const int* dx_class;       // [n_c][n_c]
   const double* class_weight;  // [n_classes] 1/(n_anchors * #sites of the class)
@@ -94,6 +95,10 @@ struct Chain {
   T* Mg[2];                  // measurement: g_b columns, ld x n_anchors
   T* Mv[2];                  // measurement: v_b = N g_b, ld x n_anchors
   double* Mpts[2];           // measurement: value per (anchor, site, bin)
+  float* Yh[2];              // mixed form: split K-major flush operands, rows x kp
+  float* Yl[2];
+  float* Xh[2];
+  float* Xl[2];
   T* kpart[2];               // split-K partial tiles
   int* ticket[2];            // split-K arrival counters per output tile
   double* work;              // refresh: [spin][2][ld][ld] float64 ping-pong

@@ -1,0 +1,325 @@
+// Woodbury flush of the mixed form on the 5th-generation tensor cores:
+//   N'[a][b] = N[S_a][S_b] - sum_r Y[a][r] X[r][b],  X = N[P, S]
+// (Eq. Nshermanmorrison with the s=0 rows and columns removed, Sec. IV C),
+// as a tcgen05 GEMM with the split 3xTF32 product of Ootomo & Yokota (2022):
+// every float32 operand is split into hi = tf32(x) and lo = tf32(x - hi), and
+// hi*hi + hi*lo + lo*hi accumulate in one float32 TMEM accumulator.
+//
+// Operands are K-major split buffers written by the flush preparation kernels
+// (Yh/Yl: rows a, Xh/Xl: rows b, KP = k_max rounded up to 32 float32 per row,
+// zero beyond k_acc), loaded by TMA into 128-byte-swizzled shared memory
+// (one TMA load per 128 x 32 tile, no multicast).  One CTA of 128 threads per
+// 128 x 128 output tile: thread 0 issues the TMA loads and the MMAs, all four
+// warps read the accumulator back with tcgen05.ld and write the compacted
+// result.  Every mbarrier wait is bounded; on timeout the chain's status gets
+// DS_TIMEOUT, the CTA waits (bounded) for its copies in flight, frees its TMEM
+// and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "ctaux_dev.cuh"
+#include "ctaux_kernels.h"
+
+namespace ctaux {
+
+namespace {
+
+constexpr int kTileBytes = kTcBM * kTcBK * 4;   // one 128 x 32 float32 operand tile
+constexpr int kStageBytes = 4 * kTileBytes;     // Ah, Al, Bh, Bl
+constexpr uint32_t kWaitLimit = 1u << 24;
+constexpr uint32_t kTmemCols = 128;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity) {
+  for (uint32_t i = 0; i < kWaitLimit; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                            uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(mbar)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, rows of 128 B,
+// 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);   // start address
+  d |= (uint64_t)(16u >> 4) << 16;            // leading byte offset (unused for this layout)
+  d |= (uint64_t)(1024u >> 4) << 32;          // stride byte offset
+  d |= (uint64_t)1 << 46;                     // descriptor version
+  d |= (uint64_t)2 << 61;                     // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor, kind::tf32: D float32, A and B tf32, both K-major,
+// N = 128, M = 128.
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTcBN >> 3) << 17) |
+                            ((uint32_t)(kTcBM >> 4) << 24);
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   mbar)
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+      "%30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+}  // namespace
+
+// float32 -> (hi, lo) tf32 pair, hi rounded to nearest (cvt.rna.tf32.f32).
+__device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
+  uint32_t h, l;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+  hi = __uint_as_float(h);
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(x - hi));
+  lo = __uint_as_float(l);
+}
+
+// X = N[P, S] as K-major split rows: Xh/Xl[b * KP + r], zero for r >= k_acc.
+// One warp per output row b.
+__global__ void __launch_bounds__(256) k_flush_split_x(Chain<float>* chains) {
+  const Chain<float>& c = chains[blockIdx.z];
+  const Dyn& d = *c.dyn;
+  if (d.status) return;
+  const int spin = blockIdx.y, nn = d.n_new, kacc = d.k_acc, KP = c.kp;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const float* Nb = c.N[d.buf][spin];
+  for (int b = warp; b < nn; b += nwarps) {
+    const long col = (long)c.S[b] * c.ld;
+    for (int r = lane; r < KP; r += 32) {
+      float hi = 0.f, lo = 0.f;
+      if (r < kacc) split_tf32(Nb[col + c.P[r]], hi, lo);
+      c.Xh[spin][(size_t)b * KP + r] = hi;
+      c.Xl[spin][(size_t)b * KP + r] = lo;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(128) k_flush_tc(Chain<float>* chains, const TcMaps* maps) {
+  const Chain<float>& c = chains[blockIdx.z];
+  Dyn& d = *c.dyn;
+  if (d.status) return;
+  const int spin = blockIdx.y;
+  const int nn = d.n_new, kacc = d.k_acc, ld = c.ld;
+  const int tiles = (nn + kTcBM - 1) / kTcBM;
+  if ((int)blockIdx.x >= tiles * tiles) return;
+  const int m0 = (blockIdx.x / tiles) * kTcBM, n0 = (blockIdx.x % tiles) * kTcBN;
+  const int nk = (kacc + kTcBK - 1) / kTcBK;
+  const float* Nb = c.N[d.buf][spin];
+  float* out = c.N[1 - d.buf][spin];
+  const int* S = c.S;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      ((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = reinterpret_cast<uint64_t*>(base + kTcStages * kStageBytes);
+  uint64_t* mdone = full + kTcStages;
+  uint64_t* accb = mdone + kTcStages;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accb + 1);
+  int* err_s = reinterpret_cast<int*>(tmem_slot + 1);
+
+  if (nk == 0) {  // no accepted change: the flush is a pure compaction
+    for (int e = threadIdx.x; e < kTcBM * kTcBN; e += blockDim.x) {
+      const int m = m0 + (e % kTcBM), n = n0 + (e / kTcBM);
+      if (m < nn && n < nn) out[(long)n * ld + m] = Nb[(long)S[n] * ld + S[m]];
+    }
+    return;
+  }
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kTcStages; ++s) {
+      mbar_init(smem_u32(full + s), 1);
+      mbar_init(smem_u32(mdone + s), 1);
+    }
+    mbar_init(smem_u32(accb), 1);
+    *err_s = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (threadIdx.x == 0) {
+    const TcMaps& mp = maps[blockIdx.z * 2 + spin];
+    int loads_issued = 0, loads_done = 0;
+    auto issue = [&](int kc) {
+      const int s = kc % kTcStages;
+      unsigned char* st = base + s * kStageBytes;
+      const uint32_t fb = smem_u32(full + s);
+      mbar_expect_tx(fb, kStageBytes);
+      tma_load_2d(smem_u32(st + 0 * kTileBytes), &mp.yh, kc * kTcBK, m0, fb);
+      tma_load_2d(smem_u32(st + 1 * kTileBytes), &mp.yl, kc * kTcBK, m0, fb);
+      tma_load_2d(smem_u32(st + 2 * kTileBytes), &mp.xh, kc * kTcBK, n0, fb);
+      tma_load_2d(smem_u32(st + 3 * kTileBytes), &mp.xl, kc * kTcBK, n0, fb);
+      ++loads_issued;
+    };
+    for (int kc = 0; kc < nk && kc < kTcStages; ++kc) issue(kc);
+    bool ok = true;
+    for (int kc = 0; kc < nk; ++kc) {
+      const int s = kc % kTcStages;
+      const uint32_t ph = (uint32_t)((kc / kTcStages) & 1);
+      if (!mbar_wait(smem_u32(full + s), ph)) {
+        ok = false;
+        break;
+      }
+      ++loads_done;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      unsigned char* st = base + s * kStageBytes;
+      const uint32_t ah = smem_u32(st), al = ah + kTileBytes, bh = ah + 2 * kTileBytes,
+                     bl = ah + 3 * kTileBytes;
+#pragma unroll
+      for (int kk = 0; kk < kTcBK / 8; ++kk) {
+        const uint32_t off = kk * 32;  // 8 tf32 = 32 bytes along K
+        const uint32_t first = (kc == 0 && kk == 0) ? 0u : 1u;
+        mma_tf32(tmem, smem_desc(ah + off), smem_desc(bl + off), first);  // hi * lo
+        mma_tf32(tmem, smem_desc(al + off), smem_desc(bh + off), 1u);     // lo * hi
+        mma_tf32(tmem, smem_desc(ah + off), smem_desc(bh + off), 1u);     // hi * hi
+      }
+      mma_commit(smem_u32(mdone + s));
+      if (kc + kTcStages < nk) {
+        if (!mbar_wait(smem_u32(mdone + s), ph)) {
+          ok = false;
+          break;
+        }
+        issue(kc + kTcStages);
+      }
+    }
+    if (!ok) {
+      *err_s = 1;
+      atomicOr(&d.status, DS_TIMEOUT);
+      // let the copies already issued land before the CTA releases its shared memory
+      for (int kc = loads_done; kc < loads_issued; ++kc)
+        mbar_wait(smem_u32(full + kc % kTcStages), (uint32_t)((kc / kTcStages) & 1));
+    }
+    mma_commit(smem_u32(accb));  // arrives when every MMA issued so far has completed
+  }
+  __syncthreads();
+  const bool acc_ok = mbar_wait(smem_u32(accb), 0);
+  // one decision for the whole CTA: tcgen05.ld is warp-collective
+  const bool all_ok = __syncthreads_and(acc_ok && *err_s == 0) != 0;
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (all_ok) {
+    const int m = m0 + warp * 32 + lane;
+    float v[32];
+#pragma unroll 1
+    for (int cc = 0; cc < kTcBN / 32; ++cc) {
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cc * 32), v);
+      if (m < nn) {
+        const long srow = S[m];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int n = n0 + cc * 32 + j;
+          if (n < nn) out[(long)n * ld + m] = Nb[(long)S[n] * ld + srow] - v[j];
+        }
+      }
+    }
+  } else if (threadIdx.x == 0) {
+    atomicOr(&d.status, DS_TIMEOUT);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(kTmemCols)
+                 : "memory");
+}
+
+int tc_smem_bytes() { return kTcStages * kStageBytes + 1024 + 256; }
+
+cudaError_t configure_flush_tc() {
+  return cudaFuncSetAttribute(k_flush_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              tc_smem_bytes());
+}
+
+void launch_flush_tc(Chain<float>* dchains, const TcMaps* maps, const LaunchShape& ls,
+                     cudaStream_t st) {
+  k_flush_split_x<<<dim3(ls.split_x_blocks, 2, ls.n_chains), 256, 0, st>>>(dchains);
+  k_flush_tc<<<dim3(ls.tc_tiles, 2, ls.n_chains), 128, tc_smem_bytes(), st>>>(dchains, maps);
+}
+
+// Host: the four TMA descriptors of one (chain, spin): K-major float32 buffers of
+// rows x kp, boxes of 128 rows x 32 float32 (128 bytes), 128-byte swizzle.
+cudaError_t encode_tc_maps(TcMaps* out, float* yh, float* yl, float* xh, float* xl, int rows,
+                           int kp) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                     cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)kp * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)kTcBK, (cuuint32_t)kTcBM};
+  const cuuint32_t estr[2] = {1, 1};
+  float* ptrs[4] = {yh, yl, xh, xl};
+  CUtensorMap* maps[4] = {&out->yh, &out->yl, &out->xh, &out->xl};
+  for (int i = 0; i < 4; ++i) {
+    const CUresult r = encode(maps[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, ptrs[i], dims, strides,
+                              box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace ctaux

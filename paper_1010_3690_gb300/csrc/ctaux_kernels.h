@@ -1,5 +1,6 @@
 // Host-side interface between the C ABI (ctaux_api.cu) and the kernels.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "ctaux_dev.cuh"
@@ -9,6 +10,14 @@ namespace ctaux {
 // Fixed launch shapes of one context (derived from capacities at init, so
 // that a sweep needs no host-side knowledge of the current orders).
 constexpr int kMeasChunk = 64;  // vertices per measurement evaluation chunk
+
+// tensor-core flush (mixed form): 128 x 128 output tiles, K chunks of 32 float32
+constexpr int kTcBM = 128, kTcBN = 128, kTcBK = 32, kTcStages = 2;
+
+// TMA descriptors of one (chain, spin): split Y (rows a) and split X (rows b)
+struct TcMaps {
+  CUtensorMap yh, yl, xh, xl;
+};
 
 enum { PH_RTILDE = 0, PH_GCOL_OLD = 1, PH_GCOL_NEW = 2, PH_FLUSH = 3, PH_MEAS = 4, PH_COUNT = 5 };
 
@@ -25,6 +34,9 @@ struct LaunchShape {
   int meas_lchunks;      // vertex chunks of the measurement evaluation
   int meas_cb_blocks;
   int refresh_grid;
+  int use_tc;            // mixed form: flush on the tensor cores
+  int tc_tiles;          // bound on 128 x 128 flush tiles per (chain, spin)
+  int split_x_blocks;
 };
 
 // CUDA-event timing of the sweep phases and kernel launch counts.  Phases:
@@ -75,7 +87,8 @@ struct PhaseTimer {
 };
 
 template <typename T>
-void launch_block(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t st, PhaseTimer* pt);
+void launch_block(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t st, PhaseTimer* pt,
+                  const TcMaps* maps);
 template <typename T>
 cudaError_t configure_block_kernels(const LaunchShape& ls);
 template <typename T>
@@ -89,6 +102,12 @@ cudaError_t launch_refresh(Chain<T>* dchains, const LaunchShape& ls, int only_ch
                            cudaStream_t st, PhaseTimer* pt);
 template <typename T>
 void launch_reset_measure(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t st);
+int tc_smem_bytes();
+cudaError_t configure_flush_tc();
+void launch_flush_tc(Chain<float>* dchains, const TcMaps* maps, const LaunchShape& ls,
+                     cudaStream_t st);
+cudaError_t encode_tc_maps(TcMaps* out, float* yh, float* yl, float* xh, float* xl, int rows,
+                           int kp);
 void launch_philox_test(uint64_t seed, uint32_t chain, int64_t t0, int count, int purpose,
                         double* out, cudaStream_t st);
 
