@@ -123,6 +123,19 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+def reduce_over_ranks(torch, dist, total_ms, accepted, device):
+    """Whole-job numbers: the slowest rank's timed milliseconds, the sum of accepted updates.
+
+    Chains are independent (each rank runs its own, with its own Philox chain ids), so
+    this is the only exchange between ranks.
+    """
+    t = torch.tensor([total_ms, float(accepted)], dtype=torch.float64, device=device)
+    tmax = t.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(t[1])
+
+
 def cpu_baseline(chains, meta, seconds=15.0):
     """The oracle as it stands, single process, on a bounded sample of the workload."""
     os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
@@ -193,7 +206,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--precision", choices=["both", "fp64", "mixed"], default="both")
     ap.add_argument("--workload", default="cube8")
     ap.add_argument("--K", type=float, default=256.0)
     ap.add_argument("--k-max", dest="k_max", type=int, default=64)
@@ -213,10 +226,34 @@ def main():
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-
     import paper_1010_3690_gb300 as pk
+
     chains, meta = workload(args.workload, args.K, args.k_max, chain_id=rank)
-    precision = pk.CTAUX_MIXED if args.precision == "mixed" else pk.CTAUX_FP64
+    forms = ["fp64", "mixed"] if args.precision == "both" else [args.precision]
+    results = {}
+    for form in forms:
+        results[form] = measure_form(args, pk, torch, dist, chains, form, local, world,
+                                     with_e2e=(form == forms[0]))
+    prim = results[forms[0]]
+    line = dict(prim["line"])
+    if len(forms) > 1:
+        sec = results[forms[1]]
+        line["mixed"] = {k: sec["line"][k] for k in ("value", "ms_per_step", "dtype", "roofline",
+                                                    "flush_roofline", "phase_ms_per_step",
+                                                    "drift_max_last_refresh", "near_ties",
+                                                    "gpu_launches", "clocks")}
+        line["mixed_vs_fp64"] = sec["line"]["value"] / prim["line"]["value"]
+        line["gpu_launches"] = prim["line"]["gpu_launches"] + sec["line"]["gpu_launches"]
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(chains, meta, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def measure_form(args, pk, torch, dist, chains, form, local, world, with_e2e):
+    precision = pk.CTAUX_MIXED if form == "mixed" else pk.CTAUX_FP64
     ctx = pk.Context(chains, precision=precision, refresh_every=REFRESH_EVERY,
                      n_tau_bins=N_TAU_BINS, n_anchors=N_ANCHORS, device=local)
     stream = torch.cuda.current_stream()
@@ -230,18 +267,20 @@ def main():
         return sum(sum(ctx.stats(i)["accepted"]) for i in range(len(chains)))
 
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    steps = args.steps
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     acc0 = accepted_total()
     work0 = ctx.work()
     ms0, kern0 = ctx.phase_times()
+    ties0 = sum(ctx.stats(i)["near_ties"] for i in range(len(chains)))
     ctx.set_profiling(True)
     clocks = ClockSampler(local)
     clocks.start()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    for i in range(args.steps):
+    for i in range(steps):
         flush.zero_()
         starts[i].record(stream)
         ctx.sweep(1, measure=True, stream=sh)
@@ -251,47 +290,50 @@ def main():
         dist.barrier()
     clk = clocks.stop()
     ctx.set_profiling(False)
-    total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    total_ms = sum(s_.elapsed_time(e_) for s_, e_ in zip(starts, ends))
     acc = accepted_total() - acc0
     ms1, kern1 = ctx.phase_times()
     work1 = ctx.work()
     phase_ms = ms1 - ms0
     kernels = int((kern1 - kern0).sum())
+    ties = sum(ctx.stats(i)["near_ties"] for i in range(len(chains))) - ties0
     if world > 1:
-        t = torch.tensor([total_ms, float(acc)], dtype=torch.float64, device="cuda")
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        total_ms, acc = float(tmax[0]), float(t[1])
+        total_ms, acc = reduce_over_ranks(torch, dist, total_ms, acc, "cuda")
     value = acc / (total_ms / 1e3)
 
-    # ---------------- roofline of the dominant kernel (CUDA events, live)
+    # ---------------- rooflines (live CUDA-event phase times, algorithmic work from the device)
     peaks, peak_kind = load_peaks()
     names = ctx.PHASES
-    dom = int(phase_ms.argmax())
-    steps = args.steps
     fp64_peak = peaks["bf16_tflops"] * NOMINAL["fp64"] / NOMINAL["bf16"]
-    fp32_simt_peak = 152 * 128 * 2 * 2.07e9 / 1e12     # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
-    prep_flop = work1["prep_flop"] - work0["prep_flop"]
-    flush_flop = work1["flush_flop"] - work0["flush_flop"]
-    flush_bytes = work1["flush_bytes"] - work0["flush_bytes"]
+    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12     # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
+    tf32x3_peak = peaks["bf16_tflops"] * NOMINAL["tf32"] / NOMINAL["bf16"] / 3.0
+    alu_peak = fp64_peak if precision == pk.CTAUX_FP64 else fp32_peak
+    alu_src = (f"FP64 = bf16 {peak_kind} x 1.25/2250" if precision == pk.CTAUX_FP64
+               else "FP32 = 152 SMs x 128 lanes x 2 x 2.07 GHz")
+    dw = {k: work1[k] - work0[k] for k in work1}
+    n_sm = min(152, len(chains))   # one CTA (one SM) per chain for the Gamma growth
+
     def roof(phase):
         sec = phase_ms[phase] / 1e3
-        if names[phase] == "flush_gemm":
-            if precision == pk.CTAUX_FP64:
-                return dict(bound="alu", achieved=flush_flop / sec / 1e12, peak=fp64_peak,
-                            unit="TFLOP/s", peak_source=f"FP64 = bf16 {peak_kind} x 1.25/2250")
-            return dict(bound="alu", achieved=flush_flop / sec / 1e12, peak=fp32_simt_peak,
-                        unit="TFLOP/s", peak_source="FP32 FMA lanes x max clock")
-        if names[phase] == "prep":
-            pk_ = fp64_peak if precision == pk.CTAUX_FP64 else fp32_simt_peak
-            return dict(bound="alu", achieved=prep_flop / sec / 1e12, peak=pk_, unit="TFLOP/s",
-                        peak_source="FP64 = bf16 x 1.25/2250" if precision == pk.CTAUX_FP64 else
-                        "FP32 FMA lanes x max clock")
-        # latency-bound phases: report bytes of N touched per block against HBM
-        nbytes = flush_bytes / 2.0
-        return dict(bound="hbm", achieved=nbytes / sec / 1e9, peak=peaks["hbm_gbs"], unit="GB/s",
-                    peak_source=f"hbm_gbs {peak_kind}")
+        nm = names[phase]
+        if nm == "flush_gemm":
+            if precision == pk.CTAUX_MIXED:
+                return dict(bound="tensor", achieved=dw["flush_flop"] / sec / 1e12, peak=tf32x3_peak,
+                            unit="TFLOP/s",
+                            peak_source=f"3xTF32 = bf16 {peak_kind} x 1100/2250 / 3 products")
+            return dict(bound="alu", achieved=dw["flush_flop"] / sec / 1e12, peak=alu_peak,
+                        unit="TFLOP/s", peak_source=alu_src)
+        if nm == "prep":
+            return dict(bound="alu", achieved=dw["prep_flop"] / sec / 1e12, peak=alu_peak,
+                        unit="TFLOP/s", peak_source=alu_src)
+        if nm == "proposals":
+            return dict(bound="alu", achieved=dw["gamma_flop"] / sec / 1e12,
+                        peak=alu_peak * n_sm / 152.0, unit="TFLOP/s",
+                        peak_source=alu_src + f", {n_sm} of 152 SMs (one CTA per chain)")
+        return dict(bound="hbm", achieved=dw["flush_bytes"] / 2.0 / sec / 1e9, peak=peaks["hbm_gbs"],
+                    unit="GB/s", peak_source=f"hbm_gbs {peak_kind}")
+
+    dom = int(phase_ms.argmax())
     r = roof(dom)
     roofline = {"kernel": names[dom], "bound": r["bound"], "achieved": r["achieved"],
                 "peak": r["peak"], "unit": r["unit"], "frac": r["achieved"] / r["peak"],
@@ -302,21 +344,22 @@ def main():
                   "unit": fr["unit"], "frac": fr["achieved"] / fr["peak"],
                   "ms_per_step": phase_ms[3] / steps, "peak_source": fr["peak_source"]}
 
-    # ---------------- end to end through the C ABI with host buffers
-    e2e_steps = max(5, min(args.steps, 50))
-    acc_e0 = accepted_total()
-    t_e2e = 0.0
-    d2h = 0
-    for _ in range(e2e_steps):
-        t0 = time.perf_counter()
-        ctx.sweep(1, measure=True, stream=sh)
-        G, E, nm = ctx.measure_G(0)
-        st = ctx.stats(0)
-        t_e2e += time.perf_counter() - t0
-        d2h = 2 * G.nbytes + 512   # sums and squares of G, plus the counters
-    acc_e = accepted_total() - acc_e0
-    e2e = {"value": acc_e / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 0,
-           "d2h_bytes_per_step": d2h}
+    e2e = None
+    if with_e2e:
+        e2e_steps = max(5, min(steps, 50))
+        acc_e0 = accepted_total()
+        t_e2e = 0.0
+        d2h = 0
+        for _ in range(e2e_steps):
+            t0 = time.perf_counter()
+            ctx.sweep(1, measure=True, stream=sh)
+            G, E, nm_ = ctx.measure_G(0)
+            ctx.stats(0)
+            t_e2e += time.perf_counter() - t0
+            d2h = 2 * G.nbytes + 512   # sums and squares of G(tau), plus the counters
+        acc_e = accepted_total() - acc_e0
+        e2e = {"value": acc_e / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 0,
+               "d2h_bytes_per_step": d2h}
 
     st = ctx.stats(0)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
@@ -327,7 +370,7 @@ def main():
             "config": {"workload": f"{chains[0].name} N_c={chains[0].n_c} beta={chains[0].beta} "
                                    f"U={chains[0].U} K={chains[0].K} k_max={chains[0].k_max}, "
                                    f"{len(chains)} chain(s) per GPU",
-                       "order_n": st["n"], "precision": args.precision,
+                       "order_n": st["n"], "precision": form,
                        "l2": "flushed between timed steps (512 MB write)",
                        "refresh_every": REFRESH_EVERY, "n_tau_bins": N_TAU_BINS,
                        "n_anchors": N_ANCHORS},
@@ -335,15 +378,14 @@ def main():
             "phase_ms_per_step": {names[i]: phase_ms[i] / steps for i in range(len(names))},
             "gpu_launches": kernels,
             "accept_rate": acc / max(1, steps * sum(c.k_max for c in chains) * world),
-            "drift_max_last_refresh": st["last_drift_max"],
-            "clocks": clk, "e2e": e2e}
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(chains, meta, args.cpu_seconds)
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+            "drift_max_last_refresh": st["last_drift_max"], "near_ties": ties,
+            "clocks": clk}
+    if e2e is not None:
+        line["e2e"] = e2e
     ctx.close()
-    if world > 1:
-        dist.destroy_process_group()
+    del flush
+    torch.cuda.empty_cache()
+    return {"line": line}
 
 
 if __name__ == "__main__":

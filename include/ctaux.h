@@ -186,10 +186,11 @@ ctaux_status ctaux_set_profiling(ctaux_ctx *ctx, int on);
 ctaux_status ctaux_get_phase_times(ctaux_ctx *ctx, double *ms_out, int64_t *kernels_out);
 
 /* Algorithmic work of the blocks run so far, summed over chains (for
- * rooflines): flop counts of prep and flush products, bytes of N read and
- * written by the flush. */
+ * rooflines): flop counts of the prep products, the flush products and the
+ * Gamma growth (both spins), bytes of N read and written by the flush.  Any
+ * output may be NULL. */
 ctaux_status ctaux_get_work(ctaux_ctx *ctx, double *prep_flop, double *flush_flop,
-                            double *flush_bytes);
+                            double *flush_bytes, double *gamma_flop);
 
 /* Philox-4x32-10 on the device: for counters (t0 + i, chain, purpose), i <
  * count, write the two 53-bit uniforms of each draw to out[2*i], out[2*i+1].

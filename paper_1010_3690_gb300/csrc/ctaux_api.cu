@@ -231,9 +231,11 @@ ctaux_status build_chains(ctaux_ctx* ctx) {
     }
     c.P = dalloc<int>(ctx, K, &err);
     c.S = dalloc<int>(ctx, ld, &err);
-    c.work = dalloc<double>(ctx, (size_t)2 * 2 * ld * ld, &err);
+    c.work = dalloc<double>(ctx, refresh_work_doubles((int)ld), &err);
     c.perm = dalloc<int>(ctx, 2 * ld, &err);
     c.used = dalloc<int8_t>(ctx, 2 * ld, &err);
+    c.pcol = dalloc<int>(ctx, 2 * ld, &err);
+    if (c.pcol) CUDA_TRY(ctx, cudaMemset(c.pcol, 0xFF, 2 * ld * sizeof(int)));
     c.pkeys = dalloc<unsigned long long>(ctx, 2 * ld, &err);
     c.work_drift = dalloc<double>(ctx, 2, &err);
     c.work_logdet = dalloc<double>(ctx, 2, &err);
@@ -611,9 +613,10 @@ ctaux_status ctaux_get_phase_times(ctaux_ctx* ctx, double* ms_out, int64_t* kern
   return CTAUX_OK;
 }
 
-ctaux_status ctaux_get_work(ctaux_ctx* ctx, double* prep_flop, double* flush_flop, double* flush_bytes) {
+ctaux_status ctaux_get_work(ctaux_ctx* ctx, double* prep_flop, double* flush_flop, double* flush_bytes,
+                            double* gamma_flop) {
   if (!ctx) return CTAUX_EINVAL;
-  double a = 0.0, b = 0.0, c = 0.0;
+  double a = 0.0, b = 0.0, c = 0.0, g = 0.0;
   for (size_t ci = 0; ci < ctx->chains.size(); ++ci) {
     Dyn d;
     ctaux_status r = read_dyn(ctx, (int)ci, &d);
@@ -621,7 +624,9 @@ ctaux_status ctaux_get_work(ctaux_ctx* ctx, double* prep_flop, double* flush_flo
     a += d.work_prep;
     b += d.work_flush;
     c += d.bytes_flush;
+    g += d.work_gamma;
   }
+  if (gamma_flop) *gamma_flop = g;
   if (prep_flop) *prep_flop = a;
   if (flush_flop) *flush_flop = b;
   if (flush_bytes) *flush_bytes = c;

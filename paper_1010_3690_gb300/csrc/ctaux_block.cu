@@ -408,6 +408,7 @@ __global__ void __launch_bounds__(256) k_proposals(Chain<T>* chains, int gamma_i
   __shared__ int jP;
   __shared__ int n_cur, sign_s;
   __shared__ long long cnt_prop[3], cnt_acc[3], numeric, ties;
+  __shared__ double flops;
 
   for (int i = tid; i < m; i += 256) pmap[i] = -1;
   for (int w = tid; w < n_words; w += 256) {
@@ -425,6 +426,7 @@ __global__ void __launch_bounds__(256) k_proposals(Chain<T>* chains, int gamma_i
     for (int q = 0; q < 3; ++q) cnt_prop[q] = cnt_acc[q] = 0;
     numeric = 0;
     ties = 0;
+    flops = 0.0;
   }
   __syncthreads();
 
@@ -533,6 +535,12 @@ __global__ void __launch_bounds__(256) k_proposals(Chain<T>* chains, int gamma_i
     if (!finite) accept = false;
     if (tid == 0) {
       cnt_prop[move]++;
+      // algorithmic flops, both spins: y and z GEMVs and the dot (first touch),
+      // bordered or rank-one update of Gamma^{-1} (accept)
+      const double jd = (double)j;
+      double fl = (q < 0) ? (4.0 * jd * jd + 2.0 * jd) : 4.0;
+      if (accept) fl += (q < 0) ? 3.0 * (jd + 1.0) * (jd + 1.0) : 3.0 * jd * jd;
+      flops += 2.0 * fl;
       if (!finite) numeric++;
       if (sizeof(T) == 4 && finite && fabs(dr.u_acc - pacc) < kTieGuard * fmax(dr.u_acc, pacc)) ties++;
       if (c.trace_cap > 0) {
@@ -642,6 +650,7 @@ __global__ void __launch_bounds__(256) k_proposals(Chain<T>* chains, int gamma_i
     }
     d.numeric_rejects += numeric;
     d.near_ties += ties;
+    d.work_gamma += flops;
     if (c.trace_cap > 0) d.trace_written += KM;
   }
 }

@@ -61,6 +61,7 @@ struct Dyn {
   double work_prep;       // algorithmic flops of the prep products (both spins)
   double work_flush;      // algorithmic flops of the flush products
   double bytes_flush;     // algorithmic bytes of the flush (N read + N' written)
+  double work_gamma;      // algorithmic flops of the Gamma growth (both spins)
 };
 
 template <typename T>
@@ -101,9 +102,10 @@ struct Chain {
   float* Xl[2];
   T* kpart[2];               // split-K partial tiles
   int* ticket[2];            // split-K arrival counters per output tile
-  double* work;              // refresh: [spin][2][ld][ld] float64 ping-pong
+  double* work;              // refresh: per spin X (ld x ld), two panels, pivot rows (float64)
   int* perm;                 // refresh pivot rows [spin][ld]
   int8_t* used;              // refresh pivot flags [spin][ld]
+  int* pcol;                 // refresh: column at which a row was pivoted, -1 if not [spin][ld]
   unsigned long long* pkeys; // refresh pivot keys [spin][ld]
   double* work_drift;        // refresh: max, sum of squares
   double* work_logdet;       // refresh: [spin]

@@ -8,10 +8,12 @@
 // Operands are K-major split buffers written by the flush preparation kernels
 // (Yh/Yl: rows a, Xh/Xl: rows b, KP = k_max rounded up to 32 float32 per row,
 // zero beyond k_acc), loaded by TMA into 128-byte-swizzled shared memory
-// (one TMA load per 128 x 32 tile, no multicast).  One CTA of 128 threads per
-// 128 x 128 output tile: thread 0 issues the TMA loads and the MMAs, all four
-// warps read the accumulator back with tcgen05.ld and write the compacted
-// result.  Every mbarrier wait is bounded; on timeout the chain's status gets
+// (one TMA load per 128 x 32 tile, no multicast).  One CTA of 256 threads per
+// 128 x 128 output tile, one 64 KB stage so that three CTAs share an SM:
+// thread 0 issues the TMA loads and the MMAs; in the epilogue warps w and
+// w + 4 read TMEM lane quarter w (columns 0-63 and 64-127), with the 32
+// gathered inputs N[S_m][S_n] of each column chunk loaded before the
+// accumulator.  Every mbarrier wait is bounded; on timeout the chain's status gets
 // DS_TIMEOUT, the CTA waits (bounded) for its copies in flight, frees its TMEM
 // and returns.
 #include <cuda.h>
@@ -141,7 +143,7 @@ __global__ void __launch_bounds__(256) k_flush_split_x(Chain<float>* chains) {
   }
 }
 
-__global__ void __launch_bounds__(128) k_flush_tc(Chain<float>* chains, const TcMaps* maps) {
+__global__ void __launch_bounds__(kTcThreads) k_flush_tc(Chain<float>* chains, const TcMaps* maps) {
   const Chain<float>& c = chains[blockIdx.z];
   Dyn& d = *c.dyn;
   if (d.status) return;
@@ -164,11 +166,14 @@ __global__ void __launch_bounds__(128) k_flush_tc(Chain<float>* chains, const Tc
   uint64_t* accb = mdone + kTcStages;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accb + 1);
   int* err_s = reinterpret_cast<int*>(tmem_slot + 1);
+  int* Scol = err_s + 1;  // S[n0 .. n0 + 127]
+  for (int e = threadIdx.x; e < kTcBN; e += blockDim.x) Scol[e] = (n0 + e < nn) ? S[n0 + e] : 0;
 
   if (nk == 0) {  // no accepted change: the flush is a pure compaction
+    __syncthreads();
     for (int e = threadIdx.x; e < kTcBM * kTcBN; e += blockDim.x) {
       const int m = m0 + (e % kTcBM), n = n0 + (e / kTcBM);
-      if (m < nn && n < nn) out[(long)n * ld + m] = Nb[(long)S[n] * ld + S[m]];
+      if (m < nn && n < nn) out[(long)n * ld + m] = Nb[(long)Scol[n - n0] * ld + S[m]];
     }
     return;
   }
@@ -255,17 +260,25 @@ __global__ void __launch_bounds__(128) k_flush_tc(Chain<float>* chains, const Tc
   const bool all_ok = __syncthreads_and(acc_ok && *err_s == 0) != 0;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (all_ok) {
-    const int m = m0 + warp * 32 + lane;
-    float v[32];
+    const int quarter = warp & 3, colhalf = warp >> 2;
+    const int m = m0 + quarter * 32 + lane;
+    const bool row_ok = m < nn;
+    const long srow = row_ok ? S[m] : 0;
+    float v[32], cin[32];
 #pragma unroll 1
-    for (int cc = 0; cc < kTcBN / 32; ++cc) {
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cc * 32), v);
-      if (m < nn) {
-        const long srow = S[m];
+    for (int cc = colhalf * 2; cc < colhalf * 2 + 2; ++cc) {
+      // the 32 gathered inputs of this chunk: independent loads, issued first
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int n = n0 + cc * 32 + j;
+        cin[j] = (row_ok && n < nn) ? Nb[(long)Scol[cc * 32 + j] * ld + srow] : 0.f;
+      }
+      tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(cc * 32), v);
+      if (row_ok) {
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const int n = n0 + cc * 32 + j;
-          if (n < nn) out[(long)n * ld + m] = Nb[(long)S[n] * ld + srow] - v[j];
+          if (n < nn) out[(long)n * ld + m] = cin[j] - v[j];
         }
       }
     }
@@ -280,7 +293,7 @@ __global__ void __launch_bounds__(128) k_flush_tc(Chain<float>* chains, const Tc
                  : "memory");
 }
 
-int tc_smem_bytes() { return kTcStages * kStageBytes + 1024 + 256; }
+int tc_smem_bytes() { return kTcStages * kStageBytes + 1024 + 1024; }
 
 cudaError_t configure_flush_tc() {
   return cudaFuncSetAttribute(k_flush_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -290,7 +303,7 @@ cudaError_t configure_flush_tc() {
 void launch_flush_tc(Chain<float>* dchains, const TcMaps* maps, const LaunchShape& ls,
                      cudaStream_t st) {
   k_flush_split_x<<<dim3(ls.split_x_blocks, 2, ls.n_chains), 256, 0, st>>>(dchains);
-  k_flush_tc<<<dim3(ls.tc_tiles, 2, ls.n_chains), 128, tc_smem_bytes(), st>>>(dchains, maps);
+  k_flush_tc<<<dim3(ls.tc_tiles, 2, ls.n_chains), kTcThreads, tc_smem_bytes(), st>>>(dchains, maps);
 }
 
 // Host: the four TMA descriptors of one (chain, spin): K-major float32 buffers of

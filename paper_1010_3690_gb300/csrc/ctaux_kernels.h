@@ -12,7 +12,7 @@ namespace ctaux {
 constexpr int kMeasChunk = 64;  // vertices per measurement evaluation chunk
 
 // tensor-core flush (mixed form): 128 x 128 output tiles, K chunks of 32 float32
-constexpr int kTcBM = 128, kTcBN = 128, kTcBK = 32, kTcStages = 2;
+constexpr int kTcBM = 128, kTcBN = 128, kTcBK = 32, kTcStages = 1, kTcThreads = 256;
 
 // TMA descriptors of one (chain, spin): split Y (rows a) and split X (rows b)
 struct TcMaps {
@@ -95,6 +95,7 @@ template <typename T>
 void launch_gemm(Chain<T>* dchains, const LaunchShape& ls, int phase, cudaStream_t st);
 template <typename T>
 int refresh_blocks_per_sm();
+size_t refresh_work_doubles(int ld);
 template <typename T>
 void launch_measure(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t st, PhaseTimer* pt);
 template <typename T>

@@ -1,18 +1,21 @@
 // From-scratch FP64 recomputation of N for every chain: build
 // N^{-1} = e^V - G0 (e^V - 1) (Eq. Nmatrix) from the configuration, invert
-// by Gauss-Jordan with partial pivoting, report the drift of the running N
-// and replace it.  One cooperative launch: the column steps of all chains
-// and spins run in lockstep, separated by grid-wide barriers (no spin waits).
+// by blocked Gauss-Jordan with partial pivoting, report the drift of the
+// running N and replace it.  One cooperative launch: all chains and spins
+// advance in lockstep, separated by grid-wide barriers (no spin waits).
 //
-// Column step c reads matrix X and writes Y (ping-pong), with pivot row pr:
-//   Y[pr][j] = X[pr][j] / X[pr][c]            (j != c),  Y[pr][c] = 1 / X[pr][c]
-//   Y[i][j]  = X[i][j] - X[i][c] X[pr][j] / X[pr][c]   (i != pr, j != c)
-//   Y[i][c]  = -X[i][c] / X[pr][c]                      (i != pr)
-// After m steps with pivot rows perm[c], N[c][perm[j]] = X[perm[c]][j] and
-// det N^{-1} = sign(perm) prod_c X_c[perm[c]][c].
-// The pivot of the next column is found while a step writes it: each CTA
-// folds max |Y[i][c+1]| over not-yet-pivoted rows into one 64-bit key per
-// (chain, spin, step) with atomicMax (float magnitude, ties to the lower row).
+// Unblocked column step c (pivot row pr) maps X to
+//   X[pr][j] / X[pr][c] (j != c), 1 / X[pr][c] at (pr, c),
+//   -X[i][c] / X[pr][c] at (i, c), X[i][j] - X[i][c] X[pr][j] / X[pr][c] elsewhere.
+// Blocked: for a panel C of 32 columns with pivot rows R, the column steps are
+// applied to the panel alone (a copy, ping-pong), giving P' = X'[:, C]; every
+// other column then follows in one rank-32 product
+//   X'[:, J] = Z[:, J] + P' X[R, J],  Z = X with the rows R set to zero.
+// After all panels, N[c][perm[j]] = X[perm[c]][j] and
+// log|det N^{-1}| = sum_c log|pivot_c|.
+// Pivots: the largest |value| over rows not yet pivoted, folded while the
+// previous step writes that column: atomicMax of a 64-bit key (float
+// magnitude, ties to the lower row) per (chain, spin, column).
 #include <cooperative_groups.h>
 
 #include "ctaux_dev.cuh"
@@ -30,15 +33,24 @@ __device__ __forceinline__ int key_row(unsigned long long k) {
   return (int)(0xffffffffu - (unsigned)(k & 0xffffffffull));
 }
 
+constexpr int kPB = 32;  // panel width
+
+// per-spin work area: X (ld x ld), two panel buffers (ld x kPB), pivot rows (ld x kPB)
+__host__ __device__ inline size_t refresh_work_per_spin(int ld) {
+  return (size_t)ld * ld + (size_t)3 * kPB * ld;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_refresh(Chain<T>* chains, int n_chains, int only_chain) {
   cg::grid_group grid = cg::this_grid();
-  const long gtid = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long gthreads = (long)gridDim.x * blockDim.x;
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int gthreads = gridDim.x * blockDim.x;
   const int c_lo = only_chain >= 0 ? only_chain : 0;
   const int c_hi = only_chain >= 0 ? only_chain + 1 : n_chains;
+  __shared__ double Ps[32][kPB + 1];
+  __shared__ double Rs[kPB][33];
 
-  // ---- stage 1: N^{-1} of the current configuration into work[0]; pivot of column 0
+  // ---- stage 1: N^{-1} of the current configuration into X; pivot of column 0
   int max_m = 0;
   for (int ci = c_lo; ci < c_hi; ++ci) {
     const Chain<T>& c = chains[ci];
@@ -48,57 +60,151 @@ __global__ void __launch_bounds__(256) k_refresh(Chain<T>* chains, int n_chains,
     max_m = max(max_m, m);
     if (gtid == 0) c.work_logdet[0] = c.work_logdet[1] = 0.0;
     for (int spin = 0; spin < 2; ++spin) {
-      double* X = c.work + (size_t)spin * 2 * ld * ld;
+      double* X = c.work + (size_t)spin * refresh_work_per_spin(ld);
       unsigned long long* keys = c.pkeys + (size_t)spin * ld;
-      int8_t* used = c.used + spin * ld;
-      for (long e = gtid; e < (long)m * m; e += gthreads) {
-        const int i = (int)(e % m), j = (int)(e / m);
+      for (int j = blockIdx.x; j < m; j += gridDim.x) {
         const double evj = c.ev[spin][c.s[buf][j] + 2];
-        double v = -g0_eval(c, spin, c.tau[buf][i], c.site[buf][i], c.tau[buf][j], c.site[buf][j]) *
-                   (evj - 1.0);
-        if (i == j) v += evj;
-        X[(size_t)j * ld + i] = v;
-        if (j == 0) atomicMax(keys, pivot_key(v, i));
+        const double tj = c.tau[buf][j];
+        const int sj = c.site[buf][j];
+        for (int i = threadIdx.x; i < m; i += blockDim.x) {
+          double v = -g0_eval(c, spin, c.tau[buf][i], c.site[buf][i], tj, sj) * (evj - 1.0);
+          if (i == j) v += evj;
+          X[(size_t)j * ld + i] = v;
+          if (j == 0) atomicMax(keys, pivot_key(v, i));
+        }
       }
     }
   }
   grid.sync();
 
-  // ---- stage 2: m Gauss-Jordan column steps
-  for (int col = 0; col < max_m; ++col) {
+  // ---- stage 2: panels
+  for (int c0 = 0; c0 < max_m; c0 += kPB) {
+    // A0: copy the panel columns
     for (int ci = c_lo; ci < c_hi; ++ci) {
       const Chain<T>& c = chains[ci];
       const Dyn& d = *c.dyn;
       if (d.status & ~DS_SINGULAR) continue;
       const int m = d.n, ld = c.ld;
-      if (col >= m) continue;
+      if (c0 >= m) continue;
+      const int bw = min(kPB, m - c0);
       for (int spin = 0; spin < 2; ++spin) {
-        const double* X = c.work + (size_t)spin * 2 * ld * ld + (size_t)(col & 1) * ld * ld;
-        double* Y = c.work + (size_t)spin * 2 * ld * ld + (size_t)((col + 1) & 1) * ld * ld;
-        unsigned long long* keys = c.pkeys + (size_t)spin * ld;
-        int8_t* used = c.used + spin * ld;
-        const int pr = key_row(keys[col]);
-        const double piv = X[(size_t)col * ld + pr];
-        if (gtid == 0) {
-          c.perm[spin * ld + col] = pr;
-          used[pr] = 1;
-          if (!(fabs(piv) > 0.0) || !isfinite(piv)) atomicOr(&c.dyn->status, DS_SINGULAR);
-          c.work_logdet[spin] += log(fabs(piv));
+        const double* X = c.work + (size_t)spin * refresh_work_per_spin(ld);
+        double* Pa = const_cast<double*>(X) + (size_t)ld * ld;
+        for (int e = gtid; e < m * bw; e += gthreads) {
+          const int i = e % m, k = e / m;
+          Pa[(size_t)k * ld + i] = X[(size_t)(c0 + k) * ld + i];
         }
-        const double ipiv = 1.0 / piv;
-        // columns over CTAs, rows over threads
-        for (int j = blockIdx.x; j < m; j += gridDim.x) {
-          const double xpj = X[(size_t)j * ld + pr] * ipiv;
-          const double* Xj = X + (size_t)j * ld;
-          const double* Xc = X + (size_t)col * ld;
-          double* Yj = Y + (size_t)j * ld;
-          for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      }
+    }
+    grid.sync();
+    // A1: the column steps, on the panel only
+    for (int k = 0; k < kPB; ++k) {
+      for (int ci = c_lo; ci < c_hi; ++ci) {
+        const Chain<T>& c = chains[ci];
+        const Dyn& d = *c.dyn;
+        if (d.status & ~DS_SINGULAR) continue;
+        const int m = d.n, ld = c.ld;
+        if (c0 + k >= m) continue;
+        const int bw = min(kPB, m - c0), col = c0 + k;
+        for (int spin = 0; spin < 2; ++spin) {
+          double* X = c.work + (size_t)spin * refresh_work_per_spin(ld);
+          double* Pa = X + (size_t)ld * ld;
+          double* Pb = Pa + (size_t)kPB * ld;
+          const double* src = (k & 1) ? Pb : Pa;
+          double* dst = (k & 1) ? Pa : Pb;
+          unsigned long long* keys = c.pkeys + (size_t)spin * ld;
+          int8_t* used = c.used + spin * ld;
+          const int pr = key_row(keys[col]);
+          const double piv = src[(size_t)k * ld + pr];
+          if (gtid == 0) {
+            c.perm[spin * ld + col] = pr;
+            used[pr] = 1;
+            c.pcol[spin * ld + pr] = col;
+            if (!(fabs(piv) > 0.0) || !isfinite(piv)) atomicOr(&c.dyn->status, DS_SINGULAR);
+            c.work_logdet[spin] += log(fabs(piv));
+          }
+          const double ipiv = 1.0 / piv;
+          // one (row, panel column) pair per thread
+          for (int e = gtid; e < m * bw; e += gthreads) {
+            const int i = e % m, kk = e / m;
+            const double xic = src[(size_t)k * ld + i];
             double v;
-            if (i == pr) v = (j == col) ? ipiv : xpj;
-            else if (j == col) v = -Xc[i] * ipiv;
-            else v = Xj[i] - Xc[i] * xpj;
-            Yj[i] = v;
-            if (j == col + 1 && i != pr && !used[i]) atomicMax(keys + col + 1, pivot_key(v, i));
+            if (i == pr) v = (kk == k) ? ipiv : src[(size_t)kk * ld + pr] * ipiv;
+            else if (kk == k) v = -xic * ipiv;
+            else v = src[(size_t)kk * ld + i] - xic * (src[(size_t)kk * ld + pr] * ipiv);
+            dst[(size_t)kk * ld + i] = v;
+            if (kk == k + 1 && i != pr && !used[i]) atomicMax(keys + col + 1, pivot_key(v, i));
+          }
+        }
+      }
+      grid.sync();
+    }
+    // B0: pivot rows of this panel, outside it, from X before the update: Rr[j][k] = X[R_k][j]
+    for (int ci = c_lo; ci < c_hi; ++ci) {
+      const Chain<T>& c = chains[ci];
+      const Dyn& d = *c.dyn;
+      if (d.status & ~DS_SINGULAR) continue;
+      const int m = d.n, ld = c.ld;
+      if (c0 >= m) continue;
+      const int bw = min(kPB, m - c0);
+      for (int spin = 0; spin < 2; ++spin) {
+        const double* X = c.work + (size_t)spin * refresh_work_per_spin(ld);
+        double* Rr = const_cast<double*>(X) + (size_t)ld * ld + (size_t)2 * kPB * ld;
+        const int* perm = c.perm + spin * ld;
+        for (int e = gtid; e < m * kPB; e += gthreads) {
+          const int k = e % kPB, j = e / kPB;
+          Rr[(size_t)j * kPB + k] = (k < bw) ? X[(size_t)j * ld + perm[c0 + k]] : 0.0;
+        }
+      }
+    }
+    grid.sync();
+    // B1: trailing rank-bw update in 32 x 32 tiles, panel written back,
+    // pivot key of the next panel's first column
+    for (int ci = c_lo; ci < c_hi; ++ci) {
+      const Chain<T>& c = chains[ci];
+      const Dyn& d = *c.dyn;
+      if (d.status & ~DS_SINGULAR) continue;
+      const int m = d.n, ld = c.ld;
+      if (c0 >= m) continue;
+      const int bw = min(kPB, m - c0), cn = c0 + bw;
+      const int tb = (m + 31) / 32;
+      for (int spin = 0; spin < 2; ++spin) {
+        double* X = c.work + (size_t)spin * refresh_work_per_spin(ld);
+        double* Pa = X + (size_t)ld * ld;
+        const double* Pf = (bw & 1) ? Pa + (size_t)kPB * ld : Pa;  // panel after bw steps
+        const double* Rr = Pa + (size_t)2 * kPB * ld;
+        unsigned long long* keys = c.pkeys + (size_t)spin * ld;
+        const int8_t* used = c.used + spin * ld;
+        const int* pcol = c.pcol + spin * ld;
+        for (int tile = blockIdx.x; tile < tb * tb; tile += gridDim.x) {
+          const int i0 = (tile % tb) * 32, j0 = (tile / tb) * 32;
+          __syncthreads();
+          for (int e = threadIdx.x; e < 32 * kPB; e += blockDim.x) {
+            const int r = e % 32, k = e / 32;
+            Ps[r][k] = (i0 + r < m && k < bw) ? Pf[(size_t)k * ld + i0 + r] : 0.0;
+            const int jj = e % 32, kk = e / 32;
+            Rs[kk][jj] = (j0 + jj < m) ? Rr[(size_t)(j0 + jj) * kPB + kk] : 0.0;
+          }
+          __syncthreads();
+          const int r = threadIdx.x % 32, i = i0 + r;
+          if (i < m) {
+            const int pci = pcol[i];
+            const bool in_R = pci >= c0 && pci < cn;
+            for (int q = threadIdx.x / 32; q < 32; q += blockDim.x / 32) {
+              const int j = j0 + q;
+              if (j >= m) continue;
+              double v;
+              if (j >= c0 && j < cn) {
+                v = Ps[r][j - c0];
+              } else {
+                double acc = in_R ? 0.0 : X[(size_t)j * ld + i];
+#pragma unroll 8
+                for (int k = 0; k < kPB; ++k) acc += Ps[r][k] * Rs[k][q];
+                v = acc;
+              }
+              X[(size_t)j * ld + i] = v;
+              if (j == cn && !used[i]) atomicMax(keys + cn, pivot_key(v, i));
+            }
           }
         }
       }
@@ -114,24 +220,27 @@ __global__ void __launch_bounds__(256) k_refresh(Chain<T>* chains, int n_chains,
     if (d.status & ~DS_SINGULAR) continue;
     const int m = d.n, ld = c.ld, buf = d.buf;
     for (int spin = 0; spin < 2; ++spin) {
-      const double* X = c.work + (size_t)spin * 2 * ld * ld + (size_t)(m & 1) * ld * ld;
+      const double* X = c.work + (size_t)spin * refresh_work_per_spin(ld);
       const int* perm = c.perm + spin * ld;
       T* Nr = c.N[buf][spin];
-      for (long e = gtid; e < (long)m * m; e += gthreads) {
-        const int cc = (int)(e % m), j = (int)(e / m);
-        const double v = X[(size_t)j * ld + perm[cc]];  // N[cc][perm[j]]
-        const long o = (long)perm[j] * ld + cc;
-        const double diff = fabs((double)Nr[o] - v);
-        if (diff > 0.0) {
-          atomicMax(reinterpret_cast<unsigned long long*>(&c.work_drift[0]),
-                    (unsigned long long)__double_as_longlong(diff));
-          atomicAdd(&c.work_drift[1], diff * diff);
+      for (int j = blockIdx.x; j < m; j += gridDim.x) {
+        const int pj = perm[j];
+        for (int cc = threadIdx.x; cc < m; cc += blockDim.x) {
+          const double v = X[(size_t)j * ld + perm[cc]];  // N[cc][perm[j]]
+          const long o = (long)pj * ld + cc;
+          const double diff = fabs((double)Nr[o] - v);
+          if (diff > 0.0) {
+            atomicMax(reinterpret_cast<unsigned long long*>(&c.work_drift[0]),
+                      (unsigned long long)__double_as_longlong(diff));
+            atomicAdd(&c.work_drift[1], diff * diff);
+          }
+          Nr[o] = (T)v;
         }
-        Nr[o] = (T)v;
       }
-      for (long e = gtid; e < m; e += gthreads) {
+      for (int e = gtid; e < m; e += gthreads) {
         c.pkeys[(size_t)spin * ld + e] = 0ull;
         c.used[spin * ld + e] = 0;
+        c.pcol[spin * ld + e] = -1;
       }
     }
   }
@@ -184,6 +293,8 @@ template cudaError_t launch_refresh<double>(Chain<double>*, const LaunchShape&, 
                                             PhaseTimer*);
 template cudaError_t launch_refresh<float>(Chain<float>*, const LaunchShape&, int, cudaStream_t,
                                            PhaseTimer*);
+size_t refresh_work_doubles(int ld) { return 2 * refresh_work_per_spin(ld); }
+
 template int refresh_blocks_per_sm<double>();
 template int refresh_blocks_per_sm<float>();
 

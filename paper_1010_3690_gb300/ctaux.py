@@ -88,7 +88,8 @@ def _load():
         "ctaux_get_N": (C.c_int, [vp, C.c_int, C.c_int, P(C.c_double), C.c_int, P(C.c_int)]),
         "ctaux_set_profiling": (C.c_int, [vp, C.c_int]),
         "ctaux_get_phase_times": (C.c_int, [vp, P(C.c_double), P(C.c_int64)]),
-        "ctaux_get_work": (C.c_int, [vp, P(C.c_double), P(C.c_double), P(C.c_double)]),
+        "ctaux_get_work": (C.c_int, [vp, P(C.c_double), P(C.c_double), P(C.c_double),
+                                     P(C.c_double)]),
         "ctaux_philox_uniforms": (C.c_int, [C.c_uint64, C.c_uint32, C.c_int64, C.c_int, C.c_int,
                                             P(C.c_double)]),
         "ctaux_synchronize": (C.c_int, [vp]),
@@ -274,6 +275,8 @@ class Context:
         return ms, ln
 
     def work(self):
-        a, b, c = C.c_double(), C.c_double(), C.c_double()
-        self._check(lib.ctaux_get_work(self.h, C.byref(a), C.byref(b), C.byref(c)), "get_work")
-        return dict(prep_flop=a.value, flush_flop=b.value, flush_bytes=c.value)
+        a, b, c, g = C.c_double(), C.c_double(), C.c_double(), C.c_double()
+        self._check(lib.ctaux_get_work(self.h, C.byref(a), C.byref(b), C.byref(c), C.byref(g)),
+                    "get_work")
+        return dict(prep_flop=a.value, flush_flop=b.value, flush_bytes=c.value,
+                    gamma_flop=g.value)
