@@ -124,6 +124,13 @@ ctaux_status build_chains(ctaux_ctx* ctx) {
     const size_t te = sizeof(T) == 8 ? 32 : 64;
     if (ks > 1) kpart_elems = std::max(kpart_elems, (size_t)ls.tiles[ph] * ks * te * te);
   }
+  ls.kstride = *std::max_element(ls.ksplit, ls.ksplit + PH_COUNT);
+  kpart_elems = 0;
+  for (int ph = 0; ph < PH_COUNT; ++ph) {
+    const size_t te = sizeof(T) == 8 ? 32 : 64;
+    if (ls.ksplit[ph] > 1) kpart_elems = std::max(kpart_elems, (size_t)ls.tiles[ph] * ls.kstride * te * te);
+  }
+  ls.persist_ctas = 8 * ctx->sm_count;   // 256-thread CTAs: up to 8 resident per SM
   ls.gather_slices = std::max(1, std::min(64, (2 * ctx->sm_count + items - 1) / items));
   ls.y_blocks = (max_ld + 15) / 16;
   ls.meas_point_blocks = (max_pts + 255) / 256;
@@ -142,11 +149,17 @@ ctaux_status build_chains(ctaux_ctx* ctx) {
   int max_rows = 128;
   for (const auto& cp : ctx->chains) max_rows = std::max(max_rows, round_up(cp.capacity + cp.k_max, 128));
   ls.tc_tiles = (max_rows / 128) * (max_rows / 128);
+  ls.tc_ctas = 2 * ctx->sm_count;
   ls.split_x_blocks = std::max(1, std::min(256, (max_rows + 7) / 8));
   if (mixed_tc) CUDA_TRY(ctx, configure_flush_tc());
   std::vector<TcMaps> host_maps(mixed_tc ? 2 * ctx->chains.size() : 0);
   int nb = refresh_blocks_per_sm<T>();
   ls.refresh_grid = std::max(1, nb) * ctx->sm_count;
+  // many chains: one CTA per (chain, spin) (panel of 16 columns in shared memory);
+  // few chains: the cooperative whole-GPU refresh
+  ls.refresh_cta_smem = (int)(16 * sizeof(double) * (size_t)max_ld);
+  ls.refresh_per_cta = (ctx->chains.size() >= 16 && ls.refresh_cta_smem <= 200 * 1024) ? 1 : 0;
+  if (ls.refresh_per_cta) CUDA_TRY(ctx, configure_refresh_cta<T>(ls.refresh_cta_smem));
 
   for (size_t ci = 0; ci < ctx->chains.size(); ++ci) {
     const ctaux_chain_params& cp = ctx->chains[ci];

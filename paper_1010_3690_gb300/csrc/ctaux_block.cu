@@ -179,116 +179,139 @@ struct TileEdge {
   static constexpr int v = sizeof(T) == 8 ? 32 : 64;
 };
 
-// One output tile (TileEdge) and one slice of the inner dimension per CTA
-// (256 threads); grid (tiles x max slices, 2 spins, chains), CTAs
-// beyond the problem exit at once.  Slices have a fixed width kchunk, so the
-// partition of a product, and with it the rounding, depends only on that
-// product's own sizes (a chain gives the same bits alone or in a batch).
-// With more than one slice every slice stores its partial tile, and the slice
-// that arrives last at the tile's ticket adds the partials in slice order
-// (deterministic, no waiting) and writes the result.
+// Work items of one product for one chain: 2 spins x output tiles x slices
+// of the inner dimension (fixed width kchunk, so the partition, and with it
+// the rounding, depends only on the product's own sizes: a chain gives the
+// same bits alone or in a batch).
 template <typename T, int PHASE>
-__global__ void __launch_bounds__(256) k_gemm(Chain<T>* chains, int ksplit, int kchunk) {
-  constexpr int phase = PHASE;
-  constexpr int GBM = TileEdge<T>::v, GBN = TileEdge<T>::v, TM = GBM / 16, TN = GBN / 16;
-  const Chain<T>& c = chains[blockIdx.z];
-  const Dyn& d = *c.dyn;
-  if (d.status) return;
-  const int spin = blockIdx.y;
+__device__ __forceinline__ int gemm_items(const Chain<T>& c, const Dyn& d, int kchunk, int& tiles_m,
+                                          int& tiles_n, int& nslices) {
+  constexpr int GE = TileEdge<T>::v;
   Gemm<T> g;
-  if (!setup_gemm(c, d, spin, phase, g)) return;
-  const int tiles_n = (g.Nn + GBN - 1) / GBN;
-  const int tiles_m = (g.M + GBM - 1) / GBM;
-  const int tile = blockIdx.x / ksplit, ks = blockIdx.x % ksplit;
-  if (tile >= tiles_m * tiles_n) return;
-  const int nslices = max(1, (g.Kk + kchunk - 1) / kchunk);
-  if (ks >= nslices) return;
-  const int i0 = (tile / tiles_n) * GBM, j0 = (tile % tiles_n) * GBN;
-  const int kb = ks * kchunk, ke = min(g.Kk, kb + kchunk);
+  if (d.status || !setup_gemm(c, d, 0, PHASE, g)) return 0;
+  tiles_m = (g.M + GE - 1) / GE;
+  tiles_n = (g.Nn + GE - 1) / GE;
+  nslices = max(1, (g.Kk + kchunk - 1) / kchunk);
+  return 2 * tiles_m * tiles_n * nslices;
+}
+
+// Persistent batched product: CTAs loop over the (chain, spin, tile, slice)
+// items of all chains.  One output tile (TileEdge) and one slice per item (256
+// threads).  With more than one slice every slice stores its partial tile,
+// and the slice that arrives last at the tile's ticket adds the partials in
+// slice order (deterministic, no waiting) and writes the result.
+template <typename T, int PHASE>
+__global__ void __launch_bounds__(256) k_gemm(Chain<T>* chains, int n_chains, int kchunk,
+                                              int kstride) {
+  constexpr int GBM = TileEdge<T>::v, GBN = TileEdge<T>::v, TM = GBM / 16, TN = GBN / 16;
+  constexpr int phase = PHASE;
+  __shared__ int off[kMaxChains + 1];
   __shared__ T As[GBK][GBM + 1];
   __shared__ T Bs[GBK][GBN + 1];
   __shared__ int s_last;
+  for (int ci = threadIdx.x; ci < n_chains; ci += blockDim.x) {
+    int a, b, q;
+    off[ci] = gemm_items<T, PHASE>(chains[ci], *chains[ci].dyn, kchunk, a, b, q);
+  }
+  __syncthreads();
+  block_exclusive_scan(off, n_chains);
+  const int total = off[n_chains];
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  T acc[TM][TN];
+  for (int w = blockIdx.x; w < total; w += gridDim.x) {
+    const int ci = find_chain(off, n_chains, w);
+    const Chain<T>& c = chains[ci];
+    const Dyn& d = *c.dyn;
+    int tiles_m, tiles_n, nslices;
+    gemm_items<T, PHASE>(c, d, kchunk, tiles_m, tiles_n, nslices);
+    const int l = w - off[ci];
+    const int per_spin = tiles_m * tiles_n * nslices;
+    const int spin = l / per_spin, r0 = l % per_spin;
+    const int tile = r0 / nslices, ks = r0 % nslices;
+    Gemm<T> g;
+    setup_gemm(c, d, spin, phase, g);
+    const int i0 = (tile / tiles_n) * GBM, j0 = (tile % tiles_n) * GBN;
+    const int kb = ks * kchunk, ke = min(g.Kk, kb + kchunk);
+    T acc[TM][TN];
 #pragma unroll
-  for (int a = 0; a < TM; ++a)
+    for (int a = 0; a < TM; ++a)
 #pragma unroll
-    for (int b = 0; b < TN; ++b) acc[a][b] = (T)0;
-  for (int k0 = kb; k0 < ke; k0 += GBK) {
-    for (int e = threadIdx.x; e < GBK * GBM; e += 256) {
-      const int ii = e % GBM, kk = e / GBM;
-      const int i = i0 + ii, k = k0 + kk;
-      As[kk][ii] = (i < g.M && k < ke) ? g.A.at(i, k) : (T)0;
+      for (int b = 0; b < TN; ++b) acc[a][b] = (T)0;
+    for (int k0 = kb; k0 < ke; k0 += GBK) {
+      for (int e = threadIdx.x; e < GBK * GBM; e += 256) {
+        const int ii = e % GBM, kk = e / GBM;
+        const int i = i0 + ii, k = k0 + kk;
+        As[kk][ii] = (i < g.M && k < ke) ? g.A.at(i, k) : (T)0;
+      }
+      for (int e = threadIdx.x; e < GBK * GBN; e += 256) {
+        const int kk = e % GBK, jj = e / GBK;
+        const int j = j0 + jj, k = k0 + kk;
+        Bs[kk][jj] = (j < g.Nn && k < ke) ? g.B.at(k, j) : (T)0;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < GBK; ++kk) {
+        T av[TM], bv[TN];
+#pragma unroll
+        for (int a = 0; a < TM; ++a) av[a] = As[kk][ty + 16 * a];
+#pragma unroll
+        for (int b = 0; b < TN; ++b) bv[b] = Bs[kk][tx + 16 * b];
+#pragma unroll
+        for (int a = 0; a < TM; ++a)
+#pragma unroll
+          for (int b = 0; b < TN; ++b) acc[a][b] += av[a] * bv[b];
+      }
+      __syncthreads();
     }
-    for (int e = threadIdx.x; e < GBK * GBN; e += 256) {
-      const int kk = e % GBK, jj = e / GBK;
-      const int j = j0 + jj, k = k0 + kk;
-      Bs[kk][jj] = (j < g.Nn && k < ke) ? g.B.at(k, j) : (T)0;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < GBK; ++kk) {
-      T av[TM], bv[TN];
-#pragma unroll
-      for (int a = 0; a < TM; ++a) av[a] = As[kk][ty + 16 * a];
-#pragma unroll
-      for (int b = 0; b < TN; ++b) bv[b] = Bs[kk][tx + 16 * b];
+    if (nslices > 1) {
+      T* part = c.kpart[spin] + (size_t)tile * kstride * GBM * GBN;
 #pragma unroll
       for (int a = 0; a < TM; ++a)
 #pragma unroll
-        for (int b = 0; b < TN; ++b) acc[a][b] += av[a] * bv[b];
+        for (int b = 0; b < TN; ++b)
+          part[(size_t)ks * GBM * GBN + (ty + 16 * a) * GBN + tx + 16 * b] = acc[a][b];
+      __threadfence();
+      __syncthreads();
+      if (threadIdx.x == 0) s_last = (atomicAdd(c.ticket[spin] + tile, 1) == nslices - 1);
+      __syncthreads();
+      if (!s_last) continue;
+      __threadfence();
+#pragma unroll
+      for (int a = 0; a < TM; ++a)
+#pragma unroll
+        for (int b = 0; b < TN; ++b) {
+          T v = (T)0;
+          for (int q = 0; q < nslices; ++q)
+            v += __ldcg(part + (size_t)q * GBM * GBN + (ty + 16 * a) * GBN + tx + 16 * b);
+          acc[a][b] = v;
+        }
+      if (threadIdx.x == 0) c.ticket[spin][tile] = 0;
     }
-    __syncthreads();
-  }
-  if (nslices > 1) {
-    T* part = c.kpart[spin] + (size_t)tile * ksplit * GBM * GBN;
 #pragma unroll
-    for (int a = 0; a < TM; ++a)
-#pragma unroll
-      for (int b = 0; b < TN; ++b)
-        part[(size_t)ks * GBM * GBN + (ty + 16 * a) * GBN + tx + 16 * b] = acc[a][b];
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) s_last = (atomicAdd(c.ticket[spin] + tile, 1) == nslices - 1);
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-#pragma unroll
-    for (int a = 0; a < TM; ++a)
+    for (int a = 0; a < TM; ++a) {
+      const int i = i0 + ty + 16 * a;
+      if (i >= g.M) continue;
 #pragma unroll
       for (int b = 0; b < TN; ++b) {
-        T v = (T)0;
-        for (int q = 0; q < nslices; ++q)
-          v += __ldcg(part + (size_t)q * GBM * GBN + (ty + 16 * a) * GBN + tx + 16 * b);
-        acc[a][b] = v;
+        const int j = j0 + tx + 16 * b;
+        if (j >= g.Nn) continue;
+        T v = (T)g.alpha * acc[a][b];
+        if (g.has_cin) v += g.Cin.at(i, j);
+        g.out[(long)i * g.out_rs + (long)j * g.out_cs] = v;
       }
-    if (threadIdx.x == 0) c.ticket[spin][tile] = 0;
-  }
-#pragma unroll
-  for (int a = 0; a < TM; ++a) {
-    const int i = i0 + ty + 16 * a;
-    if (i >= g.M) continue;
-#pragma unroll
-    for (int b = 0; b < TN; ++b) {
-      const int j = j0 + tx + 16 * b;
-      if (j >= g.Nn) continue;
-      T v = (T)g.alpha * acc[a][b];
-      if (g.has_cin) v += g.Cin.at(i, j);
-      g.out[(long)i * g.out_rs + (long)j * g.out_cs] = v;
     }
   }
 }
 
 template <typename T>
 void launch_gemm(Chain<T>* dchains, const LaunchShape& ls, int phase, cudaStream_t st) {
-  const dim3 grid(ls.tiles[phase] * ls.ksplit[phase], 2, ls.n_chains);
-  const int ks = ls.ksplit[phase], kc = ls.kchunk;
+  const dim3 grid(ls.persist_ctas);
+  const int n = ls.n_chains, kc = ls.kchunk, ks = ls.kstride;
   switch (phase) {
-    case PH_RTILDE: k_gemm<T, PH_RTILDE><<<grid, 256, 0, st>>>(dchains, ks, kc); break;
-    case PH_GCOL_OLD: k_gemm<T, PH_GCOL_OLD><<<grid, 256, 0, st>>>(dchains, ks, kc); break;
-    case PH_GCOL_NEW: k_gemm<T, PH_GCOL_NEW><<<grid, 256, 0, st>>>(dchains, ks, kc); break;
-    case PH_FLUSH: k_gemm<T, PH_FLUSH><<<grid, 256, 0, st>>>(dchains, ks, kc); break;
-    default: k_gemm<T, PH_MEAS><<<grid, 256, 0, st>>>(dchains, ks, kc); break;
+    case PH_RTILDE: k_gemm<T, PH_RTILDE><<<grid, 256, 0, st>>>(dchains, n, kc, ks); break;
+    case PH_GCOL_OLD: k_gemm<T, PH_GCOL_OLD><<<grid, 256, 0, st>>>(dchains, n, kc, ks); break;
+    case PH_GCOL_NEW: k_gemm<T, PH_GCOL_NEW><<<grid, 256, 0, st>>>(dchains, n, kc, ks); break;
+    case PH_FLUSH: k_gemm<T, PH_FLUSH><<<grid, 256, 0, st>>>(dchains, n, kc, ks); break;
+    default: k_gemm<T, PH_MEAS><<<grid, 256, 0, st>>>(dchains, n, kc, ks); break;
   }
 }
 
@@ -719,58 +742,74 @@ __device__ __forceinline__ void split_tf32_y(float x, float& hi, float& lo) {
 }
 
 template <typename T, bool SPLIT>
-__global__ void __launch_bounds__(256) k_flush_y(Chain<T>* chains) {
-  const Chain<T>& c = chains[blockIdx.z];
-  const Dyn& d = *c.dyn;
-  if (d.status) return;
-  const int spin = blockIdx.y;
-  const int kacc = d.k_acc, nn = d.n_new, KM = c.k_max;
-  const int a0 = blockIdx.x * kYRows;
-  if ((!SPLIT && kacc == 0) || a0 >= nn) return;
+__device__ __forceinline__ int flush_y_items(const Dyn& d) {
+  if (d.status || (!SPLIT && d.k_acc == 0)) return 0;
+  return 2 * ((d.n_new + kYRows - 1) / kYRows);
+}
+
+template <typename T, bool SPLIT>
+__global__ void __launch_bounds__(256) k_flush_y(Chain<T>* chains, int n_chains) {
   using A = T;
+  __shared__ int off[kMaxChains + 1];
   __shared__ A gh[kYRows * kMaxK];
   __shared__ int Ps[kMaxK];
   __shared__ int Si[kYRows];
-  for (int e = threadIdx.x; e < kacc; e += blockDim.x) Ps[e] = c.P[e];
-  for (int e = threadIdx.x; e < kYRows; e += blockDim.x) Si[e] = (a0 + e < nn) ? c.S[a0 + e] : -1;
+  for (int ci = threadIdx.x; ci < n_chains; ci += blockDim.x)
+    off[ci] = flush_y_items<T, SPLIT>(*chains[ci].dyn);
   __syncthreads();
-  const T* Nb = c.N[d.buf][spin];
-  const T* Gc = c.Gcol[spin];
-  const int n_old = d.n;
-  for (int e = threadIdx.x; e < kYRows * kacc; e += blockDim.x) {
-    const int aa = e % kYRows, q = e / kYRows;
-    const int i = Si[aa];
-    A v = (A)0;
-    if (i >= 0) {
-      const int pq = Ps[q];
-      v = g_int<A>(c, Nb, Gc, n_old, spin, i, pq) - (i == pq ? (A)1 : (A)0);
-    }
-    gh[q * kYRows + aa] = v;
-  }
-  __syncthreads();
-  const T* Gi = c.Ginv[spin];
-  if constexpr (!SPLIT) {
+  block_exclusive_scan(off, n_chains);
+  const int total = off[n_chains];
+  for (int w = blockIdx.x; w < total; w += gridDim.x) {
+    const int ci = find_chain(off, n_chains, w);
+    const Chain<T>& c = chains[ci];
+    const Dyn& d = *c.dyn;
+    const int l = w - off[ci];
+    const int groups = (d.n_new + kYRows - 1) / kYRows;
+    const int spin = l / groups;
+    const int kacc = d.k_acc, nn = d.n_new, KM = c.k_max;
+    const int a0 = (l % groups) * kYRows;
+    __syncthreads();
+    for (int e = threadIdx.x; e < kacc; e += blockDim.x) Ps[e] = c.P[e];
+    for (int e = threadIdx.x; e < kYRows; e += blockDim.x) Si[e] = (a0 + e < nn) ? c.S[a0 + e] : -1;
+    __syncthreads();
+    const T* Nb = c.N[d.buf][spin];
+    const T* Gc = c.Gcol[spin];
+    const int n_old = d.n;
     for (int e = threadIdx.x; e < kYRows * kacc; e += blockDim.x) {
-      const int aa = e % kYRows, r = e / kYRows;
-      if (Si[aa] < 0) continue;
-      A acc = (A)0;
-      for (int q = 0; q < kacc; ++q) acc += gh[q * kYRows + aa] * (A)Gi[(size_t)q * (KM + 1) + r];
-      c.Y[spin][(size_t)r * c.ld + a0 + aa] = (T)acc;
-    }
-  } else {
-    const int KP = c.kp;
-    for (int e = threadIdx.x; e < kYRows * KP; e += blockDim.x) {
-      const int r = e % KP, aa = e / KP;
-      if (Si[aa] < 0) continue;
-      float hi = 0.f, lo = 0.f;
-      if (r < kacc) {
-        float acc = 0.f;
-        for (int q = 0; q < kacc; ++q)
-          acc += (float)gh[q * kYRows + aa] * (float)Gi[(size_t)q * (KM + 1) + r];
-        split_tf32_y(acc, hi, lo);
+      const int aa = e % kYRows, q = e / kYRows;
+      const int i = Si[aa];
+      A v = (A)0;
+      if (i >= 0) {
+        const int pq = Ps[q];
+        v = g_int<A>(c, Nb, Gc, n_old, spin, i, pq) - (i == pq ? (A)1 : (A)0);
       }
-      c.Yh[spin][(size_t)(a0 + aa) * KP + r] = hi;
-      c.Yl[spin][(size_t)(a0 + aa) * KP + r] = lo;
+      gh[q * kYRows + aa] = v;
+    }
+    __syncthreads();
+    const T* Gi = c.Ginv[spin];
+    if constexpr (!SPLIT) {
+      for (int e = threadIdx.x; e < kYRows * kacc; e += blockDim.x) {
+        const int aa = e % kYRows, r = e / kYRows;
+        if (Si[aa] < 0) continue;
+        A acc = (A)0;
+        for (int q = 0; q < kacc; ++q) acc += gh[q * kYRows + aa] * (A)Gi[(size_t)q * (KM + 1) + r];
+        c.Y[spin][(size_t)r * c.ld + a0 + aa] = (T)acc;
+      }
+    } else {
+      const int KP = c.kp;
+      for (int e = threadIdx.x; e < kYRows * KP; e += blockDim.x) {
+        const int r = e % KP, aa = e / KP;
+        if (Si[aa] < 0) continue;
+        float hi = 0.f, lo = 0.f;
+        if (r < kacc) {
+          float acc = 0.f;
+          for (int q = 0; q < kacc; ++q)
+            acc += (float)gh[q * kYRows + aa] * (float)Gi[(size_t)q * (KM + 1) + r];
+          split_tf32_y(acc, hi, lo);
+        }
+        c.Yh[spin][(size_t)(a0 + aa) * KP + r] = hi;
+        c.Yl[spin][(size_t)(a0 + aa) * KP + r] = lo;
+      }
     }
   }
 }
@@ -831,9 +870,9 @@ void launch_block(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t st, Pha
   k_survivors<T><<<nch, 1024, 0, st>>>(dchains);
   if (tc) {
     if constexpr (std::is_same<T, float>::value)
-      k_flush_y<float, true><<<dim3(ls.y_blocks, 2, nch), 256, 0, st>>>(dchains);
+      k_flush_y<float, true><<<ls.persist_ctas, 256, 0, st>>>(dchains, nch);
   } else {
-    k_flush_y<T, false><<<dim3(ls.y_blocks, 2, nch), 256, 0, st>>>(dchains);
+    k_flush_y<T, false><<<ls.persist_ctas, 256, 0, st>>>(dchains, nch);
   }
   pt->end(4, st, 2);
   pt->begin(3, st);

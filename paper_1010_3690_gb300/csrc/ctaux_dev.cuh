@@ -211,6 +211,52 @@ __device__ __forceinline__ float g0_eval_f(const Chain<T>& c, int spin, float ti
   return -(float)__ldg(row + c.n_tau - 1);
 }
 
+// ------------------------------------------------------------ work lists
+// Batched kernels loop over (chain, item) pairs: every CTA computes each
+// chain's item count from its device-side sizes, an exclusive prefix sum in
+// shared memory (off[0..n_chains], off[n_chains] = total), and finds the chain
+// of a linear item index by binary search.
+constexpr int kMaxChains = 2048;
+
+__device__ __forceinline__ void block_exclusive_scan(int* a, int n) {
+  // a[0..n] in shared memory; on return a[i] = sum_{k<i} a_k, a[n] = total
+  __shared__ int part[1024];
+  const int nt = blockDim.x, t = threadIdx.x;
+  const int per = (n + nt - 1) / nt;
+  const int lo = min(n, t * per), hi = min(n, lo + per);
+  int sum = 0;
+  for (int i = lo; i < hi; ++i) sum += a[i];
+  part[t] = sum;
+  __syncthreads();
+  if (t == 0) {
+    int run = 0;
+    for (int i = 0; i < nt; ++i) {
+      const int v = part[i];
+      part[i] = run;
+      run += v;
+    }
+    a[n] = run;
+  }
+  __syncthreads();
+  int run = part[t];
+  for (int i = lo; i < hi; ++i) {
+    const int v = a[i];
+    a[i] = run;
+    run += v;
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ int find_chain(const int* off, int n, int w) {
+  int lo = 0, hi = n;  // off[lo] <= w < off[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (off[mid] <= w) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
 // ----------------------------------------------------------- reductions
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll

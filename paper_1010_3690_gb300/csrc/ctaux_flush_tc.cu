@@ -143,40 +143,34 @@ __global__ void __launch_bounds__(256) k_flush_split_x(Chain<float>* chains) {
   }
 }
 
-__global__ void __launch_bounds__(kTcThreads) k_flush_tc(Chain<float>* chains, const TcMaps* maps) {
-  const Chain<float>& c = chains[blockIdx.z];
-  Dyn& d = *c.dyn;
-  if (d.status) return;
-  const int spin = blockIdx.y;
-  const int nn = d.n_new, kacc = d.k_acc, ld = c.ld;
-  const int tiles = (nn + kTcBM - 1) / kTcBM;
-  if ((int)blockIdx.x >= tiles * tiles) return;
-  const int m0 = (blockIdx.x / tiles) * kTcBM, n0 = (blockIdx.x % tiles) * kTcBN;
-  const int nk = (kacc + kTcBK - 1) / kTcBK;
-  const float* Nb = c.N[d.buf][spin];
-  float* out = c.N[1 - d.buf][spin];
-  const int* S = c.S;
+__device__ __forceinline__ int tc_items(const Dyn& d) {
+  if (d.status) return 0;
+  const int tiles = (d.n_new + kTcBM - 1) / kTcBM;
+  return 2 * tiles * tiles;
+}
+
+// Persistent over the (chain, spin, tile) items of all chains.  Each mbarrier
+// phase is waited exactly once and in order (full and mdone by thread 0, acc
+// by every thread), so no parity wait can be overtaken by a later phase.
+__global__ void __launch_bounds__(kTcThreads) k_flush_tc(Chain<float>* chains, int n_chains,
+                                                         const TcMaps* maps) {
+  __shared__ int off[kMaxChains + 1];
+  for (int ci = threadIdx.x; ci < n_chains; ci += blockDim.x) off[ci] = tc_items(*chains[ci].dyn);
+  __syncthreads();
+  block_exclusive_scan(off, n_chains);
+  const int total = off[n_chains];
+  if ((int)blockIdx.x >= total) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
       ((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = reinterpret_cast<uint64_t*>(base + kTcStages * kStageBytes);
-  uint64_t* mdone = full + kTcStages;
-  uint64_t* accb = mdone + kTcStages;
+  uint64_t* mdone = full + 1;
+  uint64_t* accb = mdone + 1;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accb + 1);
   int* err_s = reinterpret_cast<int*>(tmem_slot + 1);
-  int* Scol = err_s + 1;  // S[n0 .. n0 + 127]
-  for (int e = threadIdx.x; e < kTcBN; e += blockDim.x) Scol[e] = (n0 + e < nn) ? S[n0 + e] : 0;
-
-  if (nk == 0) {  // no accepted change: the flush is a pure compaction
-    __syncthreads();
-    for (int e = threadIdx.x; e < kTcBM * kTcBN; e += blockDim.x) {
-      const int m = m0 + (e % kTcBM), n = n0 + (e / kTcBM);
-      if (m < nn && n < nn) out[(long)n * ld + m] = Nb[(long)Scol[n - n0] * ld + S[m]];
-    }
-    return;
-  }
+  int* Scol = err_s + 1;  // S[n0 .. n0 + 127] of the current tile
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -186,10 +180,8 @@ __global__ void __launch_bounds__(kTcThreads) k_flush_tc(Chain<float>* chains, c
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kTcStages; ++s) {
-      mbar_init(smem_u32(full + s), 1);
-      mbar_init(smem_u32(mdone + s), 1);
-    }
+    mbar_init(smem_u32(full), 1);
+    mbar_init(smem_u32(mdone), 1);
     mbar_init(smem_u32(accb), 1);
     *err_s = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -199,93 +191,106 @@ __global__ void __launch_bounds__(kTcThreads) k_flush_tc(Chain<float>* chains, c
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
+  uint32_t full_uses = 0, mdone_uses = 0, acc_uses = 0;
 
-  if (threadIdx.x == 0) {
-    const TcMaps& mp = maps[blockIdx.z * 2 + spin];
-    int loads_issued = 0, loads_done = 0;
-    auto issue = [&](int kc) {
-      const int s = kc % kTcStages;
-      unsigned char* st = base + s * kStageBytes;
-      const uint32_t fb = smem_u32(full + s);
-      mbar_expect_tx(fb, kStageBytes);
-      tma_load_2d(smem_u32(st + 0 * kTileBytes), &mp.yh, kc * kTcBK, m0, fb);
-      tma_load_2d(smem_u32(st + 1 * kTileBytes), &mp.yl, kc * kTcBK, m0, fb);
-      tma_load_2d(smem_u32(st + 2 * kTileBytes), &mp.xh, kc * kTcBK, n0, fb);
-      tma_load_2d(smem_u32(st + 3 * kTileBytes), &mp.xl, kc * kTcBK, n0, fb);
-      ++loads_issued;
-    };
-    for (int kc = 0; kc < nk && kc < kTcStages; ++kc) issue(kc);
-    bool ok = true;
-    for (int kc = 0; kc < nk; ++kc) {
-      const int s = kc % kTcStages;
-      const uint32_t ph = (uint32_t)((kc / kTcStages) & 1);
-      if (!mbar_wait(smem_u32(full + s), ph)) {
-        ok = false;
-        break;
+  for (int w = blockIdx.x; w < total; w += gridDim.x) {
+    const int ci = find_chain(off, n_chains, w);
+    const Chain<float>& c = chains[ci];
+    Dyn& d = *c.dyn;
+    const int nn = d.n_new, kacc = d.k_acc, ld = c.ld;
+    const int tiles = (nn + kTcBM - 1) / kTcBM;
+    const int l = w - off[ci];
+    const int spin = l / (tiles * tiles), tile = l % (tiles * tiles);
+    const int m0 = (tile / tiles) * kTcBM, n0 = (tile % tiles) * kTcBN;
+    const int nk = (kacc + kTcBK - 1) / kTcBK;
+    const float* Nb = c.N[d.buf][spin];
+    float* out = c.N[1 - d.buf][spin];
+    const int* S = c.S;
+    for (int e = threadIdx.x; e < kTcBN; e += blockDim.x) Scol[e] = (n0 + e < nn) ? S[n0 + e] : 0;
+    __syncthreads();
+    if (nk == 0) {  // no accepted change: the flush is a pure compaction
+      for (int e = threadIdx.x; e < kTcBM * kTcBN; e += blockDim.x) {
+        const int m = m0 + (e % kTcBM), n = n0 + (e / kTcBM);
+        if (m < nn && n < nn) out[(long)n * ld + m] = Nb[(long)Scol[n - n0] * ld + S[m]];
       }
-      ++loads_done;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      unsigned char* st = base + s * kStageBytes;
-      const uint32_t ah = smem_u32(st), al = ah + kTileBytes, bh = ah + 2 * kTileBytes,
-                     bl = ah + 3 * kTileBytes;
-#pragma unroll
-      for (int kk = 0; kk < kTcBK / 8; ++kk) {
-        const uint32_t off = kk * 32;  // 8 tf32 = 32 bytes along K
-        const uint32_t first = (kc == 0 && kk == 0) ? 0u : 1u;
-        mma_tf32(tmem, smem_desc(ah + off), smem_desc(bl + off), first);  // hi * lo
-        mma_tf32(tmem, smem_desc(al + off), smem_desc(bh + off), 1u);     // lo * hi
-        mma_tf32(tmem, smem_desc(ah + off), smem_desc(bh + off), 1u);     // hi * hi
-      }
-      mma_commit(smem_u32(mdone + s));
-      if (kc + kTcStages < nk) {
-        if (!mbar_wait(smem_u32(mdone + s), ph)) {
+      __syncthreads();
+      continue;
+    }
+    if (threadIdx.x == 0) {
+      const TcMaps& mp = maps[ci * 2 + spin];
+      bool ok = true;
+      for (int kc = 0; kc < nk && ok; ++kc) {
+        const uint32_t fb = smem_u32(full);
+        mbar_expect_tx(fb, kStageBytes);
+        tma_load_2d(smem_u32(base + 0 * kTileBytes), &mp.yh, kc * kTcBK, m0, fb);
+        tma_load_2d(smem_u32(base + 1 * kTileBytes), &mp.yl, kc * kTcBK, m0, fb);
+        tma_load_2d(smem_u32(base + 2 * kTileBytes), &mp.xh, kc * kTcBK, n0, fb);
+        tma_load_2d(smem_u32(base + 3 * kTileBytes), &mp.xl, kc * kTcBK, n0, fb);
+        // bounded; on timeout the same wait is retried (bounded) so that the
+        // copies land before the shared memory is reused or released
+        if (!mbar_wait(fb, full_uses & 1)) {
           ok = false;
-          break;
+          mbar_wait(fb, full_uses & 1);
         }
-        issue(kc + kTcStages);
-      }
-    }
-    if (!ok) {
-      *err_s = 1;
-      atomicOr(&d.status, DS_TIMEOUT);
-      // let the copies already issued land before the CTA releases its shared memory
-      for (int kc = loads_done; kc < loads_issued; ++kc)
-        mbar_wait(smem_u32(full + kc % kTcStages), (uint32_t)((kc / kTcStages) & 1));
-    }
-    mma_commit(smem_u32(accb));  // arrives when every MMA issued so far has completed
-  }
-  __syncthreads();
-  const bool acc_ok = mbar_wait(smem_u32(accb), 0);
-  // one decision for the whole CTA: tcgen05.ld is warp-collective
-  const bool all_ok = __syncthreads_and(acc_ok && *err_s == 0) != 0;
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (all_ok) {
-    const int quarter = warp & 3, colhalf = warp >> 2;
-    const int m = m0 + quarter * 32 + lane;
-    const bool row_ok = m < nn;
-    const long srow = row_ok ? S[m] : 0;
-    float v[32], cin[32];
-#pragma unroll 1
-    for (int cc = colhalf * 2; cc < colhalf * 2 + 2; ++cc) {
-      // the 32 gathered inputs of this chunk: independent loads, issued first
+        ++full_uses;
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t ah = smem_u32(base), al = ah + kTileBytes, bh = ah + 2 * kTileBytes,
+                       bl = ah + 3 * kTileBytes;
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const int n = n0 + cc * 32 + j;
-        cin[j] = (row_ok && n < nn) ? Nb[(long)Scol[cc * 32 + j] * ld + srow] : 0.f;
+        for (int kk = 0; kk < kTcBK / 8; ++kk) {
+          const uint32_t offk = kk * 32;  // 8 tf32 = 32 bytes along K
+          const uint32_t first = (kc == 0 && kk == 0) ? 0u : 1u;
+          mma_tf32(tmem, smem_desc(ah + offk), smem_desc(bl + offk), first);  // hi * lo
+          mma_tf32(tmem, smem_desc(al + offk), smem_desc(bh + offk), 1u);     // lo * hi
+          mma_tf32(tmem, smem_desc(ah + offk), smem_desc(bh + offk), 1u);     // hi * hi
+        }
+        mma_commit(smem_u32(mdone));
+        if (!mbar_wait(smem_u32(mdone), mdone_uses & 1)) ok = false;
+        ++mdone_uses;
       }
-      tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(cc * 32), v);
-      if (row_ok) {
+      if (!ok) {
+        *err_s = 1;
+        atomicOr(&d.status, DS_TIMEOUT);
+      }
+      mma_commit(smem_u32(accb));  // arrives when every MMA issued so far has completed
+    }
+    __syncthreads();
+    const bool acc_ok = mbar_wait(smem_u32(accb), acc_uses & 1);
+    ++acc_uses;
+    // one decision for the whole CTA: tcgen05.ld is warp-collective
+    const bool all_ok = __syncthreads_and(acc_ok && *err_s == 0) != 0;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (all_ok) {
+      const int quarter = warp & 3, colhalf = warp >> 2;
+      const int m = m0 + quarter * 32 + lane;
+      const bool row_ok = m < nn;
+      const long srow = row_ok ? S[m] : 0;
+      float v[32], cin[32];
+#pragma unroll 1
+      for (int cc = colhalf * 2; cc < colhalf * 2 + 2; ++cc) {
+        // the 32 gathered inputs of this chunk: independent loads, issued first
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const int n = n0 + cc * 32 + j;
-          if (n < nn) out[(long)n * ld + m] = cin[j] - v[j];
+          cin[j] = (row_ok && n < nn) ? Nb[(long)Scol[cc * 32 + j] * ld + srow] : 0.f;
+        }
+        tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(cc * 32), v);
+        if (row_ok) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int n = n0 + cc * 32 + j;
+            if (n < nn) out[(long)n * ld + m] = cin[j] - v[j];
+          }
         }
       }
+    } else if (threadIdx.x == 0) {
+      atomicOr(&d.status, DS_TIMEOUT);
     }
-  } else if (threadIdx.x == 0) {
-    atomicOr(&d.status, DS_TIMEOUT);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (!all_ok) break;
   }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
@@ -303,7 +308,7 @@ cudaError_t configure_flush_tc() {
 void launch_flush_tc(Chain<float>* dchains, const TcMaps* maps, const LaunchShape& ls,
                      cudaStream_t st) {
   k_flush_split_x<<<dim3(ls.split_x_blocks, 2, ls.n_chains), 256, 0, st>>>(dchains);
-  k_flush_tc<<<dim3(ls.tc_tiles, 2, ls.n_chains), kTcThreads, tc_smem_bytes(), st>>>(dchains, maps);
+  k_flush_tc<<<ls.tc_ctas, kTcThreads, tc_smem_bytes(), st>>>(dchains, ls.n_chains, maps);
 }
 
 // Host: the four TMA descriptors of one (chain, spin): K-major float32 buffers of

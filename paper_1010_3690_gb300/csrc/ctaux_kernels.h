@@ -27,6 +27,10 @@ struct LaunchShape {
   int tiles[PH_COUNT];   // bound on output tiles per (chain, spin)
   int ksplit[PH_COUNT];  // most slices of the inner dimension a product can need
   int kchunk;            // fixed slice width of the inner dimension
+  int kstride;           // partial-tile stride per output tile (most slices of any product)
+  int persist_ctas;      // grid of the persistent batched kernels
+  int refresh_per_cta;   // batched form: one CTA per (chain, spin) for the refresh
+  int refresh_cta_smem;
   int y_blocks;
   int prop_smem;
   int gamma_in_smem;
@@ -36,6 +40,7 @@ struct LaunchShape {
   int refresh_grid;
   int use_tc;            // mixed form: flush on the tensor cores
   int tc_tiles;          // bound on 128 x 128 flush tiles per (chain, spin)
+  int tc_ctas;           // persistent grid of the tensor-core flush (two CTAs per SM)
   int split_x_blocks;
 };
 
@@ -96,6 +101,8 @@ void launch_gemm(Chain<T>* dchains, const LaunchShape& ls, int phase, cudaStream
 template <typename T>
 int refresh_blocks_per_sm();
 size_t refresh_work_doubles(int ld);
+template <typename T>
+cudaError_t configure_refresh_cta(int smem);
 template <typename T>
 void launch_measure(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t st, PhaseTimer* pt);
 template <typename T>

@@ -32,48 +32,66 @@ __global__ void __launch_bounds__(256) k_meas_gather(Chain<T>* chains) {
 }
 
 // One thread per evaluation point (anchor, site, bin) and chunk of kMeasChunk
-// vertices; partial sums go to Mpts[spin][chunk][point].
+// vertices; partial sums go to Mpts[spin][chunk][point].  Persistent over the
+// (chain, spin, point block, chunk) items of all chains.
 template <typename T>
-__global__ void __launch_bounds__(256) k_meas_eval(Chain<T>* chains, int point_blocks) {
-  const Chain<T>& c = chains[blockIdx.z];
-  const Dyn& d = *c.dyn;
-  if (d.status) return;
-  const int spin = blockIdx.y, n = d.n, buf = d.buf, A = c.n_anchors, B = c.n_bins;
-  const int npts = A * c.n_c * B;
-  const int chunk = blockIdx.x / point_blocks;
-  const int l0 = chunk * kMeasChunk;
-  if (l0 > 0 && l0 >= n) return;
-  const int pt = (blockIdx.x % point_blocks) * blockDim.x + threadIdx.x;
-  if (pt >= npts) return;
-  const int bin = pt % B, xa = (pt / B) % c.n_c, b = pt / (B * c.n_c);
-  const double tb = (double)b * c.beta / (double)A;
-  const double tc = ((double)bin + 0.5) * c.beta / (double)B;
-  double ta = tb + tc, sg = 1.0;
-  if (ta >= c.beta) {
-    ta -= c.beta;
-    sg = -1.0;
-  }
-  double val = (chunk == 0) ? g0_eval(c, spin, ta, xa, tb, 0) : 0.0;
-  const double* tau = c.tau[buf];
-  const int* site = c.site[buf];
-  const int8_t* s = c.s[buf];
-  const T* V = c.Mv[spin] + (long)b * c.ld;  // v_b = N g_b
-  const int l1 = min(n, l0 + kMeasChunk);
-  if (sizeof(T) == 8) {
-    for (int l = l0; l < l1; ++l) {
-      const double vl = (c.ev[spin][s[l] + 2] - 1.0) * (double)V[l];
-      val += g0_eval(c, spin, ta, xa, tau[l], site[l]) * vl;
+__device__ __forceinline__ int meas_items(const Chain<T>& c, const Dyn& d) {
+  if (d.status) return 0;
+  const int npts = c.n_anchors * c.n_c * c.n_bins;
+  return 2 * ((npts + 255) / 256) * max(1, (d.n + kMeasChunk - 1) / kMeasChunk);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_meas_eval(Chain<T>* chains, int n_chains) {
+  __shared__ int off[kMaxChains + 1];
+  for (int ci = threadIdx.x; ci < n_chains; ci += blockDim.x)
+    off[ci] = meas_items(chains[ci], *chains[ci].dyn);
+  __syncthreads();
+  block_exclusive_scan(off, n_chains);
+  const int total = off[n_chains];
+  for (int w = blockIdx.x; w < total; w += gridDim.x) {
+    const int ci = find_chain(off, n_chains, w);
+    const Chain<T>& c = chains[ci];
+    const Dyn& d = *c.dyn;
+    const int n = d.n, buf = d.buf, A = c.n_anchors, B = c.n_bins;
+    const int npts = A * c.n_c * B;
+    const int pblocks = (npts + 255) / 256, nchunks = max(1, (n + kMeasChunk - 1) / kMeasChunk);
+    const int l = w - off[ci];
+    const int spin = l / (pblocks * nchunks), r0 = l % (pblocks * nchunks);
+    const int chunk = r0 / pblocks;
+    const int l0 = chunk * kMeasChunk;
+    const int pt = (r0 % pblocks) * blockDim.x + threadIdx.x;
+    if (pt >= npts) continue;
+    const int bin = pt % B, xa = (pt / B) % c.n_c, b = pt / (B * c.n_c);
+    const double tb = (double)b * c.beta / (double)A;
+    const double tc = ((double)bin + 0.5) * c.beta / (double)B;
+    double ta = tb + tc, sg = 1.0;
+    if (ta >= c.beta) {
+      ta -= c.beta;
+      sg = -1.0;
     }
-  } else {  // mixed form: float32 interpolation and products
-    float acc = 0.f;
-    const float taf = (float)ta;
-    for (int l = l0; l < l1; ++l) {
-      const float vl = ((float)c.ev[spin][s[l] + 2] - 1.f) * (float)V[l];
-      acc += g0_eval_f(c, spin, taf, xa, (float)tau[l], site[l]) * vl;
+    double val = (chunk == 0) ? g0_eval(c, spin, ta, xa, tb, 0) : 0.0;
+    const double* tau = c.tau[buf];
+    const int* site = c.site[buf];
+    const int8_t* s = c.s[buf];
+    const T* V = c.Mv[spin] + (long)b * c.ld;  // v_b = N g_b
+    const int l1 = min(n, l0 + kMeasChunk);
+    if (sizeof(T) == 8) {
+      for (int q = l0; q < l1; ++q) {
+        const double vl = (c.ev[spin][s[q] + 2] - 1.0) * (double)V[q];
+        val += g0_eval(c, spin, ta, xa, tau[q], site[q]) * vl;
+      }
+    } else {  // mixed form: float32 interpolation and products
+      float acc = 0.f;
+      const float taf = (float)ta;
+      for (int q = l0; q < l1; ++q) {
+        const float vl = ((float)c.ev[spin][s[q] + 2] - 1.f) * (float)V[q];
+        acc += g0_eval_f(c, spin, taf, xa, (float)tau[q], site[q]) * vl;
+      }
+      val += (double)acc;
     }
-    val += (double)acc;
+    c.Mpts[spin][(size_t)chunk * npts + pt] = sg * val;
   }
-  c.Mpts[spin][(size_t)chunk * npts + pt] = sg * val;
 }
 
 // Per (chain, spin, class, bin): fixed-order sum over vertex chunks, anchors
@@ -133,8 +151,7 @@ void launch_measure(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t st, P
   pt->begin(5, st);
   k_meas_gather<T><<<dim3(ls.gather_slices, 2, nch), 256, 0, st>>>(dchains);
   launch_gemm<T>(dchains, ls, PH_MEAS, st);
-  k_meas_eval<T><<<dim3(ls.meas_point_blocks * ls.meas_lchunks, 2, nch), 256, 0, st>>>(
-      dchains, ls.meas_point_blocks);
+  k_meas_eval<T><<<ls.persist_ctas, 256, 0, st>>>(dchains, nch);
   k_meas_accumulate<T><<<dim3(ls.meas_cb_blocks, 2, nch), 256, 0, st>>>(dchains);
   pt->end(5, st, 4);
 }

@@ -246,6 +246,172 @@ __global__ void __launch_bounds__(256) k_refresh(Chain<T>* chains, int n_chains,
   }
 }
 
+// ---------------------------------------------------------------------------
+// Batched form: one CTA per (chain, spin), the same blocked Gauss-Jordan with
+// block-level barriers.  The panel (m x 16 float64) lives in shared memory and
+// is updated in place (the pivot row is copied first); pivots come from a
+// block reduction; the trailing rank-16 update streams X through the CTA,
+// with the pivot rows X[R, :] saved in the work area beforehand.
+constexpr int kPBc = 16;
+
+__device__ __forceinline__ void block_argmax(double v, int row, double* rv, int* ri) {
+  // max |v| (ties to the lower row) over the block; result in rv[0], ri[0]
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) {
+    const double v2 = __shfl_down_sync(0xffffffffu, v, o);
+    const int r2 = __shfl_down_sync(0xffffffffu, row, o);
+    if (v2 > v || (v2 == v && r2 < row)) {
+      v = v2;
+      row = r2;
+    }
+  }
+  __syncthreads();
+  if (lane == 0) {
+    rv[w] = v;
+    ri[w] = row;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k)
+      if (rv[k] > rv[0] || (rv[k] == rv[0] && ri[k] < ri[0])) {
+        rv[0] = rv[k];
+        ri[0] = ri[k];
+      }
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) k_refresh_cta(Chain<T>* chains, int n_chains) {
+  const int ci = blockIdx.x >> 1, spin = blockIdx.x & 1;
+  if (ci >= n_chains) return;
+  const Chain<T>& c = chains[ci];
+  Dyn& d = *c.dyn;
+  if (d.status & ~DS_SINGULAR) return;
+  const int m = d.n, ld = c.ld, buf = d.buf;
+  double* X = c.work + (size_t)spin * refresh_work_per_spin(ld);
+  double* Rr = X + (size_t)ld * ld;       // pivot rows of the current panel, [j][k]
+  int* perm = c.perm + spin * ld;
+  int8_t* used = c.used + spin * ld;
+  int* pcol = c.pcol + spin * ld;
+  extern __shared__ __align__(16) double panel[];  // [k][i], kPBc x m
+  __shared__ double prow[kPBc];
+  __shared__ double rv[32];
+  __shared__ int ri[32];
+  __shared__ double logdet_s;
+  if (threadIdx.x == 0) logdet_s = 0.0;
+  // N^{-1} of the configuration
+  for (int j = 0; j < m; ++j) {
+    const double evj = c.ev[spin][c.s[buf][j] + 2];
+    const double tj = c.tau[buf][j];
+    const int sj = c.site[buf][j];
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      double v = -g0_eval(c, spin, c.tau[buf][i], c.site[buf][i], tj, sj) * (evj - 1.0);
+      if (i == j) v += evj;
+      X[(size_t)j * ld + i] = v;
+    }
+  }
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    used[i] = 0;
+    pcol[i] = -1;
+  }
+  __syncthreads();
+  for (int c0 = 0; c0 < m; c0 += kPBc) {
+    const int bw = min(kPBc, m - c0);
+    for (int e = threadIdx.x; e < m * bw; e += blockDim.x) {
+      const int i = e % m, k = e / m;
+      panel[(size_t)k * m + i] = X[(size_t)(c0 + k) * ld + i];
+    }
+    __syncthreads();
+    for (int k = 0; k < bw; ++k) {
+      const int col = c0 + k;
+      double best = -1.0;
+      int brow = 0x7fffffff;
+      for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        const double a = used[i] ? -1.0 : fabs(panel[(size_t)k * m + i]);
+        if (a > best || (a == best && i < brow)) {
+          best = a;
+          brow = i;
+        }
+      }
+      block_argmax(best, brow, rv, ri);
+      const int pr = ri[0];
+      const double piv = panel[(size_t)k * m + pr];
+      if (threadIdx.x == 0) {
+        perm[col] = pr;
+        used[pr] = 1;
+        pcol[pr] = col;
+        if (!(fabs(piv) > 0.0) || !isfinite(piv)) atomicOr(&d.status, DS_SINGULAR);
+        logdet_s += log(fabs(piv));
+      }
+      const double ipiv = 1.0 / piv;
+      if (threadIdx.x < bw) prow[threadIdx.x] = panel[(size_t)threadIdx.x * m + pr] * ipiv;
+      __syncthreads();
+      for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        const double xic = panel[(size_t)k * m + i];
+        for (int kk = 0; kk < bw; ++kk) {
+          double v;
+          if (i == pr) v = (kk == k) ? ipiv : prow[kk];
+          else if (kk == k) v = -xic * ipiv;
+          else v = panel[(size_t)kk * m + i] - xic * prow[kk];
+          panel[(size_t)kk * m + i] = v;
+        }
+      }
+      __syncthreads();
+    }
+    // pivot rows outside the panel, before the update
+    for (int e = threadIdx.x; e < m * bw; e += blockDim.x) {
+      const int k = e % bw, j = e / bw;
+      Rr[(size_t)j * kPBc + k] = X[(size_t)j * ld + perm[c0 + k]];
+    }
+    __syncthreads();
+    for (int j = 0; j < m; ++j) {
+      double* Xj = X + (size_t)j * ld;
+      if (j >= c0 && j < c0 + bw) {
+        for (int i = threadIdx.x; i < m; i += blockDim.x) Xj[i] = panel[(size_t)(j - c0) * m + i];
+        continue;
+      }
+      double r[kPBc];
+#pragma unroll
+      for (int k = 0; k < kPBc; ++k) r[k] = (k < bw) ? Rr[(size_t)j * kPBc + k] : 0.0;
+      for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        const int pci = pcol[i];
+        double acc = (pci >= c0 && pci < c0 + bw) ? 0.0 : Xj[i];
+#pragma unroll
+        for (int k = 0; k < kPBc; ++k)
+          if (k < bw) acc += panel[(size_t)k * m + i] * r[k];
+        Xj[i] = acc;
+      }
+    }
+    __syncthreads();
+  }
+  // unscramble, drift, replace
+  T* Nr = c.N[buf][spin];
+  double dmax = 0.0, dsq = 0.0;
+  for (int j = 0; j < m; ++j) {
+    const int pj = perm[j];
+    for (int cc = threadIdx.x; cc < m; cc += blockDim.x) {
+      const double v = X[(size_t)j * ld + perm[cc]];
+      const long o = (long)pj * ld + cc;
+      const double diff = fabs((double)Nr[o] - v);
+      dmax = fmax(dmax, diff);
+      dsq += diff * diff;
+      Nr[o] = (T)v;
+    }
+  }
+  if (dmax > 0.0)
+    atomicMax(reinterpret_cast<unsigned long long*>(&c.work_drift[0]),
+              (unsigned long long)__double_as_longlong(dmax));
+  if (dsq > 0.0) atomicAdd(&c.work_drift[1], dsq);
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    used[i] = 0;
+    pcol[i] = -1;
+    c.pkeys[(size_t)spin * ld + i] = 0ull;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) c.work_logdet[spin] = logdet_s;
+}
+
 // Small follow-up kernel: permutation signs, log det, drift into the stats.
 template <typename T>
 __global__ void k_refresh_finish(Chain<T>* chains, int n_chains, int only_chain) {
@@ -268,9 +434,18 @@ cudaError_t launch_refresh(Chain<T>* dchains, const LaunchShape& ls, int only_ch
                            cudaStream_t st, PhaseTimer* pt) {
   pt->begin(6, st);
   int nch = ls.n_chains;
+  cudaError_t e = cudaSuccess;
+  if (only_chain < 0 && ls.refresh_per_cta) {
+    k_refresh_cta<T><<<2 * nch, 512, ls.refresh_cta_smem, st>>>(dchains, nch);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) k_refresh_finish<T><<<(nch + 127) / 128, 128, 0, st>>>(dchains, nch, -1);
+    e = cudaGetLastError();
+    pt->end(6, st, 2);
+    return e;
+  }
   void* args[] = {&dchains, &nch, &only_chain};
-  cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_refresh<T>, dim3(ls.refresh_grid),
-                                              dim3(256), args, 0, st);
+  e = cudaLaunchCooperativeKernel((const void*)k_refresh<T>, dim3(ls.refresh_grid),
+                                  dim3(256), args, 0, st);
   if (e == cudaSuccess) {
     if (only_chain >= 0)
       k_refresh_finish<T><<<1, 1, 0, st>>>(dchains, nch, only_chain);
@@ -281,6 +456,13 @@ cudaError_t launch_refresh(Chain<T>* dchains, const LaunchShape& ls, int only_ch
   pt->end(6, st, 2);
   return e;
 }
+
+template <typename T>
+cudaError_t configure_refresh_cta(int smem) {
+  return cudaFuncSetAttribute(k_refresh_cta<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+template cudaError_t configure_refresh_cta<double>(int);
+template cudaError_t configure_refresh_cta<float>(int);
 
 template <typename T>
 int refresh_blocks_per_sm() {

@@ -119,14 +119,16 @@ def cube100(K=1.0, k_max=256, capacity=9216, seed=0, chain_id=0):
 def batch(n_chains=512, seed=12345, k_max=32, K=1.0, capacity=None, n_tau=1024):
     """Independent chains of uneven size: N_c in {4,8,16}, beta~U[2,10], U~U[4,10].
 
-    Parameters are drawn from a numpy Generator with a fixed seed; the Philox
-    seed of chain i is i (the chain id goes into the counter as well).
+    Parameters are drawn from a numpy Generator with a fixed seed; beta is
+    rounded to a multiple of 0.5 so that chains share G0 tables (17 x 3
+    tables instead of one per chain); the Philox seed of chain i is i (the
+    chain id goes into the counter as well).
     """
     rng = np.random.default_rng(seed)
     chains = []
     for i in range(n_chains):
         n_c = int(rng.choice([4, 8, 16]))
-        beta = float(np.round(rng.uniform(2.0, 10.0), 3))
+        beta = float(np.round(rng.uniform(2.0, 10.0) * 2.0) / 2.0)
         U = float(np.round(rng.uniform(4.0, 10.0), 3))
         cap = capacity
         if cap is None:
