@@ -56,7 +56,7 @@ def workload(name, K, k_max, chain_id=0):
         ch = configs.aim1(K=K, k_max=k_max, capacity=256, seed=chain_id)
         return [ch], dict(n_target=20)
     if name == "batch":
-        chs = configs.batch(n_chains=512, k_max=k_max, K=K)
+        chs = configs.batch(n_chains=512, k_max=k_max)   # K per chain, matched to n ~ 50..1200
         for c in chs:
             c.chain_id += 512 * chain_id
         return chs, dict(n_target=None)

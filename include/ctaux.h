@@ -92,6 +92,10 @@ typedef struct {
   int device;                         /* CUDA device ordinal */
   int mixed_flush_tc;                 /* mixed form: 1 = flush on the tensor cores (tcgen05,
                                          split 3xTF32), 0 = float32 CUDA-core product */
+  double tie_guard;                   /* mixed form: a proposal with |u - min(1,|R|)| below
+                                         tie_guard * max(u, min(1,|R|)) is decided in FP64
+                                         (the block stops there; FP64 refresh; exact first-touch
+                                         ratio); 0 = off; must be < 1 */
 } ctaux_params;
 
 typedef struct {
@@ -104,7 +108,8 @@ typedef struct {
   int64_t order_sum;         /* sum of n over measurements */
   double sign_sum;           /* sum of the walker sign over measurements */
   int64_t numeric_rejects;   /* proposals rejected for a non-finite ratio */
-  int64_t near_ties;         /* mixed form: decisions with |u - min(1,|R|)| < 1e-4 max(u, min(1,|R|)) */
+  int64_t near_ties;         /* mixed form: decisions within the guard band (tie_guard, or 1e-4
+                                when the FP64 re-evaluation is off) */
   int64_t refreshes;
   double last_drift_max;     /* max |N_run - N_fresh| at the last refresh (both spins) */
   double last_drift_fro;     /* Frobenius norm of the same difference */
@@ -119,7 +124,7 @@ typedef struct {
   int32_t n;                 /* order before the proposal */
   int64_t birth;             /* birth stamp (insertion counter) of the vertex; -1 if none */
   int32_t s_new;             /* proposed auxiliary spin */
-  int32_t accept;            /* 1 if accepted */
+  int32_t accept;            /* bit 0: accepted; bit 1: decided in FP64 (mixed form near tie) */
   double ratio[2];           /* det N'^{-1}_sigma / det N^{-1}_sigma per spin */
   double R;                  /* full Metropolis ratio */
   double u;                  /* accept uniform */

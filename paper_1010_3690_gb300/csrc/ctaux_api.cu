@@ -227,6 +227,9 @@ ctaux_status build_chains(ctaux_ctx* ctx) {
       c.ticket[spin] = dalloc<int>(ctx, *std::max_element(ls.tiles, ls.tiles + PH_COUNT), &err);
     }
     c.kp = round_up(cp.k_max, 32);
+    c.tie_guard = (sizeof(T) == 4) ? P.tie_guard : 0.0;
+    if (c.tie_guard > 0.0)
+      for (int spin = 0; spin < 2; ++spin) c.N64[spin] = dalloc<double>(ctx, ld * ld, &err);
     if (mixed_tc) {
       const int rows = round_up(c.cap_m, 128);
       for (int spin = 0; spin < 2; ++spin) {
@@ -243,6 +246,7 @@ ctaux_status build_chains(ctaux_ctx* ctx) {
       }
     }
     c.P = dalloc<int>(ctx, K, &err);
+    c.draws = dalloc<BlockDraw>(ctx, K, &err);
     c.S = dalloc<int>(ctx, ld, &err);
     c.work = dalloc<double>(ctx, refresh_work_doubles((int)ld), &err);
     c.perm = dalloc<int>(ctx, 2 * ld, &err);
@@ -319,8 +323,20 @@ template <typename T>
 ctaux_status do_sweeps(ctaux_ctx* ctx, int n_sweeps, int measure, cudaStream_t st) {
   Chain<T>* dc = reinterpret_cast<Chain<T>*>(ctx->chains_dev);
   PhaseTimer* pt = ctx->timer;
+  const bool ties = (sizeof(T) == 4) && ctx->params.tie_guard > 0.0;
   for (int s = 0; s < n_sweeps; ++s) {
     launch_block<T>(dc, ctx->ls, st, pt, ctx->tc_maps_dev);
+    if (ties) {
+      // near-tie decisions in FP64: refresh with an FP64 copy of N, decide,
+      // rebuild N after an accepted move (kernels exit at once without a tie)
+      cudaError_t e = launch_refresh<T>(dc, ctx->ls, -1, st, pt, 1);
+      if (e == cudaSuccess) {
+        launch_tie_eval(reinterpret_cast<Chain<float>*>(dc), ctx->ls, st);
+        pt->kernels[6] += 1;
+        e = launch_refresh<T>(dc, ctx->ls, -1, st, pt, 2);
+      }
+      if (e != cudaSuccess) return set_err(ctx, CTAUX_ECUDA, "tie refresh launch: %s", cudaGetErrorString(e));
+    }
     ctx->blocks_since_refresh += 1;
     if (ctx->params.refresh_every > 0 && ctx->blocks_since_refresh >= ctx->params.refresh_every) {
       ctaux_status r = do_refresh<T>(ctx, -1, st);
@@ -346,6 +362,7 @@ ctaux_status ctaux_init(const ctaux_params* params, ctaux_ctx** out) {
   if (params->precision != CTAUX_FP64 && params->precision != CTAUX_MIXED) return CTAUX_EINVAL;
   if (params->p_insert < 0 || params->p_flip < 0 || params->p_insert + params->p_flip > 1.0)
     return CTAUX_EINVAL;
+  if (!(params->tie_guard >= 0.0) || params->tie_guard >= 1.0) return CTAUX_EINVAL;
   if (params->n_tau_bins < 1 || params->n_anchors < 1 || params->n_anchors > 64 ||
       params->trace_capacity < 0 || params->refresh_every < 0)
     return CTAUX_EINVAL;

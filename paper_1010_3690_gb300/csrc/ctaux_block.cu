@@ -41,6 +41,16 @@ __global__ void __launch_bounds__(256) k_plan(Chain<T>* chains) {
     if (j == 0) atomicOr(&d.status, DS_CAPACITY);
     return;
   }
+  if (j < c.k_max) {
+    BlockDraw bd;
+    bd.u_acc = dr.u_acc;
+    bd.u_idx = dr.u_idx;
+    bd.move = (int8_t)move_of(dr.u_move, c.p_insert, c.p_remove);
+    bd.s_new = (int8_t)((dr.u_spin < 0.5) ? 1 : -1);
+    bd.slot = is_ins ? n + scan[j] - 1 : -1;
+    bd.pad = 0;
+    c.draws[j] = bd;
+  }
   if (is_ins) {
     const int slot = n + scan[j] - 1;
     int site = (int)floor(dr.u_site * (double)c.n_c);
@@ -432,6 +442,7 @@ __global__ void __launch_bounds__(256) k_proposals(Chain<T>* chains, int gamma_i
   __shared__ int n_cur, sign_s;
   __shared__ long long cnt_prop[3], cnt_acc[3], numeric, ties;
   __shared__ double flops;
+  __shared__ BlockDraw bd_s[kMaxK];
 
   for (int i = tid; i < m; i += 256) pmap[i] = -1;
   for (int w = tid; w < n_words; w += 256) {
@@ -451,20 +462,20 @@ __global__ void __launch_bounds__(256) k_proposals(Chain<T>* chains, int gamma_i
     ties = 0;
     flops = 0.0;
   }
+  for (int e = tid; e < KM; e += 256) bd_s[e] = c.draws[e];
   __syncthreads();
+  int consumed = KM;
 
-  int ins_count = 0;
   for (int jj = 0; jj < KM; ++jj) {
     const int64_t t = t0 + jj;
-    const Draws dr = draw(c.seed, c.chain_id, t);
-    const int move = move_of(dr.u_move, c.p_insert, c.p_remove);
+    const BlockDraw dr = bd_s[jj];
+    const int move = dr.move;
     const int nc = n_cur;
     int p = -1, s_new = 0;
     double f = 0.0;
     if (move == MV_INSERT) {
-      p = n_old + ins_count;
-      ++ins_count;
-      s_new = (dr.u_spin < 0.5) ? 1 : -1;
+      p = dr.slot;
+      s_new = dr.s_new;
       f = c.K / (double)(nc + 1);
     } else if (nc > 0) {
       int idx = (int)floor(dr.u_idx * (double)nc);
@@ -509,29 +520,41 @@ __global__ void __launch_bounds__(256) k_proposals(Chain<T>* chains, int gamma_i
       __syncthreads();
       // y = Gamma^{-1} s (threads 0..63 of the half, one row each) and
       // z = w^T Gamma^{-1} (threads 64..127, one column each), concurrently
+      // (two accumulators per dot product for instruction-level parallelism;
+      // the y threads also form their part of w . y)
       if (ht < 64) {
+        A part = (A)0;
         for (int r = ht; r < j; r += 64) {
-          A acc = (A)0;
+          A a0 = (A)0, a1 = (A)0;
           const T* Gr = G + (size_t)r * LG;
-          for (int cc = 0; cc < j; ++cc) acc += (A)Gr[cc] * sv[cc];
-          yv[r] = acc;
+          int cc = 0;
+          for (; cc + 1 < j; cc += 2) {
+            a0 += (A)Gr[cc] * sv[cc];
+            a1 += (A)Gr[cc + 1] * sv[cc + 1];
+          }
+          if (cc < j) a0 += (A)Gr[cc] * sv[cc];
+          const A y = a0 + a1;
+          yv[r] = y;
+          part += wv[r] * y;
         }
+        part = warp_sum_t(part);
+        if (lane == 0) red[half][hw] = part;
       } else {
         for (int cc = ht - 64; cc < j; cc += 64) {
-          A acc = (A)0;
-          for (int r = 0; r < j; ++r) acc += wv[r] * (A)G[(size_t)r * LG + cc];
-          zv[cc] = acc;
+          A a0 = (A)0, a1 = (A)0;
+          int r = 0;
+          for (; r + 1 < j; r += 2) {
+            a0 += wv[r] * (A)G[(size_t)r * LG + cc];
+            a1 += wv[r + 1] * (A)G[(size_t)(r + 1) * LG + cc];
+          }
+          if (r < j) a0 += wv[r] * (A)G[(size_t)r * LG + cc];
+          zv[cc] = a0 + a1;
         }
       }
       __syncthreads();
-      A part = (A)0;
-      for (int r = ht; r < j; r += 128) part += wv[r] * yv[r];
-      part = warp_sum_t(part);
-      if (lane == 0) red[half][hw] = part;
-      __syncthreads();
       if (ht == 0) {
         const A dd = gpp_s[half] - ((A)1 + lam_a) / lam_a;
-        const A beta = dd - (red[half][0] + red[half][1] + red[half][2] + red[half][3]);
+        const A beta = dd - (red[half][0] + red[half][1]);
         beta_s[half] = (double)beta;
         ratio_s[half] = (double)(-lam_a * beta);
       }
@@ -556,6 +579,18 @@ __global__ void __launch_bounds__(256) k_proposals(Chain<T>* chains, int gamma_i
     bool accept = dr.u_acc < pacc;
     const bool finite = isfinite(R);
     if (!finite) accept = false;
+    if (sizeof(T) == 4 && c.tie_guard > 0.0 && finite &&
+        fabs(dr.u_acc - pacc) < c.tie_guard * fmax(dr.u_acc, pacc)) {
+      // near tie in the float32 form: the block ends before this proposal,
+      // which is decided in FP64 after the flush (k_tie_eval)
+      if (tid == 0) {
+        d.tie_pending = 1;
+        d.tie_jj = jj;
+        ties++;
+      }
+      consumed = jj;
+      break;
+    }
     if (tid == 0) {
       cnt_prop[move]++;
       // algorithmic flops, both spins: y and z GEMVs and the dot (first touch),
@@ -565,7 +600,9 @@ __global__ void __launch_bounds__(256) k_proposals(Chain<T>* chains, int gamma_i
       if (accept) fl += (q < 0) ? 3.0 * (jd + 1.0) * (jd + 1.0) : 3.0 * jd * jd;
       flops += 2.0 * fl;
       if (!finite) numeric++;
-      if (sizeof(T) == 4 && finite && fabs(dr.u_acc - pacc) < kTieGuard * fmax(dr.u_acc, pacc)) ties++;
+      if (sizeof(T) == 4 && c.tie_guard == 0.0 && finite &&
+          fabs(dr.u_acc - pacc) < kTieGuard * fmax(dr.u_acc, pacc))
+        ties++;  // detection only (FP64 re-evaluation off)
       if (c.trace_cap > 0) {
         TraceRec& rr = c.trace[(d.trace_written + jj) % c.trace_cap];
         rr.t = t; rr.move = move; rr.n = nc;
@@ -674,7 +711,7 @@ __global__ void __launch_bounds__(256) k_proposals(Chain<T>* chains, int gamma_i
     d.numeric_rejects += numeric;
     d.near_ties += ties;
     d.work_gamma += flops;
-    if (c.trace_cap > 0) d.trace_written += KM;
+    if (c.trace_cap > 0) d.trace_written += consumed;
   }
 }
 
@@ -828,8 +865,125 @@ __global__ void k_finish_block(Chain<T>* chains, int n_chains) {
   d.bytes_flush += 2.0 * (2.0 * nn * nn + 2.0 * nn * ka) * sizeof(T);
   d.n = d.n_new;
   d.buf = 1 - d.buf;
-  d.t += c.k_max;
+  d.t += (d.tie_pending == 1) ? d.tie_jj : c.k_max;
   d.sweeps += 1;
+}
+
+// ------------------------------------------------- FP64 near-tie decision
+// Mixed form: the proposal d.t that the float32 block stopped at is decided
+// from the FP64 N of the tie refresh (N64), with the first-touch formula
+// ratio_sigma = 1 + lambda (1 - G_pp) (Eq. Akp1Ak, reading C2):
+//   removal / flip of slot p: G_pp = (N_pp e^{V_p} - 1) / (e^{V_p} - 1) (Eq. NfromG);
+//   insertion of a vertex p:  G_pp = G0(p,p) + sum_l G0(p,l)(e^{V_l}-1) (N g)_l,
+//                             g_k = G0(k,p) (the s=0 row of N_ext, Sec. IV A).
+// The proposal is applied to the configuration; an accepted one asks for a
+// rebuild of N (tie_pending = 2).  One CTA per chain.
+__global__ void __launch_bounds__(256) k_tie_eval(Chain<float>* chains) {
+  const Chain<float>& c = chains[blockIdx.x];
+  Dyn& d = *c.dyn;
+  if (d.status || d.tie_pending != 1) return;
+  const int n = d.n, buf = d.buf, ld = c.ld;
+  const int64_t t = d.t;
+  const Draws dr = draw(c.seed, c.chain_id, t);
+  const int move = move_of(dr.u_move, c.p_insert, c.p_remove);
+  double* tau = c.tau[buf];
+  int* site = c.site[buf];
+  int8_t* sv = c.s[buf];
+  int64_t* birth = c.birth[buf];
+  __shared__ double red[8];
+  __shared__ double ratio_s[2];
+  int p = -1, s_new = 0;
+  double f = 0.0, tau_new = 0.0;
+  int site_new = 0;
+  if (move == MV_INSERT) {
+    tau_new = dr.u_tau * c.beta;
+    site_new = (int)floor(dr.u_site * (double)c.n_c);
+    if (site_new > c.n_c - 1) site_new = c.n_c - 1;
+    s_new = (dr.u_spin < 0.5) ? 1 : -1;
+    f = c.K / (double)(n + 1);
+  } else if (n > 0) {
+    int idx = (int)floor(dr.u_idx * (double)n);
+    if (idx > n - 1) idx = n - 1;
+    p = idx;
+    s_new = (move == MV_REMOVE) ? 0 : -(int)sv[p];
+    f = (move == MV_REMOVE) ? (double)n / c.K : 1.0;
+  }
+  const bool none = (move != MV_INSERT && n == 0);
+  for (int spin = 0; spin < 2 && !none; ++spin) {
+    const double* N64 = c.N64[spin];
+    double gpp, lam;
+    if (move == MV_INSERT) {
+      double* gvec = c.work + (size_t)spin * ((size_t)ld * ld + (size_t)96 * ld);  // scratch
+      for (int k = threadIdx.x; k < n; k += blockDim.x)
+        gvec[k] = g0_eval(c, spin, tau[k], site[k], tau_new, site_new);
+      __syncthreads();
+      double part = 0.0;
+      for (int l = threadIdx.x; l < n; l += blockDim.x) {
+        double v = 0.0;
+        for (int k = 0; k < n; ++k) v += N64[(size_t)k * ld + l] * gvec[k];
+        part += g0_eval(c, spin, tau_new, site_new, tau[l], site[l]) * (c.ev[spin][sv[l] + 2] - 1.0) * v;
+      }
+      part = warp_sum(part);
+      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+      __syncthreads();
+      double tot = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+      gpp = g0_eval(c, spin, tau_new, site_new, tau_new, site_new) + tot;
+      lam = c.ev[spin][s_new + 2] - 1.0;
+      __syncthreads();
+    } else {
+      const int k = sv[p] + 2;
+      gpp = (N64[(size_t)p * ld + p] * c.ev[spin][k] - 1.0) * c.inv_em1[spin][k];
+      lam = c.ev[spin][s_new - sv[p] + 2] - 1.0;
+    }
+    if (threadIdx.x == 0) ratio_s[spin] = 1.0 + lam * (1.0 - gpp);
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  const double R = none ? 0.0 : f * ratio_s[0] * ratio_s[1];
+  const bool finite = isfinite(R);
+  const bool accept = !none && finite && dr.u_acc < fmin(1.0, fabs(R));
+  d.proposals[move] += 1;
+  if (accept) d.accepted[move] += 1;
+  if (!finite) d.numeric_rejects += 1;
+  if (c.trace_cap > 0) {
+    TraceRec& rr = c.trace[d.trace_written % c.trace_cap];
+    rr.t = t; rr.move = move; rr.n = n;
+    rr.birth = none ? -1 : (move == MV_INSERT ? t : birth[p]);
+    rr.s_new = none ? 0 : s_new;
+    rr.accept = (accept ? 1 : 0) | 2;  // bit 1: decided in FP64
+    rr.ratio[0] = none ? 0.0 : ratio_s[0];
+    rr.ratio[1] = none ? 0.0 : ratio_s[1];
+    rr.R = R;
+    rr.u = dr.u_acc;
+    d.trace_written += 1;
+  }
+  if (accept) {
+    if (R < 0.0) d.sign = -d.sign;
+    if (move == MV_INSERT) {
+      tau[n] = tau_new;
+      site[n] = site_new;
+      sv[n] = (int8_t)s_new;
+      birth[n] = t;
+      d.n = n + 1;
+    } else if (move == MV_REMOVE) {
+      for (int q = p; q + 1 < n; ++q) {
+        tau[q] = tau[q + 1];
+        site[q] = site[q + 1];
+        sv[q] = sv[q + 1];
+        birth[q] = birth[q + 1];
+      }
+      d.n = n - 1;
+    } else {
+      sv[p] = (int8_t)s_new;
+    }
+  }
+  d.t = t + 1;
+  d.tie_pending = accept ? 2 : 0;
+}
+
+void launch_tie_eval(Chain<float>* dchains, const LaunchShape& ls, cudaStream_t st) {
+  k_tie_eval<<<ls.n_chains, 256, 0, st>>>(dchains);
 }
 
 __global__ void k_philox_test(uint64_t seed, uint32_t chain, int64_t t0, int count, int purpose,

@@ -38,6 +38,16 @@ struct TraceRec {  // layout of ctaux_trace_rec
   double u;
 };
 
+// The block's proposals, drawn once by the plan kernel (Philox counter t0 + j).
+struct BlockDraw {
+  double u_acc;    // Metropolis uniform
+  double u_idx;    // vertex choice of a removal or flip
+  int32_t slot;    // insertion: slot of the pre-inserted vertex; else -1
+  int8_t move;     // MV_*
+  int8_t s_new;    // insertion: proposed auxiliary spin (+1 / -1)
+  int16_t pad;
+};
+
 struct Dyn {
   int n;        // interacting vertices (slots [0, n) after a flush)
   int m;        // n + k_ins during a block
@@ -62,6 +72,8 @@ struct Dyn {
   double work_flush;      // algorithmic flops of the flush products
   double bytes_flush;     // algorithmic bytes of the flush (N read + N' written)
   double work_gamma;      // algorithmic flops of the Gamma growth (both spins)
+  int tie_pending;        // mixed form: 1 = proposal d.t awaits an FP64 decision, 2 = N needs a rebuild
+  int tie_jj;             // index in the block of the near-tie proposal
 };
 
 template <typename T>
@@ -76,6 +88,8 @@ struct Chain {
   int trace_cap;
   int n_bins, n_anchors;
   int kp;                    // mixed form: k_max rounded up to 32 (split operand row length)
+  double tie_guard;          // mixed form: relative guard band of the FP64 re-evaluation (0 = off)
+  double* N64[2];            // mixed form: FP64 N of a tie refresh [spin], ld x ld
   const double* g0;          // [2][n_classes][n_tau]
   const int* dx_class;       // [n_c][n_c]
   const double* class_weight;  // [n_classes] 1/(n_anchors * #sites of the class)
@@ -92,6 +106,7 @@ struct Chain {
   double* lam[2];
   int* P;
   int* S;
+  BlockDraw* draws;          // [k_max] proposals of the current block
   T* Y[2];
   T* Mg[2];                  // measurement: g_b columns, ld x n_anchors
   T* Mv[2];                  // measurement: v_b = N g_b, ld x n_anchors

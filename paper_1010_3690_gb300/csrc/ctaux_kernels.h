@@ -9,7 +9,7 @@ namespace ctaux {
 
 // Fixed launch shapes of one context (derived from capacities at init, so
 // that a sweep needs no host-side knowledge of the current orders).
-constexpr int kMeasChunk = 64;  // vertices per measurement evaluation chunk
+constexpr int kMeasChunk = 32;  // vertices per measurement evaluation chunk
 
 // tensor-core flush (mixed form): 128 x 128 output tiles, K chunks of 32 float32
 constexpr int kTcBM = 128, kTcBN = 128, kTcBK = 32, kTcStages = 1, kTcThreads = 256;
@@ -107,7 +107,8 @@ template <typename T>
 void launch_measure(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t st, PhaseTimer* pt);
 template <typename T>
 cudaError_t launch_refresh(Chain<T>* dchains, const LaunchShape& ls, int only_chain,
-                           cudaStream_t st, PhaseTimer* pt);
+                           cudaStream_t st, PhaseTimer* pt, int filter = 0);
+void launch_tie_eval(Chain<float>* dchains, const LaunchShape& ls, cudaStream_t st);
 template <typename T>
 void launch_reset_measure(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t st);
 int tc_smem_bytes();

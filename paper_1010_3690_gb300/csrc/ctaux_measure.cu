@@ -31,14 +31,33 @@ __global__ void __launch_bounds__(256) k_meas_gather(Chain<T>* chains) {
   }
 }
 
-// One thread per evaluation point (anchor, site, bin) and chunk of kMeasChunk
-// vertices; partial sums go to Mpts[spin][chunk][point].  Persistent over the
-// (chain, spin, point block, chunk) items of all chains.
+// Evaluation of the estimator, persistent over the (chain, spin, point block,
+// vertex chunk) items of all chains; partial sums over a chunk of kMeasChunk
+// vertices go to Mpts[spin][chunk][(anchor * N_c + site) * B + bin].
+//
+// When the number of bins B is a multiple of the number of anchors A, every
+// evaluation time tau_b + tau_c (folded into [0, beta)) is one of the B points
+// tau_p = (p + 1/2) beta / B, shifted by B/A points per anchor.  A thread then
+// owns a (site, tau_p) point, interpolates G0(a, l) once per vertex l and
+// accumulates it for all A anchors (anchor b reads bin (p - b B/A) mod B, with
+// the antiperiodic sign when the fold wrapped).  Otherwise a thread owns one
+// (anchor, site, bin) point.
+constexpr int kMaxSharedAnchors = 16;
+
+template <typename T>
+__device__ __forceinline__ bool meas_shared(const Chain<T>& c) {
+  return c.n_anchors <= kMaxSharedAnchors && (c.n_bins % c.n_anchors) == 0;
+}
+
+template <typename T>
+__device__ __forceinline__ int meas_points(const Chain<T>& c) {
+  return (meas_shared(c) ? 1 : c.n_anchors) * c.n_c * c.n_bins;
+}
+
 template <typename T>
 __device__ __forceinline__ int meas_items(const Chain<T>& c, const Dyn& d) {
   if (d.status) return 0;
-  const int npts = c.n_anchors * c.n_c * c.n_bins;
-  return 2 * ((npts + 255) / 256) * max(1, (d.n + kMeasChunk - 1) / kMeasChunk);
+  return 2 * ((meas_points(c) + 255) / 256) * max(1, (d.n + kMeasChunk - 1) / kMeasChunk);
 }
 
 template <typename T>
@@ -54,14 +73,56 @@ __global__ void __launch_bounds__(256) k_meas_eval(Chain<T>* chains, int n_chain
     const Chain<T>& c = chains[ci];
     const Dyn& d = *c.dyn;
     const int n = d.n, buf = d.buf, A = c.n_anchors, B = c.n_bins;
-    const int npts = A * c.n_c * B;
+    const int npts_out = A * c.n_c * B;
+    const int npts = meas_points(c);
     const int pblocks = (npts + 255) / 256, nchunks = max(1, (n + kMeasChunk - 1) / kMeasChunk);
     const int l = w - off[ci];
     const int spin = l / (pblocks * nchunks), r0 = l % (pblocks * nchunks);
     const int chunk = r0 / pblocks;
-    const int l0 = chunk * kMeasChunk;
+    const int l0 = chunk * kMeasChunk, l1 = min(n, l0 + kMeasChunk);
     const int pt = (r0 % pblocks) * blockDim.x + threadIdx.x;
     if (pt >= npts) continue;
+    const double* tau = c.tau[buf];
+    const int* site = c.site[buf];
+    const int8_t* s = c.s[buf];
+    double* out = c.Mpts[spin] + (size_t)chunk * npts_out;
+    if (meas_shared(c)) {
+      const int p = pt % B, xa = pt / B, shift = B / A;
+      const double tp = ((double)p + 0.5) * c.beta / (double)B;
+      double acc[kMaxSharedAnchors];
+#pragma unroll
+      for (int b = 0; b < kMaxSharedAnchors; ++b) acc[b] = 0.0;
+      if (sizeof(T) == 8) {
+        for (int q = l0; q < l1; ++q) {
+          const double g = g0_eval(c, spin, tp, xa, tau[q], site[q]) * (c.ev[spin][s[q] + 2] - 1.0);
+#pragma unroll
+          for (int b = 0; b < kMaxSharedAnchors; ++b)
+            if (b < A) acc[b] += g * (double)c.Mv[spin][(long)b * c.ld + q];
+        }
+      } else {  // mixed form: float32 interpolation and products
+        float accf[kMaxSharedAnchors];
+#pragma unroll
+        for (int b = 0; b < kMaxSharedAnchors; ++b) accf[b] = 0.f;
+        const float tpf = (float)tp;
+        for (int q = l0; q < l1; ++q) {
+          const float g = g0_eval_f(c, spin, tpf, xa, (float)tau[q], site[q]) *
+                          ((float)c.ev[spin][s[q] + 2] - 1.f);
+#pragma unroll
+          for (int b = 0; b < kMaxSharedAnchors; ++b)
+            if (b < A) accf[b] += g * (float)c.Mv[spin][(long)b * c.ld + q];
+        }
+#pragma unroll
+        for (int b = 0; b < kMaxSharedAnchors; ++b) acc[b] = (double)accf[b];
+      }
+      for (int b = 0; b < A; ++b) {
+        const int i = (p - b * shift + B) % B;
+        const double sg = (p < b * shift) ? -1.0 : 1.0;
+        double val = acc[b];
+        if (chunk == 0) val += g0_eval(c, spin, tp, xa, (double)b * c.beta / (double)A, 0);
+        out[((size_t)b * c.n_c + xa) * B + i] = sg * val;
+      }
+      continue;
+    }
     const int bin = pt % B, xa = (pt / B) % c.n_c, b = pt / (B * c.n_c);
     const double tb = (double)b * c.beta / (double)A;
     const double tc = ((double)bin + 0.5) * c.beta / (double)B;
@@ -71,26 +132,22 @@ __global__ void __launch_bounds__(256) k_meas_eval(Chain<T>* chains, int n_chain
       sg = -1.0;
     }
     double val = (chunk == 0) ? g0_eval(c, spin, ta, xa, tb, 0) : 0.0;
-    const double* tau = c.tau[buf];
-    const int* site = c.site[buf];
-    const int8_t* s = c.s[buf];
     const T* V = c.Mv[spin] + (long)b * c.ld;  // v_b = N g_b
-    const int l1 = min(n, l0 + kMeasChunk);
     if (sizeof(T) == 8) {
       for (int q = l0; q < l1; ++q) {
         const double vl = (c.ev[spin][s[q] + 2] - 1.0) * (double)V[q];
         val += g0_eval(c, spin, ta, xa, tau[q], site[q]) * vl;
       }
     } else {  // mixed form: float32 interpolation and products
-      float acc = 0.f;
+      float accf = 0.f;
       const float taf = (float)ta;
       for (int q = l0; q < l1; ++q) {
         const float vl = ((float)c.ev[spin][s[q] + 2] - 1.f) * (float)V[q];
-        acc += g0_eval_f(c, spin, taf, xa, (float)tau[q], site[q]) * vl;
+        accf += g0_eval_f(c, spin, taf, xa, (float)tau[q], site[q]) * vl;
       }
-      val += (double)acc;
+      val += (double)accf;
     }
-    c.Mpts[spin][(size_t)chunk * npts + pt] = sg * val;
+    out[pt] = sg * val;
   }
 }
 

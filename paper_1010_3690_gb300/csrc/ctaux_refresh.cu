@@ -41,7 +41,8 @@ __host__ __device__ inline size_t refresh_work_per_spin(int ld) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_refresh(Chain<T>* chains, int n_chains, int only_chain) {
+__global__ void __launch_bounds__(256) k_refresh(Chain<T>* chains, int n_chains, int only_chain,
+                                                 int filter) {
   cg::grid_group grid = cg::this_grid();
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
   const int gthreads = gridDim.x * blockDim.x;
@@ -55,7 +56,7 @@ __global__ void __launch_bounds__(256) k_refresh(Chain<T>* chains, int n_chains,
   for (int ci = c_lo; ci < c_hi; ++ci) {
     const Chain<T>& c = chains[ci];
     const Dyn& d = *c.dyn;
-    if (d.status & ~DS_SINGULAR) continue;
+    if ((d.status & ~DS_SINGULAR) || (filter && d.tie_pending != filter)) continue;
     const int m = d.n, buf = d.buf, ld = c.ld;
     max_m = max(max_m, m);
     if (gtid == 0) c.work_logdet[0] = c.work_logdet[1] = 0.0;
@@ -83,7 +84,7 @@ __global__ void __launch_bounds__(256) k_refresh(Chain<T>* chains, int n_chains,
     for (int ci = c_lo; ci < c_hi; ++ci) {
       const Chain<T>& c = chains[ci];
       const Dyn& d = *c.dyn;
-      if (d.status & ~DS_SINGULAR) continue;
+      if ((d.status & ~DS_SINGULAR) || (filter && d.tie_pending != filter)) continue;
       const int m = d.n, ld = c.ld;
       if (c0 >= m) continue;
       const int bw = min(kPB, m - c0);
@@ -102,7 +103,7 @@ __global__ void __launch_bounds__(256) k_refresh(Chain<T>* chains, int n_chains,
       for (int ci = c_lo; ci < c_hi; ++ci) {
         const Chain<T>& c = chains[ci];
         const Dyn& d = *c.dyn;
-        if (d.status & ~DS_SINGULAR) continue;
+        if ((d.status & ~DS_SINGULAR) || (filter && d.tie_pending != filter)) continue;
         const int m = d.n, ld = c.ld;
         if (c0 + k >= m) continue;
         const int bw = min(kPB, m - c0), col = c0 + k;
@@ -143,7 +144,7 @@ __global__ void __launch_bounds__(256) k_refresh(Chain<T>* chains, int n_chains,
     for (int ci = c_lo; ci < c_hi; ++ci) {
       const Chain<T>& c = chains[ci];
       const Dyn& d = *c.dyn;
-      if (d.status & ~DS_SINGULAR) continue;
+      if ((d.status & ~DS_SINGULAR) || (filter && d.tie_pending != filter)) continue;
       const int m = d.n, ld = c.ld;
       if (c0 >= m) continue;
       const int bw = min(kPB, m - c0);
@@ -163,7 +164,7 @@ __global__ void __launch_bounds__(256) k_refresh(Chain<T>* chains, int n_chains,
     for (int ci = c_lo; ci < c_hi; ++ci) {
       const Chain<T>& c = chains[ci];
       const Dyn& d = *c.dyn;
-      if (d.status & ~DS_SINGULAR) continue;
+      if ((d.status & ~DS_SINGULAR) || (filter && d.tie_pending != filter)) continue;
       const int m = d.n, ld = c.ld;
       if (c0 >= m) continue;
       const int bw = min(kPB, m - c0), cn = c0 + bw;
@@ -217,17 +218,19 @@ __global__ void __launch_bounds__(256) k_refresh(Chain<T>* chains, int n_chains,
   for (int ci = c_lo; ci < c_hi; ++ci) {
     const Chain<T>& c = chains[ci];
     Dyn& d = *c.dyn;
-    if (d.status & ~DS_SINGULAR) continue;
+    if ((d.status & ~DS_SINGULAR) || (filter && d.tie_pending != filter)) continue;
     const int m = d.n, ld = c.ld, buf = d.buf;
     for (int spin = 0; spin < 2; ++spin) {
       const double* X = c.work + (size_t)spin * refresh_work_per_spin(ld);
       const int* perm = c.perm + spin * ld;
       T* Nr = c.N[buf][spin];
+      double* N64 = (filter == 1) ? c.N64[spin] : nullptr;
       for (int j = blockIdx.x; j < m; j += gridDim.x) {
         const int pj = perm[j];
         for (int cc = threadIdx.x; cc < m; cc += blockDim.x) {
           const double v = X[(size_t)j * ld + perm[cc]];  // N[cc][perm[j]]
           const long o = (long)pj * ld + cc;
+          if (N64) N64[o] = v;
           const double diff = fabs((double)Nr[o] - v);
           if (diff > 0.0) {
             atomicMax(reinterpret_cast<unsigned long long*>(&c.work_drift[0]),
@@ -282,12 +285,12 @@ __device__ __forceinline__ void block_argmax(double v, int row, double* rv, int*
 }
 
 template <typename T>
-__global__ void __launch_bounds__(512) k_refresh_cta(Chain<T>* chains, int n_chains) {
+__global__ void __launch_bounds__(512) k_refresh_cta(Chain<T>* chains, int n_chains, int filter) {
   const int ci = blockIdx.x >> 1, spin = blockIdx.x & 1;
   if (ci >= n_chains) return;
   const Chain<T>& c = chains[ci];
   Dyn& d = *c.dyn;
-  if (d.status & ~DS_SINGULAR) return;
+  if ((d.status & ~DS_SINGULAR) || (filter && d.tie_pending != filter)) return;
   const int m = d.n, ld = c.ld, buf = d.buf;
   double* X = c.work + (size_t)spin * refresh_work_per_spin(ld);
   double* Rr = X + (size_t)ld * ld;       // pivot rows of the current panel, [j][k]
@@ -387,12 +390,14 @@ __global__ void __launch_bounds__(512) k_refresh_cta(Chain<T>* chains, int n_cha
   }
   // unscramble, drift, replace
   T* Nr = c.N[buf][spin];
+  double* N64 = (filter == 1) ? c.N64[spin] : nullptr;
   double dmax = 0.0, dsq = 0.0;
   for (int j = 0; j < m; ++j) {
     const int pj = perm[j];
     for (int cc = threadIdx.x; cc < m; cc += blockDim.x) {
       const double v = X[(size_t)j * ld + perm[cc]];
       const long o = (long)pj * ld + cc;
+      if (N64) N64[o] = v;
       const double diff = fabs((double)Nr[o] - v);
       dmax = fmax(dmax, diff);
       dsq += diff * diff;
@@ -414,43 +419,45 @@ __global__ void __launch_bounds__(512) k_refresh_cta(Chain<T>* chains, int n_cha
 
 // Small follow-up kernel: permutation signs, log det, drift into the stats.
 template <typename T>
-__global__ void k_refresh_finish(Chain<T>* chains, int n_chains, int only_chain) {
+__global__ void k_refresh_finish(Chain<T>* chains, int n_chains, int only_chain, int filter) {
   const int ci = (only_chain >= 0) ? only_chain : (int)(blockIdx.x * blockDim.x + threadIdx.x);
   if (ci >= n_chains) return;
   if (only_chain >= 0 && (blockIdx.x | threadIdx.x)) return;
   const Chain<T>& c = chains[ci];
   Dyn& d = *c.dyn;
-  if (d.status & ~DS_SINGULAR) return;
+  if ((d.status & ~DS_SINGULAR) || (filter && d.tie_pending != filter)) return;
   d.refreshes += 1;
   d.drift_max = c.work_drift[0];
   d.drift_fro = sqrt(c.work_drift[1]);
   c.work_drift[0] = 0.0;
   c.work_drift[1] = 0.0;
   for (int spin = 0; spin < 2; ++spin) d.logdet[spin] = c.work_logdet[spin];
+  if (filter == 2) d.tie_pending = 0;
 }
 
 template <typename T>
 cudaError_t launch_refresh(Chain<T>* dchains, const LaunchShape& ls, int only_chain,
-                           cudaStream_t st, PhaseTimer* pt) {
+                           cudaStream_t st, PhaseTimer* pt, int filter) {
   pt->begin(6, st);
   int nch = ls.n_chains;
   cudaError_t e = cudaSuccess;
   if (only_chain < 0 && ls.refresh_per_cta) {
-    k_refresh_cta<T><<<2 * nch, 512, ls.refresh_cta_smem, st>>>(dchains, nch);
+    k_refresh_cta<T><<<2 * nch, 512, ls.refresh_cta_smem, st>>>(dchains, nch, filter);
     e = cudaGetLastError();
-    if (e == cudaSuccess) k_refresh_finish<T><<<(nch + 127) / 128, 128, 0, st>>>(dchains, nch, -1);
+    if (e == cudaSuccess)
+      k_refresh_finish<T><<<(nch + 127) / 128, 128, 0, st>>>(dchains, nch, -1, filter);
     e = cudaGetLastError();
     pt->end(6, st, 2);
     return e;
   }
-  void* args[] = {&dchains, &nch, &only_chain};
-  e = cudaLaunchCooperativeKernel((const void*)k_refresh<T>, dim3(ls.refresh_grid),
-                                  dim3(256), args, 0, st);
+  void* args[] = {&dchains, &nch, &only_chain, &filter};
+  e = cudaLaunchCooperativeKernel((const void*)k_refresh<T>, dim3(ls.refresh_grid), dim3(256),
+                                  args, 0, st);
   if (e == cudaSuccess) {
     if (only_chain >= 0)
-      k_refresh_finish<T><<<1, 1, 0, st>>>(dchains, nch, only_chain);
+      k_refresh_finish<T><<<1, 1, 0, st>>>(dchains, nch, only_chain, filter);
     else
-      k_refresh_finish<T><<<(nch + 127) / 128, 128, 0, st>>>(dchains, nch, -1);
+      k_refresh_finish<T><<<(nch + 127) / 128, 128, 0, st>>>(dchains, nch, -1, filter);
     e = cudaGetLastError();
   }
   pt->end(6, st, 2);
@@ -472,9 +479,9 @@ int refresh_blocks_per_sm() {
 }
 
 template cudaError_t launch_refresh<double>(Chain<double>*, const LaunchShape&, int, cudaStream_t,
-                                            PhaseTimer*);
+                                            PhaseTimer*, int);
 template cudaError_t launch_refresh<float>(Chain<float>*, const LaunchShape&, int, cudaStream_t,
-                                           PhaseTimer*);
+                                           PhaseTimer*, int);
 size_t refresh_work_doubles(int ld) { return 2 * refresh_work_per_spin(ld); }
 
 template int refresh_blocks_per_sm<double>();

@@ -35,7 +35,7 @@ class Params(C.Structure):
                 ("p_insert", C.c_double), ("p_flip", C.c_double),
                 ("n_tau_bins", C.c_int), ("n_anchors", C.c_int),
                 ("trace_capacity", C.c_int), ("device", C.c_int),
-                ("mixed_flush_tc", C.c_int)]
+                ("mixed_flush_tc", C.c_int), ("tie_guard", C.c_double)]
 
 
 class Stats(C.Structure):
@@ -153,7 +153,8 @@ class Context:
     """
 
     def __init__(self, chains, precision=CTAUX_FP64, refresh_every=32, p_insert=0.5, p_flip=0.0,
-                 n_tau_bins=32, n_anchors=4, trace_capacity=0, device=0, mixed_flush_tc=1):
+                 n_tau_bins=32, n_anchors=4, trace_capacity=0, device=0, mixed_flush_tc=1,
+                 tie_guard=1e-4):
         self._keep = []
         cps = (ChainParams * len(chains))()
         self.chain_inputs = list(chains)
@@ -166,7 +167,8 @@ class Context:
                                  int(ch.k_max), int(ch.capacity), int(ch.seed),
                                  int(ch.chain_id))
         self.params = Params(len(chains), cps, precision, refresh_every, p_insert, p_flip,
-                             n_tau_bins, n_anchors, trace_capacity, device, mixed_flush_tc)
+                             n_tau_bins, n_anchors, trace_capacity, device, mixed_flush_tc,
+                             tie_guard)
         self.n_tau_bins = n_tau_bins
         self.trace_capacity = trace_capacity
         h = C.c_void_p()

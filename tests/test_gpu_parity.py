@@ -280,3 +280,33 @@ def test_refresh_inverse_at_panel_edges(n, precision):
             np.testing.assert_allclose(ctx.get_N(0, spin), No, rtol=tol, atol=tol * np.abs(No).max())
             assert st["logdet"][spin] == pytest.approx(oc.slogdet(spin, oc.tau, oc.site, oc.s)[1],
                                                        rel=1e-11, abs=1e-9)
+
+
+def test_mixed_near_ties_are_decided_in_fp64():
+    """Float32 ratios at K=1 on the 2x2x2 cluster carry ~1% error; with a guard band of
+    0.5 every decision they could get wrong is re-decided from an FP64 refresh, so the
+    whole accept sequence equals the FP64 oracle's and those ratios are FP64-accurate."""
+    ch = configs.cube8(K=1.0, k_max=32, capacity=256)
+    cfg = configs.synthetic_configuration(ch, 140, seed=3)
+    oc = oracle_for(ch)
+    oc.set_config(cfg["tau"], cfg["site"], cfg["s"], cfg["birth"], cfg["t"])
+    with pk.Context([ch], precision=pk.CTAUX_MIXED, trace_capacity=4096, refresh_every=8,
+                    tie_guard=0.5) as ctx:
+        ctx.set_config(0, cfg["tau"], cfg["site"], cfg["s"], cfg["birth"], cfg["t"])
+        ctx.sweep(24)   # each block stops at its first near tie
+        ctx.synchronize()
+        tr = ctx.trace(0)
+        st = ctx.stats(0)
+    recs = oc.run(len(tr))
+    assert st["t"] == oc.t
+    n_fp64 = 0
+    for g, o in zip(tr, recs):
+        assert int(g["t"]) == o["t"] and int(g["move"]) == o["move"]
+        assert int(g["birth"]) == o["birth"]
+        assert bool(int(g["accept"]) & 1) == o["accept"], (g, o)
+        if int(g["accept"]) & 2 and o["birth"] >= 0:
+            n_fp64 += 1
+            for s in (0, 1):
+                ref = o["ratio"][s]
+                assert abs(g["ratio"][s] - ref) <= 1e-9 * max(1.0, abs(ref)), (g, o)
+    assert n_fp64 >= 10 and st["near_ties"] >= n_fp64

@@ -116,13 +116,16 @@ def cube100(K=1.0, k_max=256, capacity=9216, seed=0, chain_id=0):
                          seed=seed, chain_id=chain_id)
 
 
-def batch(n_chains=512, seed=12345, k_max=32, K=1.0, capacity=None, n_tau=1024):
+def batch(n_chains=512, seed=12345, k_max=32, K=None, capacity=None, n_tau=1024):
     """Independent chains of uneven size: N_c in {4,8,16}, beta~U[2,10], U~U[4,10].
 
     Parameters are drawn from a numpy Generator with a fixed seed; beta is
     rounded to a multiple of 0.5 so that chains share G0 tables (17 x 3
     tables instead of one per chain); the Philox seed of chain i is i (the
-    chain id goes into the counter as well).
+    chain id goes into the counter as well).  K=None picks the expansion
+    constant per chain as K = 0.3 beta U N_c + 30, which puts the orders at
+    n ~ K + 0.4 beta U N_c ~ 50..1200 (the batch's named range) and keeps
+    cosh(gamma) = 1 + beta U N_c / (2K) below ~2.7.
     """
     rng = np.random.default_rng(seed)
     chains = []
@@ -130,11 +133,12 @@ def batch(n_chains=512, seed=12345, k_max=32, K=1.0, capacity=None, n_tau=1024):
         n_c = int(rng.choice([4, 8, 16]))
         beta = float(np.round(rng.uniform(2.0, 10.0) * 2.0) / 2.0)
         U = float(np.round(rng.uniform(4.0, 10.0), 3))
+        Ki = float(K) if K is not None else round(0.3 * beta * U * n_c + 30.0, 3)
         cap = capacity
         if cap is None:
             # expected order K + beta U N_c / 2 (no double occupancy) plus headroom
-            cap = int(math.ceil((K + 0.5 * beta * U * n_c) * 1.25 / 32.0)) * 32 + 64
-        chains.append(cluster_chain("batch", n_c, beta, U, K, k_max, cap, n_tau=n_tau,
+            cap = int(math.ceil((Ki + 0.5 * beta * U * n_c) * 1.25 / 32.0)) * 32 + 64
+        chains.append(cluster_chain("batch", n_c, beta, U, Ki, k_max, cap, n_tau=n_tau,
                                     seed=i, chain_id=i))
     return chains
 
