@@ -110,6 +110,8 @@ typedef struct {
   int64_t numeric_rejects;   /* proposals rejected for a non-finite ratio */
   int64_t near_ties;         /* mixed form: decisions within the guard band (tie_guard, or 1e-4
                                 when the FP64 re-evaluation is off) */
+  int64_t tie_refreshes;     /* near ties decided through a from-scratch FP64 refresh because
+                                the iterative refinement did not converge */
   int64_t refreshes;
   double last_drift_max;     /* max |N_run - N_fresh| at the last refresh (both spins) */
   double last_drift_fro;     /* Frobenius norm of the same difference */
@@ -185,8 +187,9 @@ ctaux_status ctaux_get_N(ctaux_ctx *ctx, int chain, int spin, double *out, int l
  * stream while profiling is on, and the number of kernels launched per phase
  * (always counted).  Phases: 0 plan + G0 gather, 1 prep products,
  * 2 proposals (Gamma growth), 3 flush product, 4 flush support (survivor
- * list, Y = (G-1) Gamma^{-1}, end of block), 5 measurement, 6 FP64 refresh.
- * ms_out[7], kernels_out[7]; either may be NULL. */
+ * list, Y = (G-1) Gamma^{-1}, end of block), 5 measurement, 6 FP64 refresh
+ * (periodic, and the fallback of a near-tie decision), 7 near-tie FP64
+ * refinement (mixed form).  ms_out[8], kernels_out[8]; either may be NULL. */
 ctaux_status ctaux_set_profiling(ctaux_ctx *ctx, int on);
 ctaux_status ctaux_get_phase_times(ctaux_ctx *ctx, double *ms_out, int64_t *kernels_out);
 

@@ -24,6 +24,7 @@ struct ctaux_ctx {
   LaunchShape ls{};
   void* chains_dev = nullptr;        // Chain<double>[] or Chain<float>[]
   TcMaps* tc_maps_dev = nullptr;     // mixed form: TMA descriptors [chain][spin]
+  double* tie_part = nullptr;        // mixed form: per-CTA partials of the tie refinement
   std::vector<Chain<double>> hc64;   // host copies of the descriptors
   std::vector<Chain<float>> hc32;
   std::vector<void*> allocations;
@@ -152,6 +153,10 @@ ctaux_status build_chains(ctaux_ctx* ctx) {
   ls.tc_ctas = 2 * ctx->sm_count;
   ls.split_x_blocks = std::max(1, std::min(256, (max_rows + 7) / 8));
   if (mixed_tc) CUDA_TRY(ctx, configure_flush_tc());
+  if (sizeof(T) == 4 && P.tie_guard > 0.0) {
+    ls.tie_grid = std::max(1, tie_refine_blocks_per_sm()) * ctx->sm_count;
+    ctx->tie_part = dalloc<double>(ctx, 2 * (size_t)ls.tie_grid + (size_t)kTieSlices * max_ld, &err);
+  }
   std::vector<TcMaps> host_maps(mixed_tc ? 2 * ctx->chains.size() : 0);
   int nb = refresh_blocks_per_sm<T>();
   ls.refresh_grid = std::max(1, nb) * ctx->sm_count;
@@ -267,6 +272,7 @@ ctaux_status build_chains(ctaux_ctx* ctx) {
     Dyn d0;
     std::memset(&d0, 0, sizeof(d0));
     d0.sign = 1;
+    d0.forced_t = -1;
     CUDA_TRY(ctx, cudaMemcpy(c.dyn, &d0, sizeof(Dyn), cudaMemcpyHostToDevice));
   }
   if (mixed_tc) {
@@ -327,13 +333,16 @@ ctaux_status do_sweeps(ctaux_ctx* ctx, int n_sweeps, int measure, cudaStream_t s
   for (int s = 0; s < n_sweeps; ++s) {
     launch_block<T>(dc, ctx->ls, st, pt, ctx->tc_maps_dev);
     if (ties) {
-      // near-tie decisions in FP64: refresh with an FP64 copy of N, decide,
-      // rebuild N after an accepted move (kernels exit at once without a tie)
-      cudaError_t e = launch_refresh<T>(dc, ctx->ls, -1, st, pt, 1);
+      // near-tie decisions in FP64: iterative refinement against the float32 N;
+      // where it does not converge, a from-scratch FP64 refresh keeping the
+      // FP64 N (kernels exit at once without a pending tie)
+      pt->begin(7, st);
+      cudaError_t e = launch_tie_refine(reinterpret_cast<Chain<float>*>(dc), ctx->ls, ctx->tie_part, st);
+      pt->end(7, st, 1);
+      if (e == cudaSuccess) e = launch_refresh<T>(dc, ctx->ls, -1, st, pt, 1);
       if (e == cudaSuccess) {
         launch_tie_eval(reinterpret_cast<Chain<float>*>(dc), ctx->ls, st);
         pt->kernels[6] += 1;
-        e = launch_refresh<T>(dc, ctx->ls, -1, st, pt, 2);
       }
       if (e != cudaSuccess) return set_err(ctx, CTAUX_ECUDA, "tie refresh launch: %s", cudaGetErrorString(e));
     }
@@ -490,6 +499,7 @@ ctaux_status ctaux_get_stats(ctaux_ctx* ctx, int chain, ctaux_stats* out) {
   out->sign_sum = d.sign_sum;
   out->numeric_rejects = d.numeric_rejects;
   out->near_ties = d.near_ties;
+  out->tie_refreshes = d.tie_refreshes;
   out->refreshes = d.refreshes;
   out->last_drift_max = d.drift_max;
   out->last_drift_fro = d.drift_fro;
@@ -589,6 +599,8 @@ ctaux_status ctaux_set_config(ctaux_ctx* ctx, int chain, const double* tau, cons
   d.n = n;
   d.t = t;
   d.status = 0;
+  d.tie_pending = 0;
+  d.forced_t = -1;
   int sg = 1;
   d.sign = sg;
   CUDA_TRY(ctx, cudaMemcpy(dyn_of(ctx, chain), &d, sizeof(Dyn), cudaMemcpyHostToDevice));

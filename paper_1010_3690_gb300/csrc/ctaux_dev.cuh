@@ -72,8 +72,13 @@ struct Dyn {
   double work_flush;      // algorithmic flops of the flush products
   double bytes_flush;     // algorithmic bytes of the flush (N read + N' written)
   double work_gamma;      // algorithmic flops of the Gamma growth (both spins)
-  int tie_pending;        // mixed form: 1 = proposal d.t awaits an FP64 decision, 2 = N needs a rebuild
+  int tie_pending;        // mixed form: 1 = proposal d.t awaits an FP64 decision
   int tie_jj;             // index in the block of the near-tie proposal
+  int forced_accept;      // FP64 decision of proposal forced_t
+  int64_t forced_t;       // proposal whose decision was taken in FP64 (-1: none)
+  int64_t tie_refreshes;  // near ties decided through a from-scratch refresh (refinement failed)
+  double forced_ratio[2];
+  double forced_R;
 };
 
 template <typename T>

@@ -9,6 +9,7 @@ namespace ctaux {
 
 // Fixed launch shapes of one context (derived from capacities at init, so
 // that a sweep needs no host-side knowledge of the current orders).
+constexpr int kTieSlices = 64;   // column slices of the near-tie matrix-vector products
 constexpr int kMeasChunk = 32;  // vertices per measurement evaluation chunk
 
 // tensor-core flush (mixed form): 128 x 128 output tiles, K chunks of 32 float32
@@ -30,6 +31,7 @@ struct LaunchShape {
   int kstride;           // partial-tile stride per output tile (most slices of any product)
   int persist_ctas;      // grid of the persistent batched kernels
   int refresh_per_cta;   // batched form: one CTA per (chain, spin) for the refresh
+  int tie_grid;          // cooperative grid of the near-tie refinement
   int refresh_cta_smem;
   int y_blocks;
   int prop_smem;
@@ -50,15 +52,15 @@ struct LaunchShape {
 // 6 FP64 refresh.  Events are recorded only while profiling is on; launch
 // counts are always kept.
 struct PhaseTimer {
-  static constexpr int kPhases = 7;
+  static constexpr int kPhases = 8;
   static constexpr int kPool = 1024;
   cudaEvent_t ev[kPool];
   int phase_of[kPool / 2];
   int used = 0;
   int open_slot[kPhases];
-  double ms[kPhases] = {0, 0, 0, 0, 0, 0, 0};
-  long long timed[kPhases] = {0, 0, 0, 0, 0, 0, 0};
-  long long kernels[kPhases] = {0, 0, 0, 0, 0, 0, 0};
+  double ms[kPhases] = {0, 0, 0, 0, 0, 0, 0, 0};
+  long long timed[kPhases] = {0, 0, 0, 0, 0, 0, 0, 0};
+  long long kernels[kPhases] = {0, 0, 0, 0, 0, 0, 0, 0};
   bool created = false;
   bool on = false;
   void begin(int ph, cudaStream_t st) {
@@ -109,6 +111,10 @@ template <typename T>
 cudaError_t launch_refresh(Chain<T>* dchains, const LaunchShape& ls, int only_chain,
                            cudaStream_t st, PhaseTimer* pt, int filter = 0);
 void launch_tie_eval(Chain<float>* dchains, const LaunchShape& ls, cudaStream_t st);
+// part: 2*tie_grid + kTieSlices*max_ld doubles of device scratch
+cudaError_t launch_tie_refine(Chain<float>* dchains, const LaunchShape& ls, double* part,
+                              cudaStream_t st);
+int tie_refine_blocks_per_sm();
 template <typename T>
 void launch_reset_measure(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t st);
 int tc_smem_bytes();

@@ -432,7 +432,6 @@ __global__ void k_refresh_finish(Chain<T>* chains, int n_chains, int only_chain,
   c.work_drift[0] = 0.0;
   c.work_drift[1] = 0.0;
   for (int spin = 0; spin < 2; ++spin) d.logdet[spin] = c.work_logdet[spin];
-  if (filter == 2) d.tie_pending = 0;
 }
 
 template <typename T>

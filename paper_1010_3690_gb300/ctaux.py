@@ -43,6 +43,7 @@ class Stats(C.Structure):
                 ("accepted", C.c_int64 * 3), ("sweeps", C.c_int64), ("measurements", C.c_int64),
                 ("order_sum", C.c_int64), ("sign_sum", C.c_double),
                 ("numeric_rejects", C.c_int64), ("near_ties", C.c_int64),
+                ("tie_refreshes", C.c_int64),
                 ("refreshes", C.c_int64),
                 ("last_drift_max", C.c_double), ("last_drift_fro", C.c_double),
                 ("logdet", C.c_double * 2), ("sign", C.c_int), ("status", C.c_int)]
@@ -267,12 +268,12 @@ class Context:
         self._check(lib.ctaux_set_profiling(self.h, int(bool(on))), "set_profiling")
 
     PHASES = ("plan_gather", "prep", "proposals", "flush_gemm", "flush_support", "measure",
-              "refresh")
+              "refresh", "tie_refine")
 
     def phase_times(self):
         """(ms per phase while profiling was on, kernels launched per phase)."""
-        ms = np.zeros(7)
-        ln = np.zeros(7, np.int64)
+        ms = np.zeros(len(self.PHASES))
+        ln = np.zeros(len(self.PHASES), np.int64)
         self._check(lib.ctaux_get_phase_times(self.h, _dp(ms), _lp(ln)), "phase_times")
         return ms, ln
 
