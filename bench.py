@@ -253,6 +253,21 @@ def main():
         dist.destroy_process_group()
 
 
+def workload_name(chains):
+    c0 = chains[0]
+    if len(chains) == 1:
+        return f"{c0.name} N_c={c0.n_c} beta={c0.beta} U={c0.U} K={c0.K} k_max={c0.k_max}, 1 chain per GPU"
+    if all(c.name == c0.name and c.n_c == c0.n_c and c.beta == c0.beta and c.U == c0.U and c.K == c0.K
+           for c in chains):
+        return (f"{c0.name} N_c={c0.n_c} beta={c0.beta} U={c0.U} K={c0.K} k_max={c0.k_max}, "
+                f"{len(chains)} chains per GPU")
+    ncs = sorted({c.n_c for c in chains})
+    return (f"{c0.name}: {len(chains)} independent chains per GPU, N_c in {ncs}, "
+            f"beta in [{min(c.beta for c in chains)}, {max(c.beta for c in chains)}], "
+            f"U in [{min(c.U for c in chains):.2f}, {max(c.U for c in chains):.2f}], "
+            f"K = 0.3 beta U N_c + 30, k_max={c0.k_max}")
+
+
 def measure_form(args, pk, torch, dist, chains, form, local, world, with_e2e):
     precision = pk.CTAUX_MIXED if form == "mixed" else pk.CTAUX_FP64
     ctx = pk.Context(chains, precision=precision, refresh_every=args.refresh_every,
@@ -332,15 +347,22 @@ def measure_form(args, pk, torch, dist, chains, form, local, world, with_e2e):
             return dict(bound="alu", achieved=dw["gamma_flop"] / sec / 1e12,
                         peak=alu_peak * n_sm / 152.0, unit="TFLOP/s",
                         peak_source=alu_src + f", {n_sm} of 152 SMs (one CTA per chain)")
-        return dict(bound="hbm", achieved=dw["flush_bytes"] / 2.0 / sec / 1e9, peak=peaks["hbm_gbs"],
-                    unit="GB/s", peak_source=f"hbm_gbs {peak_kind}")
+        if nm == "measure":
+            return dict(bound="alu", achieved=dw["meas_flop"] / sec / 1e12, peak=alu_peak,
+                        unit="TFLOP/s", peak_source=alu_src + " (estimator flops, interpolations not counted)")
+        if nm == "refresh":
+            return dict(bound="alu", achieved=dw["refresh_flop"] / sec / 1e12, peak=fp64_peak,
+                        unit="TFLOP/s", peak_source=f"FP64 = bf16 {peak_kind} x 1.25/2250 (2 m^3 per spin)")
+        # plan/gather and flush support: latency-bound, no algorithmic roofline
+        return dict(bound="latency", achieved=None, peak=None, unit=None, peak_source=None)
 
     # dominant among the phases of every block; the near-tie refinement (rare by
     # construction) is reported in phase_ms_per_step only
     dom = int(phase_ms[:names.index("tie_refine")].argmax())
     r = roof(dom)
     roofline = {"kernel": names[dom], "bound": r["bound"], "achieved": r["achieved"],
-                "peak": r["peak"], "unit": r["unit"], "frac": r["achieved"] / r["peak"],
+                "peak": r["peak"], "unit": r["unit"],
+                "frac": r["achieved"] / r["peak"] if r["peak"] else None,
                 "traffic": None, "peak_source": r["peak_source"],
                 "ms_per_step": phase_ms[dom] / steps}
     fr = roof(names.index("flush_gemm"))
@@ -366,15 +388,16 @@ def measure_form(args, pk, torch, dist, chains, form, local, world, with_e2e):
                "d2h_bytes_per_step": d2h}
 
     st = ctx.stats(0)
+    orders = [ctx.stats(i)["n"] for i in range(len(chains))]
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
             "warmup": args.warmup, "ms_per_step": total_ms / steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if precision == pk.CTAUX_FP64 else "f32",
             "data": "synthetic",
-            "config": {"workload": f"{chains[0].name} N_c={chains[0].n_c} beta={chains[0].beta} "
-                                   f"U={chains[0].U} K={chains[0].K} k_max={chains[0].k_max}, "
-                                   f"{len(chains)} chain(s) per GPU",
-                       "order_n": st["n"], "precision": form,
+            "config": {"workload": workload_name(chains),
+                       "order_n": st["n"] if len(chains) == 1 else
+                       {"mean": sum(orders) / len(orders), "min": int(min(orders)), "max": int(max(orders))},
+                       "precision": form,
                        "l2": "flushed between timed steps (512 MB write)",
                        "refresh_every": args.refresh_every, "n_tau_bins": N_TAU_BINS,
                        "n_anchors": N_ANCHORS},

@@ -195,10 +195,13 @@ ctaux_status ctaux_get_phase_times(ctaux_ctx *ctx, double *ms_out, int64_t *kern
 
 /* Algorithmic work of the blocks run so far, summed over chains (for
  * rooflines): flop counts of the prep products, the flush products and the
- * Gamma growth (both spins), bytes of N read and written by the flush.  Any
- * output may be NULL. */
+ * Gamma growth (both spins), bytes of N read and written by the flush, flops
+ * of the G(tau) estimator (the products v_b = N g_b and the contraction with
+ * G0(a, l); the table interpolations are not counted) and of the FP64
+ * refreshes (2 m^3 per spin and refresh).  Any output may be NULL. */
 ctaux_status ctaux_get_work(ctaux_ctx *ctx, double *prep_flop, double *flush_flop,
-                            double *flush_bytes, double *gamma_flop);
+                            double *flush_bytes, double *gamma_flop, double *meas_flop,
+                            double *refresh_flop);
 
 /* Philox-4x32-10 on the device: for counters (t0 + i, chain, purpose), i <
  * count, write the two 53-bit uniforms of each draw to out[2*i], out[2*i+1].

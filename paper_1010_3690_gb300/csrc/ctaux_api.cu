@@ -160,11 +160,6 @@ ctaux_status build_chains(ctaux_ctx* ctx) {
   std::vector<TcMaps> host_maps(mixed_tc ? 2 * ctx->chains.size() : 0);
   int nb = refresh_blocks_per_sm<T>();
   ls.refresh_grid = std::max(1, nb) * ctx->sm_count;
-  // many chains: one CTA per (chain, spin) (panel of 16 columns in shared memory);
-  // few chains: the cooperative whole-GPU refresh
-  ls.refresh_cta_smem = (int)(16 * sizeof(double) * (size_t)max_ld);
-  ls.refresh_per_cta = (ctx->chains.size() >= 16 && ls.refresh_cta_smem <= 200 * 1024) ? 1 : 0;
-  if (ls.refresh_per_cta) CUDA_TRY(ctx, configure_refresh_cta<T>(ls.refresh_cta_smem));
 
   for (size_t ci = 0; ci < ctx->chains.size(); ++ci) {
     const ctaux_chain_params& cp = ctx->chains[ci];
@@ -656,9 +651,9 @@ ctaux_status ctaux_get_phase_times(ctaux_ctx* ctx, double* ms_out, int64_t* kern
 }
 
 ctaux_status ctaux_get_work(ctaux_ctx* ctx, double* prep_flop, double* flush_flop, double* flush_bytes,
-                            double* gamma_flop) {
+                            double* gamma_flop, double* meas_flop, double* refresh_flop) {
   if (!ctx) return CTAUX_EINVAL;
-  double a = 0.0, b = 0.0, c = 0.0, g = 0.0;
+  double a = 0.0, b = 0.0, c = 0.0, g = 0.0, me = 0.0, rf = 0.0;
   for (size_t ci = 0; ci < ctx->chains.size(); ++ci) {
     Dyn d;
     ctaux_status r = read_dyn(ctx, (int)ci, &d);
@@ -667,8 +662,12 @@ ctaux_status ctaux_get_work(ctaux_ctx* ctx, double* prep_flop, double* flush_flo
     b += d.work_flush;
     c += d.bytes_flush;
     g += d.work_gamma;
+    me += d.work_meas;
+    rf += d.work_refresh;
   }
   if (gamma_flop) *gamma_flop = g;
+  if (meas_flop) *meas_flop = me;
+  if (refresh_flop) *refresh_flop = rf;
   if (prep_flop) *prep_flop = a;
   if (flush_flop) *flush_flop = b;
   if (flush_bytes) *flush_bytes = c;

@@ -72,6 +72,8 @@ struct Dyn {
   double work_flush;      // algorithmic flops of the flush products
   double bytes_flush;     // algorithmic bytes of the flush (N read + N' written)
   double work_gamma;      // algorithmic flops of the Gamma growth (both spins)
+  double work_meas;       // algorithmic flops of the G(tau) estimator (both spins)
+  double work_refresh;    // algorithmic flops of the FP64 refreshes (2 m^3 per spin)
   int tie_pending;        // mixed form: 1 = proposal d.t awaits an FP64 decision
   int tie_jj;             // index in the block of the near-tie proposal
   int forced_accept;      // FP64 decision of proposal forced_t
@@ -187,36 +189,36 @@ __device__ __forceinline__ int move_of(double u_move, double p_insert, double p_
 // operations keep the arithmetic free of FMA contraction.
 __device__ __forceinline__ double interp_row(const double* row, int n_tau, double inv_dtau, double x) {
   const double pos = x * inv_dtau;
-  double fi = floor(pos);
-  if (fi < 0.0) fi = 0.0;
-  if (fi > (double)(n_tau - 2)) fi = (double)(n_tau - 2);
-  const int idx = (int)fi;
-  const double f = pos - fi;
-  return __dadd_rn(__dmul_rn(1.0 - f, __ldg(row + idx)), __dmul_rn(f, __ldg(row + idx + 1)));
+  const int idx = min(max((int)floor(pos), 0), n_tau - 2);
+  const double f = pos - (double)idx;
+  const double g0 = __ldg(row + idx), g1 = __ldg(row + idx + 1);
+  return fma(f, g1 - g0, g0);
 }
 
 // G0_sigma(x_i - x_j, tau_i - tau_j): antiperiodic in tau; equal times take
 // G0(0-) = -G0(beta-) (the density convention of Eq. Nmatrix's diagonal).
+// Branch-free in the sign of tau_i - tau_j (neighbouring threads of the
+// measurement and refresh see both signs).
 template <typename T>
 __device__ __forceinline__ double g0_eval(const Chain<T>& c, int spin, double ti, int xi, double tj,
                                           int xj) {
   const double dt = ti - tj;
   const int cls = __ldg(c.dx_class + xi * c.n_c + xj);
   const double* row = c.g0 + ((size_t)spin * c.n_classes + cls) * c.n_tau;
-  if (dt > 0.0) return interp_row(row, c.n_tau, c.inv_dtau, dt);
-  if (dt < 0.0) return -interp_row(row, c.n_tau, c.inv_dtau, dt + c.beta);
-  return -__ldg(row + c.n_tau - 1);
+  const bool neg = dt < 0.0;
+  const double v = interp_row(row, c.n_tau, c.inv_dtau, neg ? dt + c.beta : dt);
+  if (dt == 0.0) return -__ldg(row + c.n_tau - 1);
+  return neg ? -v : v;
 }
 
 // Same interpolation in float32 (the mixed form's measurement): table entries
 // rounded to float, position and weights in float.
 __device__ __forceinline__ float interp_row_f(const double* row, int n_tau, float inv_dtau, float x) {
   const float pos = x * inv_dtau;
-  float fi = floorf(pos);
-  fi = fminf(fmaxf(fi, 0.f), (float)(n_tau - 2));
-  const int idx = (int)fi;
-  const float f = pos - fi;
-  return (1.f - f) * (float)__ldg(row + idx) + f * (float)__ldg(row + idx + 1);
+  const int idx = min(max((int)floorf(pos), 0), n_tau - 2);
+  const float f = pos - (float)idx;
+  const float g0 = (float)__ldg(row + idx), g1 = (float)__ldg(row + idx + 1);
+  return fmaf(f, g1 - g0, g0);
 }
 
 template <typename T>
@@ -225,10 +227,10 @@ __device__ __forceinline__ float g0_eval_f(const Chain<T>& c, int spin, float ti
   const float dt = ti - tj;
   const int cls = __ldg(c.dx_class + xi * c.n_c + xj);
   const double* row = c.g0 + ((size_t)spin * c.n_classes + cls) * c.n_tau;
-  const float idt = (float)c.inv_dtau;
-  if (dt > 0.f) return interp_row_f(row, c.n_tau, idt, dt);
-  if (dt < 0.f) return -interp_row_f(row, c.n_tau, idt, dt + (float)c.beta);
-  return -(float)__ldg(row + c.n_tau - 1);
+  const bool neg = dt < 0.f;
+  const float v = interp_row_f(row, c.n_tau, (float)c.inv_dtau, neg ? dt + (float)c.beta : dt);
+  if (dt == 0.f) return -(float)__ldg(row + c.n_tau - 1);
+  return neg ? -v : v;
 }
 
 // ------------------------------------------------------------ work lists

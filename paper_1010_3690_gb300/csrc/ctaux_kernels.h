@@ -30,9 +30,7 @@ struct LaunchShape {
   int kchunk;            // fixed slice width of the inner dimension
   int kstride;           // partial-tile stride per output tile (most slices of any product)
   int persist_ctas;      // grid of the persistent batched kernels
-  int refresh_per_cta;   // batched form: one CTA per (chain, spin) for the refresh
   int tie_grid;          // cooperative grid of the near-tie refinement
-  int refresh_cta_smem;
   int y_blocks;
   int prop_smem;
   int gamma_in_smem;
@@ -103,8 +101,6 @@ void launch_gemm(Chain<T>* dchains, const LaunchShape& ls, int phase, cudaStream
 template <typename T>
 int refresh_blocks_per_sm();
 size_t refresh_work_doubles(int ld);
-template <typename T>
-cudaError_t configure_refresh_cta(int smem);
 template <typename T>
 void launch_measure(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t st, PhaseTimer* pt);
 template <typename T>

@@ -60,9 +60,65 @@ __device__ __forceinline__ int meas_items(const Chain<T>& c, const Dyn& d) {
   return 2 * ((meas_points(c) + 255) / 256) * max(1, (d.n + kMeasChunk - 1) / kMeasChunk);
 }
 
+// Per-chunk vertex data staged in shared memory by every CTA of an item:
+// tau_q, site_q and w_b(q) = (e^{V_q} - 1) v_b(q) for the anchors.
+template <typename A>
+struct MeasStage {
+  double tau[kMeasChunk];
+  int site[kMeasChunk];
+  A w[kMaxSharedAnchors][kMeasChunk];
+};
+
+// Shared-anchor evaluation of one (site, tau_p) point over the staged chunk,
+// NA anchors known at compile time.
+template <int NA, typename T>
+__device__ __forceinline__ void meas_point_shared(const Chain<T>& c, int spin, int xa, double tp,
+                                                  int nq, const MeasStage<T>& st, double* acc) {
+  if (sizeof(T) == 8) {
+    double a[NA];
+#pragma unroll
+    for (int b = 0; b < NA; ++b) a[b] = 0.0;
+    for (int q = 0; q < nq; ++q) {
+      const double g = g0_eval(c, spin, tp, xa, st.tau[q], st.site[q]);
+#pragma unroll
+      for (int b = 0; b < NA; ++b) a[b] = fma(g, (double)st.w[b][q], a[b]);
+    }
+#pragma unroll
+    for (int b = 0; b < NA; ++b) acc[b] = a[b];
+  } else {  // mixed form: float32 interpolation and products
+    float a[NA];
+#pragma unroll
+    for (int b = 0; b < NA; ++b) a[b] = 0.f;
+    const float tpf = (float)tp;
+    for (int q = 0; q < nq; ++q) {
+      const float g = g0_eval_f(c, spin, tpf, xa, (float)st.tau[q], st.site[q]);
+#pragma unroll
+      for (int b = 0; b < NA; ++b) a[b] = fmaf(g, (float)st.w[b][q], a[b]);
+    }
+#pragma unroll
+    for (int b = 0; b < NA; ++b) acc[b] = (double)a[b];
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void meas_point_shared_n(int na, const Chain<T>& c, int spin, int xa,
+                                                    double tp, int nq, const MeasStage<T>& st,
+                                                    double* acc) {
+  switch (na) {
+    case 1: meas_point_shared<1>(c, spin, xa, tp, nq, st, acc); break;
+    case 2: meas_point_shared<2>(c, spin, xa, tp, nq, st, acc); break;
+    case 3: meas_point_shared<3>(c, spin, xa, tp, nq, st, acc); break;
+    case 4: meas_point_shared<4>(c, spin, xa, tp, nq, st, acc); break;
+    case 5: case 6: meas_point_shared<6>(c, spin, xa, tp, nq, st, acc); break;
+    case 7: case 8: meas_point_shared<8>(c, spin, xa, tp, nq, st, acc); break;
+    default: meas_point_shared<kMaxSharedAnchors>(c, spin, xa, tp, nq, st, acc); break;
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_meas_eval(Chain<T>* chains, int n_chains) {
   __shared__ int off[kMaxChains + 1];
+  __shared__ MeasStage<T> st;
   for (int ci = threadIdx.x; ci < n_chains; ci += blockDim.x)
     off[ci] = meas_items(chains[ci], *chains[ci].dyn);
   __syncthreads();
@@ -80,40 +136,30 @@ __global__ void __launch_bounds__(256) k_meas_eval(Chain<T>* chains, int n_chain
     const int spin = l / (pblocks * nchunks), r0 = l % (pblocks * nchunks);
     const int chunk = r0 / pblocks;
     const int l0 = chunk * kMeasChunk, l1 = min(n, l0 + kMeasChunk);
+    const int nq = max(0, l1 - l0);
     const int pt = (r0 % pblocks) * blockDim.x + threadIdx.x;
+    const bool shared = meas_shared(c);
+    __syncthreads();  // the previous item's readers are done with the stage
+    if (shared) {
+      for (int e = threadIdx.x; e < nq * (A + 1); e += blockDim.x) {
+        const int q = e % nq, b = e / nq, v = l0 + q;
+        if (b == A) {
+          st.tau[q] = c.tau[buf][v];
+          st.site[q] = c.site[buf][v];
+        } else {
+          const double em1 = c.ev[spin][c.s[buf][v] + 2] - 1.0;
+          st.w[b][q] = (T)(em1 * (double)c.Mv[spin][(long)b * c.ld + v]);
+        }
+      }
+    }
+    __syncthreads();
     if (pt >= npts) continue;
-    const double* tau = c.tau[buf];
-    const int* site = c.site[buf];
-    const int8_t* s = c.s[buf];
     double* out = c.Mpts[spin] + (size_t)chunk * npts_out;
-    if (meas_shared(c)) {
+    if (shared) {
       const int p = pt % B, xa = pt / B, shift = B / A;
       const double tp = ((double)p + 0.5) * c.beta / (double)B;
       double acc[kMaxSharedAnchors];
-#pragma unroll
-      for (int b = 0; b < kMaxSharedAnchors; ++b) acc[b] = 0.0;
-      if (sizeof(T) == 8) {
-        for (int q = l0; q < l1; ++q) {
-          const double g = g0_eval(c, spin, tp, xa, tau[q], site[q]) * (c.ev[spin][s[q] + 2] - 1.0);
-#pragma unroll
-          for (int b = 0; b < kMaxSharedAnchors; ++b)
-            if (b < A) acc[b] += g * (double)c.Mv[spin][(long)b * c.ld + q];
-        }
-      } else {  // mixed form: float32 interpolation and products
-        float accf[kMaxSharedAnchors];
-#pragma unroll
-        for (int b = 0; b < kMaxSharedAnchors; ++b) accf[b] = 0.f;
-        const float tpf = (float)tp;
-        for (int q = l0; q < l1; ++q) {
-          const float g = g0_eval_f(c, spin, tpf, xa, (float)tau[q], site[q]) *
-                          ((float)c.ev[spin][s[q] + 2] - 1.f);
-#pragma unroll
-          for (int b = 0; b < kMaxSharedAnchors; ++b)
-            if (b < A) accf[b] += g * (float)c.Mv[spin][(long)b * c.ld + q];
-        }
-#pragma unroll
-        for (int b = 0; b < kMaxSharedAnchors; ++b) acc[b] = (double)accf[b];
-      }
+      meas_point_shared_n(A, c, spin, xa, tp, nq, st, acc);
       for (int b = 0; b < A; ++b) {
         const int i = (p - b * shift + B) % B;
         const double sg = (p < b * shift) ? -1.0 : 1.0;
@@ -123,6 +169,9 @@ __global__ void __launch_bounds__(256) k_meas_eval(Chain<T>* chains, int n_chain
       }
       continue;
     }
+    const double* tau = c.tau[buf];
+    const int* site = c.site[buf];
+    const int8_t* s = c.s[buf];
     const int bin = pt % B, xa = (pt / B) % c.n_c, b = pt / (B * c.n_c);
     const double tb = (double)b * c.beta / (double)A;
     const double tc = ((double)bin + 0.5) * c.beta / (double)B;
@@ -183,6 +232,10 @@ __global__ void k_meas_accumulate(Chain<T>* chains) {
     d.measurements += 1;
     d.order_sum += d.n;
     d.sign_sum += (double)d.sign;
+    // both spins: v_b = N g_b (2 n^2 per anchor) and the contraction with
+    // G0(a, l) (2 flops per point, vertex and anchor)
+    const double n = (double)d.n;
+    d.work_meas += 2.0 * (2.0 * n * n * A + 2.0 * A * (double)c.n_c * B * n);
   }
 }
 

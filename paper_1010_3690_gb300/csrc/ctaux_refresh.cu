@@ -2,7 +2,8 @@
 // N^{-1} = e^V - G0 (e^V - 1) (Eq. Nmatrix) from the configuration, invert
 // by blocked Gauss-Jordan with partial pivoting, report the drift of the
 // running N and replace it.  One cooperative launch: all chains and spins
-// advance in lockstep, separated by grid-wide barriers (no spin waits).
+// advance in lockstep, separated by grid-wide barriers (no spin waits); the
+// work of each stage is spread over the whole grid across chains.
 //
 // Unblocked column step c (pivot row pr) maps X to
 //   X[pr][j] / X[pr][c] (j != c), 1 / X[pr][c] at (pr, c),
@@ -40,6 +41,32 @@ __host__ __device__ inline size_t refresh_work_per_spin(int ld) {
   return (size_t)ld * ld + (size_t)3 * kPB * ld;
 }
 
+// Size of the refresh of chain ci (0 when it does not take part).
+template <typename T>
+__device__ __forceinline__ int refresh_order(const Chain<T>& c, int ci, int c_lo, int c_hi, int filter) {
+  if (ci < c_lo || ci >= c_hi) return 0;
+  const Dyn& d = *c.dyn;
+  if ((d.status & ~DS_SINGULAR) || (filter && d.tie_pending != filter)) return 0;
+  return d.n;
+}
+
+// Work of every stage is spread over the grid across all chains: "row units"
+// (chain, spin, row or column index; 2m per chain) go to threads or CTAs by a
+// prefix sum over chains, "tile units" (chain, spin, 32 x 32 tile) to CTAs.
+struct RowUnit {
+  int ci, spin, i, m;
+};
+
+__device__ __forceinline__ RowUnit row_unit(const int* offr, int n_chains, int u) {
+  RowUnit r;
+  r.ci = find_chain(offr, n_chains, u);
+  r.m = (offr[r.ci + 1] - offr[r.ci]) >> 1;
+  const int l = u - offr[r.ci];
+  r.spin = l / r.m;
+  r.i = l - r.spin * r.m;
+  return r;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_refresh(Chain<T>* chains, int n_chains, int only_chain,
                                                  int filter) {
@@ -48,354 +75,175 @@ __global__ void __launch_bounds__(256) k_refresh(Chain<T>* chains, int n_chains,
   const int gthreads = gridDim.x * blockDim.x;
   const int c_lo = only_chain >= 0 ? only_chain : 0;
   const int c_hi = only_chain >= 0 ? only_chain + 1 : n_chains;
+  __shared__ int offr[kMaxChains + 1];
+  __shared__ int offt[kMaxChains + 1];
+  __shared__ int max_m_s;
   __shared__ double Ps[32][kPB + 1];
   __shared__ double Rs[kPB][33];
+  __shared__ double red[2][8];
 
-  // ---- stage 1: N^{-1} of the current configuration into X; pivot of column 0
-  int max_m = 0;
-  for (int ci = c_lo; ci < c_hi; ++ci) {
-    const Chain<T>& c = chains[ci];
-    const Dyn& d = *c.dyn;
-    if ((d.status & ~DS_SINGULAR) || (filter && d.tie_pending != filter)) continue;
-    const int m = d.n, buf = d.buf, ld = c.ld;
-    max_m = max(max_m, m);
-    if (gtid == 0) c.work_logdet[0] = c.work_logdet[1] = 0.0;
-    for (int spin = 0; spin < 2; ++spin) {
-      double* X = c.work + (size_t)spin * refresh_work_per_spin(ld);
-      unsigned long long* keys = c.pkeys + (size_t)spin * ld;
-      for (int j = blockIdx.x; j < m; j += gridDim.x) {
-        const double evj = c.ev[spin][c.s[buf][j] + 2];
-        const double tj = c.tau[buf][j];
-        const int sj = c.site[buf][j];
-        for (int i = threadIdx.x; i < m; i += blockDim.x) {
-          double v = -g0_eval(c, spin, c.tau[buf][i], c.site[buf][i], tj, sj) * (evj - 1.0);
-          if (i == j) v += evj;
-          X[(size_t)j * ld + i] = v;
-          if (j == 0) atomicMax(keys, pivot_key(v, i));
-        }
-      }
+  if (threadIdx.x == 0) max_m_s = 0;
+  __syncthreads();
+  for (int ci = threadIdx.x; ci < n_chains; ci += blockDim.x) {
+    const int m = refresh_order(chains[ci], ci, c_lo, c_hi, filter);
+    const int tb = (m + 31) / 32;
+    offr[ci] = 2 * m;
+    offt[ci] = 2 * tb * tb;
+    atomicMax(&max_m_s, m);
+  }
+  __syncthreads();
+  block_exclusive_scan(offr, n_chains);
+  block_exclusive_scan(offt, n_chains);
+  const int tot_r = offr[n_chains], tot_t = offt[n_chains], max_m = max_m_s;
+
+  // ---- stage 1: N^{-1} of the current configuration into X (one column per
+  // CTA and unit); pivot key of column 0
+  for (int u = blockIdx.x; u < tot_r; u += gridDim.x) {
+    const RowUnit ru = row_unit(offr, n_chains, u);
+    const Chain<T>& c = chains[ru.ci];
+    const int m = ru.m, spin = ru.spin, j = ru.i, buf = c.dyn->buf, ld = c.ld;
+    double* X = c.work + (size_t)spin * refresh_work_per_spin(ld);
+    unsigned long long* keys = c.pkeys + (size_t)spin * ld;
+    const double evj = c.ev[spin][c.s[buf][j] + 2];
+    const double tj = c.tau[buf][j];
+    const int sj = c.site[buf][j];
+    if (j == 0 && threadIdx.x == 0) c.work_logdet[spin] = 0.0;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      double v = -g0_eval(c, spin, c.tau[buf][i], c.site[buf][i], tj, sj) * (evj - 1.0);
+      if (i == j) v += evj;
+      X[(size_t)j * ld + i] = v;
+      if (j == 0) atomicMax(keys, pivot_key(v, i));
     }
   }
   grid.sync();
 
   // ---- stage 2: panels
   for (int c0 = 0; c0 < max_m; c0 += kPB) {
-    // A0: copy the panel columns
-    for (int ci = c_lo; ci < c_hi; ++ci) {
-      const Chain<T>& c = chains[ci];
-      const Dyn& d = *c.dyn;
-      if ((d.status & ~DS_SINGULAR) || (filter && d.tie_pending != filter)) continue;
-      const int m = d.n, ld = c.ld;
-      if (c0 >= m) continue;
-      const int bw = min(kPB, m - c0);
-      for (int spin = 0; spin < 2; ++spin) {
-        const double* X = c.work + (size_t)spin * refresh_work_per_spin(ld);
-        double* Pa = const_cast<double*>(X) + (size_t)ld * ld;
-        for (int e = gtid; e < m * bw; e += gthreads) {
-          const int i = e % m, k = e / m;
-          Pa[(size_t)k * ld + i] = X[(size_t)(c0 + k) * ld + i];
-        }
-      }
+    // A0: copy the panel columns ((row unit, panel column) pairs)
+    for (int u = gtid; u < tot_r * kPB; u += gthreads) {
+      const int k = u / tot_r;
+      const RowUnit ru = row_unit(offr, n_chains, u - k * tot_r);
+      if (c0 + k >= ru.m) continue;
+      const Chain<T>& c = chains[ru.ci];
+      const int ld = c.ld;
+      const double* X = c.work + (size_t)ru.spin * refresh_work_per_spin(ld);
+      double* Pa = const_cast<double*>(X) + (size_t)ld * ld;
+      Pa[(size_t)k * ld + ru.i] = X[(size_t)(c0 + k) * ld + ru.i];
     }
     grid.sync();
-    // A1: the column steps, on the panel only
+    // A1: the column steps, on the panel only ((row unit, panel column) pairs)
     for (int k = 0; k < kPB; ++k) {
-      for (int ci = c_lo; ci < c_hi; ++ci) {
-        const Chain<T>& c = chains[ci];
-        const Dyn& d = *c.dyn;
-        if ((d.status & ~DS_SINGULAR) || (filter && d.tie_pending != filter)) continue;
-        const int m = d.n, ld = c.ld;
-        if (c0 + k >= m) continue;
-        const int bw = min(kPB, m - c0), col = c0 + k;
-        for (int spin = 0; spin < 2; ++spin) {
-          double* X = c.work + (size_t)spin * refresh_work_per_spin(ld);
-          double* Pa = X + (size_t)ld * ld;
-          double* Pb = Pa + (size_t)kPB * ld;
-          const double* src = (k & 1) ? Pb : Pa;
-          double* dst = (k & 1) ? Pa : Pb;
-          unsigned long long* keys = c.pkeys + (size_t)spin * ld;
-          int8_t* used = c.used + spin * ld;
-          const int pr = key_row(keys[col]);
-          const double piv = src[(size_t)k * ld + pr];
-          if (gtid == 0) {
-            c.perm[spin * ld + col] = pr;
-            used[pr] = 1;
-            c.pcol[spin * ld + pr] = col;
-            if (!(fabs(piv) > 0.0) || !isfinite(piv)) atomicOr(&c.dyn->status, DS_SINGULAR);
-            c.work_logdet[spin] += log(fabs(piv));
-          }
-          const double ipiv = 1.0 / piv;
-          // one (row, panel column) pair per thread
-          for (int e = gtid; e < m * bw; e += gthreads) {
-            const int i = e % m, kk = e / m;
-            const double xic = src[(size_t)k * ld + i];
-            double v;
-            if (i == pr) v = (kk == k) ? ipiv : src[(size_t)kk * ld + pr] * ipiv;
-            else if (kk == k) v = -xic * ipiv;
-            else v = src[(size_t)kk * ld + i] - xic * (src[(size_t)kk * ld + pr] * ipiv);
-            dst[(size_t)kk * ld + i] = v;
-            if (kk == k + 1 && i != pr && !used[i]) atomicMax(keys + col + 1, pivot_key(v, i));
-          }
+      for (int u = gtid; u < tot_r * kPB; u += gthreads) {
+        const int kk = u / tot_r;
+        const RowUnit ru = row_unit(offr, n_chains, u - kk * tot_r);
+        if (c0 + k >= ru.m || c0 + kk >= ru.m) continue;
+        const Chain<T>& c = chains[ru.ci];
+        const int ld = c.ld, col = c0 + k, i = ru.i, spin = ru.spin;
+        double* X = c.work + (size_t)spin * refresh_work_per_spin(ld);
+        double* Pa = X + (size_t)ld * ld;
+        double* Pb = Pa + (size_t)kPB * ld;
+        const double* src = (k & 1) ? Pb : Pa;
+        double* dst = (k & 1) ? Pa : Pb;
+        unsigned long long* keys = c.pkeys + (size_t)spin * ld;
+        int8_t* used = c.used + spin * ld;
+        const int pr = key_row(keys[col]);
+        const double piv = src[(size_t)k * ld + pr];
+        if (i == 0 && kk == 0) {
+          c.perm[spin * ld + col] = pr;
+          used[pr] = 1;  // read below only for rows other than pr
+          c.pcol[spin * ld + pr] = col;
+          if (!(fabs(piv) > 0.0) || !isfinite(piv)) atomicOr(&c.dyn->status, DS_SINGULAR);
+          c.work_logdet[spin] += log(fabs(piv));
         }
+        const double ipiv = 1.0 / piv;
+        const double xic = src[(size_t)k * ld + i];
+        double v;
+        if (i == pr) v = (kk == k) ? ipiv : src[(size_t)kk * ld + pr] * ipiv;
+        else if (kk == k) v = -xic * ipiv;
+        else v = src[(size_t)kk * ld + i] - xic * (src[(size_t)kk * ld + pr] * ipiv);
+        dst[(size_t)kk * ld + i] = v;
+        if (kk == k + 1 && i != pr && !used[i]) atomicMax(keys + col + 1, pivot_key(v, i));
       }
       grid.sync();
     }
-    // B0: pivot rows of this panel, outside it, from X before the update: Rr[j][k] = X[R_k][j]
-    for (int ci = c_lo; ci < c_hi; ++ci) {
-      const Chain<T>& c = chains[ci];
-      const Dyn& d = *c.dyn;
-      if ((d.status & ~DS_SINGULAR) || (filter && d.tie_pending != filter)) continue;
-      const int m = d.n, ld = c.ld;
-      if (c0 >= m) continue;
-      const int bw = min(kPB, m - c0);
-      for (int spin = 0; spin < 2; ++spin) {
-        const double* X = c.work + (size_t)spin * refresh_work_per_spin(ld);
-        double* Rr = const_cast<double*>(X) + (size_t)ld * ld + (size_t)2 * kPB * ld;
-        const int* perm = c.perm + spin * ld;
-        for (int e = gtid; e < m * kPB; e += gthreads) {
-          const int k = e % kPB, j = e / kPB;
-          Rr[(size_t)j * kPB + k] = (k < bw) ? X[(size_t)j * ld + perm[c0 + k]] : 0.0;
-        }
-      }
+    // B0: pivot rows of this panel, outside it, from X before the update:
+    // Rr[j][k] = X[R_k][j] ((row unit = column j, k) pairs)
+    for (int u = gtid; u < tot_r * kPB; u += gthreads) {
+      const int k = u % kPB;
+      const RowUnit ru = row_unit(offr, n_chains, u / kPB);
+      if (c0 >= ru.m) continue;
+      const Chain<T>& c = chains[ru.ci];
+      const int ld = c.ld, j = ru.i;
+      const double* X = c.work + (size_t)ru.spin * refresh_work_per_spin(ld);
+      double* Rr = const_cast<double*>(X) + (size_t)ld * ld + (size_t)2 * kPB * ld;
+      const int* perm = c.perm + ru.spin * ld;
+      Rr[(size_t)j * kPB + k] = (c0 + k < ru.m) ? X[(size_t)j * ld + perm[c0 + k]] : 0.0;
     }
     grid.sync();
-    // B1: trailing rank-bw update in 32 x 32 tiles, panel written back,
-    // pivot key of the next panel's first column
-    for (int ci = c_lo; ci < c_hi; ++ci) {
+    // B1: trailing rank-bw update in 32 x 32 tiles (tile units), panel written
+    // back, pivot key of the next panel's first column
+    for (int u = blockIdx.x; u < tot_t; u += gridDim.x) {
+      const int ci = find_chain(offt, n_chains, u);
+      const int m = (offr[ci + 1] - offr[ci]) >> 1;
+      if (c0 >= m) continue;  // uniform over the CTA
       const Chain<T>& c = chains[ci];
-      const Dyn& d = *c.dyn;
-      if ((d.status & ~DS_SINGULAR) || (filter && d.tie_pending != filter)) continue;
-      const int m = d.n, ld = c.ld;
-      if (c0 >= m) continue;
-      const int bw = min(kPB, m - c0), cn = c0 + bw;
-      const int tb = (m + 31) / 32;
-      for (int spin = 0; spin < 2; ++spin) {
-        double* X = c.work + (size_t)spin * refresh_work_per_spin(ld);
-        double* Pa = X + (size_t)ld * ld;
-        const double* Pf = (bw & 1) ? Pa + (size_t)kPB * ld : Pa;  // panel after bw steps
-        const double* Rr = Pa + (size_t)2 * kPB * ld;
-        unsigned long long* keys = c.pkeys + (size_t)spin * ld;
-        const int8_t* used = c.used + spin * ld;
-        const int* pcol = c.pcol + spin * ld;
-        for (int tile = blockIdx.x; tile < tb * tb; tile += gridDim.x) {
-          const int i0 = (tile % tb) * 32, j0 = (tile / tb) * 32;
-          __syncthreads();
-          for (int e = threadIdx.x; e < 32 * kPB; e += blockDim.x) {
-            const int r = e % 32, k = e / 32;
-            Ps[r][k] = (i0 + r < m && k < bw) ? Pf[(size_t)k * ld + i0 + r] : 0.0;
-            const int jj = e % 32, kk = e / 32;
-            Rs[kk][jj] = (j0 + jj < m) ? Rr[(size_t)(j0 + jj) * kPB + kk] : 0.0;
-          }
-          __syncthreads();
-          const int r = threadIdx.x % 32, i = i0 + r;
-          if (i < m) {
-            const int pci = pcol[i];
-            const bool in_R = pci >= c0 && pci < cn;
-            for (int q = threadIdx.x / 32; q < 32; q += blockDim.x / 32) {
-              const int j = j0 + q;
-              if (j >= m) continue;
-              double v;
-              if (j >= c0 && j < cn) {
-                v = Ps[r][j - c0];
-              } else {
-                double acc = in_R ? 0.0 : X[(size_t)j * ld + i];
-#pragma unroll 8
-                for (int k = 0; k < kPB; ++k) acc += Ps[r][k] * Rs[k][q];
-                v = acc;
-              }
-              X[(size_t)j * ld + i] = v;
-              if (j == cn && !used[i]) atomicMax(keys + cn, pivot_key(v, i));
-            }
-          }
-        }
-      }
-    }
-    grid.sync();
-  }
-
-  // ---- stage 3: unscramble, drift against the running N, replace it;
-  // clear the pivot keys and flags for the next refresh
-  for (int ci = c_lo; ci < c_hi; ++ci) {
-    const Chain<T>& c = chains[ci];
-    Dyn& d = *c.dyn;
-    if ((d.status & ~DS_SINGULAR) || (filter && d.tie_pending != filter)) continue;
-    const int m = d.n, ld = c.ld, buf = d.buf;
-    for (int spin = 0; spin < 2; ++spin) {
-      const double* X = c.work + (size_t)spin * refresh_work_per_spin(ld);
-      const int* perm = c.perm + spin * ld;
-      T* Nr = c.N[buf][spin];
-      double* N64 = (filter == 1) ? c.N64[spin] : nullptr;
-      for (int j = blockIdx.x; j < m; j += gridDim.x) {
-        const int pj = perm[j];
-        for (int cc = threadIdx.x; cc < m; cc += blockDim.x) {
-          const double v = X[(size_t)j * ld + perm[cc]];  // N[cc][perm[j]]
-          const long o = (long)pj * ld + cc;
-          if (N64) N64[o] = v;
-          const double diff = fabs((double)Nr[o] - v);
-          if (diff > 0.0) {
-            atomicMax(reinterpret_cast<unsigned long long*>(&c.work_drift[0]),
-                      (unsigned long long)__double_as_longlong(diff));
-            atomicAdd(&c.work_drift[1], diff * diff);
-          }
-          Nr[o] = (T)v;
-        }
-      }
-      for (int e = gtid; e < m; e += gthreads) {
-        c.pkeys[(size_t)spin * ld + e] = 0ull;
-        c.used[spin * ld + e] = 0;
-        c.pcol[spin * ld + e] = -1;
-      }
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Batched form: one CTA per (chain, spin), the same blocked Gauss-Jordan with
-// block-level barriers.  The panel (m x 16 float64) lives in shared memory and
-// is updated in place (the pivot row is copied first); pivots come from a
-// block reduction; the trailing rank-16 update streams X through the CTA,
-// with the pivot rows X[R, :] saved in the work area beforehand.
-constexpr int kPBc = 16;
-
-__device__ __forceinline__ void block_argmax(double v, int row, double* rv, int* ri) {
-  // max |v| (ties to the lower row) over the block; result in rv[0], ri[0]
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int o = 16; o > 0; o >>= 1) {
-    const double v2 = __shfl_down_sync(0xffffffffu, v, o);
-    const int r2 = __shfl_down_sync(0xffffffffu, row, o);
-    if (v2 > v || (v2 == v && r2 < row)) {
-      v = v2;
-      row = r2;
-    }
-  }
-  __syncthreads();
-  if (lane == 0) {
-    rv[w] = v;
-    ri[w] = row;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int k = 1; k < (int)(blockDim.x >> 5); ++k)
-      if (rv[k] > rv[0] || (rv[k] == rv[0] && ri[k] < ri[0])) {
-        rv[0] = rv[k];
-        ri[0] = ri[k];
-      }
-  }
-  __syncthreads();
-}
-
-template <typename T>
-__global__ void __launch_bounds__(512) k_refresh_cta(Chain<T>* chains, int n_chains, int filter) {
-  const int ci = blockIdx.x >> 1, spin = blockIdx.x & 1;
-  if (ci >= n_chains) return;
-  const Chain<T>& c = chains[ci];
-  Dyn& d = *c.dyn;
-  if ((d.status & ~DS_SINGULAR) || (filter && d.tie_pending != filter)) return;
-  const int m = d.n, ld = c.ld, buf = d.buf;
-  double* X = c.work + (size_t)spin * refresh_work_per_spin(ld);
-  double* Rr = X + (size_t)ld * ld;       // pivot rows of the current panel, [j][k]
-  int* perm = c.perm + spin * ld;
-  int8_t* used = c.used + spin * ld;
-  int* pcol = c.pcol + spin * ld;
-  extern __shared__ __align__(16) double panel[];  // [k][i], kPBc x m
-  __shared__ double prow[kPBc];
-  __shared__ double rv[32];
-  __shared__ int ri[32];
-  __shared__ double logdet_s;
-  if (threadIdx.x == 0) logdet_s = 0.0;
-  // N^{-1} of the configuration
-  for (int j = 0; j < m; ++j) {
-    const double evj = c.ev[spin][c.s[buf][j] + 2];
-    const double tj = c.tau[buf][j];
-    const int sj = c.site[buf][j];
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
-      double v = -g0_eval(c, spin, c.tau[buf][i], c.site[buf][i], tj, sj) * (evj - 1.0);
-      if (i == j) v += evj;
-      X[(size_t)j * ld + i] = v;
-    }
-  }
-  for (int i = threadIdx.x; i < m; i += blockDim.x) {
-    used[i] = 0;
-    pcol[i] = -1;
-  }
-  __syncthreads();
-  for (int c0 = 0; c0 < m; c0 += kPBc) {
-    const int bw = min(kPBc, m - c0);
-    for (int e = threadIdx.x; e < m * bw; e += blockDim.x) {
-      const int i = e % m, k = e / m;
-      panel[(size_t)k * m + i] = X[(size_t)(c0 + k) * ld + i];
-    }
-    __syncthreads();
-    for (int k = 0; k < bw; ++k) {
-      const int col = c0 + k;
-      double best = -1.0;
-      int brow = 0x7fffffff;
-      for (int i = threadIdx.x; i < m; i += blockDim.x) {
-        const double a = used[i] ? -1.0 : fabs(panel[(size_t)k * m + i]);
-        if (a > best || (a == best && i < brow)) {
-          best = a;
-          brow = i;
-        }
-      }
-      block_argmax(best, brow, rv, ri);
-      const int pr = ri[0];
-      const double piv = panel[(size_t)k * m + pr];
-      if (threadIdx.x == 0) {
-        perm[col] = pr;
-        used[pr] = 1;
-        pcol[pr] = col;
-        if (!(fabs(piv) > 0.0) || !isfinite(piv)) atomicOr(&d.status, DS_SINGULAR);
-        logdet_s += log(fabs(piv));
-      }
-      const double ipiv = 1.0 / piv;
-      if (threadIdx.x < bw) prow[threadIdx.x] = panel[(size_t)threadIdx.x * m + pr] * ipiv;
+      const int tb = (m + 31) / 32, l = u - offt[ci];
+      const int spin = l / (tb * tb), tile = l - spin * tb * tb;
+      const int ld = c.ld, bw = min(kPB, m - c0), cn = c0 + bw;
+      double* X = c.work + (size_t)spin * refresh_work_per_spin(ld);
+      double* Pa = X + (size_t)ld * ld;
+      const double* Pf = (bw & 1) ? Pa + (size_t)kPB * ld : Pa;  // panel after bw steps
+      const double* Rr = Pa + (size_t)2 * kPB * ld;
+      unsigned long long* keys = c.pkeys + (size_t)spin * ld;
+      const int8_t* used = c.used + spin * ld;
+      const int* pcol = c.pcol + spin * ld;
+      const int i0 = (tile % tb) * 32, j0 = (tile / tb) * 32;
       __syncthreads();
-      for (int i = threadIdx.x; i < m; i += blockDim.x) {
-        const double xic = panel[(size_t)k * m + i];
-        for (int kk = 0; kk < bw; ++kk) {
-          double v;
-          if (i == pr) v = (kk == k) ? ipiv : prow[kk];
-          else if (kk == k) v = -xic * ipiv;
-          else v = panel[(size_t)kk * m + i] - xic * prow[kk];
-          panel[(size_t)kk * m + i] = v;
-        }
+      for (int e = threadIdx.x; e < 32 * kPB; e += blockDim.x) {
+        const int r = e % 32, k = e / 32;
+        Ps[r][k] = (i0 + r < m && k < bw) ? Pf[(size_t)k * ld + i0 + r] : 0.0;
+        const int jj = e % 32, kk = e / 32;
+        Rs[kk][jj] = (j0 + jj < m) ? Rr[(size_t)(j0 + jj) * kPB + kk] : 0.0;
       }
       __syncthreads();
-    }
-    // pivot rows outside the panel, before the update
-    for (int e = threadIdx.x; e < m * bw; e += blockDim.x) {
-      const int k = e % bw, j = e / bw;
-      Rr[(size_t)j * kPBc + k] = X[(size_t)j * ld + perm[c0 + k]];
-    }
-    __syncthreads();
-    for (int j = 0; j < m; ++j) {
-      double* Xj = X + (size_t)j * ld;
-      if (j >= c0 && j < c0 + bw) {
-        for (int i = threadIdx.x; i < m; i += blockDim.x) Xj[i] = panel[(size_t)(j - c0) * m + i];
-        continue;
-      }
-      double r[kPBc];
-#pragma unroll
-      for (int k = 0; k < kPBc; ++k) r[k] = (k < bw) ? Rr[(size_t)j * kPBc + k] : 0.0;
-      for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      const int r = threadIdx.x % 32, i = i0 + r;
+      if (i < m) {
         const int pci = pcol[i];
-        double acc = (pci >= c0 && pci < c0 + bw) ? 0.0 : Xj[i];
-#pragma unroll
-        for (int k = 0; k < kPBc; ++k)
-          if (k < bw) acc += panel[(size_t)k * m + i] * r[k];
-        Xj[i] = acc;
+        const bool in_R = pci >= c0 && pci < cn;
+        for (int q = threadIdx.x / 32; q < 32; q += blockDim.x / 32) {
+          const int j = j0 + q;
+          if (j >= m) continue;
+          double v;
+          if (j >= c0 && j < cn) {
+            v = Ps[r][j - c0];
+          } else {
+            double acc = in_R ? 0.0 : X[(size_t)j * ld + i];
+#pragma unroll 8
+            for (int k = 0; k < kPB; ++k) acc += Ps[r][k] * Rs[k][q];
+            v = acc;
+          }
+          X[(size_t)j * ld + i] = v;
+          if (j == cn && !used[i]) atomicMax(keys + cn, pivot_key(v, i));
+        }
       }
     }
-    __syncthreads();
+    grid.sync();
   }
-  // unscramble, drift, replace
-  T* Nr = c.N[buf][spin];
-  double* N64 = (filter == 1) ? c.N64[spin] : nullptr;
-  double dmax = 0.0, dsq = 0.0;
-  for (int j = 0; j < m; ++j) {
+
+  // ---- stage 3: unscramble, drift against the running N (reduced per CTA
+  // and column), replace it; clear the pivot keys and flags for the next refresh
+  for (int u = blockIdx.x; u < tot_r; u += gridDim.x) {
+    const RowUnit ru = row_unit(offr, n_chains, u);
+    const Chain<T>& c = chains[ru.ci];
+    const int m = ru.m, spin = ru.spin, j = ru.i, ld = c.ld, buf = c.dyn->buf;
+    const double* X = c.work + (size_t)spin * refresh_work_per_spin(ld);
+    const int* perm = c.perm + spin * ld;
+    T* Nr = c.N[buf][spin];
+    double* N64 = (filter == 1) ? c.N64[spin] : nullptr;
     const int pj = perm[j];
+    double dmax = 0.0, dsq = 0.0;
     for (int cc = threadIdx.x; cc < m; cc += blockDim.x) {
-      const double v = X[(size_t)j * ld + perm[cc]];
+      const double v = X[(size_t)j * ld + perm[cc]];  // N[cc][perm[j]]
       const long o = (long)pj * ld + cc;
       if (N64) N64[o] = v;
       const double diff = fabs((double)Nr[o] - v);
@@ -403,18 +251,37 @@ __global__ void __launch_bounds__(512) k_refresh_cta(Chain<T>* chains, int n_cha
       dsq += diff * diff;
       Nr[o] = (T)v;
     }
+    for (int o = 16; o > 0; o >>= 1) {
+      dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+      dsq += __shfl_xor_sync(0xffffffffu, dsq, o);
+    }
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) {
+      red[0][threadIdx.x >> 5] = dmax;
+      red[1][threadIdx.x >> 5] = dsq;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double bm = 0.0, bs = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        bm = fmax(bm, red[0][w]);
+        bs += red[1][w];
+      }
+      if (bm > 0.0)
+        atomicMax(reinterpret_cast<unsigned long long*>(&c.work_drift[0]),
+                  (unsigned long long)__double_as_longlong(bm));
+      if (bs > 0.0) atomicAdd(&c.work_drift[1], bs);
+    }
   }
-  if (dmax > 0.0)
-    atomicMax(reinterpret_cast<unsigned long long*>(&c.work_drift[0]),
-              (unsigned long long)__double_as_longlong(dmax));
-  if (dsq > 0.0) atomicAdd(&c.work_drift[1], dsq);
-  for (int i = threadIdx.x; i < m; i += blockDim.x) {
-    used[i] = 0;
-    pcol[i] = -1;
-    c.pkeys[(size_t)spin * ld + i] = 0ull;
+  grid.sync();  // every column has read perm before the flags are cleared
+  for (int u = gtid; u < tot_r; u += gthreads) {
+    const RowUnit ru = row_unit(offr, n_chains, u);
+    const Chain<T>& c = chains[ru.ci];
+    const int ld = c.ld;
+    c.pkeys[(size_t)ru.spin * ld + ru.i] = 0ull;
+    c.used[ru.spin * ld + ru.i] = 0;
+    c.pcol[ru.spin * ld + ru.i] = -1;
   }
-  __syncthreads();
-  if (threadIdx.x == 0) c.work_logdet[spin] = logdet_s;
 }
 
 // Small follow-up kernel: permutation signs, log det, drift into the stats.
@@ -427,6 +294,7 @@ __global__ void k_refresh_finish(Chain<T>* chains, int n_chains, int only_chain,
   Dyn& d = *c.dyn;
   if ((d.status & ~DS_SINGULAR) || (filter && d.tie_pending != filter)) return;
   d.refreshes += 1;
+  d.work_refresh += 4.0 * (double)d.n * (double)d.n * (double)d.n;  // 2 m^3 per spin
   d.drift_max = c.work_drift[0];
   d.drift_fro = sqrt(c.work_drift[1]);
   c.work_drift[0] = 0.0;
@@ -440,15 +308,6 @@ cudaError_t launch_refresh(Chain<T>* dchains, const LaunchShape& ls, int only_ch
   pt->begin(6, st);
   int nch = ls.n_chains;
   cudaError_t e = cudaSuccess;
-  if (only_chain < 0 && ls.refresh_per_cta) {
-    k_refresh_cta<T><<<2 * nch, 512, ls.refresh_cta_smem, st>>>(dchains, nch, filter);
-    e = cudaGetLastError();
-    if (e == cudaSuccess)
-      k_refresh_finish<T><<<(nch + 127) / 128, 128, 0, st>>>(dchains, nch, -1, filter);
-    e = cudaGetLastError();
-    pt->end(6, st, 2);
-    return e;
-  }
   void* args[] = {&dchains, &nch, &only_chain, &filter};
   e = cudaLaunchCooperativeKernel((const void*)k_refresh<T>, dim3(ls.refresh_grid), dim3(256),
                                   args, 0, st);
@@ -462,13 +321,6 @@ cudaError_t launch_refresh(Chain<T>* dchains, const LaunchShape& ls, int only_ch
   pt->end(6, st, 2);
   return e;
 }
-
-template <typename T>
-cudaError_t configure_refresh_cta(int smem) {
-  return cudaFuncSetAttribute(k_refresh_cta<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-}
-template cudaError_t configure_refresh_cta<double>(int);
-template cudaError_t configure_refresh_cta<float>(int);
 
 template <typename T>
 int refresh_blocks_per_sm() {

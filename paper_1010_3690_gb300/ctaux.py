@@ -90,7 +90,7 @@ def _load():
         "ctaux_set_profiling": (C.c_int, [vp, C.c_int]),
         "ctaux_get_phase_times": (C.c_int, [vp, P(C.c_double), P(C.c_int64)]),
         "ctaux_get_work": (C.c_int, [vp, P(C.c_double), P(C.c_double), P(C.c_double),
-                                     P(C.c_double)]),
+                                     P(C.c_double), P(C.c_double), P(C.c_double)]),
         "ctaux_philox_uniforms": (C.c_int, [C.c_uint64, C.c_uint32, C.c_int64, C.c_int, C.c_int,
                                             P(C.c_double)]),
         "ctaux_synchronize": (C.c_int, [vp]),
@@ -278,8 +278,8 @@ class Context:
         return ms, ln
 
     def work(self):
-        a, b, c, g = C.c_double(), C.c_double(), C.c_double(), C.c_double()
-        self._check(lib.ctaux_get_work(self.h, C.byref(a), C.byref(b), C.byref(c), C.byref(g)),
-                    "get_work")
+        a, b, c, g, me, rf = (C.c_double() for _ in range(6))
+        self._check(lib.ctaux_get_work(self.h, C.byref(a), C.byref(b), C.byref(c), C.byref(g),
+                                       C.byref(me), C.byref(rf)), "get_work")
         return dict(prep_flop=a.value, flush_flop=b.value, flush_bytes=c.value,
-                    gamma_flop=g.value)
+                    gamma_flop=g.value, meas_flop=me.value, refresh_flop=rf.value)

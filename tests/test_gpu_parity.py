@@ -102,12 +102,14 @@ def test_set_config_builds_N_from_scratch():
                                                        rel=1e-10, abs=1e-9)
 
 
-def test_measurement_matches_oracle_per_configuration():
+@pytest.mark.parametrize("bins,anchors", [(12, 3), (10, 3), (16, 16), (8, 1), (15, 5)])
+def test_measurement_matches_oracle_per_configuration(bins, anchors):
+    """Shared-anchor evaluation (bins a multiple of anchors) and the general path."""
     ch = configs.cube8(K=16.0, k_max=32, capacity=512)
     cfg = configs.synthetic_configuration(ch, 60, seed=5)
     oc = oracle_for(ch)
     oc.set_config(cfg["tau"], cfg["site"], cfg["s"], cfg["birth"], cfg["t"])
-    with pk.Context([ch], n_tau_bins=12, n_anchors=3) as ctx:
+    with pk.Context([ch], n_tau_bins=bins, n_anchors=anchors) as ctx:
         ctx.set_config(0, cfg["tau"], cfg["site"], cfg["s"], cfg["birth"], cfg["t"])
         ctx.reset_measurements()
         ctx.sweep(1, measure=True)
@@ -115,8 +117,28 @@ def test_measurement_matches_oracle_per_configuration():
         assert nm == 1
         oc.run(ch.k_max)
         compare_config(ctx, 0, oc)
-        ref = oc.measure_G(12, 3)
+        ref = oc.measure_G(bins, anchors)
         np.testing.assert_allclose(G, ref, rtol=1e-9, atol=1e-11)
+
+
+@pytest.mark.parametrize("bins,anchors", [(12, 3), (10, 3)])
+def test_mixed_measurement_matches_oracle(bins, anchors):
+    """Float32 interpolation and products: |G - G_oracle| within 1e-4 of max|G|
+    (float32 positions on a 4096-point table and float32 N: ~1e-6 per term)."""
+    ch = configs.cube8(K=16.0, k_max=32, capacity=512)
+    cfg = configs.synthetic_configuration(ch, 60, seed=5)
+    oc = oracle_for(ch)
+    oc.set_config(cfg["tau"], cfg["site"], cfg["s"], cfg["birth"], cfg["t"])
+    with pk.Context([ch], precision=pk.CTAUX_MIXED, n_tau_bins=bins, n_anchors=anchors) as ctx:
+        ctx.set_config(0, cfg["tau"], cfg["site"], cfg["s"], cfg["birth"], cfg["t"])
+        ctx.reset_measurements()
+        ctx.sweep(1, measure=True)
+        G, E, nm = ctx.measure_G(0)
+        assert nm == 1
+        oc.run(ch.k_max)
+        compare_config(ctx, 0, oc)
+        ref = oc.measure_G(bins, anchors)
+        np.testing.assert_allclose(G, ref, rtol=0, atol=1e-4 * np.abs(ref).max())
 
 
 def test_refresh_drift_small_fp64():
