@@ -50,8 +50,12 @@ def workload(name, K, k_max, chain_id=0):
         ch.chain_id = chain_id
         return [ch], dict(n_target=2000 if K >= 1000 else 640)
     if name == "cube100":
-        ch = configs.cube100(K=K, k_max=k_max, capacity=9216, seed=chain_id, chain_id=chain_id)
-        return [ch], dict(n_target=7000 if K >= 4000 else 1400)
+        # 8 independent chains; K-matched (K=5700: <n> ~ 7000) chains start from a
+        # seeded configuration of that order instead of growing from n=0
+        chs = [configs.cube100(K=K, k_max=k_max, capacity=9216, seed=8 * chain_id + i,
+                               chain_id=8 * chain_id + i) for i in range(8)]
+        n_t = 7000 if K >= 4000 else 1400
+        return chs, dict(n_target=n_t, start_order=n_t if K >= 4000 else 0)
     if name == "aim1":
         ch = configs.aim1(K=K, k_max=k_max, capacity=256, seed=chain_id)
         return [ch], dict(n_target=20)
@@ -214,6 +218,8 @@ def main():
     ap.add_argument("--refresh-every", dest="refresh_every", type=int, default=REFRESH_EVERY)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--k-sweep", dest="k_sweep", default=None,
+                    help="comma-separated k_max values: print proposals/s per k instead")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -229,11 +235,15 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     import paper_1010_3690_gb300 as pk
 
+    if args.k_sweep:
+        if rank == 0:
+            run_k_sweep(args, pk, torch, local)
+        return
     chains, meta = workload(args.workload, args.K, args.k_max, chain_id=rank)
     forms = ["fp64", "mixed"] if args.precision == "both" else [args.precision]
     results = {}
     for form in forms:
-        results[form] = measure_form(args, pk, torch, dist, chains, form, local, world,
+        results[form] = measure_form(args, pk, torch, dist, chains, meta, form, local, world,
                                      with_e2e=(form == forms[0]))
     prim = results[forms[0]]
     line = dict(prim["line"])
@@ -253,6 +263,62 @@ def main():
         dist.destroy_process_group()
 
 
+def run_k_sweep(args, pk, torch, local):
+    """Updates/s against the submatrix size k (k=1 is the rank-one fast update).
+
+    Same workload and starting configuration for every k, the same number of
+    proposals per timing (k_max x steps = 4096), no measurement and no refresh
+    (both are the same for every k), FP64 and mixed forms.  The paper's claim
+    to set this against: submatrix updates ~8x faster than rank-one updates
+    on CPUs at orders 512-2048 (Sec. V A, Fig. 2).
+    """
+    from workloads import configs
+    ks = [int(x) for x in args.k_sweep.split(",")]
+    forms = ["fp64", "mixed"] if args.precision == "both" else [args.precision]
+    rows = []
+    for form in forms:
+        precision = pk.CTAUX_MIXED if form == "mixed" else pk.CTAUX_FP64
+        for k in ks:
+            chains, meta = workload(args.workload, args.K, k)
+            ctx = pk.Context(chains, precision=precision, refresh_every=0,
+                             n_tau_bins=N_TAU_BINS, n_anchors=N_ANCHORS, device=local)
+            n0 = meta["n_target"] or 100
+            for i, ch in enumerate(chains):
+                cfg = configs.synthetic_configuration(ch, n0, seed=1000 + ch.chain_id)
+                ctx.set_config(i, cfg["tau"], cfg["site"], cfg["s"], cfg["birth"], cfg["t"])
+            stream = torch.cuda.current_stream()
+            sh = stream.cuda_stream
+            ctx.sweep(max(3, 512 // k), stream=sh)     # relax the seeded start
+            ctx.recompute()
+            n_prop = 4096
+            steps = max(1, n_prop // k)
+            acc0 = sum(sum(ctx.stats(i)["accepted"]) for i in range(len(chains)))
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.sweep(steps, stream=sh)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            acc = sum(sum(ctx.stats(i)["accepted"]) for i in range(len(chains))) - acc0
+            st = ctx.stats(0)
+            rows.append({"form": form, "k_max": k, "order_n": st["n"],
+                         "proposals_per_s": steps * k * len(chains) / (ms / 1e3),
+                         "accepted_per_s": acc / (ms / 1e3), "us_per_proposal": ms * 1e3 / (steps * k)})
+            ctx.close()
+    out = {"metric": "CT-AUX proposals/s against submatrix size k (k=1: rank-one updates)",
+           "workload": workload_name(workload(args.workload, args.K, ks[0])[0]),
+           "note": "no measurement, no refresh, no L2 flush; 4096 proposals per k after 512 "
+                   "relaxation proposals from a seeded configuration", "rows": rows}
+    for form in forms:
+        r = {x["k_max"]: x["proposals_per_s"] for x in rows if x["form"] == form}
+        if 1 in r:
+            best = max(r, key=r.get)
+            out[f"{form}_submatrix_over_rank_one"] = {"k_best": best, "speedup": r[best] / r[1]}
+    print(json.dumps(out), flush=True)
+
+
 def workload_name(chains):
     c0 = chains[0]
     if len(chains) == 1:
@@ -268,12 +334,17 @@ def workload_name(chains):
             f"K = 0.3 beta U N_c + 30, k_max={c0.k_max}")
 
 
-def measure_form(args, pk, torch, dist, chains, form, local, world, with_e2e):
+def measure_form(args, pk, torch, dist, chains, meta, form, local, world, with_e2e):
     precision = pk.CTAUX_MIXED if form == "mixed" else pk.CTAUX_FP64
     ctx = pk.Context(chains, precision=precision, refresh_every=args.refresh_every,
                      n_tau_bins=N_TAU_BINS, n_anchors=N_ANCHORS, device=local)
     stream = torch.cuda.current_stream()
     sh = stream.cuda_stream
+    if meta.get("start_order"):
+        from workloads import configs
+        for i, ch in enumerate(chains):
+            cfg = configs.synthetic_configuration(ch, meta["start_order"], seed=1000 + ch.chain_id)
+            ctx.set_config(i, cfg["tau"], cfg["site"], cfg["s"], cfg["birth"], cfg["t"])
     ctx.sweep(args.thermalize, measure=False, stream=sh)
     for _ in range(max(3, args.warmup)):
         ctx.sweep(1, measure=True, stream=sh)

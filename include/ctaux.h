@@ -71,7 +71,8 @@ typedef struct {
                                sign G0 = -<T d d^dagger>; j=0 holds G0(0+), j=n_tau-1 G0(beta-) */
   const int *dx_class;      /* [n_c][n_c]: class of the displacement x_i - x_j */
   double beta;              /* inverse temperature */
-  double U;                 /* Hubbard interaction */
+  double U;                 /* Hubbard interaction, > 0 (at U = 0 every lambda vanishes and
+                               the ratio formulas of Eq. ratS divide by zero) */
   double K;                 /* expansion constant (Eq. gamma), > 0 */
   int k_max;                /* proposals per submatrix block, 1..256 */
   int capacity;             /* largest expansion order n the chain may reach */

@@ -90,7 +90,6 @@ ctaux_status build_chains(ctaux_ctx* ctx) {
   hc.resize(ctx->chains.size());
   cudaError_t err = cudaSuccess;
   int max_ld = 0, max_k = 1, max_cls_bins = 1, max_pts = 1;
-  size_t kpart_elems = 0;
   int max_tiles[PH_COUNT] = {0, 0, 0, 0, 0};
   // launch shape first (tile bounds and k splits from the capacities)
   const int items = 2 * (int)ctx->chains.size();
@@ -115,21 +114,24 @@ ctaux_status build_chains(ctaux_ctx* ctx) {
   // fixed slice width of the inner dimension: narrow for FP64 (the FP64 pipe
   // is the bottleneck, so more CTAs), wider for FP32
   ls.kchunk = (sizeof(T) == 8) ? 32 : 128;
-  for (int ph = 0; ph < PH_COUNT; ++ph) {
-    ls.tiles[ph] = std::max(1, max_tiles[ph]);
-    int max_k_inner = 0;
-    for (const auto& cp : ctx->chains)
-      max_k_inner = std::max(max_k_inner, ph == PH_FLUSH ? cp.k_max : cp.capacity + cp.k_max);
-    const int ks = std::max(1, (max_k_inner + ls.kchunk - 1) / ls.kchunk);
-    ls.ksplit[ph] = ks;
-    const size_t te = sizeof(T) == 8 ? 32 : 64;
-    if (ks > 1) kpart_elems = std::max(kpart_elems, (size_t)ls.tiles[ph] * ks * te * te);
-  }
-  ls.kstride = *std::max_element(ls.ksplit, ls.ksplit + PH_COUNT);
-  kpart_elems = 0;
-  for (int ph = 0; ph < PH_COUNT; ++ph) {
-    const size_t te = sizeof(T) == 8 ? 32 : 64;
-    if (ls.ksplit[ph] > 1) kpart_elems = std::max(kpart_elems, (size_t)ls.tiles[ph] * ls.kstride * te * te);
+  for (int ph = 0; ph < PH_COUNT; ++ph) ls.tiles[ph] = std::max(1, max_tiles[ph]);
+  // split-K partial tiles per (chain, spin): the most any product of the chain
+  // can use at its capacity, at most kMaxPartials (device rule in gemm_items)
+  std::vector<size_t> kpart_of(ctx->chains.size(), 1);
+  const size_t te2 = sizeof(T) == 8 ? 32 * 32 : 64 * 64;
+  for (size_t ci = 0; ci < ctx->chains.size(); ++ci) {
+    const ctaux_chain_params& cp = ctx->chains[ci];
+    const int te = sizeof(T) == 8 ? 32 : 64;
+    const int cap_m = cp.capacity + cp.k_max;
+    const long tm = (cap_m + te - 1) / te, tk = (cp.k_max + te - 1) / te;
+    const long tiles[PH_COUNT] = {tk * tm, tm * tk, tk * tk, tm * tm, tm * ((P.n_anchors + te - 1) / te)};
+    size_t need = 1;
+    for (int ph = 0; ph < PH_COUNT; ++ph) {
+      const int k_inner = ph == PH_FLUSH ? cp.k_max : cap_m;
+      const long ks = std::max(1, (k_inner + ls.kchunk - 1) / ls.kchunk);
+      if (ks > 1) need = std::max(need, (size_t)std::min<long>(kMaxPartials, tiles[ph] * ks));
+    }
+    kpart_of[ci] = need * te2;
   }
   ls.persist_ctas = 8 * ctx->sm_count;   // 256-thread CTAs: up to 8 resident per SM
   ls.gather_slices = std::max(1, std::min(64, (2 * ctx->sm_count + items - 1) / items));
@@ -154,7 +156,9 @@ ctaux_status build_chains(ctaux_ctx* ctx) {
   ls.split_x_blocks = std::max(1, std::min(256, (max_rows + 7) / 8));
   if (mixed_tc) CUDA_TRY(ctx, configure_flush_tc());
   if (sizeof(T) == 4 && P.tie_guard > 0.0) {
-    ls.tie_grid = std::max(1, tie_refine_blocks_per_sm()) * ctx->sm_count;
+    // one CTA per SM: the refinement is a chain of short grid-wide steps, so
+    // barrier latency (which grows with the number of CTAs) dominates
+    ls.tie_grid = ctx->sm_count;
     ctx->tie_part = dalloc<double>(ctx, 2 * (size_t)ls.tie_grid + (size_t)kTieSlices * max_ld, &err);
   }
   std::vector<TcMaps> host_maps(mixed_tc ? 2 * ctx->chains.size() : 0);
@@ -223,8 +227,8 @@ ctaux_status build_chains(ctaux_ctx* ctx) {
       c.Mg[spin] = dalloc<T>(ctx, ld * P.n_anchors, &err);
       c.Mv[spin] = dalloc<T>(ctx, ld * P.n_anchors, &err);
       c.Mpts[spin] = dalloc<double>(ctx, (size_t)ls.meas_lchunks * P.n_anchors * cp.n_c * P.n_tau_bins, &err);
-      c.kpart[spin] = dalloc<T>(ctx, kpart_elems, &err);
-      c.ticket[spin] = dalloc<int>(ctx, *std::max_element(ls.tiles, ls.tiles + PH_COUNT), &err);
+      c.kpart[spin] = dalloc<T>(ctx, kpart_of[ci], &err);
+      c.ticket[spin] = dalloc<int>(ctx, kMaxPartials, &err);
     }
     c.kp = round_up(cp.k_max, 32);
     c.tie_guard = (sizeof(T) == 4) ? P.tie_guard : 0.0;
@@ -373,7 +377,7 @@ ctaux_status ctaux_init(const ctaux_params* params, ctaux_ctx** out) {
   for (int i = 0; i < params->n_chains; ++i) {
     const ctaux_chain_params& c = params->chains[i];
     if (c.n_c < 1 || c.n_classes < 1 || c.n_tau < 2 || !c.g0_table || !c.dx_class) return CTAUX_EINVAL;
-    if (!(c.beta > 0) || !(c.K > 0) || !(c.U >= 0) || c.k_max < 1 || c.k_max > kMaxK || c.capacity < 1)
+    if (!(c.beta > 0) || !(c.K > 0) || !(c.U > 0) || c.k_max < 1 || c.k_max > kMaxK || c.capacity < 1)
       return CTAUX_EINVAL;
     if (c.capacity + c.k_max > 30000) return CTAUX_EINVAL;
     for (int k = 0; k < c.n_c * c.n_c; ++k)

@@ -168,7 +168,7 @@ __device__ __forceinline__ bool setup_gemm(const Chain<T>& c, const Dyn& d, int 
       g.out = c.Gcol[spin] + n; g.out_rs = 1; g.out_cs = ld;
       break;
     case PH_FLUSH:  // N'[a,b] = N[S_a,S_b] - Y[a,:] N[P,S_b]
-      g.M = d.n_new; g.Nn = d.n_new; g.Kk = d.k_acc;
+      g.M = d.flush_noop ? 0 : d.n_new; g.Nn = d.n_new; g.Kk = d.k_acc;
       g.alpha = -1.0;
       g.A.p = c.Y[spin]; g.A.rs = 1; g.A.cs = ld;
       g.B.p = Nb; g.B.rs = 1; g.B.cs = ld; g.B.ri = c.P; g.B.ci = c.S;
@@ -194,18 +194,21 @@ struct TileEdge {
 };
 
 // Work items of one product for one chain: 2 spins x output tiles x slices
-// of the inner dimension (fixed width kchunk, so the partition, and with it
-// the rounding, depends only on the product's own sizes: a chain gives the
-// same bits alone or in a batch).
+// of the inner dimension.  Slices are kchunk wide while the partial tiles
+// they need fit in kMaxPartials per spin; products with more output tiles
+// than that get fewer, wider slices (down to one).  The partition, and with
+// it the rounding, depends only on the product's own sizes: a chain gives the
+// same bits alone or in a batch.
 template <typename T, int PHASE>
 __device__ __forceinline__ int gemm_items(const Chain<T>& c, const Dyn& d, int kchunk, int& tiles_m,
-                                          int& tiles_n, int& nslices) {
+                                          int& tiles_n, int& nslices, int& width) {
   constexpr int GE = TileEdge<T>::v;
   Gemm<T> g;
   if (d.status || !setup_gemm(c, d, 0, PHASE, g)) return 0;
   tiles_m = (g.M + GE - 1) / GE;
   tiles_n = (g.Nn + GE - 1) / GE;
-  nslices = max(1, (g.Kk + kchunk - 1) / kchunk);
+  nslices = max(1, min((g.Kk + kchunk - 1) / kchunk, kMaxPartials / (tiles_m * tiles_n)));
+  width = max(1, (g.Kk + nslices - 1) / nslices);
   return 2 * tiles_m * tiles_n * nslices;
 }
 
@@ -215,8 +218,7 @@ __device__ __forceinline__ int gemm_items(const Chain<T>& c, const Dyn& d, int k
 // and the slice that arrives last at the tile's ticket adds the partials in
 // slice order (deterministic, no waiting) and writes the result.
 template <typename T, int PHASE>
-__global__ void __launch_bounds__(256) k_gemm(Chain<T>* chains, int n_chains, int kchunk,
-                                              int kstride) {
+__global__ void __launch_bounds__(256) k_gemm(Chain<T>* chains, int n_chains, int kchunk) {
   constexpr int GBM = TileEdge<T>::v, GBN = TileEdge<T>::v, TM = GBM / 16, TN = GBN / 16;
   constexpr int phase = PHASE;
   __shared__ int off[kMaxChains + 1];
@@ -224,8 +226,8 @@ __global__ void __launch_bounds__(256) k_gemm(Chain<T>* chains, int n_chains, in
   __shared__ T Bs[GBK][GBN + 1];
   __shared__ int s_last;
   for (int ci = threadIdx.x; ci < n_chains; ci += blockDim.x) {
-    int a, b, q;
-    off[ci] = gemm_items<T, PHASE>(chains[ci], *chains[ci].dyn, kchunk, a, b, q);
+    int a, b, q, wd;
+    off[ci] = gemm_items<T, PHASE>(chains[ci], *chains[ci].dyn, kchunk, a, b, q, wd);
   }
   __syncthreads();
   block_exclusive_scan(off, n_chains);
@@ -235,8 +237,8 @@ __global__ void __launch_bounds__(256) k_gemm(Chain<T>* chains, int n_chains, in
     const int ci = find_chain(off, n_chains, w);
     const Chain<T>& c = chains[ci];
     const Dyn& d = *c.dyn;
-    int tiles_m, tiles_n, nslices;
-    gemm_items<T, PHASE>(c, d, kchunk, tiles_m, tiles_n, nslices);
+    int tiles_m, tiles_n, nslices, width;
+    gemm_items<T, PHASE>(c, d, kchunk, tiles_m, tiles_n, nslices, width);
     const int l = w - off[ci];
     const int per_spin = tiles_m * tiles_n * nslices;
     const int spin = l / per_spin, r0 = l % per_spin;
@@ -244,7 +246,7 @@ __global__ void __launch_bounds__(256) k_gemm(Chain<T>* chains, int n_chains, in
     Gemm<T> g;
     setup_gemm(c, d, spin, phase, g);
     const int i0 = (tile / tiles_n) * GBM, j0 = (tile % tiles_n) * GBN;
-    const int kb = ks * kchunk, ke = min(g.Kk, kb + kchunk);
+    const int kb = ks * width, ke = min(g.Kk, kb + width);
     T acc[TM][TN];
 #pragma unroll
     for (int a = 0; a < TM; ++a)
@@ -277,7 +279,7 @@ __global__ void __launch_bounds__(256) k_gemm(Chain<T>* chains, int n_chains, in
       __syncthreads();
     }
     if (nslices > 1) {
-      T* part = c.kpart[spin] + (size_t)tile * kstride * GBM * GBN;
+      T* part = c.kpart[spin] + (size_t)tile * nslices * GBM * GBN;
 #pragma unroll
       for (int a = 0; a < TM; ++a)
 #pragma unroll
@@ -319,13 +321,13 @@ __global__ void __launch_bounds__(256) k_gemm(Chain<T>* chains, int n_chains, in
 template <typename T>
 void launch_gemm(Chain<T>* dchains, const LaunchShape& ls, int phase, cudaStream_t st) {
   const dim3 grid(ls.persist_ctas);
-  const int n = ls.n_chains, kc = ls.kchunk, ks = ls.kstride;
+  const int n = ls.n_chains, kc = ls.kchunk;
   switch (phase) {
-    case PH_RTILDE: k_gemm<T, PH_RTILDE><<<grid, 256, 0, st>>>(dchains, n, kc, ks); break;
-    case PH_GCOL_OLD: k_gemm<T, PH_GCOL_OLD><<<grid, 256, 0, st>>>(dchains, n, kc, ks); break;
-    case PH_GCOL_NEW: k_gemm<T, PH_GCOL_NEW><<<grid, 256, 0, st>>>(dchains, n, kc, ks); break;
-    case PH_FLUSH: k_gemm<T, PH_FLUSH><<<grid, 256, 0, st>>>(dchains, n, kc, ks); break;
-    default: k_gemm<T, PH_MEAS><<<grid, 256, 0, st>>>(dchains, n, kc, ks); break;
+    case PH_RTILDE: k_gemm<T, PH_RTILDE><<<grid, 256, 0, st>>>(dchains, n, kc); break;
+    case PH_GCOL_OLD: k_gemm<T, PH_GCOL_OLD><<<grid, 256, 0, st>>>(dchains, n, kc); break;
+    case PH_GCOL_NEW: k_gemm<T, PH_GCOL_NEW><<<grid, 256, 0, st>>>(dchains, n, kc); break;
+    case PH_FLUSH: k_gemm<T, PH_FLUSH><<<grid, 256, 0, st>>>(dchains, n, kc); break;
+    default: k_gemm<T, PH_MEAS><<<grid, 256, 0, st>>>(dchains, n, kc); break;
   }
 }
 
@@ -440,7 +442,9 @@ __global__ void __launch_bounds__(256) k_proposals(Chain<T>* chains, int gamma_i
   __shared__ A red[2][4];
   __shared__ A gpp_s[2];
   __shared__ double ratio_s[2];
-  __shared__ double beta_s[2];
+  __shared__ A scal_s[2];       // per spin: 1/beta, Sherman-Morrison coefficient or Schur pivot
+  __shared__ double lamn_s[2];  // per spin: lambda of the proposed change
+  __shared__ int dec_s;         // 0 reject, 1 accept, 2 near tie (stop)
   __shared__ int sel_p;
   __shared__ int jP;
   __shared__ int n_cur, sign_s;
@@ -470,21 +474,23 @@ __global__ void __launch_bounds__(256) k_proposals(Chain<T>* chains, int gamma_i
   __syncthreads();
   int consumed = KM;
 
+  // Scalar float64 work (the move factor, divisions, the Metropolis decision)
+  // runs on one thread per spin half or per CTA and is shared through shared
+  // memory: GB300 executes float64 at 1/64 of the float32 rate, and a scalar
+  // computed redundantly by all eight warps costs eight times the pipe time.
   for (int jj = 0; jj < KM; ++jj) {
     const int64_t t = t0 + jj;
     const BlockDraw dr = bd_s[jj];
     const int move = dr.move;
     const int nc = n_cur;
     int p = -1, s_new = 0;
-    double f = 0.0;
     if (move == MV_INSERT) {
       p = dr.slot;
       s_new = dr.s_new;
-      f = c.K / (double)(nc + 1);
     } else if (nc > 0) {
-      int idx = (int)floor(dr.u_idx * (double)nc);
-      if (idx > nc - 1) idx = nc - 1;
       if (tid < 32) {
+        int idx = (int)floor(dr.u_idx * (double)nc);
+        if (idx > nc - 1) idx = nc - 1;
         const int ps = select_bit(alive, n_words, idx, lane);
         if (lane == 0) sel_p = ps;
       }
@@ -495,7 +501,6 @@ __global__ void __launch_bounds__(256) k_proposals(Chain<T>* chains, int gamma_i
         break;
       }
       s_new = (move == MV_REMOVE) ? 0 : -(int)s_cur[p];
-      f = (move == MV_REMOVE) ? (double)nc / c.K : 1.0;
     }
     if (p < 0) {  // removal or flip with no vertex: automatic rejection
       if (tid == 0) {
@@ -511,8 +516,7 @@ __global__ void __launch_bounds__(256) k_proposals(Chain<T>* chains, int gamma_i
     const int q = pmap[p];
     const int j = jP;
     const int s_start = c.s0[p];
-    const double lam_new = c.ev[spin][s_new - s_start + 2] - 1.0;
-    const A lam_a = (A)lam_new;
+    const bool to_start = (s_new == s_start);  // lambda_new = 0
     if (q < 0) {
       // first touch: gather s = G^0_{P,p}, w = G^0_{p,P}, G^0_pp
       for (int r = ht; r < j; r += 128) {
@@ -522,13 +526,12 @@ __global__ void __launch_bounds__(256) k_proposals(Chain<T>* chains, int gamma_i
       }
       if (ht == 127) gpp_s[half] = g_int<A>(c, Nb, Gc, n_old, spin, p, p);
       __syncthreads();
-      // y = Gamma^{-1} s (threads 0..63 of the half, one row each) and
-      // z = w^T Gamma^{-1} (threads 64..127, one column each), concurrently
-      // (two accumulators per dot product for instruction-level parallelism;
-      // the y threads also form their part of w . y)
-      if (ht < 64) {
+      // y = Gamma^{-1} s, one row per thread (two accumulators per dot
+      // product for instruction-level parallelism), and the partial sums of
+      // w . y; z = w^T Gamma^{-1} is needed only on acceptance
+      {
         A part = (A)0;
-        for (int r = ht; r < j; r += 64) {
+        for (int r = ht; r < j; r += 128) {
           A a0 = (A)0, a1 = (A)0;
           const T* Gr = G + (size_t)r * LG;
           int cc = 0;
@@ -543,8 +546,102 @@ __global__ void __launch_bounds__(256) k_proposals(Chain<T>* chains, int gamma_i
         }
         part = warp_sum_t(part);
         if (lane == 0) red[half][hw] = part;
+      }
+      __syncthreads();
+      if (ht == 0) {
+        const double lam_new = c.ev[spin][s_new - s_start + 2] - 1.0;
+        const A lam_a = (A)lam_new;
+        const A dd = gpp_s[half] - ((A)1 + lam_a) / lam_a;
+        const A beta = dd - ((red[half][0] + red[half][1]) + (red[half][2] + red[half][3]));
+        ratio_s[half] = (double)(-lam_a * beta);
+        scal_s[half] = (A)1 / beta;  // the bordered inverse's 1/beta
+        lamn_s[half] = lam_new;
+      }
+    } else if (ht == 0) {
+      const double lam_new = c.ev[spin][s_new - s_start + 2] - 1.0;
+      const A lam_a = (A)lam_new;
+      const A lam_old = (A)lam[q];
+      const A gqq = (A)G[(size_t)q * LG + q];
+      A r;
+      if (!to_start) {
+        const A delta = (A)1 / lam_old - (A)1 / lam_a;
+        r = (lam_a / lam_old) * ((A)1 + delta * gqq);
+        scal_s[half] = delta / ((A)1 + delta * gqq);  // Sherman-Morrison coefficient
       } else {
-        for (int cc = ht - 64; cc < j; cc += 64) {
+        r = -gqq / lam_old;
+        scal_s[half] = (A)1 / gqq;  // Schur complement pivot
+      }
+      ratio_s[half] = (double)r;
+      lamn_s[half] = lam_new;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      const double f = (move == MV_INSERT) ? c.K / (double)(nc + 1)
+                                           : (move == MV_REMOVE ? (double)nc / c.K : 1.0);
+      double R = f * ratio_s[0] * ratio_s[1];
+      const double pacc = fmin(1.0, fabs(R));
+      bool accept = dr.u_acc < pacc;
+      bool finite = isfinite(R);
+      if (!finite) accept = false;
+      const bool forced = (sizeof(T) == 4) && d.forced_t == t;
+      int dec;
+      if (forced) {
+        // decided in FP64 after the previous block stopped here (k_tie_refine / k_tie_eval)
+        accept = d.forced_accept != 0;
+        R = d.forced_R;
+        finite = true;
+        dec = accept ? 1 : 0;
+      } else if (sizeof(T) == 4 && c.tie_guard > 0.0 && finite &&
+                 fabs(dr.u_acc - pacc) < c.tie_guard * fmax(dr.u_acc, pacc)) {
+        // near tie in the float32 form: the block ends before this proposal,
+        // which is decided in FP64 after the flush
+        d.tie_pending = 1;
+        d.tie_jj = jj;
+        ties++;
+        dec = 2;
+      } else {
+        dec = accept ? 1 : 0;
+      }
+      if (dec != 2) {
+        cnt_prop[move]++;
+        // algorithmic flops, both spins: y GEMV and the dot (first touch); on
+        // acceptance the z GEMV and the bordered update, or the rank-one update
+        const double jd = (double)j;
+        double fl = (q < 0) ? (2.0 * jd * jd + 2.0 * jd) : 4.0;
+        if (accept) fl += (q < 0) ? 2.0 * jd * jd + 3.0 * (jd + 1.0) * (jd + 1.0) : 3.0 * jd * jd;
+        flops += 2.0 * fl;
+        if (!finite) numeric++;
+        if (sizeof(T) == 4 && c.tie_guard == 0.0 && finite &&
+            fabs(dr.u_acc - pacc) < kTieGuard * fmax(dr.u_acc, pacc))
+          ties++;  // detection only (FP64 re-evaluation off)
+        if (c.trace_cap > 0) {
+          TraceRec& rr = c.trace[(d.trace_written + jj) % c.trace_cap];
+          rr.t = t; rr.move = move; rr.n = nc;
+          rr.birth = birth[p]; rr.s_new = s_new; rr.accept = (accept ? 1 : 0) | (forced ? 2 : 0);
+          rr.ratio[0] = forced ? d.forced_ratio[0] : ratio_s[0];
+          rr.ratio[1] = forced ? d.forced_ratio[1] : ratio_s[1];
+          rr.R = R; rr.u = dr.u_acc;
+        }
+        if (forced) d.forced_t = -1;
+        if (accept) {
+          if (R < 0.0) sign_s = -sign_s;
+          cnt_acc[move]++;
+        }
+      }
+      dec_s = dec;
+    }
+    __syncthreads();
+    const int dec = dec_s;
+    if (dec == 2) {
+      consumed = jj;
+      break;
+    }
+    if (dec == 1) {
+      const A sc = scal_s[half];
+      if (q < 0) {
+        // z = w^T Gamma^{-1} (one column per thread), scaled by 1/beta, then the
+        // bordered inverse (Sec. III D): [[G + y z / beta, -y / beta], [-z / beta, 1 / beta]]
+        for (int cc = ht; cc < j; cc += 128) {
           A a0 = (A)0, a1 = (A)0;
           int r = 0;
           for (; r + 1 < j; r += 2) {
@@ -552,105 +649,31 @@ __global__ void __launch_bounds__(256) k_proposals(Chain<T>* chains, int gamma_i
             a1 += wv[r + 1] * (A)G[(size_t)(r + 1) * LG + cc];
           }
           if (r < j) a0 += wv[r] * (A)G[(size_t)r * LG + cc];
-          zv[cc] = a0 + a1;
+          zv[cc] = (a0 + a1) * sc;
         }
-      }
-      __syncthreads();
-      if (ht == 0) {
-        const A dd = gpp_s[half] - ((A)1 + lam_a) / lam_a;
-        const A beta = dd - (red[half][0] + red[half][1]);
-        beta_s[half] = (double)beta;
-        ratio_s[half] = (double)(-lam_a * beta);
-      }
-    } else {
-      if (ht == 0) {
-        const A lam_old = (A)lam[q];
-        const A gqq = (A)G[(size_t)q * LG + q];
-        A r;
-        if (lam_new != 0.0) {
-          const A delta = (A)1 / lam_old - (A)1 / lam_a;
-          r = (lam_a / lam_old) * ((A)1 + delta * gqq);
-          beta_s[half] = (double)delta;
-        } else {
-          r = -gqq / lam_old;
-        }
-        ratio_s[half] = (double)r;
-      }
-    }
-    __syncthreads();
-    double R = f * ratio_s[0] * ratio_s[1];
-    const double pacc = fmin(1.0, fabs(R));
-    bool accept = dr.u_acc < pacc;
-    bool finite = isfinite(R);
-    if (!finite) accept = false;
-    const bool forced = (sizeof(T) == 4) && d.forced_t == t;
-    if (forced) {
-      // decided in FP64 after the previous block stopped here (k_tie_refine / k_tie_eval)
-      accept = d.forced_accept != 0;
-      R = d.forced_R;
-      finite = true;
-    } else if (sizeof(T) == 4 && c.tie_guard > 0.0 && finite &&
-        fabs(dr.u_acc - pacc) < c.tie_guard * fmax(dr.u_acc, pacc)) {
-      // near tie in the float32 form: the block ends before this proposal,
-      // which is decided in FP64 after the flush (k_tie_eval)
-      if (tid == 0) {
-        d.tie_pending = 1;
-        d.tie_jj = jj;
-        ties++;
-      }
-      consumed = jj;
-      break;
-    }
-    if (tid == 0) {
-      cnt_prop[move]++;
-      // algorithmic flops, both spins: y and z GEMVs and the dot (first touch),
-      // bordered or rank-one update of Gamma^{-1} (accept)
-      const double jd = (double)j;
-      double fl = (q < 0) ? (4.0 * jd * jd + 2.0 * jd) : 4.0;
-      if (accept) fl += (q < 0) ? 3.0 * (jd + 1.0) * (jd + 1.0) : 3.0 * jd * jd;
-      flops += 2.0 * fl;
-      if (!finite) numeric++;
-      if (sizeof(T) == 4 && c.tie_guard == 0.0 && finite &&
-          fabs(dr.u_acc - pacc) < kTieGuard * fmax(dr.u_acc, pacc))
-        ties++;  // detection only (FP64 re-evaluation off)
-      if (c.trace_cap > 0) {
-        TraceRec& rr = c.trace[(d.trace_written + jj) % c.trace_cap];
-        rr.t = t; rr.move = move; rr.n = nc;
-        rr.birth = birth[p]; rr.s_new = s_new; rr.accept = (accept ? 1 : 0) | (forced ? 2 : 0);
-        rr.ratio[0] = forced ? d.forced_ratio[0] : ratio_s[0];
-        rr.ratio[1] = forced ? d.forced_ratio[1] : ratio_s[1];
-        rr.R = R; rr.u = dr.u_acc;
-      }
-      if (forced) d.forced_t = -1;
-    }
-    if (accept) {
-      if (q < 0) {
-        // bordered inverse (Sec. III D): [[G + y z / beta, -y / beta], [-z / beta, 1 / beta]]
-        const A ib = (A)1 / (A)beta_s[half];
+        __syncthreads();
         for (int e = ht; e < (j + 1) * (j + 1); e += 128) {
           const int r = e / (j + 1), cc = e % (j + 1);
           A v;
-          if (r < j && cc < j) v = (A)G[(size_t)r * LG + cc] + yv[r] * zv[cc] * ib;
-          else if (r < j) v = -yv[r] * ib;
-          else if (cc < j) v = -zv[cc] * ib;
-          else v = ib;
+          if (r < j && cc < j) v = (A)G[(size_t)r * LG + cc] + yv[r] * zv[cc];
+          else if (r < j) v = -yv[r] * sc;
+          else if (cc < j) v = -zv[cc];
+          else v = sc;
           G[(size_t)r * LG + cc] = (T)v;
         }
-        if (ht == 0) lam[j] = lam_new;
-      } else if (lam_new != 0.0) {
+        if (ht == 0) lam[j] = lamn_s[half];
+      } else if (!to_start) {
         // diagonal change delta of Gamma_qq: Sherman-Morrison on Gamma^{-1}
         for (int r = ht; r < j; r += 128) {
           sv[r] = (A)G[(size_t)r * LG + q];
           wv[r] = (A)G[(size_t)q * LG + r];
         }
         __syncthreads();
-        const A delta = (A)beta_s[half];
-        const A coef = delta / ((A)1 + delta * sv[q]);
         for (int e = ht; e < j * j; e += 128) {
           const int r = e / j, cc = e % j;
-          G[(size_t)r * LG + cc] = (T)((A)G[(size_t)r * LG + cc] - coef * sv[r] * wv[cc]);
+          G[(size_t)r * LG + cc] = (T)((A)G[(size_t)r * LG + cc] - sc * sv[r] * wv[cc]);
         }
-        if (ht == 0) lam[q] = lam_new;
+        if (ht == 0) lam[q] = lamn_s[half];
       } else {
         // back to the block-start spin: Schur complement removes q from P,
         // then the last entry of P moves into position q
@@ -659,10 +682,9 @@ __global__ void __launch_bounds__(256) k_proposals(Chain<T>* chains, int gamma_i
           wv[r] = (A)G[(size_t)q * LG + r];
         }
         __syncthreads();
-        const A igqq = (A)1 / sv[q];
         for (int e = ht; e < j * j; e += 128) {
           const int r = e / j, cc = e % j;
-          G[(size_t)r * LG + cc] = (T)((A)G[(size_t)r * LG + cc] - sv[r] * wv[cc] * igqq);
+          G[(size_t)r * LG + cc] = (T)((A)G[(size_t)r * LG + cc] - sv[r] * wv[cc] * sc);
         }
         __syncthreads();
         const int last = j - 1;
@@ -684,7 +706,7 @@ __global__ void __launch_bounds__(256) k_proposals(Chain<T>* chains, int gamma_i
           P_s[j] = p;
           pmap[p] = (short)j;
           jP = j + 1;
-        } else if (lam_new == 0.0) {
+        } else if (to_start) {
           const int last = j - 1;
           if (q != last) {
             P_s[q] = P_s[last];
@@ -698,8 +720,6 @@ __global__ void __launch_bounds__(256) k_proposals(Chain<T>* chains, int gamma_i
         else alive[p >> 5] |= (1u << (p & 31));
         if (move == MV_INSERT) n_cur = nc + 1;
         else if (move == MV_REMOVE) n_cur = nc - 1;
-        if (R < 0.0) sign_s = -sign_s;
-        cnt_acc[move]++;
       }
     }
     __syncthreads();
@@ -771,7 +791,12 @@ __global__ void __launch_bounds__(1024) k_survivors(Chain<T>* chains) {
     if (threadIdx.x == 1023) base_s += warp_tot[31] + __popc(bal);
     __syncthreads();
   }
-  if (threadIdx.x == 0) d.n_new = base_s;
+  if (threadIdx.x == 0) {
+    d.n_new = base_s;
+    // nothing accepted and the survivors are the slots [0, n_new) in order:
+    // N'_SS is the leading block of N_ext, which holds N unchanged in place
+    d.flush_noop = (d.k_acc == 0 && (base_s == 0 || c.S[base_s - 1] == base_s - 1)) ? 1 : 0;
+  }
 }
 
 // Y = (G^0 - 1)_{S,P} Gamma^{-1}, so that N'_{SS} = N_{SS} - Y N_{P,S}
@@ -793,7 +818,7 @@ __device__ __forceinline__ void split_tf32_y(float x, float& hi, float& lo) {
 
 template <typename T, bool SPLIT>
 __device__ __forceinline__ int flush_y_items(const Dyn& d) {
-  if (d.status || (!SPLIT && d.k_acc == 0)) return 0;
+  if (d.status || d.flush_noop || (!SPLIT && d.k_acc == 0)) return 0;
   return 2 * ((d.n_new + kYRows - 1) / kYRows);
 }
 
@@ -874,10 +899,12 @@ __global__ void k_finish_block(Chain<T>* chains, int n_chains) {
   if (d.status) return;
   const double n = d.n, ki = d.k_ins, ka = d.k_acc, nn = d.n_new;
   d.work_prep += 2.0 * (2.0 * ki * n * n + 2.0 * n * n * ki + 2.0 * ki * ki * n);
-  d.work_flush += 2.0 * (2.0 * nn * nn * ka + 2.0 * nn * ka * ka);
-  d.bytes_flush += 2.0 * (2.0 * nn * nn + 2.0 * nn * ka) * sizeof(T);
   d.n = d.n_new;
-  d.buf = 1 - d.buf;
+  if (!d.flush_noop) {
+    d.work_flush += 2.0 * (2.0 * nn * nn * ka + 2.0 * nn * ka * ka);
+    d.bytes_flush += 2.0 * (2.0 * nn * nn + 2.0 * nn * ka) * sizeof(T);
+    d.buf = 1 - d.buf;
+  }
   d.t += (d.tie_pending == 1) ? d.tie_jj : c.k_max;
   d.sweeps += 1;
 }
@@ -1153,11 +1180,6 @@ cudaError_t launch_tie_refine(Chain<float>* dchains, const LaunchShape& ls, doub
                                      0, st);
 }
 
-int tie_refine_blocks_per_sm() {
-  int nb = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tie_refine, 256, 0);
-  return nb;
-}
 
 void launch_tie_eval(Chain<float>* dchains, const LaunchShape& ls, cudaStream_t st) {
   k_tie_eval<<<ls.n_chains, 256, 0, st>>>(dchains);

@@ -74,6 +74,7 @@ struct Dyn {
   double work_gamma;      // algorithmic flops of the Gamma growth (both spins)
   double work_meas;       // algorithmic flops of the G(tau) estimator (both spins)
   double work_refresh;    // algorithmic flops of the FP64 refreshes (2 m^3 per spin)
+  int flush_noop;         // block left N unchanged (nothing accepted, survivors = [0, n))
   int tie_pending;        // mixed form: 1 = proposal d.t awaits an FP64 decision
   int tie_jj;             // index in the block of the near-tie proposal
   int forced_accept;      // FP64 decision of proposal forced_t

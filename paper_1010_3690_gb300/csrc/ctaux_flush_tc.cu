@@ -127,7 +127,7 @@ __device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
 __global__ void __launch_bounds__(256) k_flush_split_x(Chain<float>* chains) {
   const Chain<float>& c = chains[blockIdx.z];
   const Dyn& d = *c.dyn;
-  if (d.status) return;
+  if (d.status || d.flush_noop) return;
   const int spin = blockIdx.y, nn = d.n_new, kacc = d.k_acc, KP = c.kp;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(256) k_flush_split_x(Chain<float>* chains) {
 }
 
 __device__ __forceinline__ int tc_items(const Dyn& d) {
-  if (d.status) return 0;
+  if (d.status || d.flush_noop) return 0;
   const int tiles = (d.n_new + kTcBM - 1) / kTcBM;
   return 2 * tiles * tiles;
 }

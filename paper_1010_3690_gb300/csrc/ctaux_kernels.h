@@ -9,6 +9,7 @@ namespace ctaux {
 
 // Fixed launch shapes of one context (derived from capacities at init, so
 // that a sweep needs no host-side knowledge of the current orders).
+constexpr int kMaxPartials = 4096;  // split-K partial tiles per (chain, spin) and product
 constexpr int kTieSlices = 64;   // column slices of the near-tie matrix-vector products
 constexpr int kMeasChunk = 32;  // vertices per measurement evaluation chunk
 
@@ -26,9 +27,7 @@ struct LaunchShape {
   int n_chains;
   int gather_slices;
   int tiles[PH_COUNT];   // bound on output tiles per (chain, spin)
-  int ksplit[PH_COUNT];  // most slices of the inner dimension a product can need
-  int kchunk;            // fixed slice width of the inner dimension
-  int kstride;           // partial-tile stride per output tile (most slices of any product)
+  int kchunk;            // slice width of the inner dimension (while partial tiles fit)
   int persist_ctas;      // grid of the persistent batched kernels
   int tie_grid;          // cooperative grid of the near-tie refinement
   int y_blocks;
@@ -110,7 +109,6 @@ void launch_tie_eval(Chain<float>* dchains, const LaunchShape& ls, cudaStream_t 
 // part: 2*tie_grid + kTieSlices*max_ld doubles of device scratch
 cudaError_t launch_tie_refine(Chain<float>* dchains, const LaunchShape& ls, double* part,
                               cudaStream_t st);
-int tie_refine_blocks_per_sm();
 template <typename T>
 void launch_reset_measure(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t st);
 int tc_smem_bytes();

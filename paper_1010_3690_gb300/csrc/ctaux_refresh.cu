@@ -95,6 +95,7 @@ __global__ void __launch_bounds__(256) k_refresh(Chain<T>* chains, int n_chains,
   block_exclusive_scan(offr, n_chains);
   block_exclusive_scan(offt, n_chains);
   const int tot_r = offr[n_chains], tot_t = offt[n_chains], max_m = max_m_s;
+  if (tot_r == 0) return;  // nothing to refresh (same decision in every CTA, before any barrier)
 
   // ---- stage 1: N^{-1} of the current configuration into X (one column per
   // CTA and unit); pivot key of column 0
