@@ -152,7 +152,7 @@ ctaux_status build_chains(ctaux_ctx* ctx) {
   int max_rows = 128;
   for (const auto& cp : ctx->chains) max_rows = std::max(max_rows, round_up(cp.capacity + cp.k_max, 128));
   ls.tc_tiles = (max_rows / 128) * (max_rows / 128);
-  ls.tc_ctas = 2 * ctx->sm_count;
+  ls.tc_ctas = ctx->sm_count;
   ls.split_x_blocks = std::max(1, std::min(256, (max_rows + 7) / 8));
   if (mixed_tc) CUDA_TRY(ctx, configure_flush_tc());
   if (sizeof(T) == 4 && P.tie_guard > 0.0) {

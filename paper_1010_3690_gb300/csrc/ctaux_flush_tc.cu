@@ -7,15 +7,23 @@
 //
 // Operands are K-major split buffers written by the flush preparation kernels
 // (Yh/Yl: rows a, Xh/Xl: rows b, KP = k_max rounded up to 32 float32 per row,
-// zero beyond k_acc), loaded by TMA into 128-byte-swizzled shared memory
-// (one TMA load per 128 x 32 tile, no multicast).  One CTA of 256 threads per
-// 128 x 128 output tile, one 64 KB stage so that three CTAs share an SM:
-// thread 0 issues the TMA loads and the MMAs; in the epilogue warps w and
-// w + 4 read TMEM lane quarter w (columns 0-63 and 64-127), with the 32
-// gathered inputs N[S_m][S_n] of each column chunk loaded before the
-// accumulator.  Every mbarrier wait is bounded; on timeout the chain's status gets
-// DS_TIMEOUT, the CTA waits (bounded) for its copies in flight, frees its TMEM
-// and returns.
+// zero beyond k_acc), loaded by TMA into 128-byte-swizzled shared memory (one
+// TMA load per 128 x 32 tile, no multicast).
+//
+// One persistent CTA per SM, warp-specialised, over the (chain, spin,
+// 128 x 128 tile) items of all chains:
+//   warp 0 (one thread): TMA producer into a ring of kTcStages 64 KB stages;
+//   warp 1 (one thread): MMA issuer, 12 tcgen05.mma per 32-wide K step into
+//     one of two 128-column TMEM accumulators, each stage released to the
+//     producer by tcgen05.commit when its MMAs are done;
+//   warps 4-11: epilogue; warp w reads TMEM lane quarter w % 4 (64 of the 128
+//     columns), adds the gathered N[S_m][S_n] and writes the compacted N',
+//     then releases the accumulator, so that the epilogue of one tile overlaps
+//     the loads and MMAs of the next.
+// Every mbarrier wait is bounded.  On timeout the chain's status gets
+// DS_TIMEOUT and every role stops; before the CTA exits, the producer waits
+// (bounded) for the copies it issued, the MMA thread for its MMAs, and the
+// TMEM is freed.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -29,7 +37,7 @@ namespace {
 constexpr int kTileBytes = kTcBM * kTcBK * 4;   // one 128 x 32 float32 operand tile
 constexpr int kStageBytes = 4 * kTileBytes;     // Ah, Al, Bh, Bl
 constexpr uint32_t kWaitLimit = 1u << 24;
-constexpr uint32_t kTmemCols = 128;
+constexpr uint32_t kTmemCols = 2 * kTcBN;       // two accumulators
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -37,6 +45,9 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
 
 __device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t a) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
 }
 __device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes)
@@ -149,11 +160,28 @@ __device__ __forceinline__ int tc_items(const Dyn& d) {
   return 2 * tiles * tiles;
 }
 
-// Persistent over the (chain, spin, tile) items of all chains.  Each mbarrier
-// phase is waited exactly once and in order (full and mdone by thread 0, acc
-// by every thread), so no parity wait can be overtaken by a later phase.
-__global__ void __launch_bounds__(kTcThreads) k_flush_tc(Chain<float>* chains, int n_chains,
-                                                         const TcMaps* maps) {
+struct TcItem {
+  int ci, spin, m0, n0, nk, nn;
+};
+
+__device__ __forceinline__ TcItem tc_item(Chain<float>* chains, const int* off, int n_chains, int w) {
+  TcItem it;
+  it.ci = find_chain(off, n_chains, w);
+  const Dyn& d = *chains[it.ci].dyn;
+  it.nn = d.n_new;
+  const int tiles = (it.nn + kTcBM - 1) / kTcBM;
+  const int l = w - off[it.ci];
+  it.spin = l / (tiles * tiles);
+  const int tile = l % (tiles * tiles);
+  it.m0 = (tile / tiles) * kTcBM;
+  it.n0 = (tile % tiles) * kTcBN;
+  it.nk = (d.k_acc + kTcBK - 1) / kTcBK;
+  return it;
+}
+
+// Barrier completion c (0-based) of an mbarrier has parity c & 1.
+__global__ void __launch_bounds__(kTcThreads, 1) k_flush_tc(Chain<float>* chains, int n_chains,
+                                                            const TcMaps* maps) {
   __shared__ int off[kMaxChains + 1];
   for (int ci = threadIdx.x; ci < n_chains; ci += blockDim.x) off[ci] = tc_items(*chains[ci].dyn);
   __syncthreads();
@@ -166,13 +194,15 @@ __global__ void __launch_bounds__(kTcThreads) k_flush_tc(Chain<float>* chains, i
   unsigned char* base = reinterpret_cast<unsigned char*>(
       ((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = reinterpret_cast<uint64_t*>(base + kTcStages * kStageBytes);
-  uint64_t* mdone = full + 1;
-  uint64_t* accb = mdone + 1;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accb + 1);
-  int* err_s = reinterpret_cast<int*>(tmem_slot + 1);
-  int* Scol = err_s + 1;  // S[n0 .. n0 + 127] of the current tile
+  uint64_t* empty = full + kTcStages;
+  uint64_t* accfull = empty + kTcStages;
+  uint64_t* accempty = accfull + 2;
+  uint64_t* drain = accempty + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  volatile int* err_s = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  uint32_t* mma_taken = reinterpret_cast<uint32_t*>(tmem_slot + 2);  // stages the MMA thread waited for
 
-  if (warp == 0) {
+  if (warp == 2) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tmem_slot)),
                  "r"(kTmemCols)
@@ -180,10 +210,17 @@ __global__ void __launch_bounds__(kTcThreads) k_flush_tc(Chain<float>* chains, i
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (threadIdx.x == 0) {
-    mbar_init(smem_u32(full), 1);
-    mbar_init(smem_u32(mdone), 1);
-    mbar_init(smem_u32(accb), 1);
+    for (int s = 0; s < kTcStages; ++s) {
+      mbar_init(smem_u32(full + s), 1);
+      mbar_init(smem_u32(empty + s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(accfull + b), 1);
+      mbar_init(smem_u32(accempty + b), 8);  // one arrival per epilogue warp
+    }
+    mbar_init(smem_u32(drain), 1);
     *err_s = 0;
+    *mma_taken = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -191,114 +228,147 @@ __global__ void __launch_bounds__(kTcThreads) k_flush_tc(Chain<float>* chains, i
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
-  uint32_t full_uses = 0, mdone_uses = 0, acc_uses = 0;
+  uint32_t issued = 0;  // producer: stages issued
 
-  for (int w = blockIdx.x; w < total; w += gridDim.x) {
-    const int ci = find_chain(off, n_chains, w);
-    const Chain<float>& c = chains[ci];
-    Dyn& d = *c.dyn;
-    const int nn = d.n_new, kacc = d.k_acc, ld = c.ld;
-    const int tiles = (nn + kTcBM - 1) / kTcBM;
-    const int l = w - off[ci];
-    const int spin = l / (tiles * tiles), tile = l % (tiles * tiles);
-    const int m0 = (tile / tiles) * kTcBM, n0 = (tile % tiles) * kTcBN;
-    const int nk = (kacc + kTcBK - 1) / kTcBK;
-    const float* Nb = c.N[d.buf][spin];
-    float* out = c.N[1 - d.buf][spin];
-    const int* S = c.S;
-    for (int e = threadIdx.x; e < kTcBN; e += blockDim.x) Scol[e] = (n0 + e < nn) ? S[n0 + e] : 0;
-    __syncthreads();
-    if (nk == 0) {  // no accepted change: the flush is a pure compaction
-      for (int e = threadIdx.x; e < kTcBM * kTcBN; e += blockDim.x) {
-        const int m = m0 + (e % kTcBM), n = n0 + (e / kTcBM);
-        if (m < nn && n < nn) out[(long)n * ld + m] = Nb[(long)Scol[n - n0] * ld + S[m]];
-      }
-      __syncthreads();
-      continue;
-    }
-    if (threadIdx.x == 0) {
-      const TcMaps& mp = maps[ci * 2 + spin];
-      bool ok = true;
-      for (int kc = 0; kc < nk && ok; ++kc) {
-        const uint32_t fb = smem_u32(full);
-        mbar_expect_tx(fb, kStageBytes);
-        tma_load_2d(smem_u32(base + 0 * kTileBytes), &mp.yh, kc * kTcBK, m0, fb);
-        tma_load_2d(smem_u32(base + 1 * kTileBytes), &mp.yl, kc * kTcBK, m0, fb);
-        tma_load_2d(smem_u32(base + 2 * kTileBytes), &mp.xh, kc * kTcBK, n0, fb);
-        tma_load_2d(smem_u32(base + 3 * kTileBytes), &mp.xl, kc * kTcBK, n0, fb);
-        // bounded; on timeout the same wait is retried (bounded) so that the
-        // copies land before the shared memory is reused or released
-        if (!mbar_wait(fb, full_uses & 1)) {
-          ok = false;
-          mbar_wait(fb, full_uses & 1);
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer
+    for (int w = blockIdx.x; w < total && !*err_s; w += gridDim.x) {
+      const TcItem t = tc_item(chains, off, n_chains, w);
+      if (t.nk == 0) continue;
+      const TcMaps& mp = maps[t.ci * 2 + t.spin];
+      for (int kc = 0; kc < t.nk; ++kc) {
+        const uint32_t stage = issued % kTcStages, use = issued / kTcStages;
+        if (use > 0 && !mbar_wait(smem_u32(empty + stage), (use - 1) & 1)) {
+          *err_s = 1;
+          atomicOr(&chains[t.ci].dyn->status, DS_TIMEOUT);
+          break;
         }
-        ++full_uses;
-        if (!ok) break;
+        const uint32_t fb = smem_u32(full + stage);
+        unsigned char* sb = base + stage * kStageBytes;
+        mbar_expect_tx(fb, kStageBytes);
+        tma_load_2d(smem_u32(sb + 0 * kTileBytes), &mp.yh, kc * kTcBK, t.m0, fb);
+        tma_load_2d(smem_u32(sb + 1 * kTileBytes), &mp.yl, kc * kTcBK, t.m0, fb);
+        tma_load_2d(smem_u32(sb + 2 * kTileBytes), &mp.xh, kc * kTcBK, t.n0, fb);
+        tma_load_2d(smem_u32(sb + 3 * kTileBytes), &mp.xl, kc * kTcBK, t.n0, fb);
+        ++issued;
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer
+    uint32_t taken = 0, q = 0;
+    for (int w = blockIdx.x; w < total && !*err_s; w += gridDim.x) {
+      const TcItem t = tc_item(chains, off, n_chains, w);
+      if (t.nk == 0) continue;
+      const uint32_t b = q & 1, ub = q >> 1;
+      bool ok = ub == 0 || mbar_wait(smem_u32(accempty + b), (ub - 1) & 1);
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t acc = tmem + b * kTcBN;
+      for (int kc = 0; kc < t.nk && ok; ++kc) {
+        const uint32_t stage = taken % kTcStages, use = taken / kTcStages;
+        if (!mbar_wait(smem_u32(full + stage), use & 1)) {
+          ok = false;
+          break;
+        }
+        ++taken;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t ah = smem_u32(base), al = ah + kTileBytes, bh = ah + 2 * kTileBytes,
-                       bl = ah + 3 * kTileBytes;
+        const uint32_t ah = smem_u32(base + stage * kStageBytes), al = ah + kTileBytes,
+                       bh = ah + 2 * kTileBytes, bl = ah + 3 * kTileBytes;
 #pragma unroll
         for (int kk = 0; kk < kTcBK / 8; ++kk) {
           const uint32_t offk = kk * 32;  // 8 tf32 = 32 bytes along K
           const uint32_t first = (kc == 0 && kk == 0) ? 0u : 1u;
-          mma_tf32(tmem, smem_desc(ah + offk), smem_desc(bl + offk), first);  // hi * lo
-          mma_tf32(tmem, smem_desc(al + offk), smem_desc(bh + offk), 1u);     // lo * hi
-          mma_tf32(tmem, smem_desc(ah + offk), smem_desc(bh + offk), 1u);     // hi * hi
+          mma_tf32(acc, smem_desc(ah + offk), smem_desc(bl + offk), first);  // hi * lo
+          mma_tf32(acc, smem_desc(al + offk), smem_desc(bh + offk), 1u);     // lo * hi
+          mma_tf32(acc, smem_desc(ah + offk), smem_desc(bh + offk), 1u);     // hi * hi
         }
-        mma_commit(smem_u32(mdone));
-        if (!mbar_wait(smem_u32(mdone), mdone_uses & 1)) ok = false;
-        ++mdone_uses;
+        mma_commit(smem_u32(empty + stage));  // stage free once these MMAs are done
       }
       if (!ok) {
         *err_s = 1;
-        atomicOr(&d.status, DS_TIMEOUT);
+        atomicOr(&chains[t.ci].dyn->status, DS_TIMEOUT);
+        break;
       }
-      mma_commit(smem_u32(accb));  // arrives when every MMA issued so far has completed
+      mma_commit(smem_u32(accfull + b));
+      ++q;
     }
-    __syncthreads();
-    const bool acc_ok = mbar_wait(smem_u32(accb), acc_uses & 1);
-    ++acc_uses;
-    // one decision for the whole CTA: tcgen05.ld is warp-collective
-    const bool all_ok = __syncthreads_and(acc_ok && *err_s == 0) != 0;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (all_ok) {
-      const int quarter = warp & 3, colhalf = warp >> 2;
-      const int m = m0 + quarter * 32 + lane;
+    *mma_taken = taken;
+    // every MMA issued so far has completed before the TMEM can be freed
+    mma_commit(smem_u32(drain));
+    mbar_wait(smem_u32(drain), 0);
+  } else if (warp >= 4) {
+    // ---- epilogue: warp w, TMEM lanes 32 (w % 4) .. + 31, column half (w - 4) / 4
+    const int quarter = warp & 3, colhalf = (warp - 4) >> 2;
+    uint32_t q = 0;
+    for (int w = blockIdx.x; w < total; w += gridDim.x) {
+      if (__any_sync(0xffffffffu, *err_s != 0)) break;
+      const TcItem t = tc_item(chains, off, n_chains, w);
+      const Chain<float>& c = chains[t.ci];
+      const Dyn& d = *c.dyn;
+      const int ld = c.ld, nn = t.nn;
+      const float* Nb = c.N[d.buf][t.spin];
+      float* out = c.N[1 - d.buf][t.spin];
+      const int* S = c.S;
+      const int m = t.m0 + quarter * 32 + lane;
       const bool row_ok = m < nn;
       const long srow = row_ok ? S[m] : 0;
+      if (t.nk == 0) {  // no accepted change: the flush is a pure compaction
+        if (row_ok)
+          for (int j = colhalf * 64; j < colhalf * 64 + 64; ++j) {
+            const int n = t.n0 + j;
+            if (n < nn) out[(long)n * ld + m] = Nb[(long)__ldg(S + n) * ld + srow];
+          }
+        continue;
+      }
+      const uint32_t b = q & 1, ub = q >> 1;
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(accfull + b), ub & 1));
+      if (!ok) {
+        if (lane == 0) {
+          *err_s = 1;
+          atomicOr(&c.dyn->status, DS_TIMEOUT);
+        }
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       float v[32], cin[32];
 #pragma unroll 1
       for (int cc = colhalf * 2; cc < colhalf * 2 + 2; ++cc) {
         // the 32 gathered inputs of this chunk: independent loads, issued first
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
-          const int n = n0 + cc * 32 + j;
-          cin[j] = (row_ok && n < nn) ? Nb[(long)Scol[cc * 32 + j] * ld + srow] : 0.f;
+          const int n = t.n0 + cc * 32 + j;
+          cin[j] = (row_ok && n < nn) ? Nb[(long)__ldg(S + n) * ld + srow] : 0.f;
         }
-        tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(cc * 32), v);
+        tmem_ld32(tmem + b * kTcBN + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(cc * 32), v);
         if (row_ok) {
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
-            const int n = n0 + cc * 32 + j;
+            const int n = t.n0 + cc * 32 + j;
             if (n < nn) out[(long)n * ld + m] = cin[j] - v[j];
           }
         }
       }
-    } else if (threadIdx.x == 0) {
-      atomicOr(&d.status, DS_TIMEOUT);
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(accempty + b));
+      ++q;
     }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    if (!all_ok) break;
   }
   __syncthreads();
-  if (warp == 0)
+  if (threadIdx.x == 0) {
+    // copies issued but never waited for (only after a timeout): let them land
+    for (uint32_t i = *mma_taken; i < issued; ++i)
+      mbar_wait(smem_u32(full + i % kTcStages), (i / kTcStages) & 1);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 2)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                  "r"(kTmemCols)
                  : "memory");
 }
 
-int tc_smem_bytes() { return kTcStages * kStageBytes + 1024 + 1024; }
+int tc_smem_bytes() { return kTcStages * kStageBytes + 1024 + 256; }
 
 cudaError_t configure_flush_tc() {
   return cudaFuncSetAttribute(k_flush_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,

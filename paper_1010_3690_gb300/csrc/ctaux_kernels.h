@@ -14,7 +14,7 @@ constexpr int kTieSlices = 64;   // column slices of the near-tie matrix-vector 
 constexpr int kMeasChunk = 32;  // vertices per measurement evaluation chunk
 
 // tensor-core flush (mixed form): 128 x 128 output tiles, K chunks of 32 float32
-constexpr int kTcBM = 128, kTcBN = 128, kTcBK = 32, kTcStages = 1, kTcThreads = 256;
+constexpr int kTcBM = 128, kTcBN = 128, kTcBK = 32, kTcStages = 3, kTcThreads = 384;
 
 // TMA descriptors of one (chain, spin): split Y (rows a) and split X (rows b)
 struct TcMaps {
@@ -39,7 +39,7 @@ struct LaunchShape {
   int refresh_grid;
   int use_tc;            // mixed form: flush on the tensor cores
   int tc_tiles;          // bound on 128 x 128 flush tiles per (chain, spin)
-  int tc_ctas;           // persistent grid of the tensor-core flush (two CTAs per SM)
+  int tc_ctas;           // persistent grid of the tensor-core flush (one CTA per SM)
   int split_x_blocks;
 };
 
