@@ -95,8 +95,12 @@ typedef struct {
                                          split 3xTF32), 0 = float32 CUDA-core product */
   double tie_guard;                   /* mixed form: a proposal with |u - min(1,|R|)| below
                                          tie_guard * max(u, min(1,|R|)) is decided in FP64
-                                         (the block stops there; FP64 refresh; exact first-touch
-                                         ratio); 0 = off; must be < 1 */
+                                         (the block stops there; FP64 iterative refinement of
+                                         the first-touch ratio, or a from-scratch FP64 refresh
+                                         where it does not converge); 0 = off; must be < 1 */
+  int tie_refine_iters;               /* mixed form: most refinement iterations per near tie;
+                                         0 = 12; -1 = none, so that every near tie takes the
+                                         from-scratch fallback (for tests) */
 } ctaux_params;
 
 typedef struct {

@@ -159,6 +159,7 @@ ctaux_status build_chains(ctaux_ctx* ctx) {
     // one CTA per SM: the refinement is a chain of short grid-wide steps, so
     // barrier latency (which grows with the number of CTAs) dominates
     ls.tie_grid = ctx->sm_count;
+    ls.tie_iters = P.tie_refine_iters == 0 ? 12 : std::max(0, P.tie_refine_iters);
     ctx->tie_part = dalloc<double>(ctx, 2 * (size_t)ls.tie_grid + (size_t)kTieSlices * max_ld, &err);
   }
   std::vector<TcMaps> host_maps(mixed_tc ? 2 * ctx->chains.size() : 0);
@@ -179,6 +180,8 @@ ctaux_status build_chains(ctaux_ctx* ctx) {
       for (int dd = -2; dd <= 2; ++dd) {
         c.ev[spin][dd + 2] = (dd == 0) ? 1.0 : std::exp(c.gamma * sig * dd);
         c.inv_em1[spin][dd + 2] = (dd == 0) ? 0.0 : 1.0 / (c.ev[spin][dd + 2] - 1.0);
+        const T lam = (T)(c.ev[spin][dd + 2] - 1.0);
+        c.glam[spin][dd + 2] = (dd == 0) ? (T)0 : ((T)1 + lam) / lam;
       }
     }
     c.p_insert = P.p_insert;
@@ -332,18 +335,13 @@ ctaux_status do_sweeps(ctaux_ctx* ctx, int n_sweeps, int measure, cudaStream_t s
   for (int s = 0; s < n_sweeps; ++s) {
     launch_block<T>(dc, ctx->ls, st, pt, ctx->tc_maps_dev);
     if (ties) {
-      // near-tie decisions in FP64: iterative refinement against the float32 N;
-      // where it does not converge, a from-scratch FP64 refresh keeping the
-      // FP64 N (kernels exit at once without a pending tie)
+      // near-tie decisions in FP64: iterative refinement against the float32 N,
+      // with a from-scratch FP64 refresh in the same launch where it does not
+      // converge (exits at once without a pending tie)
       pt->begin(7, st);
       cudaError_t e = launch_tie_refine(reinterpret_cast<Chain<float>*>(dc), ctx->ls, ctx->tie_part, st);
       pt->end(7, st, 1);
-      if (e == cudaSuccess) e = launch_refresh<T>(dc, ctx->ls, -1, st, pt, 1);
-      if (e == cudaSuccess) {
-        launch_tie_eval(reinterpret_cast<Chain<float>*>(dc), ctx->ls, st);
-        pt->kernels[6] += 1;
-      }
-      if (e != cudaSuccess) return set_err(ctx, CTAUX_ECUDA, "tie refresh launch: %s", cudaGetErrorString(e));
+      if (e != cudaSuccess) return set_err(ctx, CTAUX_ECUDA, "tie decision launch: %s", cudaGetErrorString(e));
     }
     ctx->blocks_since_refresh += 1;
     if (ctx->params.refresh_every > 0 && ctx->blocks_since_refresh >= ctx->params.refresh_every) {

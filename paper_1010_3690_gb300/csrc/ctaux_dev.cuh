@@ -89,6 +89,7 @@ struct Chain {
   double beta, K, gamma, dtau, inv_dtau;
   double ev[2][5];           // e^{gamma sigma d}, d = -2..2  (index d + 2)
   double inv_em1[2][5];      // 1 / (e^{gamma sigma d} - 1), d != 0
+  T glam[2][5];              // (1 + lambda) / lambda in T, lambda = e^{gamma sigma d} - 1, d != 0
   double p_insert, p_remove;
   int n_c, n_classes, n_tau, k_max, cap_m, ld;
   uint64_t seed;

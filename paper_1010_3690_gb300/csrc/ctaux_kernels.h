@@ -30,6 +30,7 @@ struct LaunchShape {
   int kchunk;            // slice width of the inner dimension (while partial tiles fit)
   int persist_ctas;      // grid of the persistent batched kernels
   int tie_grid;          // cooperative grid of the near-tie refinement
+  int tie_iters;         // most refinement iterations (0: every near tie takes the fallback)
   int y_blocks;
   int prop_smem;
   int gamma_in_smem;
@@ -105,7 +106,6 @@ void launch_measure(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t st, P
 template <typename T>
 cudaError_t launch_refresh(Chain<T>* dchains, const LaunchShape& ls, int only_chain,
                            cudaStream_t st, PhaseTimer* pt, int filter = 0);
-void launch_tie_eval(Chain<float>* dchains, const LaunchShape& ls, cudaStream_t st);
 // part: 2*tie_grid + kTieSlices*max_ld doubles of device scratch
 cudaError_t launch_tie_refine(Chain<float>* dchains, const LaunchShape& ls, double* part,
                               cudaStream_t st);

@@ -1,0 +1,305 @@
+// From-scratch FP64 recomputation of N for every chain (device bodies, shared
+// by the refresh kernel and the near-tie fallback of the refinement kernel):
+// build
+// N^{-1} = e^V - G0 (e^V - 1) (Eq. Nmatrix) from the configuration, invert
+// by blocked Gauss-Jordan with partial pivoting, report the drift of the
+// running N and replace it.  One cooperative launch: all chains and spins
+// advance in lockstep, separated by grid-wide barriers (no spin waits); the
+// work of each stage is spread over the whole grid across chains.
+//
+// Unblocked column step c (pivot row pr) maps X to
+//   X[pr][j] / X[pr][c] (j != c), 1 / X[pr][c] at (pr, c),
+//   -X[i][c] / X[pr][c] at (i, c), X[i][j] - X[i][c] X[pr][j] / X[pr][c] elsewhere.
+// Blocked: for a panel C of 32 columns with pivot rows R, the column steps are
+// applied to the panel alone (a copy, ping-pong), giving P' = X'[:, C]; every
+// other column then follows in one rank-32 product
+//   X'[:, J] = Z[:, J] + P' X[R, J],  Z = X with the rows R set to zero.
+// After all panels, N[c][perm[j]] = X[perm[c]][j] and
+// log|det N^{-1}| = sum_c log|pivot_c|.
+// Pivots: the largest |value| over rows not yet pivoted, folded while the
+// previous step writes that column: atomicMax of a 64-bit key (float
+// magnitude, ties to the lower row) per (chain, spin, column).
+#pragma once
+
+#include <cooperative_groups.h>
+
+#include "ctaux_dev.cuh"
+#include "ctaux_kernels.h"
+
+namespace ctaux {
+
+namespace cg = cooperative_groups;
+
+__device__ __forceinline__ unsigned long long pivot_key(double v, int row) {
+  const float a = (float)fabs(v);
+  return ((unsigned long long)__float_as_uint(a) << 32) | (unsigned long long)(0xffffffffu - (unsigned)row);
+}
+__device__ __forceinline__ int key_row(unsigned long long k) {
+  return (int)(0xffffffffu - (unsigned)(k & 0xffffffffull));
+}
+
+constexpr int kPB = 32;  // panel width
+
+// per-spin work area: X (ld x ld), two panel buffers (ld x kPB), pivot rows (ld x kPB)
+__host__ __device__ inline size_t refresh_work_per_spin(int ld) {
+  return (size_t)ld * ld + (size_t)3 * kPB * ld;
+}
+
+// Size of the refresh of chain ci (0 when it does not take part).
+template <typename T>
+__device__ __forceinline__ int refresh_order(const Chain<T>& c, int ci, int c_lo, int c_hi, int filter) {
+  if (ci < c_lo || ci >= c_hi) return 0;
+  const Dyn& d = *c.dyn;
+  if ((d.status & ~DS_SINGULAR) || (filter && d.tie_pending != filter)) return 0;
+  return d.n;
+}
+
+// Work of every stage is spread over the grid across all chains: "row units"
+// (chain, spin, row or column index; 2m per chain) go to threads or CTAs by a
+// prefix sum over chains, "tile units" (chain, spin, 32 x 32 tile) to CTAs.
+struct RowUnit {
+  int ci, spin, i, m;
+};
+
+__device__ __forceinline__ RowUnit row_unit(const int* offr, int n_chains, int u) {
+  RowUnit r;
+  r.ci = find_chain(offr, n_chains, u);
+  r.m = (offr[r.ci + 1] - offr[r.ci]) >> 1;
+  const int l = u - offr[r.ci];
+  r.spin = l / r.m;
+  r.i = l - r.spin * r.m;
+  return r;
+}
+
+template <typename T>
+__device__ void refresh_body(Chain<T>* chains, int n_chains, int only_chain, int filter) {
+  cg::grid_group grid = cg::this_grid();
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int gthreads = gridDim.x * blockDim.x;
+  const int c_lo = only_chain >= 0 ? only_chain : 0;
+  const int c_hi = only_chain >= 0 ? only_chain + 1 : n_chains;
+  __shared__ int offr[kMaxChains + 1];
+  __shared__ int offt[kMaxChains + 1];
+  __shared__ int max_m_s;
+  __shared__ double Ps[32][kPB + 1];
+  __shared__ double Rs[kPB][33];
+  __shared__ double red[2][8];
+
+  if (threadIdx.x == 0) max_m_s = 0;
+  __syncthreads();
+  for (int ci = threadIdx.x; ci < n_chains; ci += blockDim.x) {
+    const int m = refresh_order(chains[ci], ci, c_lo, c_hi, filter);
+    const int tb = (m + 31) / 32;
+    offr[ci] = 2 * m;
+    offt[ci] = 2 * tb * tb;
+    atomicMax(&max_m_s, m);
+  }
+  __syncthreads();
+  block_exclusive_scan(offr, n_chains);
+  block_exclusive_scan(offt, n_chains);
+  const int tot_r = offr[n_chains], tot_t = offt[n_chains], max_m = max_m_s;
+  if (tot_r == 0) return;  // nothing to refresh (same decision in every CTA, before any barrier)
+
+  // ---- stage 1: N^{-1} of the current configuration into X (one column per
+  // CTA and unit); pivot key of column 0
+  for (int u = blockIdx.x; u < tot_r; u += gridDim.x) {
+    const RowUnit ru = row_unit(offr, n_chains, u);
+    const Chain<T>& c = chains[ru.ci];
+    const int m = ru.m, spin = ru.spin, j = ru.i, buf = c.dyn->buf, ld = c.ld;
+    double* X = c.work + (size_t)spin * refresh_work_per_spin(ld);
+    unsigned long long* keys = c.pkeys + (size_t)spin * ld;
+    const double evj = c.ev[spin][c.s[buf][j] + 2];
+    const double tj = c.tau[buf][j];
+    const int sj = c.site[buf][j];
+    if (j == 0 && threadIdx.x == 0) c.work_logdet[spin] = 0.0;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      double v = -g0_eval(c, spin, c.tau[buf][i], c.site[buf][i], tj, sj) * (evj - 1.0);
+      if (i == j) v += evj;
+      X[(size_t)j * ld + i] = v;
+      if (j == 0) atomicMax(keys, pivot_key(v, i));
+    }
+  }
+  grid.sync();
+
+  // ---- stage 2: panels
+  for (int c0 = 0; c0 < max_m; c0 += kPB) {
+    // A0: copy the panel columns ((row unit, panel column) pairs)
+    for (int u = gtid; u < tot_r * kPB; u += gthreads) {
+      const int k = u / tot_r;
+      const RowUnit ru = row_unit(offr, n_chains, u - k * tot_r);
+      if (c0 + k >= ru.m) continue;
+      const Chain<T>& c = chains[ru.ci];
+      const int ld = c.ld;
+      const double* X = c.work + (size_t)ru.spin * refresh_work_per_spin(ld);
+      double* Pa = const_cast<double*>(X) + (size_t)ld * ld;
+      Pa[(size_t)k * ld + ru.i] = X[(size_t)(c0 + k) * ld + ru.i];
+    }
+    grid.sync();
+    // A1: the column steps, on the panel only ((row unit, panel column) pairs)
+    for (int k = 0; k < kPB; ++k) {
+      for (int u = gtid; u < tot_r * kPB; u += gthreads) {
+        const int kk = u / tot_r;
+        const RowUnit ru = row_unit(offr, n_chains, u - kk * tot_r);
+        if (c0 + k >= ru.m || c0 + kk >= ru.m) continue;
+        const Chain<T>& c = chains[ru.ci];
+        const int ld = c.ld, col = c0 + k, i = ru.i, spin = ru.spin;
+        double* X = c.work + (size_t)spin * refresh_work_per_spin(ld);
+        double* Pa = X + (size_t)ld * ld;
+        double* Pb = Pa + (size_t)kPB * ld;
+        const double* src = (k & 1) ? Pb : Pa;
+        double* dst = (k & 1) ? Pa : Pb;
+        unsigned long long* keys = c.pkeys + (size_t)spin * ld;
+        int8_t* used = c.used + spin * ld;
+        const int pr = key_row(keys[col]);
+        const double piv = src[(size_t)k * ld + pr];
+        if (i == 0 && kk == 0) {
+          c.perm[spin * ld + col] = pr;
+          used[pr] = 1;  // read below only for rows other than pr
+          c.pcol[spin * ld + pr] = col;
+          if (!(fabs(piv) > 0.0) || !isfinite(piv)) atomicOr(&c.dyn->status, DS_SINGULAR);
+          c.work_logdet[spin] += log(fabs(piv));
+        }
+        const double ipiv = 1.0 / piv;
+        const double xic = src[(size_t)k * ld + i];
+        double v;
+        if (i == pr) v = (kk == k) ? ipiv : src[(size_t)kk * ld + pr] * ipiv;
+        else if (kk == k) v = -xic * ipiv;
+        else v = src[(size_t)kk * ld + i] - xic * (src[(size_t)kk * ld + pr] * ipiv);
+        dst[(size_t)kk * ld + i] = v;
+        if (kk == k + 1 && i != pr && !used[i]) atomicMax(keys + col + 1, pivot_key(v, i));
+      }
+      grid.sync();
+    }
+    // B0: pivot rows of this panel, outside it, from X before the update:
+    // Rr[j][k] = X[R_k][j] ((row unit = column j, k) pairs)
+    for (int u = gtid; u < tot_r * kPB; u += gthreads) {
+      const int k = u % kPB;
+      const RowUnit ru = row_unit(offr, n_chains, u / kPB);
+      if (c0 >= ru.m) continue;
+      const Chain<T>& c = chains[ru.ci];
+      const int ld = c.ld, j = ru.i;
+      const double* X = c.work + (size_t)ru.spin * refresh_work_per_spin(ld);
+      double* Rr = const_cast<double*>(X) + (size_t)ld * ld + (size_t)2 * kPB * ld;
+      const int* perm = c.perm + ru.spin * ld;
+      Rr[(size_t)j * kPB + k] = (c0 + k < ru.m) ? X[(size_t)j * ld + perm[c0 + k]] : 0.0;
+    }
+    grid.sync();
+    // B1: trailing rank-bw update in 32 x 32 tiles (tile units), panel written
+    // back, pivot key of the next panel's first column
+    for (int u = blockIdx.x; u < tot_t; u += gridDim.x) {
+      const int ci = find_chain(offt, n_chains, u);
+      const int m = (offr[ci + 1] - offr[ci]) >> 1;
+      if (c0 >= m) continue;  // uniform over the CTA
+      const Chain<T>& c = chains[ci];
+      const int tb = (m + 31) / 32, l = u - offt[ci];
+      const int spin = l / (tb * tb), tile = l - spin * tb * tb;
+      const int ld = c.ld, bw = min(kPB, m - c0), cn = c0 + bw;
+      double* X = c.work + (size_t)spin * refresh_work_per_spin(ld);
+      double* Pa = X + (size_t)ld * ld;
+      const double* Pf = (bw & 1) ? Pa + (size_t)kPB * ld : Pa;  // panel after bw steps
+      const double* Rr = Pa + (size_t)2 * kPB * ld;
+      unsigned long long* keys = c.pkeys + (size_t)spin * ld;
+      const int8_t* used = c.used + spin * ld;
+      const int* pcol = c.pcol + spin * ld;
+      const int i0 = (tile % tb) * 32, j0 = (tile / tb) * 32;
+      __syncthreads();
+      for (int e = threadIdx.x; e < 32 * kPB; e += blockDim.x) {
+        const int r = e % 32, k = e / 32;
+        Ps[r][k] = (i0 + r < m && k < bw) ? Pf[(size_t)k * ld + i0 + r] : 0.0;
+        const int jj = e % 32, kk = e / 32;
+        Rs[kk][jj] = (j0 + jj < m) ? Rr[(size_t)(j0 + jj) * kPB + kk] : 0.0;
+      }
+      __syncthreads();
+      const int r = threadIdx.x % 32, i = i0 + r;
+      if (i < m) {
+        const int pci = pcol[i];
+        const bool in_R = pci >= c0 && pci < cn;
+        for (int q = threadIdx.x / 32; q < 32; q += blockDim.x / 32) {
+          const int j = j0 + q;
+          if (j >= m) continue;
+          double v;
+          if (j >= c0 && j < cn) {
+            v = Ps[r][j - c0];
+          } else {
+            double acc = in_R ? 0.0 : X[(size_t)j * ld + i];
+#pragma unroll 8
+            for (int k = 0; k < kPB; ++k) acc += Ps[r][k] * Rs[k][q];
+            v = acc;
+          }
+          X[(size_t)j * ld + i] = v;
+          if (j == cn && !used[i]) atomicMax(keys + cn, pivot_key(v, i));
+        }
+      }
+    }
+    grid.sync();
+  }
+
+  // ---- stage 3: unscramble, drift against the running N (reduced per CTA
+  // and column), replace it; clear the pivot keys and flags for the next refresh
+  for (int u = blockIdx.x; u < tot_r; u += gridDim.x) {
+    const RowUnit ru = row_unit(offr, n_chains, u);
+    const Chain<T>& c = chains[ru.ci];
+    const int m = ru.m, spin = ru.spin, j = ru.i, ld = c.ld, buf = c.dyn->buf;
+    const double* X = c.work + (size_t)spin * refresh_work_per_spin(ld);
+    const int* perm = c.perm + spin * ld;
+    T* Nr = c.N[buf][spin];
+    double* N64 = (filter == 1) ? c.N64[spin] : nullptr;
+    const int pj = perm[j];
+    double dmax = 0.0, dsq = 0.0;
+    for (int cc = threadIdx.x; cc < m; cc += blockDim.x) {
+      const double v = X[(size_t)j * ld + perm[cc]];  // N[cc][perm[j]]
+      const long o = (long)pj * ld + cc;
+      if (N64) N64[o] = v;
+      const double diff = fabs((double)Nr[o] - v);
+      dmax = fmax(dmax, diff);
+      dsq += diff * diff;
+      Nr[o] = (T)v;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+      dsq += __shfl_xor_sync(0xffffffffu, dsq, o);
+    }
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) {
+      red[0][threadIdx.x >> 5] = dmax;
+      red[1][threadIdx.x >> 5] = dsq;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double bm = 0.0, bs = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        bm = fmax(bm, red[0][w]);
+        bs += red[1][w];
+      }
+      if (bm > 0.0)
+        atomicMax(reinterpret_cast<unsigned long long*>(&c.work_drift[0]),
+                  (unsigned long long)__double_as_longlong(bm));
+      if (bs > 0.0) atomicAdd(&c.work_drift[1], bs);
+    }
+  }
+  grid.sync();  // every column has read perm before the flags are cleared
+  for (int u = gtid; u < tot_r; u += gthreads) {
+    const RowUnit ru = row_unit(offr, n_chains, u);
+    const Chain<T>& c = chains[ru.ci];
+    const int ld = c.ld;
+    c.pkeys[(size_t)ru.spin * ld + ru.i] = 0ull;
+    c.used[ru.spin * ld + ru.i] = 0;
+    c.pcol[ru.spin * ld + ru.i] = -1;
+  }
+}
+
+// Permutation signs, log det and drift of a refreshed chain into its stats.
+template <typename T>
+__device__ __forceinline__ void refresh_finish_one(const Chain<T>& c, int filter) {
+  Dyn& d = *c.dyn;
+  if ((d.status & ~DS_SINGULAR) || (filter && d.tie_pending != filter)) return;
+  d.refreshes += 1;
+  d.work_refresh += 4.0 * (double)d.n * (double)d.n * (double)d.n;  // 2 m^3 per spin
+  d.drift_max = c.work_drift[0];
+  d.drift_fro = sqrt(c.work_drift[1]);
+  c.work_drift[0] = 0.0;
+  c.work_drift[1] = 0.0;
+  for (int spin = 0; spin < 2; ++spin) d.logdet[spin] = c.work_logdet[spin];
+}
+
+}  // namespace ctaux

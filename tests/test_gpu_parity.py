@@ -332,3 +332,33 @@ def test_mixed_near_ties_are_decided_in_fp64():
                 ref = o["ratio"][s]
                 assert abs(g["ratio"][s] - ref) <= 1e-9 * max(1.0, abs(ref)), (g, o)
     assert n_fp64 >= 10 and st["near_ties"] >= n_fp64
+    assert st["tie_refreshes"] == 0   # every refinement converged
+
+
+def test_mixed_near_tie_fallback_refresh_decides_in_fp64():
+    """With the refinement switched off every near tie takes the fallback: a
+    from-scratch FP64 refresh inside the same launch and the decision from its
+    FP64 N.  Same accept sequence as the FP64 oracle, FP64-accurate ratios."""
+    ch = configs.cube8(K=1.0, k_max=32, capacity=256)
+    cfg = configs.synthetic_configuration(ch, 140, seed=3)
+    oc = oracle_for(ch)
+    oc.set_config(cfg["tau"], cfg["site"], cfg["s"], cfg["birth"], cfg["t"])
+    with pk.Context([ch], precision=pk.CTAUX_MIXED, trace_capacity=4096, refresh_every=8,
+                    tie_guard=0.5, tie_refine_iters=-1) as ctx:
+        ctx.set_config(0, cfg["tau"], cfg["site"], cfg["s"], cfg["birth"], cfg["t"])
+        ctx.sweep(16)
+        ctx.synchronize()
+        tr = ctx.trace(0)
+        st = ctx.stats(0)
+    recs = oc.run(len(tr))
+    assert st["t"] == oc.t
+    n_fp64 = 0
+    for g, o in zip(tr, recs):
+        assert int(g["t"]) == o["t"] and int(g["move"]) == o["move"]
+        assert bool(int(g["accept"]) & 1) == o["accept"], (g, o)
+        if int(g["accept"]) & 2 and o["birth"] >= 0:
+            n_fp64 += 1
+            for s in (0, 1):
+                ref = o["ratio"][s]
+                assert abs(g["ratio"][s] - ref) <= 1e-9 * max(1.0, abs(ref)), (g, o)
+    assert n_fp64 >= 5 and st["tie_refreshes"] >= n_fp64
