@@ -90,7 +90,6 @@ ctaux_status build_chains(ctaux_ctx* ctx) {
   hc.resize(ctx->chains.size());
   cudaError_t err = cudaSuccess;
   int max_ld = 0, max_k = 1, max_cls_bins = 1, max_pts = 1;
-  int max_tiles[PH_COUNT] = {0, 0, 0, 0, 0};
   // launch shape first (tile bounds and k splits from the capacities)
   const int items = 2 * (int)ctx->chains.size();
   for (size_t ci = 0; ci < ctx->chains.size(); ++ci) {
@@ -101,37 +100,31 @@ ctaux_status build_chains(ctaux_ctx* ctx) {
     max_k = std::max(max_k, cp.k_max);
     max_cls_bins = std::max(max_cls_bins, cp.n_classes * P.n_tau_bins);
     max_pts = std::max(max_pts, P.n_anchors * cp.n_c * P.n_tau_bins);
-    const int te = sizeof(T) == 8 ? 32 : 64;  // output tile edge of the products
-    const int tm = (cap_m + te - 1) / te, tk = (cp.k_max + te - 1) / te, ta = (P.n_anchors + te - 1) / te;
-    max_tiles[PH_RTILDE] = std::max(max_tiles[PH_RTILDE], tk * tm);
-    max_tiles[PH_GCOL_OLD] = std::max(max_tiles[PH_GCOL_OLD], tm * tk);
-    max_tiles[PH_GCOL_NEW] = std::max(max_tiles[PH_GCOL_NEW], tk * tk);
-    max_tiles[PH_FLUSH] = std::max(max_tiles[PH_FLUSH], tm * tm);
-    max_tiles[PH_MEAS] = std::max(max_tiles[PH_MEAS], tm * ta);
   }
   LaunchShape& ls = ctx->ls;
   ls.n_chains = (int)ctx->chains.size();
   // fixed slice width of the inner dimension: narrow for FP64 (the FP64 pipe
   // is the bottleneck, so more CTAs), wider for FP32
   ls.kchunk = (sizeof(T) == 8) ? 32 : 128;
-  for (int ph = 0; ph < PH_COUNT; ++ph) ls.tiles[ph] = std::max(1, max_tiles[ph]);
   // split-K partial tiles per (chain, spin): the most any product of the chain
   // can use at its capacity, at most kMaxPartials (device rule in gemm_items)
   std::vector<size_t> kpart_of(ctx->chains.size(), 1);
-  const size_t te2 = sizeof(T) == 8 ? 32 * 32 : 64 * 64;
   for (size_t ci = 0; ci < ctx->chains.size(); ++ci) {
     const ctaux_chain_params& cp = ctx->chains[ci];
-    const int te = sizeof(T) == 8 ? 32 : 64;
-    const int cap_m = cp.capacity + cp.k_max;
-    const long tm = (cap_m + te - 1) / te, tk = (cp.k_max + te - 1) / te;
-    const long tiles[PH_COUNT] = {tk * tm, tm * tk, tk * tk, tm * tm, tm * ((P.n_anchors + te - 1) / te)};
-    size_t need = 1;
+    const long cap_m = cp.capacity + cp.k_max, k = cp.k_max;
+    // output rows and columns of each product at capacity (setup_gemm)
+    const long rows[PH_COUNT] = {k, cap_m, k, cap_m, cap_m};
+    const long cols[PH_COUNT] = {cap_m, k, k, cap_m, P.n_anchors};
+    size_t need = 1;  // elements
     for (int ph = 0; ph < PH_COUNT; ++ph) {
-      const int k_inner = ph == PH_FLUSH ? cp.k_max : cap_m;
-      const long ks = std::max(1, (k_inner + ls.kchunk - 1) / ls.kchunk);
-      if (ks > 1) need = std::max(need, (size_t)std::min<long>(kMaxPartials, tiles[ph] * ks));
+      const GemmTile tl = gemm_tile(sizeof(T) == 8, ph);
+      const long tiles = ((rows[ph] + tl.bm - 1) / tl.bm) * ((cols[ph] + tl.bn - 1) / tl.bn);
+      const long k_inner = ph == PH_FLUSH ? k : cap_m;
+      const long ks = std::max<long>(1, (k_inner + ls.kchunk - 1) / ls.kchunk);
+      if (ks > 1)
+        need = std::max(need, (size_t)std::min<long>(kMaxPartials, tiles * ks) * tl.bm * tl.bn);
     }
-    kpart_of[ci] = need * te2;
+    kpart_of[ci] = need;
   }
   ls.persist_ctas = 8 * ctx->sm_count;   // 256-thread CTAs: up to 8 resident per SM
   ls.gather_slices = std::max(1, std::min(64, (2 * ctx->sm_count + items - 1) / items));

@@ -183,12 +183,6 @@ __device__ __forceinline__ bool setup_gemm(const Chain<T>& c, const Dyn& d, int 
 }
 
 constexpr int GBK = 16;
-// Output tile edge: 32 for float64 (the FP64 pipe is the bottleneck, so padded
-// rows cost real time and more CTAs spread it over more SMs), 64 for float32.
-template <typename T>
-struct TileEdge {
-  static constexpr int v = sizeof(T) == 8 ? 32 : 64;
-};
 
 // Work items of one product for one chain: 2 spins x output tiles x slices
 // of the inner dimension.  Slices are kchunk wide while the partial tiles
@@ -199,24 +193,27 @@ struct TileEdge {
 template <typename T, int PHASE>
 __device__ __forceinline__ int gemm_items(const Chain<T>& c, const Dyn& d, int kchunk, int& tiles_m,
                                           int& tiles_n, int& nslices, int& width) {
-  constexpr int GE = TileEdge<T>::v;
+  constexpr GemmTile tl = gemm_tile(sizeof(T) == 8, PHASE);
   Gemm<T> g;
   if (d.status || !setup_gemm(c, d, 0, PHASE, g)) return 0;
-  tiles_m = (g.M + GE - 1) / GE;
-  tiles_n = (g.Nn + GE - 1) / GE;
+  tiles_m = (g.M + tl.bm - 1) / tl.bm;
+  tiles_n = (g.Nn + tl.bn - 1) / tl.bn;
   nslices = max(1, min((g.Kk + kchunk - 1) / kchunk, kMaxPartials / (tiles_m * tiles_n)));
   width = max(1, (g.Kk + nslices - 1) / nslices);
   return 2 * tiles_m * tiles_n * nslices;
 }
 
 // Persistent batched product: CTAs loop over the (chain, spin, tile, slice)
-// items of all chains.  One output tile (TileEdge) and one slice per item (256
+// items of all chains.  One output tile (gemm_tile) and one slice per item (256
 // threads).  With more than one slice every slice stores its partial tile,
 // and the slice that arrives last at the tile's ticket adds the partials in
 // slice order (deterministic, no waiting) and writes the result.
 template <typename T, int PHASE>
 __global__ void __launch_bounds__(256) k_gemm(Chain<T>* chains, int n_chains, int kchunk) {
-  constexpr int GBM = TileEdge<T>::v, GBN = TileEdge<T>::v, TM = GBM / 16, TN = GBN / 16;
+  constexpr GemmTile tl = gemm_tile(sizeof(T) == 8, PHASE);
+  constexpr int GBM = tl.bm, GBN = tl.bn, TM = tl.tm, TN = tl.tn;
+  constexpr int NTX = GBN / TN, NTY = GBM / TM;  // thread grid over the tile
+  static_assert(NTX * NTY == 256, "256 threads per output tile");
   constexpr int phase = PHASE;
   __shared__ int off[kMaxChains + 1];
   __shared__ T As[GBK][GBM + 1];
@@ -229,7 +226,7 @@ __global__ void __launch_bounds__(256) k_gemm(Chain<T>* chains, int n_chains, in
   __syncthreads();
   block_exclusive_scan(off, n_chains);
   const int total = off[n_chains];
-  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int tx = threadIdx.x % NTX, ty = threadIdx.x / NTX;
   for (int w = blockIdx.x; w < total; w += gridDim.x) {
     const int ci = find_chain(off, n_chains, w);
     const Chain<T>& c = chains[ci];
@@ -265,9 +262,9 @@ __global__ void __launch_bounds__(256) k_gemm(Chain<T>* chains, int n_chains, in
       for (int kk = 0; kk < GBK; ++kk) {
         T av[TM], bv[TN];
 #pragma unroll
-        for (int a = 0; a < TM; ++a) av[a] = As[kk][ty + 16 * a];
+        for (int a = 0; a < TM; ++a) av[a] = As[kk][ty + NTY * a];
 #pragma unroll
-        for (int b = 0; b < TN; ++b) bv[b] = Bs[kk][tx + 16 * b];
+        for (int b = 0; b < TN; ++b) bv[b] = Bs[kk][tx + NTX * b];
 #pragma unroll
         for (int a = 0; a < TM; ++a)
 #pragma unroll
@@ -281,7 +278,7 @@ __global__ void __launch_bounds__(256) k_gemm(Chain<T>* chains, int n_chains, in
       for (int a = 0; a < TM; ++a)
 #pragma unroll
         for (int b = 0; b < TN; ++b)
-          part[(size_t)ks * GBM * GBN + (ty + 16 * a) * GBN + tx + 16 * b] = acc[a][b];
+          part[(size_t)ks * GBM * GBN + (ty + NTY * a) * GBN + tx + NTX * b] = acc[a][b];
       __threadfence();
       __syncthreads();
       if (threadIdx.x == 0) s_last = (atomicAdd(c.ticket[spin] + tile, 1) == nslices - 1);
@@ -294,18 +291,18 @@ __global__ void __launch_bounds__(256) k_gemm(Chain<T>* chains, int n_chains, in
         for (int b = 0; b < TN; ++b) {
           T v = (T)0;
           for (int q = 0; q < nslices; ++q)
-            v += __ldcg(part + (size_t)q * GBM * GBN + (ty + 16 * a) * GBN + tx + 16 * b);
+            v += __ldcg(part + (size_t)q * GBM * GBN + (ty + NTY * a) * GBN + tx + NTX * b);
           acc[a][b] = v;
         }
       if (threadIdx.x == 0) c.ticket[spin][tile] = 0;
     }
 #pragma unroll
     for (int a = 0; a < TM; ++a) {
-      const int i = i0 + ty + 16 * a;
+      const int i = i0 + ty + NTY * a;
       if (i >= g.M) continue;
 #pragma unroll
       for (int b = 0; b < TN; ++b) {
-        const int j = j0 + tx + 16 * b;
+        const int j = j0 + tx + NTX * b;
         if (j >= g.Nn) continue;
         T v = (T)g.alpha * acc[a][b];
         if (g.has_cin) v += g.Cin.at(i, j);

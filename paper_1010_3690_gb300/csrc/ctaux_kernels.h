@@ -7,8 +7,6 @@
 
 namespace ctaux {
 
-// Fixed launch shapes of one context (derived from capacities at init, so
-// that a sweep needs no host-side knowledge of the current orders).
 constexpr int kMaxPartials = 4096;  // split-K partial tiles per (chain, spin) and product
 constexpr int kTieSlices = 64;   // column slices of the near-tie matrix-vector products
 constexpr int kMeasChunk = 32;  // vertices per measurement evaluation chunk
@@ -23,10 +21,28 @@ struct TcMaps {
 
 enum { PH_RTILDE = 0, PH_GCOL_OLD = 1, PH_GCOL_NEW = 2, PH_FLUSH = 3, PH_MEAS = 4, PH_COUNT = 5 };
 
+// Output tile of each product (rows x columns, per thread TM x TN; 256
+// threads).  float64 (FP64-pipe bound, so padding costs time): skinny where
+// one dimension is the number of insertions (R~: rows, G_{old,new}: columns)
+// or of anchors (measurement product), 32 x 32 otherwise.  float32 (the
+// faster pipe makes re-reads of N and per-item overheads matter more): 64 x 64,
+// and 128 x 8 for the measurement product.
+struct GemmTile {
+  int bm, bn, tm, tn;
+};
+constexpr GemmTile gemm_tile(bool fp64, int phase) {
+  return phase == PH_MEAS ? GemmTile{128, 8, 4, 1}
+         : !fp64          ? GemmTile{64, 64, 4, 4}
+         : phase == PH_RTILDE   ? GemmTile{16, 64, 1, 4}
+         : phase == PH_GCOL_OLD ? GemmTile{64, 16, 4, 1}
+                                : GemmTile{32, 32, 2, 2};
+}
+
+// Fixed launch shapes of one context (derived from capacities at init, so
+// that a sweep needs no host-side knowledge of the current orders).
 struct LaunchShape {
   int n_chains;
   int gather_slices;
-  int tiles[PH_COUNT];   // bound on output tiles per (chain, spin)
   int kchunk;            // slice width of the inner dimension (while partial tiles fit)
   int persist_ctas;      // grid of the persistent batched kernels
   int tie_grid;          // cooperative grid of the near-tie refinement
