@@ -153,7 +153,7 @@ ctaux_status build_chains(ctaux_ctx* ctx) {
     // barrier latency (which grows with the number of CTAs) dominates
     ls.tie_grid = ctx->sm_count;
     ls.tie_iters = P.tie_refine_iters == 0 ? 12 : std::max(0, P.tie_refine_iters);
-    ctx->tie_part = dalloc<double>(ctx, 2 * (size_t)ls.tie_grid + (size_t)kTieSlices * max_ld, &err);
+    ctx->tie_part = dalloc<double>(ctx, 4 * (size_t)ls.tie_grid + (size_t)2 * kTieSlices * max_ld, &err);
   }
   std::vector<TcMaps> host_maps(mixed_tc ? 2 * ctx->chains.size() : 0);
   int nb = refresh_blocks_per_sm<T>();

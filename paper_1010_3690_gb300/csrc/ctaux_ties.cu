@@ -130,16 +130,22 @@ __device__ void tie_eval_chain(const Chain<float>& c) {
 }
 
 
-// y = M v over the whole grid, M column-major with leading dimension ld:
-// slice sl of the columns writes its partial sums to P[sl*ld + i]; the caller
-// adds the ns partials in slice order after a grid barrier (deterministic).
+// y_s = M_s v_s for both spins s over the whole grid, M_s column-major with
+// leading dimension ld: slice sl of the columns of spin s writes its partial
+// sums to P_s[sl*ld + i] (P_s = P + s*kTieSlices*ld); the caller adds the ns
+// partials in slice order after a grid barrier (deterministic).
 template <typename Tm>
-__device__ __forceinline__ void grid_gemv_partials(const Tm* M, int ld, int n, const double* v,
-                                                   double* P, int ns, int gtid, int gthreads) {
+__device__ __forceinline__ void grid_gemv_partials2(const Tm* M0, const Tm* M1, int ld, int n,
+                                                    const double* v0, const double* v1, double* P,
+                                                    int ns, int gtid, int gthreads) {
   const int rp = (n + 31) & ~31;
-  for (int idx = gtid; idx < ns * rp; idx += gthreads) {
-    const int i = idx % rp, sl = idx / rp;
+  const int per_spin = ns * rp;
+  for (int idx = gtid; idx < 2 * per_spin; idx += gthreads) {
+    const int spin = idx / per_spin, l = idx - spin * per_spin;
+    const int i = l % rp, sl = l / rp;
     if (i >= n) continue;
+    const Tm* M = spin ? M1 : M0;
+    const double* v = spin ? v1 : v0;
     const int j0 = (int)((long long)sl * n / ns), j1 = (int)((long long)(sl + 1) * n / ns);
     double a0 = 0.0, a1 = 0.0;
     int j = j0;
@@ -148,122 +154,168 @@ __device__ __forceinline__ void grid_gemv_partials(const Tm* M, int ld, int n, c
       a1 += (double)M[(size_t)(j + 1) * ld + i] * v[j + 1];
     }
     if (j < j1) a0 += (double)M[(size_t)j * ld + i] * v[j];
-    P[(size_t)sl * ld + i] = a0 + a1;
+    P[(size_t)spin * kTieSlices * ld + (size_t)sl * ld + i] = a0 + a1;
   }
 }
 
-__device__ __forceinline__ double slice_sum(const double* P, int ld, int ns, int i) {
+__device__ __forceinline__ double slice_sum(const double* P, int ld, int ns, int spin, int i) {
+  const double* Ps = P + (size_t)spin * kTieSlices * ld;
   double t = 0.0;
-  for (int sl = 0; sl < ns; ++sl) t += P[(size_t)sl * ld + i];
+  for (int sl = 0; sl < ns; ++sl) t += Ps[(size_t)sl * ld + i];
   return t;
 }
 
-// Cooperative over the whole GPU, one pending tie at a time: A (FP64) is
-// built once across all CTAs, then x <- x + N (b - A x) iterates; each
-// matrix-vector product is split over column slices, and the convergence
-// maxima go through per-CTA partials read in CTA order.
+// Cooperative over the whole GPU, one pending tie at a time, both spins at
+// once: A_s (FP64) is built across all CTAs, then x_s <- x_s + N_s (b_s - A_s
+// x_s) iterates until both spins have converged; each matrix-vector product
+// is split over column slices, and the convergence maxima go through per-CTA
+// partials read in CTA order.
 __global__ void __launch_bounds__(256) k_tie_refine(Chain<float>* chains, int n_chains,
                                                     double* part, double* slices, int max_iter) {
   cg::grid_group grid = cg::this_grid();
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
   const int gthreads = gridDim.x * blockDim.x;
   __shared__ double red[8];
+  __shared__ unsigned pend[kMaxChains / 32];  // chains with a pending tie, as bits
+  const int nwords = (n_chains + 31) / 32;
+  for (int w = threadIdx.x; w < nwords; w += blockDim.x) pend[w] = 0u;
+  __syncthreads();
+  // every CTA reads the same flags: they change only after the first grid barrier
+  for (int ci = threadIdx.x; ci < n_chains; ci += blockDim.x) {
+    const Dyn& d = *chains[ci].dyn;
+    if (!d.status && d.tie_pending == 1) atomicOr(&pend[ci >> 5], 1u << (ci & 31));
+  }
+  __syncthreads();
   bool any_fail = false;
-  for (int ci = 0; ci < n_chains; ++ci) {
+  for (int wd = 0; wd < nwords; ++wd)
+  for (unsigned bits = pend[wd]; bits; bits &= bits - 1) {
+    const int ci = wd * 32 + __ffs(bits) - 1;  // increasing chain order in every CTA
     const Chain<float>& c = chains[ci];
     Dyn& d = *c.dyn;
-    if (d.status || d.tie_pending != 1) continue;  // same decision in every CTA
     const TieProposal q = tie_proposal(c, d);
     const int n = d.n, buf = d.buf, ld = c.ld;
-    const int ns = max(1, min(kTieSlices, gthreads / ((n + 31) & ~31)));
+    const int ns = max(1, min(kTieSlices, gthreads / (2 * ((n + 31) & ~31))));
     const double* tau = c.tau[buf];
     const int* site = c.site[buf];
     const int8_t* sv = c.s[buf];
     double ratio[2] = {0.0, 0.0};
     bool ok = max_iter > 0;
-    for (int spin = 0; spin < 2 && !q.none && ok; ++spin) {
-      const float* N = c.N[buf][spin];
-      double* A = c.work + (size_t)spin * ((size_t)ld * ld + (size_t)96 * ld);
-      double* x = A + (size_t)ld * ld;
-      double* r = x + ld;
-      double* b = r + ld;
-      for (int j = blockIdx.x; j < n; j += gridDim.x) {
+    if (!q.none && ok) {
+      const float* N0 = c.N[buf][0];
+      const float* N1 = c.N[buf][1];
+      double* A[2];
+      double *x[2], *r[2], *b[2];
+      for (int spin = 0; spin < 2; ++spin) {
+        A[spin] = c.work + (size_t)spin * ((size_t)ld * ld + (size_t)96 * ld);
+        x[spin] = A[spin] + (size_t)ld * ld;
+        r[spin] = x[spin] + ld;
+        b[spin] = r[spin] + ld;
+      }
+      for (int u = blockIdx.x; u < 2 * n; u += gridDim.x) {
+        const int spin = u / n, j = u - spin * n;
         const double emj = c.ev[spin][sv[j] + 2] - 1.0;
+        double* Aj = A[spin] + (size_t)j * ld;
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
           double v = -g0_eval(c, spin, tau[i], site[i], tau[j], site[j]) * emj;
           if (i == j) v += emj + 1.0;
-          A[(size_t)j * ld + i] = v;
+          Aj[i] = v;
         }
       }
-      for (int k = gtid; k < n; k += gthreads)
-        b[k] = (q.move == MV_INSERT) ? g0_eval(c, spin, tau[k], site[k], q.tau_new, q.site_new)
-                                     : (k == q.p ? 1.0 : 0.0);
+      for (int k = gtid; k < 2 * n; k += gthreads) {
+        const int spin = k / n, kk = k - spin * n;
+        b[spin][kk] = (q.move == MV_INSERT)
+                          ? g0_eval(c, spin, tau[kk], site[kk], q.tau_new, q.site_new)
+                          : (kk == q.p ? 1.0 : 0.0);
+      }
       grid.sync();
       if (q.move == MV_INSERT) {
-        grid_gemv_partials(N, ld, n, b, slices, ns, gtid, gthreads);
+        grid_gemv_partials2(N0, N1, ld, n, b[0], b[1], slices, ns, gtid, gthreads);
         grid.sync();
-        for (int i = gtid; i < n; i += gthreads) x[i] = slice_sum(slices, ld, ns, i);
+        for (int k = gtid; k < 2 * n; k += gthreads) {
+          const int spin = k / n, i = k - spin * n;
+          x[spin][i] = slice_sum(slices, ld, ns, spin, i);
+        }
       } else {
-        for (int i = gtid; i < n; i += gthreads) x[i] = (double)N[(size_t)q.p * ld + i];
+        for (int k = gtid; k < 2 * n; k += gthreads) {
+          const int spin = k / n, i = k - spin * n;
+          x[spin][i] = (double)c.N[buf][spin][(size_t)q.p * ld + i];
+        }
       }
       grid.sync();
-      bool conv = false;
-      double dprev = 1e300;
-      for (int it = 0; it < max_iter && !conv; ++it) {
-        grid_gemv_partials(A, ld, n, x, slices, ns, gtid, gthreads);
+      bool conv[2] = {false, false};
+      double dprev[2] = {1e300, 1e300};
+      for (int it = 0; it < max_iter && !(conv[0] && conv[1]); ++it) {
+        grid_gemv_partials2(A[0], A[1], ld, n, x[0], x[1], slices, ns, gtid, gthreads);
         grid.sync();
-        for (int i = gtid; i < n; i += gthreads) r[i] = b[i] - slice_sum(slices, ld, ns, i);
-        grid.sync();
-        grid_gemv_partials(N, ld, n, r, slices, ns, gtid, gthreads);
-        grid.sync();
-        double dmax = 0.0, xmax = 0.0;
-        for (int i = gtid; i < n; i += gthreads) {
-          const double dx = slice_sum(slices, ld, ns, i);
-          const double xn = x[i] + dx;
-          x[i] = xn;
-          dmax = fmax(dmax, fabs(dx));
-          xmax = fmax(xmax, fabs(xn));
-        }
-        const double bd = block_max(dmax, red);
-        const double bx = block_max(xmax, red);
-        if (threadIdx.x == 0) {
-          part[2 * blockIdx.x] = bd;
-          part[2 * blockIdx.x + 1] = bx;
+        for (int k = gtid; k < 2 * n; k += gthreads) {
+          const int spin = k / n, i = k - spin * n;
+          r[spin][i] = b[spin][i] - slice_sum(slices, ld, ns, spin, i);
         }
         grid.sync();
-        double dm = 0.0, xm = 0.0;
-        for (int k = 0; k < (int)gridDim.x; ++k) {
-          dm = fmax(dm, part[2 * k]);
-          xm = fmax(xm, part[2 * k + 1]);
+        grid_gemv_partials2(N0, N1, ld, n, r[0], r[1], slices, ns, gtid, gthreads);
+        grid.sync();
+        double dmax[2] = {0.0, 0.0}, xmax[2] = {0.0, 0.0};
+        for (int k = gtid; k < 2 * n; k += gthreads) {
+          const int spin = k / n, i = k - spin * n;
+          const double dx = slice_sum(slices, ld, ns, spin, i);
+          const double xn = conv[spin] ? x[spin][i] : x[spin][i] + dx;  // converged: frozen
+          x[spin][i] = xn;
+          dmax[spin] = fmax(dmax[spin], fabs(dx));
+          xmax[spin] = fmax(xmax[spin], fabs(xn));
         }
-        // converged at 1e-14, or stagnating at the float64 rounding level
-        conv = dm <= 1e-14 * xm || (it >= 2 && dm <= 1e-10 * xm && dm >= 0.5 * dprev);
-        dprev = dm;
+        for (int spin = 0; spin < 2; ++spin) {
+          const double bd = block_max(dmax[spin], red);
+          const double bx = block_max(xmax[spin], red);
+          if (threadIdx.x == 0) {
+            part[4 * blockIdx.x + 2 * spin] = bd;
+            part[4 * blockIdx.x + 2 * spin + 1] = bx;
+          }
+        }
+        grid.sync();
+        for (int spin = 0; spin < 2; ++spin) {
+          double dm = 0.0, xm = 0.0;
+          for (int k = 0; k < (int)gridDim.x; ++k) {
+            dm = fmax(dm, part[4 * k + 2 * spin]);
+            xm = fmax(xm, part[4 * k + 2 * spin + 1]);
+          }
+          // converged at 1e-14, or stagnating at the float64 rounding level
+          if (!conv[spin])
+            conv[spin] = dm <= 1e-14 * xm || (it >= 2 && dm <= 1e-10 * xm && dm >= 0.5 * dprev[spin]);
+          dprev[spin] = dm;
+        }
         grid.sync();  // partials are rewritten in the next iteration
       }
-      if (!conv) {
-        ok = false;
-        break;
+      ok = conv[0] && conv[1];
+      if (ok) {
+        double gpp[2], lam[2];
+        if (q.move == MV_INSERT) {
+          double v[2] = {0.0, 0.0};
+          for (int k = gtid; k < 2 * n; k += gthreads) {
+            const int spin = k / n, l = k - spin * n;
+            v[spin] += g0_eval(c, spin, q.tau_new, q.site_new, tau[l], site[l]) *
+                       (c.ev[spin][sv[l] + 2] - 1.0) * x[spin][l];
+          }
+          for (int spin = 0; spin < 2; ++spin) {
+            const double bs = block_sum(v[spin], red);
+            if (threadIdx.x == 0) part[4 * blockIdx.x + spin] = bs;
+          }
+          grid.sync();
+          for (int spin = 0; spin < 2; ++spin) {
+            double tot = 0.0;
+            for (int k = 0; k < (int)gridDim.x; ++k) tot += part[4 * k + spin];
+            gpp[spin] = g0_eval(c, spin, q.tau_new, q.site_new, q.tau_new, q.site_new) + tot;
+            lam[spin] = c.ev[spin][q.s_new + 2] - 1.0;
+          }
+          grid.sync();
+        } else {
+          const int k = sv[q.p] + 2;
+          for (int spin = 0; spin < 2; ++spin) {
+            gpp[spin] = (x[spin][q.p] * c.ev[spin][k] - 1.0) * c.inv_em1[spin][k];
+            lam[spin] = c.ev[spin][q.s_new - sv[q.p] + 2] - 1.0;
+          }
+        }
+        for (int spin = 0; spin < 2; ++spin) ratio[spin] = 1.0 + lam[spin] * (1.0 - gpp[spin]);
       }
-      double gpp, lam;
-      if (q.move == MV_INSERT) {
-        double v = 0.0;
-        for (int l = gtid; l < n; l += gthreads)
-          v += g0_eval(c, spin, q.tau_new, q.site_new, tau[l], site[l]) * (c.ev[spin][sv[l] + 2] - 1.0) * x[l];
-        const double bs = block_sum(v, red);
-        if (threadIdx.x == 0) part[blockIdx.x] = bs;
-        grid.sync();
-        double tot = 0.0;
-        for (int k = 0; k < (int)gridDim.x; ++k) tot += part[k];
-        gpp = g0_eval(c, spin, q.tau_new, q.site_new, q.tau_new, q.site_new) + tot;
-        lam = c.ev[spin][q.s_new + 2] - 1.0;
-        grid.sync();
-      } else {
-        const int k = sv[q.p] + 2;
-        gpp = (x[q.p] * c.ev[spin][k] - 1.0) * c.inv_em1[spin][k];
-        lam = c.ev[spin][q.s_new - sv[q.p] + 2] - 1.0;
-      }
-      ratio[spin] = 1.0 + lam * (1.0 - gpp);
     }
     grid.sync();  // every CTA has read the pending state before it changes
     if (gtid == 0 && ok) set_forced(c, d, q, ratio);
@@ -283,7 +335,7 @@ __global__ void __launch_bounds__(256) k_tie_refine(Chain<float>* chains, int n_
 cudaError_t launch_tie_refine(Chain<float>* dchains, const LaunchShape& ls, double* part,
                               cudaStream_t st) {
   int nch = ls.n_chains;
-  double* slices = part + 2 * (size_t)ls.tie_grid;
+  double* slices = part + 4 * (size_t)ls.tie_grid;
   int max_iter = ls.tie_iters;
   void* args[] = {&dchains, &nch, &part, &slices, &max_iter};
   return cudaLaunchCooperativeKernel((const void*)k_tie_refine, dim3(ls.tie_grid), dim3(256), args,
