@@ -101,6 +101,12 @@ typedef struct {
   int tie_refine_iters;               /* mixed form: most refinement iterations per near tie;
                                          0 = 12; -1 = none, so that every near tie takes the
                                          from-scratch fallback (for tests) */
+  int refresh_df64;                   /* mixed form: 1 = the periodic from-scratch recomputation
+                                         eliminates in double-float arithmetic (two float32,
+                                         about 48 significand bits) on the float32 pipe, which
+                                         GB300 runs 64x faster than float64; 0 = float64.  The
+                                         matrix N^{-1} is built in float64 either way, and the
+                                         near-tie fallback always eliminates in float64 */
 } ctaux_params;
 
 typedef struct {

@@ -156,6 +156,7 @@ ctaux_status build_chains(ctaux_ctx* ctx) {
     ctx->tie_part = dalloc<double>(ctx, 4 * (size_t)ls.tie_grid + (size_t)2 * kTieSlices * max_ld, &err);
   }
   std::vector<TcMaps> host_maps(mixed_tc ? 2 * ctx->chains.size() : 0);
+  ls.refresh_df64 = (sizeof(T) == 4 && P.refresh_df64) ? 1 : 0;
   int nb = refresh_blocks_per_sm<T>();
   ls.refresh_grid = std::max(1, nb) * ctx->sm_count;
 

@@ -47,6 +47,7 @@ struct LaunchShape {
   int persist_ctas;      // grid of the persistent batched kernels
   int tie_grid;          // cooperative grid of the near-tie refinement
   int tie_iters;         // most refinement iterations (0: every near tie takes the fallback)
+  int refresh_df64;      // float32 form: refresh elimination in double-float
   int y_blocks;
   int prop_smem;
   int gamma_in_smem;

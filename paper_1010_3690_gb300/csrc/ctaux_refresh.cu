@@ -1,12 +1,15 @@
-// FP64 refresh kernels (bodies in ctaux_refresh.cuh).
+// From-scratch refresh kernels (bodies in ctaux_refresh.cuh): elimination in
+// float64, or in double-float on the float32 pipe (mixed form, optional).
+#include <type_traits>
+
 #include "ctaux_refresh.cuh"
 
 namespace ctaux {
 
-template <typename T>
+template <typename T, typename E>
 __global__ void __launch_bounds__(256) k_refresh(Chain<T>* chains, int n_chains, int only_chain,
                                                  int filter) {
-  refresh_body<T>(chains, n_chains, only_chain, filter);
+  refresh_body<T, E>(chains, n_chains, only_chain, filter);
 }
 
 // Small follow-up kernel: the stats of every refreshed chain.
@@ -25,8 +28,12 @@ cudaError_t launch_refresh(Chain<T>* dchains, const LaunchShape& ls, int only_ch
   int nch = ls.n_chains;
   cudaError_t e = cudaSuccess;
   void* args[] = {&dchains, &nch, &only_chain, &filter};
-  e = cudaLaunchCooperativeKernel((const void*)k_refresh<T>, dim3(ls.refresh_grid), dim3(256),
-                                  args, 0, st);
+  // double-float elimination only for the float32 form's own refreshes; the
+  // near-tie fallback (filter 1) keeps float64, whose N it also stores
+  const void* fn = (std::is_same<T, float>::value && ls.refresh_df64 && filter == 0)
+                       ? (const void*)k_refresh<T, df64>
+                       : (const void*)k_refresh<T, double>;
+  e = cudaLaunchCooperativeKernel(fn, dim3(ls.refresh_grid), dim3(256), args, 0, st);
   if (e == cudaSuccess) {
     if (only_chain >= 0)
       k_refresh_finish<T><<<1, 1, 0, st>>>(dchains, nch, only_chain, filter);
@@ -40,9 +47,11 @@ cudaError_t launch_refresh(Chain<T>* dchains, const LaunchShape& ls, int only_ch
 
 template <typename T>
 int refresh_blocks_per_sm() {
-  int nb = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_refresh<T>, 256, 0);
-  return nb;
+  // the grid must be co-resident for either element type
+  int nb = 0, nb2 = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_refresh<T, double>, 256, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb2, k_refresh<T, df64>, 256, 0);
+  return nb < nb2 ? nb : nb2;
 }
 
 template cudaError_t launch_refresh<double>(Chain<double>*, const LaunchShape&, int, cudaStream_t,

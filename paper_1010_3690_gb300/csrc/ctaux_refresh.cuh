@@ -23,6 +23,7 @@
 
 #include <cooperative_groups.h>
 
+#include "ctaux_df64.cuh"
 #include "ctaux_dev.cuh"
 #include "ctaux_kernels.h"
 
@@ -30,10 +31,52 @@ namespace ctaux {
 
 namespace cg = cooperative_groups;
 
-__device__ __forceinline__ unsigned long long pivot_key(double v, int row) {
-  const float a = (float)fabs(v);
+__device__ __forceinline__ unsigned long long pivot_key_mag(float a, int row) {
   return ((unsigned long long)__float_as_uint(a) << 32) | (unsigned long long)(0xffffffffu - (unsigned)row);
 }
+
+// Element arithmetic of the elimination: float64, or double-float (df64, the
+// mixed form's option) on the float32 pipe.  Both are 8 bytes, so the work
+// area layout is the same.
+__device__ __forceinline__ double el_from(double x, double*) { return x; }
+__device__ __forceinline__ df64 el_from(double x, df64*) { return df_from(x); }
+__device__ __forceinline__ double el_to(double a) { return a; }
+__device__ __forceinline__ double el_to(df64 a) { return df_to(a); }
+__device__ __forceinline__ double el_mul(double a, double b) { return a * b; }
+__device__ __forceinline__ df64 el_mul(df64 a, df64 b) { return df_mul(a, b); }
+__device__ __forceinline__ double el_sub(double a, double b) { return a - b; }
+__device__ __forceinline__ df64 el_sub(df64 a, df64 b) { return df_sub(a, b); }
+__device__ __forceinline__ double el_neg(double a) { return -a; }
+__device__ __forceinline__ df64 el_neg(df64 a) { return df_neg(a); }
+__device__ __forceinline__ double el_recip(double a) { return 1.0 / a; }
+__device__ __forceinline__ df64 el_recip(df64 a) { return df_recip(a); }
+__device__ __forceinline__ unsigned long long pivot_key(double v, int row) {
+  return pivot_key_mag((float)fabs(v), row);
+}
+__device__ __forceinline__ unsigned long long pivot_key(df64 v, int row) {
+  return pivot_key_mag(fabsf(v.hi), row);
+}
+template <typename E>
+__device__ __forceinline__ E el_zero() {
+  return el_from(0.0, (E*)nullptr);
+}
+
+// acc + sum_k x_k y_k (the rank-32 trailing update)
+struct ElDot64 {
+  double a;
+  __device__ __forceinline__ explicit ElDot64(double init) : a(init) {}
+  __device__ __forceinline__ void add(double x, double y) { a = fma(x, y, a); }
+  __device__ __forceinline__ double value() const { return a; }
+};
+struct ElDotDf {
+  df64 init;
+  DfDot dot;
+  __device__ __forceinline__ explicit ElDotDf(df64 i) : init(i) {}
+  __device__ __forceinline__ void add(df64 x, df64 y) { dot.add(x, y); }
+  __device__ __forceinline__ df64 value() const { return df_add(init, dot.value()); }
+};
+__device__ __forceinline__ ElDot64 el_dot(double init) { return ElDot64(init); }
+__device__ __forceinline__ ElDotDf el_dot(df64 init) { return ElDotDf(init); }
 __device__ __forceinline__ int key_row(unsigned long long k) {
   return (int)(0xffffffffu - (unsigned)(k & 0xffffffffull));
 }
@@ -71,7 +114,7 @@ __device__ __forceinline__ RowUnit row_unit(const int* offr, int n_chains, int u
   return r;
 }
 
-template <typename T>
+template <typename T, typename E>
 __device__ void refresh_body(Chain<T>* chains, int n_chains, int only_chain, int filter) {
   cg::grid_group grid = cg::this_grid();
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -81,8 +124,8 @@ __device__ void refresh_body(Chain<T>* chains, int n_chains, int only_chain, int
   __shared__ int offr[kMaxChains + 1];
   __shared__ int offt[kMaxChains + 1];
   __shared__ int max_m_s;
-  __shared__ double Ps[32][kPB + 1];
-  __shared__ double Rs[kPB][33];
+  __shared__ E Ps[32][kPB + 1];
+  __shared__ E Rs[kPB][33];
   __shared__ double red[2][8];
 
   if (threadIdx.x == 0) max_m_s = 0;
@@ -106,7 +149,7 @@ __device__ void refresh_body(Chain<T>* chains, int n_chains, int only_chain, int
     const RowUnit ru = row_unit(offr, n_chains, u);
     const Chain<T>& c = chains[ru.ci];
     const int m = ru.m, spin = ru.spin, j = ru.i, buf = c.dyn->buf, ld = c.ld;
-    double* X = c.work + (size_t)spin * refresh_work_per_spin(ld);
+    E* X = reinterpret_cast<E*>(c.work + (size_t)spin * refresh_work_per_spin(ld));
     unsigned long long* keys = c.pkeys + (size_t)spin * ld;
     const double evj = c.ev[spin][c.s[buf][j] + 2];
     const double tj = c.tau[buf][j];
@@ -115,8 +158,9 @@ __device__ void refresh_body(Chain<T>* chains, int n_chains, int only_chain, int
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
       double v = -g0_eval(c, spin, c.tau[buf][i], c.site[buf][i], tj, sj) * (evj - 1.0);
       if (i == j) v += evj;
-      X[(size_t)j * ld + i] = v;
-      if (j == 0) atomicMax(keys, pivot_key(v, i));
+      const E ve = el_from(v, (E*)nullptr);
+      X[(size_t)j * ld + i] = ve;
+      if (j == 0) atomicMax(keys, pivot_key(ve, i));
     }
   }
   grid.sync();
@@ -130,8 +174,8 @@ __device__ void refresh_body(Chain<T>* chains, int n_chains, int only_chain, int
       if (c0 + k >= ru.m) continue;
       const Chain<T>& c = chains[ru.ci];
       const int ld = c.ld;
-      const double* X = c.work + (size_t)ru.spin * refresh_work_per_spin(ld);
-      double* Pa = const_cast<double*>(X) + (size_t)ld * ld;
+      E* X = reinterpret_cast<E*>(c.work + (size_t)ru.spin * refresh_work_per_spin(ld));
+      E* Pa = X + (size_t)ld * ld;
       Pa[(size_t)k * ld + ru.i] = X[(size_t)(c0 + k) * ld + ru.i];
     }
     grid.sync();
@@ -143,28 +187,29 @@ __device__ void refresh_body(Chain<T>* chains, int n_chains, int only_chain, int
         if (c0 + k >= ru.m || c0 + kk >= ru.m) continue;
         const Chain<T>& c = chains[ru.ci];
         const int ld = c.ld, col = c0 + k, i = ru.i, spin = ru.spin;
-        double* X = c.work + (size_t)spin * refresh_work_per_spin(ld);
-        double* Pa = X + (size_t)ld * ld;
-        double* Pb = Pa + (size_t)kPB * ld;
-        const double* src = (k & 1) ? Pb : Pa;
-        double* dst = (k & 1) ? Pa : Pb;
+        E* X = reinterpret_cast<E*>(c.work + (size_t)spin * refresh_work_per_spin(ld));
+        E* Pa = X + (size_t)ld * ld;
+        E* Pb = Pa + (size_t)kPB * ld;
+        const E* src = (k & 1) ? Pb : Pa;
+        E* dst = (k & 1) ? Pa : Pb;
         unsigned long long* keys = c.pkeys + (size_t)spin * ld;
         int8_t* used = c.used + spin * ld;
         const int pr = key_row(keys[col]);
-        const double piv = src[(size_t)k * ld + pr];
+        const E piv = src[(size_t)k * ld + pr];
         if (i == 0 && kk == 0) {
+          const double pd = el_to(piv);
           c.perm[spin * ld + col] = pr;
           used[pr] = 1;  // read below only for rows other than pr
           c.pcol[spin * ld + pr] = col;
-          if (!(fabs(piv) > 0.0) || !isfinite(piv)) atomicOr(&c.dyn->status, DS_SINGULAR);
-          c.work_logdet[spin] += log(fabs(piv));
+          if (!(fabs(pd) > 0.0) || !isfinite(pd)) atomicOr(&c.dyn->status, DS_SINGULAR);
+          c.work_logdet[spin] += log(fabs(pd));
         }
-        const double ipiv = 1.0 / piv;
-        const double xic = src[(size_t)k * ld + i];
-        double v;
-        if (i == pr) v = (kk == k) ? ipiv : src[(size_t)kk * ld + pr] * ipiv;
-        else if (kk == k) v = -xic * ipiv;
-        else v = src[(size_t)kk * ld + i] - xic * (src[(size_t)kk * ld + pr] * ipiv);
+        const E ipiv = el_recip(piv);
+        const E xic = src[(size_t)k * ld + i];
+        E v;
+        if (i == pr) v = (kk == k) ? ipiv : el_mul(src[(size_t)kk * ld + pr], ipiv);
+        else if (kk == k) v = el_neg(el_mul(xic, ipiv));
+        else v = el_sub(src[(size_t)kk * ld + i], el_mul(xic, el_mul(src[(size_t)kk * ld + pr], ipiv)));
         dst[(size_t)kk * ld + i] = v;
         if (kk == k + 1 && i != pr && !used[i]) atomicMax(keys + col + 1, pivot_key(v, i));
       }
@@ -178,10 +223,10 @@ __device__ void refresh_body(Chain<T>* chains, int n_chains, int only_chain, int
       if (c0 >= ru.m) continue;
       const Chain<T>& c = chains[ru.ci];
       const int ld = c.ld, j = ru.i;
-      const double* X = c.work + (size_t)ru.spin * refresh_work_per_spin(ld);
-      double* Rr = const_cast<double*>(X) + (size_t)ld * ld + (size_t)2 * kPB * ld;
+      E* X = reinterpret_cast<E*>(c.work + (size_t)ru.spin * refresh_work_per_spin(ld));
+      E* Rr = X + (size_t)ld * ld + (size_t)2 * kPB * ld;
       const int* perm = c.perm + ru.spin * ld;
-      Rr[(size_t)j * kPB + k] = (c0 + k < ru.m) ? X[(size_t)j * ld + perm[c0 + k]] : 0.0;
+      Rr[(size_t)j * kPB + k] = (c0 + k < ru.m) ? X[(size_t)j * ld + perm[c0 + k]] : el_zero<E>();
     }
     grid.sync();
     // B1: trailing rank-bw update in 32 x 32 tiles (tile units), panel written
@@ -194,10 +239,10 @@ __device__ void refresh_body(Chain<T>* chains, int n_chains, int only_chain, int
       const int tb = (m + 31) / 32, l = u - offt[ci];
       const int spin = l / (tb * tb), tile = l - spin * tb * tb;
       const int ld = c.ld, bw = min(kPB, m - c0), cn = c0 + bw;
-      double* X = c.work + (size_t)spin * refresh_work_per_spin(ld);
-      double* Pa = X + (size_t)ld * ld;
-      const double* Pf = (bw & 1) ? Pa + (size_t)kPB * ld : Pa;  // panel after bw steps
-      const double* Rr = Pa + (size_t)2 * kPB * ld;
+      E* X = reinterpret_cast<E*>(c.work + (size_t)spin * refresh_work_per_spin(ld));
+      E* Pa = X + (size_t)ld * ld;
+      const E* Pf = (bw & 1) ? Pa + (size_t)kPB * ld : Pa;  // panel after bw steps
+      const E* Rr = Pa + (size_t)2 * kPB * ld;
       unsigned long long* keys = c.pkeys + (size_t)spin * ld;
       const int8_t* used = c.used + spin * ld;
       const int* pcol = c.pcol + spin * ld;
@@ -205,27 +250,36 @@ __device__ void refresh_body(Chain<T>* chains, int n_chains, int only_chain, int
       __syncthreads();
       for (int e = threadIdx.x; e < 32 * kPB; e += blockDim.x) {
         const int r = e % 32, k = e / 32;
-        Ps[r][k] = (i0 + r < m && k < bw) ? Pf[(size_t)k * ld + i0 + r] : 0.0;
+        Ps[r][k] = (i0 + r < m && k < bw) ? Pf[(size_t)k * ld + i0 + r] : el_zero<E>();
         const int jj = e % 32, kk = e / 32;
-        Rs[kk][jj] = (j0 + jj < m) ? Rr[(size_t)(j0 + jj) * kPB + kk] : 0.0;
+        Rs[kk][jj] = (j0 + jj < m) ? Rr[(size_t)(j0 + jj) * kPB + kk] : el_zero<E>();
       }
       __syncthreads();
-      const int r = threadIdx.x % 32, i = i0 + r;
+      // thread (row r, column group g): columns q = g + 8c, c = 0..3, so that
+      // each panel value Ps[r][k] is loaded once for four products
+      const int r = threadIdx.x % 32, i = i0 + r, g = threadIdx.x / 32;
+      static_assert(kPB == 32, "a 32 x 32 tile per 256 threads");
       if (i < m) {
         const int pci = pcol[i];
         const bool in_R = pci >= c0 && pci < cn;
-        for (int q = threadIdx.x / 32; q < 32; q += blockDim.x / 32) {
-          const int j = j0 + q;
+        decltype(el_dot(el_zero<E>())) acc[4] = {el_dot(el_zero<E>()), el_dot(el_zero<E>()),
+                                                 el_dot(el_zero<E>()), el_dot(el_zero<E>())};
+#pragma unroll
+        for (int cq = 0; cq < 4; ++cq) {
+          const int j = j0 + g + 8 * cq;
+          if (!in_R && j < m && !(j >= c0 && j < cn)) acc[cq] = el_dot(X[(size_t)j * ld + i]);
+        }
+#pragma unroll 4
+        for (int k = 0; k < kPB; ++k) {
+          const E pk = Ps[r][k];
+#pragma unroll
+          for (int cq = 0; cq < 4; ++cq) acc[cq].add(pk, Rs[k][g + 8 * cq]);
+        }
+#pragma unroll
+        for (int cq = 0; cq < 4; ++cq) {
+          const int q = g + 8 * cq, j = j0 + q;
           if (j >= m) continue;
-          double v;
-          if (j >= c0 && j < cn) {
-            v = Ps[r][j - c0];
-          } else {
-            double acc = in_R ? 0.0 : X[(size_t)j * ld + i];
-#pragma unroll 8
-            for (int k = 0; k < kPB; ++k) acc += Ps[r][k] * Rs[k][q];
-            v = acc;
-          }
+          const E v = (j >= c0 && j < cn) ? Ps[r][j - c0] : acc[cq].value();
           X[(size_t)j * ld + i] = v;
           if (j == cn && !used[i]) atomicMax(keys + cn, pivot_key(v, i));
         }
@@ -240,14 +294,14 @@ __device__ void refresh_body(Chain<T>* chains, int n_chains, int only_chain, int
     const RowUnit ru = row_unit(offr, n_chains, u);
     const Chain<T>& c = chains[ru.ci];
     const int m = ru.m, spin = ru.spin, j = ru.i, ld = c.ld, buf = c.dyn->buf;
-    const double* X = c.work + (size_t)spin * refresh_work_per_spin(ld);
+    const E* X = reinterpret_cast<const E*>(c.work + (size_t)spin * refresh_work_per_spin(ld));
     const int* perm = c.perm + spin * ld;
     T* Nr = c.N[buf][spin];
     double* N64 = (filter == 1) ? c.N64[spin] : nullptr;
     const int pj = perm[j];
     double dmax = 0.0, dsq = 0.0;
     for (int cc = threadIdx.x; cc < m; cc += blockDim.x) {
-      const double v = X[(size_t)j * ld + perm[cc]];  // N[cc][perm[j]]
+      const double v = el_to(X[(size_t)j * ld + perm[cc]]);  // N[cc][perm[j]]
       const long o = (long)pj * ld + cc;
       if (N64) N64[o] = v;
       const double diff = fabs((double)Nr[o] - v);

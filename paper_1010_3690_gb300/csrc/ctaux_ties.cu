@@ -325,7 +325,7 @@ __global__ void __launch_bounds__(256) k_tie_refine(Chain<float>* chains, int n_
   if (!any_fail) return;
   // fallback for the chains still pending: from-scratch FP64 refresh keeping
   // the FP64 N (N64), its stats, then the decision from N64
-  refresh_body<float>(chains, n_chains, -1, 1);
+  refresh_body<float, double>(chains, n_chains, -1, 1);
   grid.sync();
   for (int ci = gtid; ci < n_chains; ci += gthreads) refresh_finish_one(chains[ci], 1);
   grid.sync();

@@ -141,6 +141,34 @@ def test_mixed_measurement_matches_oracle(bins, anchors):
         np.testing.assert_allclose(G, ref, rtol=0, atol=1e-4 * np.abs(ref).max())
 
 
+def test_mixed_refresh_in_double_float_matches_fp64():
+    """The optional double-float elimination of the mixed form's refresh gives the
+    float32 N of the float64 elimination (equal up to one float32 rounding) and the
+    oracle's N within float32 rounding; the chain then follows the oracle."""
+    ch = configs.cube8(K=256.0, k_max=64, capacity=768)
+    cfg = configs.synthetic_configuration(ch, 430, seed=3)
+    oc = oracle_for(ch)
+    oc.set_config(cfg["tau"], cfg["site"], cfg["s"], cfg["birth"], cfg["t"])
+    Ns = []
+    for df in (0, 1):
+        with pk.Context([ch], precision=pk.CTAUX_MIXED, refresh_df64=df) as ctx:
+            ctx.set_config(0, cfg["tau"], cfg["site"], cfg["s"], cfg["birth"], cfg["t"])
+            ctx.recompute()
+            Ns.append([ctx.get_N(0, s) for s in (0, 1)])
+    for s in (0, 1):
+        ref = oc.N(s)
+        scale = np.abs(ref).max()
+        for N in (Ns[0][s], Ns[1][s]):
+            np.testing.assert_allclose(N, ref, rtol=0, atol=2.0 ** -23 * scale)
+        np.testing.assert_allclose(Ns[1][s], Ns[0][s], rtol=2.0 ** -23, atol=2.0 ** -30 * scale)
+    with pk.Context([ch], precision=pk.CTAUX_MIXED, refresh_df64=1, trace_capacity=3 * 64,
+                    refresh_every=1) as ctx:
+        ctx.set_config(0, cfg["tau"], cfg["site"], cfg["s"], cfg["birth"], cfg["t"])
+        ctx.sweep(3)
+        ctx.synchronize()
+        compare_traces(ctx.trace(0), oc.run(3 * 64), RTOL_MIXED)
+
+
 def test_refresh_drift_small_fp64():
     ch = configs.cube8(K=64.0, k_max=64, capacity=768)
     with pk.Context([ch], refresh_every=0) as ctx:
