@@ -220,6 +220,9 @@ def main():
     ap.add_argument("--refresh-every", dest="refresh_every", type=int, default=REFRESH_EVERY)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--autotune", default=None,
+                    help="comma-separated k candidates: choose k_max per chain on the device "
+                         "(ctaux_autotune_k) after thermalisation; --k-max is the allocation")
     ap.add_argument("--k-sweep", dest="k_sweep", default=None,
                     help="comma-separated k_max values: print proposals/s per k instead")
     args = ap.parse_args()
@@ -349,6 +352,11 @@ def measure_form(args, pk, torch, dist, chains, meta, form, local, world, with_e
             cfg = configs.synthetic_configuration(ch, meta["start_order"], seed=1000 + ch.chain_id)
             ctx.set_config(i, cfg["tau"], cfg["site"], cfg["s"], cfg["birth"], cfg["t"])
     ctx.sweep(args.thermalize, measure=False, stream=sh)
+    k_tuned = None
+    if args.autotune:
+        cand = [int(x) for x in args.autotune.split(",")]
+        ks, _ = ctx.autotune_k(candidates=cand, n_blocks=8)
+        k_tuned = {str(k): int((ks == k).sum()) for k in sorted(set(ks.tolist()))}
     for _ in range(max(3, args.warmup)):
         ctx.sweep(1, measure=True, stream=sh)
     ctx.synchronize()
@@ -481,7 +489,9 @@ def measure_form(args, pk, torch, dist, chains, meta, form, local, world, with_e
                        "precision": form,
                        "l2": "flushed between timed steps (512 MB write)",
                        "refresh_every": args.refresh_every, "n_tau_bins": N_TAU_BINS,
-                       "n_anchors": N_ANCHORS},
+                       "n_anchors": N_ANCHORS,
+                       "k_max": ({"autotuned (chains per k)": k_tuned} if k_tuned
+                                 else sorted({c.k_max for c in chains}))},
             "roofline": roofline, "flush_roofline": flush_roof,
             "phase_ms_per_step": {names[i]: phase_ms[i] / steps for i in range(len(names))},
             "gpu_launches": kernels,

@@ -214,6 +214,27 @@ ctaux_status ctaux_get_work(ctaux_ctx *ctx, double *prep_flop, double *flush_flo
                             double *flush_bytes, double *gamma_flop, double *meas_flop,
                             double *refresh_flop);
 
+/* Change the submatrix size of one chain between sweeps: 1 <= k_max <= the
+ * chain's k_max at ctaux_init (its buffers are sized for that).  The Markov
+ * chain does not depend on k_max (every draw is keyed by the proposal
+ * counter), so this changes only the speed.  Synchronizes the last stream. */
+ctaux_status ctaux_set_kmax(ctaux_ctx *ctx, int chain, int k_max);
+
+/* Autotune the submatrix size k_max per chain (the paper finds the optimum
+ * k = 64-128 empirically, Sec. V A, and has no tuner).
+ * Chains are grouped by (cluster size, octave of the current order).  Each
+ * trial sets the k of every group, runs one untimed block and then n_blocks
+ * timed blocks (CUDA events, no measurement, no refresh), and scores
+ * proposals per second of the whole context.  First the best common k among
+ * candidates[n_candidates] is taken, then each group's k is varied in turn
+ * (most populated group first), and a change is kept only if it gains more than 2 %.
+ * A candidate above a chain's k_max at init is capped to it.  The trials are
+ * real Markov-chain steps (the chains advance); a from-scratch refresh ends
+ * the tuning.  k_out[n_chains] (may be NULL) receives the chosen k per chain,
+ * *rate_out (may be NULL) the best score.  Synchronous. */
+ctaux_status ctaux_autotune_k(ctaux_ctx *ctx, const int *candidates, int n_candidates,
+                              int n_blocks, int *k_out, double *rate_out);
+
 /* Philox-4x32-10 on the device: for counters (t0 + i, chain, purpose), i <
  * count, write the two 53-bit uniforms of each draw to out[2*i], out[2*i+1].
  * A check of the device generator; allocates and frees a small buffer. */

@@ -670,6 +670,142 @@ ctaux_status ctaux_get_work(ctaux_ctx* ctx, double* prep_flop, double* flush_flo
   return CTAUX_OK;
 }
 
+ctaux_status ctaux_set_kmax(ctaux_ctx* ctx, int chain, int k_max) {
+  if (!ctx || chain < 0 || chain >= (int)ctx->chains.size()) return CTAUX_EINVAL;
+  if (k_max < 1 || k_max > ctx->chains[chain].k_max) return CTAUX_EINVAL;  // buffers sized at init
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->last_stream));
+  if (is_mixed(ctx)) {
+    ctx->hc32[chain].k_max = k_max;
+    Chain<float>* dc = reinterpret_cast<Chain<float>*>(ctx->chains_dev) + chain;
+    CUDA_TRY(ctx, cudaMemcpy(&dc->k_max, &k_max, sizeof(int), cudaMemcpyHostToDevice));
+  } else {
+    ctx->hc64[chain].k_max = k_max;
+    Chain<double>* dc = reinterpret_cast<Chain<double>*>(ctx->chains_dev) + chain;
+    CUDA_TRY(ctx, cudaMemcpy(&dc->k_max, &k_max, sizeof(int), cudaMemcpyHostToDevice));
+  }
+  return CTAUX_OK;
+}
+
+namespace {
+int current_kmax(ctaux_ctx* ctx, int chain) {
+  return is_mixed(ctx) ? ctx->hc32[chain].k_max : ctx->hc64[chain].k_max;
+}
+}  // namespace
+
+ctaux_status ctaux_autotune_k(ctaux_ctx* ctx, const int* candidates, int n_candidates, int n_blocks,
+                              int* k_out, double* rate_out) {
+  if (!ctx || !candidates || n_candidates < 1 || n_blocks < 1) return CTAUX_EINVAL;
+  for (int i = 0; i < n_candidates; ++i)
+    if (candidates[i] < 1 || candidates[i] > kMaxK) return CTAUX_EINVAL;
+  const int nch = (int)ctx->chains.size();
+  cudaStream_t st = ctx->last_stream;
+  // buckets: (cluster size, order octave) from the current orders
+  std::vector<int> bucket(nch);
+  std::vector<std::pair<int, int>> keys;
+  std::vector<int> pop;
+  for (int c = 0; c < nch; ++c) {
+    Dyn d;
+    ctaux_status r = read_dyn(ctx, c, &d);
+    if (r != CTAUX_OK) return r;
+    int oct = 0;
+    while ((16 << oct) <= d.n && oct < 20) ++oct;
+    const std::pair<int, int> key(ctx->chains[c].n_c, oct);
+    int b = 0;
+    while (b < (int)keys.size() && keys[b] != key) ++b;
+    if (b == (int)keys.size()) {
+      keys.push_back(key);
+      pop.push_back(0);
+    }
+    bucket[c] = b;
+    pop[b] += 1;
+  }
+  const int nb = (int)keys.size();
+  const int saved_refresh = ctx->params.refresh_every;
+  ctx->params.refresh_every = 0;  // no refresh inside the timed trials
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CUDA_TRY(ctx, cudaEventCreate(&e0));
+  CUDA_TRY(ctx, cudaEventCreate(&e1));
+  ctaux_status status = CTAUX_OK;
+  // proposals per second of the whole context with bucket b at k[b] (capped by
+  // each chain's allocation); one untimed block first
+  auto evaluate = [&](const std::vector<int>& kb, double* rate) -> ctaux_status {
+    for (int c = 0; c < nch; ++c) {
+      const int k = std::min(kb[bucket[c]], ctx->chains[c].k_max);
+      if (k != current_kmax(ctx, c)) {
+        ctaux_status r = ctaux_set_kmax(ctx, c, k);
+        if (r != CTAUX_OK) return r;
+      }
+    }
+    ctaux_status r = ctaux_sweep(ctx, 1, 0, st);
+    if (r != CTAUX_OK) return r;
+    r = ctaux_synchronize(ctx);
+    if (r != CTAUX_OK) return r;
+    int64_t t0 = 0, t1 = 0;
+    for (int c = 0; c < nch; ++c) {
+      Dyn d;
+      if ((r = read_dyn(ctx, c, &d)) != CTAUX_OK) return r;
+      t0 += d.t;
+    }
+    CUDA_TRY(ctx, cudaEventRecord(e0, st));
+    if ((r = ctaux_sweep(ctx, n_blocks, 0, st)) != CTAUX_OK) return r;
+    CUDA_TRY(ctx, cudaEventRecord(e1, st));
+    if ((r = ctaux_synchronize(ctx)) != CTAUX_OK) return r;
+    float ms = 0.f;
+    CUDA_TRY(ctx, cudaEventElapsedTime(&ms, e0, e1));
+    for (int c = 0; c < nch; ++c) {
+      Dyn d;
+      if ((r = read_dyn(ctx, c, &d)) != CTAUX_OK) return r;
+      t1 += d.t;
+    }
+    *rate = (double)(t1 - t0) / (ms > 0.f ? ms * 1e-3 : 1e-9);
+    return CTAUX_OK;
+  };
+  // 1) the best common k; 2) coordinate descent over buckets, most populated
+  // first, keeping a change only if it gains more than 2 %
+  std::vector<int> best_k(nb, candidates[0]);
+  double best = -1.0;
+  for (int i = 0; i < n_candidates && status == CTAUX_OK; ++i) {
+    std::vector<int> kb(nb, candidates[i]);
+    double rate = 0.0;
+    status = evaluate(kb, &rate);
+    if (status == CTAUX_OK && rate > best) {
+      best = rate;
+      best_k = kb;
+    }
+  }
+  std::vector<int> order(nb);
+  for (int b = 0; b < nb; ++b) order[b] = b;
+  std::sort(order.begin(), order.end(), [&](int a, int b) { return pop[a] > pop[b]; });
+  if (nb > 1) {
+    for (int b : order) {
+      for (int i = 0; i < n_candidates && status == CTAUX_OK; ++i) {
+        if (candidates[i] == best_k[b]) continue;
+        std::vector<int> kb = best_k;
+        kb[b] = candidates[i];
+        double rate = 0.0;
+        status = evaluate(kb, &rate);
+        if (status == CTAUX_OK && rate > 1.02 * best) {
+          best = rate;
+          best_k = kb;
+        }
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->params.refresh_every = saved_refresh;
+  if (status != CTAUX_OK) return status;
+  for (int c = 0; c < nch; ++c) {
+    const int k = std::min(best_k[bucket[c]], ctx->chains[c].k_max);
+    ctaux_status r = ctaux_set_kmax(ctx, c, k);
+    if (r != CTAUX_OK) return r;
+    if (k_out) k_out[c] = k;
+  }
+  if (rate_out) *rate_out = best;
+  // the trials ran without refreshes: start from a fresh N
+  return ctaux_recompute(ctx, nullptr);
+}
+
 ctaux_status ctaux_philox_uniforms(uint64_t seed, uint32_t chain, int64_t t0, int count, int purpose,
                                    double* out) {
   if (count < 0 || !out || purpose < 0) return CTAUX_EINVAL;

@@ -94,6 +94,9 @@ def _load():
                                      P(C.c_double), P(C.c_double), P(C.c_double)]),
         "ctaux_philox_uniforms": (C.c_int, [C.c_uint64, C.c_uint32, C.c_int64, C.c_int, C.c_int,
                                             P(C.c_double)]),
+        "ctaux_set_kmax": (C.c_int, [vp, C.c_int, C.c_int]),
+        "ctaux_autotune_k": (C.c_int, [vp, P(C.c_int), C.c_int, C.c_int, P(C.c_int),
+                                       P(C.c_double)]),
         "ctaux_synchronize": (C.c_int, [vp]),
         "ctaux_invert_noalloc": (C.c_int, [vp, C.c_int, vp, C.c_int, C.c_int, vp, vp]),
         "ctaux_destroy": (None, [vp]),
@@ -111,6 +114,7 @@ EXPORTED = ("ctaux_init", "ctaux_sweep", "ctaux_measure_G", "ctaux_reset_measure
             "ctaux_recompute", "ctaux_get_stats", "ctaux_get_trace", "ctaux_get_config",
             "ctaux_set_config", "ctaux_get_N", "ctaux_set_profiling", "ctaux_get_phase_times",
             "ctaux_get_work", "ctaux_philox_uniforms", "ctaux_synchronize", "ctaux_destroy",
+            "ctaux_set_kmax", "ctaux_autotune_k",
             "ctaux_last_error", "ctaux_invert_noalloc")
 
 
@@ -264,6 +268,18 @@ class Context:
         out = np.zeros((max(k, 1), max(k, 1)), order="F")
         self._check(lib.ctaux_get_N(self.h, chain, spin, _dp(out), max(k, 1), C.byref(m)), "get_N")
         return out[:k, :k]
+
+    def set_kmax(self, chain, k_max):
+        self._check(lib.ctaux_set_kmax(self.h, int(chain), int(k_max)), "set_kmax")
+
+    def autotune_k(self, candidates=(16, 32, 64, 128), n_blocks=8):
+        """Choose k_max per chain on the device; returns (k per chain, proposals/s)."""
+        cand = np.ascontiguousarray(candidates, dtype=np.int32)
+        k = np.zeros(len(self.chain_inputs), np.int32)
+        rate = C.c_double()
+        self._check(lib.ctaux_autotune_k(self.h, _ip(cand), len(cand), int(n_blocks), _ip(k),
+                                         C.byref(rate)), "autotune_k")
+        return k, rate.value
 
     def set_profiling(self, on=True):
         self._check(lib.ctaux_set_profiling(self.h, int(bool(on))), "set_profiling")

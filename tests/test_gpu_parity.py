@@ -390,3 +390,54 @@ def test_mixed_near_tie_fallback_refresh_decides_in_fp64():
                 ref = o["ratio"][s]
                 assert abs(g["ratio"][s] - ref) <= 1e-9 * max(1.0, abs(ref)), (g, o)
     assert n_fp64 >= 5 and st["tie_refreshes"] >= n_fp64
+
+
+def test_set_kmax_between_sweeps_keeps_the_markov_chain():
+    """k_max changed at run time (within the allocation): same proposals, decisions and
+    ratios as the oracle, since every draw is keyed by the proposal counter."""
+    ch = configs.cube8(K=64.0, k_max=64, capacity=512)
+    cfg = configs.synthetic_configuration(ch, 200, seed=4)
+    oc = oracle_for(ch)
+    oc.set_config(cfg["tau"], cfg["site"], cfg["s"], cfg["birth"], cfg["t"])
+    with pk.Context([ch], trace_capacity=1024, refresh_every=4) as ctx:
+        ctx.set_config(0, cfg["tau"], cfg["site"], cfg["s"], cfg["birth"], cfg["t"])
+        ctx.sweep(2)
+        ctx.set_kmax(0, 16)
+        ctx.sweep(5)
+        ctx.set_kmax(0, 40)
+        ctx.sweep(3)
+        ctx.synchronize()
+        tr = ctx.trace(0)
+        assert len(tr) == 2 * 64 + 5 * 16 + 3 * 40
+        compare_traces(tr, oc.run(len(tr)), RTOL64)
+        compare_config(ctx, 0, oc)
+        with pytest.raises(pk.CtauxError):
+            ctx.set_kmax(0, 65)
+
+
+def test_autotune_k_picks_candidates_and_keeps_parity():
+    """The tuner returns a candidate per chain (capped by its allocation) and leaves
+    every chain in a state from which it still follows the oracle."""
+    chains = [configs.cube8(K=64.0, k_max=64, capacity=512, seed=s) for s in range(3)]
+    for i, ch in enumerate(chains):
+        ch.chain_id = i
+    chains.append(configs.aim1(K=4.0, k_max=16, capacity=128))
+    chains[-1].chain_id = 3
+    with pk.Context(chains, refresh_every=8, trace_capacity=256) as ctx:
+        ctx.sweep(10)
+        k, rate = ctx.autotune_k(candidates=(8, 32, 64), n_blocks=4)
+        assert rate > 0
+        for i, ch in enumerate(chains):
+            assert k[i] in (8, 32, 64) or k[i] == ch.k_max
+            assert k[i] <= ch.k_max
+        ctx.synchronize()
+        cfgs = [ctx.get_config(i) for i in range(len(chains))]
+        start = [len(ctx.trace(i)) for i in range(len(chains))]
+        ctx.sweep(3)
+        ctx.synchronize()
+        for i, ch in enumerate(chains):
+            oc = oracle_for(ch)
+            c = cfgs[i]
+            oc.set_config(c["tau"], c["site"], c["s"], c["birth"], c["t"])
+            tr = ctx.trace(i)
+            compare_traces(tr, oc.run(len(tr)), RTOL64)
