@@ -220,6 +220,8 @@ def main():
     ap.add_argument("--refresh-every", dest="refresh_every", type=int, default=REFRESH_EVERY)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graph", dest="no_graph", action="store_true",
+                    help="direct kernel launches instead of one CUDA graph per block")
     ap.add_argument("--autotune", default=None,
                     help="comma-separated k candidates: choose k_max per chain on the device "
                          "(ctaux_autotune_k) after thermalisation; --k-max is the allocation")
@@ -343,7 +345,7 @@ def measure_form(args, pk, torch, dist, chains, meta, form, local, world, with_e
     precision = pk.CTAUX_FP64 if form == "fp64" else pk.CTAUX_MIXED
     ctx = pk.Context(chains, precision=precision, refresh_every=args.refresh_every,
                      n_tau_bins=N_TAU_BINS, n_anchors=N_ANCHORS, device=local,
-                     refresh_df64=int(form == "mixed_df64"))
+                     refresh_df64=int(form == "mixed_df64"), use_graph=int(not args.no_graph))
     stream = torch.cuda.current_stream()
     sh = stream.cuda_stream
     if meta.get("start_order"):
@@ -369,10 +371,9 @@ def measure_form(args, pk, torch, dist, chains, meta, form, local, world, with_e
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     acc0 = accepted_total()
-    work0 = ctx.work()
-    ms0, kern0 = ctx.phase_times()
+    _, kern0 = ctx.phase_times()
     ties0 = sum(ctx.stats(i)["near_ties"] for i in range(len(chains)))
-    ctx.set_profiling(True)
+    # timed region: no phase events (and CUDA-graph launches unless --no-graph)
     clocks = ClockSampler(local)
     clocks.start()
     if world > 1:
@@ -387,18 +388,32 @@ def measure_form(args, pk, torch, dist, chains, meta, form, local, world, with_e
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
-    ctx.set_profiling(False)
     total_ms = sum(s_.elapsed_time(e_) for s_, e_ in zip(starts, ends))
     acc = accepted_total() - acc0
-    ms1, kern1 = ctx.phase_times()
-    work1 = ctx.work()
-    phase_ms = ms1 - ms0
+    _, kern1 = ctx.phase_times()
     kernels = int((kern1 - kern0).sum())
     ties = sum(ctx.stats(i)["near_ties"] for i in range(len(chains))) - ties0
     tie_refreshes = sum(ctx.stats(i)["tie_refreshes"] for i in range(len(chains)))
     if world > 1:
         total_ms, acc = reduce_over_ranks(torch, dist, total_ms, acc, "cuda")
     value = acc / (total_ms / 1e3)
+
+    # phase breakdown: a further profiled pass (CUDA events around every phase,
+    # direct launches) over a whole number of refresh periods
+    prof_steps = args.refresh_every if args.refresh_every > 0 else 32
+    while prof_steps < 16:
+        prof_steps += args.refresh_every
+    work0 = ctx.work()
+    ms0, _ = ctx.phase_times()
+    ctx.set_profiling(True)
+    for i in range(prof_steps):
+        flush.zero_()
+        ctx.sweep(1, measure=True, stream=sh)
+    ctx.synchronize()
+    ctx.set_profiling(False)
+    ms1, _ = ctx.phase_times()
+    work1 = ctx.work()
+    phase_ms = ms1 - ms0
 
     # ---------------- rooflines (live CUDA-event phase times, algorithmic work from the device)
     peaks, peak_kind = load_peaks()
@@ -453,11 +468,11 @@ def measure_form(args, pk, torch, dist, chains, meta, form, local, world, with_e
                 "peak": r["peak"], "unit": r["unit"],
                 "frac": r["achieved"] / r["peak"] if r["peak"] else None,
                 "traffic": None, "peak_source": r["peak_source"],
-                "ms_per_step": phase_ms[dom] / steps}
+                "ms_per_step": phase_ms[dom] / prof_steps}
     fr = roof(names.index("flush_gemm"))
     flush_roof = {"bound": fr["bound"], "achieved": fr["achieved"], "peak": fr["peak"],
                   "unit": fr["unit"], "frac": fr["achieved"] / fr["peak"],
-                  "ms_per_step": phase_ms[3] / steps, "peak_source": fr["peak_source"]}
+                  "ms_per_step": phase_ms[3] / prof_steps, "peak_source": fr["peak_source"]}
 
     e2e = None
     if with_e2e:
@@ -488,12 +503,14 @@ def measure_form(args, pk, torch, dist, chains, meta, form, local, world, with_e
                        {"mean": sum(orders) / len(orders), "min": int(min(orders)), "max": int(max(orders))},
                        "precision": form,
                        "l2": "flushed between timed steps (512 MB write)",
+                       "launch": "direct" if args.no_graph else "one CUDA graph per block and per measurement",
                        "refresh_every": args.refresh_every, "n_tau_bins": N_TAU_BINS,
                        "n_anchors": N_ANCHORS,
                        "k_max": ({"autotuned (chains per k)": k_tuned} if k_tuned
                                  else sorted({c.k_max for c in chains}))},
             "roofline": roofline, "flush_roofline": flush_roof,
-            "phase_ms_per_step": {names[i]: phase_ms[i] / steps for i in range(len(names))},
+            "phase_ms_per_step": {names[i]: phase_ms[i] / prof_steps for i in range(len(names))},
+            "phase_pass_steps": prof_steps,
             "gpu_launches": kernels,
             "accept_rate": acc / max(1, steps * sum(c.k_max for c in chains) * world),
             "drift_max_last_refresh": st["last_drift_max"], "near_ties": ties,

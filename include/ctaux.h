@@ -101,6 +101,10 @@ typedef struct {
   int tie_refine_iters;               /* mixed form: most refinement iterations per near tie;
                                          0 = 12; -1 = none, so that every near tie takes the
                                          from-scratch fallback (for tests) */
+  int use_graph;                      /* 1 = each block (with its near-tie launch) and each
+                                         measurement is launched as one CUDA graph, captured
+                                         on a private stream at first use; direct launches
+                                         while profiling is on, or if capture fails */
   int refresh_df64;                   /* mixed form: 1 = the periodic from-scratch recomputation
                                          eliminates in double-float arithmetic (two float32,
                                          about 48 significand bits) on the float32 pipe, which

@@ -34,6 +34,12 @@ struct ctaux_ctx {
   int blocks_since_refresh = 0;
   std::string err;
   int max_ld = 0;
+  // CUDA graphs of one block (with its near-tie launch) and of one measurement,
+  // captured on first use on a private stream, with their kernel counts per phase
+  cudaStream_t capture_stream = nullptr;
+  cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
+  long long graph_kernels[2][PhaseTimer::kPhases] = {};
+  bool graph_failed = false;
 };
 
 namespace {
@@ -326,24 +332,64 @@ ctaux_status do_sweeps(ctaux_ctx* ctx, int n_sweeps, int measure, cudaStream_t s
   Chain<T>* dc = reinterpret_cast<Chain<T>*>(ctx->chains_dev);
   PhaseTimer* pt = ctx->timer;
   const bool ties = (sizeof(T) == 4) && ctx->params.tie_guard > 0.0;
-  for (int s = 0; s < n_sweeps; ++s) {
-    launch_block<T>(dc, ctx->ls, st, pt, ctx->tc_maps_dev);
-    if (ties) {
-      // near-tie decisions in FP64: iterative refinement against the float32 N,
-      // with a from-scratch FP64 refresh in the same launch where it does not
-      // converge (exits at once without a pending tie)
-      pt->begin(7, st);
-      cudaError_t e = launch_tie_refine(reinterpret_cast<Chain<float>*>(dc), ctx->ls, ctx->tie_part, st);
-      pt->end(7, st, 1);
-      if (e != cudaSuccess) return set_err(ctx, CTAUX_ECUDA, "tie decision launch: %s", cudaGetErrorString(e));
+  // one block: plan, gather, prep, proposals, flush, and the near-tie decisions
+  // in FP64 (iterative refinement against the float32 N, with a from-scratch
+  // FP64 refresh in the same launch where it does not converge; the launch
+  // exits at once without a pending tie)
+  auto block = [&](cudaStream_t s, PhaseTimer* p) -> cudaError_t {
+    launch_block<T>(dc, ctx->ls, s, p, ctx->tc_maps_dev);
+    if (!ties) return cudaSuccess;
+    p->begin(7, s);
+    cudaError_t e = launch_tie_refine(reinterpret_cast<Chain<float>*>(dc), ctx->ls, ctx->tie_part, s);
+    p->end(7, s, 1);
+    return e;
+  };
+  auto meas = [&](cudaStream_t s, PhaseTimer* p) -> cudaError_t {
+    launch_measure<T>(dc, ctx->ls, s, p);
+    return cudaSuccess;
+  };
+  // graph mode (not while profiling: the phase events would be frozen into the graph)
+  const bool graphs = ctx->params.use_graph && !pt->on && !ctx->graph_failed;
+  auto run = [&](int which, auto&& body) -> cudaError_t {
+    if (graphs && !ctx->graph_exec[which]) {
+      PhaseTimer counter;  // counts the captured kernels; records no events
+      cudaGraph_t g = nullptr;
+      cudaError_t e = cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        cudaError_t eb = body(ctx->capture_stream, &counter);
+        e = cudaStreamEndCapture(ctx->capture_stream, &g);
+        if (e == cudaSuccess) e = eb;
+      }
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&ctx->graph_exec[which], g, 0);
+      if (g) cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        // capture not possible here: direct launches from now on
+        cudaGetLastError();
+        ctx->graph_failed = true;
+        ctx->graph_exec[which] = nullptr;
+      } else {
+        for (int ph = 0; ph < PhaseTimer::kPhases; ++ph) ctx->graph_kernels[which][ph] = counter.kernels[ph];
+      }
     }
+    if (graphs && ctx->graph_exec[which]) {
+      for (int ph = 0; ph < PhaseTimer::kPhases; ++ph) pt->kernels[ph] += ctx->graph_kernels[which][ph];
+      return cudaGraphLaunch(ctx->graph_exec[which], st);
+    }
+    return body(st, pt);
+  };
+  for (int s = 0; s < n_sweeps; ++s) {
+    cudaError_t e = run(0, block);
+    if (e != cudaSuccess) return set_err(ctx, CTAUX_ECUDA, "block launch: %s", cudaGetErrorString(e));
     ctx->blocks_since_refresh += 1;
     if (ctx->params.refresh_every > 0 && ctx->blocks_since_refresh >= ctx->params.refresh_every) {
       ctaux_status r = do_refresh<T>(ctx, -1, st);
       if (r != CTAUX_OK) return r;
       ctx->blocks_since_refresh = 0;
     }
-    if (measure) launch_measure<T>(dc, ctx->ls, st, pt);
+    if (measure) {
+      e = run(1, meas);
+      if (e != cudaSuccess) return set_err(ctx, CTAUX_ECUDA, "measurement launch: %s", cudaGetErrorString(e));
+    }
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return set_err(ctx, CTAUX_ECUDA, "sweep launch: %s", cudaGetErrorString(e));
@@ -395,6 +441,13 @@ ctaux_status ctaux_init(const ctaux_params* params, ctaux_ctx** out) {
   ctx->timer = new PhaseTimer();
   for (int i = 0; i < PhaseTimer::kPool; ++i) cudaEventCreate(&ctx->timer->ev[i]);
   ctx->timer->created = true;
+  if (ctx->params.use_graph) {
+    cudaError_t ge = cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking);
+    if (ge != cudaSuccess) {
+      cudaGetLastError();
+      ctx->graph_failed = true;
+    }
+  }
   *out = ctx;
   return CTAUX_OK;
 }
@@ -822,6 +875,9 @@ void ctaux_destroy(ctaux_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->last_stream);
+  for (int w = 0; w < 2; ++w)
+    if (ctx->graph_exec[w]) cudaGraphExecDestroy(ctx->graph_exec[w]);
+  if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
   for (void* p : ctx->allocations) cudaFree(p);
   if (ctx->timer) {
     if (ctx->timer->created)

@@ -36,7 +36,8 @@ class Params(C.Structure):
                 ("n_tau_bins", C.c_int), ("n_anchors", C.c_int),
                 ("trace_capacity", C.c_int), ("device", C.c_int),
                 ("mixed_flush_tc", C.c_int), ("tie_guard", C.c_double),
-                ("tie_refine_iters", C.c_int), ("refresh_df64", C.c_int)]
+                ("tie_refine_iters", C.c_int), ("use_graph", C.c_int),
+                ("refresh_df64", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -160,7 +161,7 @@ class Context:
 
     def __init__(self, chains, precision=CTAUX_FP64, refresh_every=32, p_insert=0.5, p_flip=0.0,
                  n_tau_bins=32, n_anchors=4, trace_capacity=0, device=0, mixed_flush_tc=1,
-                 tie_guard=1e-4, tie_refine_iters=0, refresh_df64=0):
+                 tie_guard=1e-4, tie_refine_iters=0, refresh_df64=0, use_graph=0):
         self._keep = []
         cps = (ChainParams * len(chains))()
         self.chain_inputs = list(chains)
@@ -174,7 +175,7 @@ class Context:
                                  int(ch.chain_id))
         self.params = Params(len(chains), cps, precision, refresh_every, p_insert, p_flip,
                              n_tau_bins, n_anchors, trace_capacity, device, mixed_flush_tc,
-                             tie_guard, tie_refine_iters, int(refresh_df64))
+                             tie_guard, tie_refine_iters, int(use_graph), int(refresh_df64))
         self.n_tau_bins = n_tau_bins
         self.trace_capacity = trace_capacity
         h = C.c_void_p()

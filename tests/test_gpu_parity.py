@@ -441,3 +441,27 @@ def test_autotune_k_picks_candidates_and_keeps_parity():
             oc.set_config(c["tau"], c["site"], c["s"], c["birth"], c["t"])
             tr = ctx.trace(i)
             compare_traces(tr, oc.run(len(tr)), RTOL64)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_graph_launches_equal_direct_launches(precision):
+    """Blocks and measurements launched as CUDA graphs give the same bits as
+    direct launches (every size is read from device memory, so one captured
+    graph serves all later blocks)."""
+    ch = configs.cube8(K=64.0, k_max=32, capacity=512)
+    prec = pk.CTAUX_MIXED if precision == "mixed" else pk.CTAUX_FP64
+    out = []
+    for graph in (0, 1):
+        with pk.Context([ch], precision=prec, refresh_every=5, trace_capacity=2048,
+                        use_graph=graph) as ctx:
+            for _ in range(4):
+                ctx.sweep(3, measure=True)
+            ctx.synchronize()
+            G, E, nm = ctx.measure_G(0)
+            out.append((ctx.trace(0), ctx.get_config(0), G, ctx.stats(0)))
+    (t0, c0, g0, s0), (t1, c1, g1, s1) = out
+    np.testing.assert_array_equal(t0, t1)
+    for key in ("tau", "site", "s", "birth"):
+        np.testing.assert_array_equal(c0[key], c1[key])
+    np.testing.assert_array_equal(g0, g1)
+    assert s0["t"] == s1["t"] and s0["refreshes"] == s1["refreshes"]
