@@ -141,7 +141,8 @@ ctaux_status build_chains(ctaux_ctx* ctx) {
   ctx->max_ld = max_ld;
   // proposal kernel shared memory
   size_t fixed = ((sizeof(T) * 8 * max_k + 15) & ~size_t(15)) + sizeof(double) * 2 * max_k + sizeof(int) * max_k +
-                 sizeof(short) * ((max_ld + 7) & ~7) + sizeof(uint32_t) * ((max_ld + 31) / 32) + 64;
+                 sizeof(short) * ((max_ld + 7) & ~7) + sizeof(uint32_t) * ((max_ld + 31) / 32) +
+                 sizeof(double) * 2 * max_k + ((max_ld + 15) & ~15) + 64;
   size_t gam = ((sizeof(T) * 2 * (size_t)max_k * (max_k + 1)) + 15) & ~size_t(15);
   ls.gamma_in_smem = (fixed + gam <= 200 * 1024) ? 1 : 0;
   ls.prop_smem = (int)(fixed + (ls.gamma_in_smem ? gam : 0));

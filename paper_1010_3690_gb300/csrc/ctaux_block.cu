@@ -408,7 +408,8 @@ __global__ void __launch_bounds__(256) k_proposals(Chain<T>* chains, int gamma_i
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   // layout: [Gamma^{-1} 2 x KM x LG (optional)] [vec 2 x 4 x KM] [lam 2 x KM double]
-  //         [P KM int] [pmap cap_m short] [alive mask]
+  //         [P KM int] [pmap cap_m short] [alive mask] [1/lambda 2 x KM double]
+  //         [block-start spins cap_m]
   unsigned char* sp = smem_raw;
   T* Gs = nullptr;
   if (gamma_in_smem) {
@@ -425,6 +426,11 @@ __global__ void __launch_bounds__(256) k_proposals(Chain<T>* chains, int gamma_i
   sp += sizeof(short) * ((c.cap_m + 7) & ~7);
   uint32_t* alive = reinterpret_cast<uint32_t*>(sp);
   const int n_words = (m + 31) / 32;
+  sp += sizeof(uint32_t) * ((c.cap_m + 31) / 32);
+  sp = reinterpret_cast<unsigned char*>(((uintptr_t)sp + 15) & ~(uintptr_t)15);
+  double* ilam_s = reinterpret_cast<double*>(sp);   // 1/lambda of the slots in P, per spin
+  sp += sizeof(double) * 2 * KM;
+  int8_t* s0_s = reinterpret_cast<int8_t*>(sp);     // block-start spins
 
   T* G = gamma_in_smem ? (Gs + (size_t)spin * KM * LG) : c.Ginv[spin];
   A* sv = vec + spin * 4 * KM;   // s (column of G^0 over P)
@@ -433,21 +439,32 @@ __global__ void __launch_bounds__(256) k_proposals(Chain<T>* chains, int gamma_i
   A* zv = yv + KM;               // w^T Gamma^{-1}
   double* lam = lam_s + spin * KM;
 
+  double* ilam = ilam_s + spin * KM;
+
   __shared__ A red[2][4];
   __shared__ A gpp_s[2];
   __shared__ double ratio_s[2];
+  __shared__ A raw_s[2];        // per spin: beta (first touch), delta or Gamma^{-1}_qq (re-touch)
+  __shared__ A gqq_s[2];
   __shared__ A scal_s[2];       // per spin: 1/beta, Sherman-Morrison coefficient or Schur pivot
   __shared__ double lamn_s[2];  // per spin: lambda of the proposed change
+  __shared__ double ev_s[2][5], iem1_s[2][5];
+  __shared__ A glam_s[2][5];
   __shared__ int dec_s;         // 0 reject, 1 accept, 2 near tie (stop)
+  __shared__ int fin_s;         // the decision's finite flag, forced flag
+  __shared__ double R_s;
   __shared__ double f_s;        // move factor K/(n+1), n/K or 1
   __shared__ int sel_p;
   __shared__ int jP;
   __shared__ int n_cur, sign_s;
   __shared__ long long cnt_prop[3], cnt_acc[3], numeric, ties;
-  __shared__ double flops;
+  __shared__ long long flops2;  // algorithmic flops / 2 (integer: no float64 work)
   __shared__ BlockDraw bd_s[kMaxK];
 
-  for (int i = tid; i < m; i += 256) pmap[i] = -1;
+  for (int i = tid; i < m; i += 256) {
+    pmap[i] = -1;
+    s0_s[i] = c.s0[i];
+  }
   for (int w = tid; w < n_words; w += 256) {
     uint32_t bits = 0;
     for (int b = 0; b < 32; ++b) {
@@ -456,6 +473,12 @@ __global__ void __launch_bounds__(256) k_proposals(Chain<T>* chains, int gamma_i
     }
     alive[w] = bits;
   }
+  if (tid < 10) {
+    const int sp_ = tid / 5, k_ = tid % 5;
+    ev_s[sp_][k_] = c.ev[sp_][k_];
+    iem1_s[sp_][k_] = c.inv_em1[sp_][k_];
+    glam_s[sp_][k_] = c.glam[sp_][k_];
+  }
   if (tid == 0) {
     jP = 0;
     n_cur = n_old;
@@ -463,26 +486,32 @@ __global__ void __launch_bounds__(256) k_proposals(Chain<T>* chains, int gamma_i
     for (int q = 0; q < 3; ++q) cnt_prop[q] = cnt_acc[q] = 0;
     numeric = 0;
     ties = 0;
-    flops = 0.0;
+    flops2 = 0;
   }
   for (int e = tid; e < KM; e += 256) bd_s[e] = c.draws[e];
+  // read once: the decision of a near tie taken in FP64 after the previous block
+  const int64_t forced_t = (sizeof(T) == 4) ? d.forced_t : -1;
+  const double tie_guard = c.tie_guard;
+  const int trace_cap = c.trace_cap;
+  const int64_t trace_base = d.trace_written;
   __syncthreads();
   int consumed = KM;
 
-  // Scalar float64 work (the move factor, divisions, the Metropolis decision)
-  // runs on one thread per spin half or per CTA and is shared through shared
-  // memory: GB300 executes float64 at 1/64 of the float32 rate, and a scalar
-  // computed redundantly by all eight warps costs eight times the pipe time.
+  // The chain of a proposal is latency-bound: every step between two barriers
+  // is kept short.  Scalar float64 work (the move factor, divisions, the
+  // Metropolis decision) runs on one thread per spin half or per CTA and is
+  // shared through shared memory (GB300 executes float64 at 1/64 of the
+  // float32 rate: a warp-wide float64 instruction holds the pipe ~16 cycles);
+  // the divisions needed only on acceptance and the trace record are done
+  // beside the decision, by other threads; warps without rows or columns skip
+  // the float64 reductions; the tables and block-start spins are in shared
+  // memory.
   for (int jj = 0; jj < KM; ++jj) {
     const int64_t t = t0 + jj;
     const BlockDraw dr = bd_s[jj];
     const int move = dr.move;
     const int nc = n_cur;
     int p = -1, s_new = 0;
-    // move factor, computed off the critical path by a thread of a warp that
-    // has no gather or matrix-vector rows while j <= 64, read by thread 0
-    if (tid == 192)
-      f_s = (move == MV_INSERT) ? c.K / (double)(nc + 1) : (move == MV_REMOVE ? (double)nc / c.K : 1.0);
     if (move == MV_INSERT) {
       p = dr.slot;
       s_new = dr.s_new;
@@ -501,11 +530,15 @@ __global__ void __launch_bounds__(256) k_proposals(Chain<T>* chains, int gamma_i
       }
       s_new = (move == MV_REMOVE) ? 0 : -(int)s_cur[p];
     }
+    // move factor, off the critical path (warp 6 has no gather or matrix-vector
+    // rows while j <= 64); read by thread 0 after two barriers
+    if (tid == 192)
+      f_s = (move == MV_INSERT) ? c.K / (double)(nc + 1) : (move == MV_REMOVE ? (double)nc / c.K : 1.0);
     if (p < 0) {  // removal or flip with no vertex: automatic rejection
       if (tid == 0) {
         cnt_prop[move]++;
-        if (c.trace_cap > 0) {
-          TraceRec& r = c.trace[(d.trace_written + jj) % c.trace_cap];
+        if (trace_cap > 0) {
+          TraceRec& r = c.trace[(trace_base + jj) % trace_cap];
           r.t = t; r.move = move; r.n = nc; r.birth = -1; r.s_new = 0; r.accept = 0;
           r.ratio[0] = r.ratio[1] = 0.0; r.R = 0.0; r.u = dr.u_acc;
         }
@@ -514,26 +547,33 @@ __global__ void __launch_bounds__(256) k_proposals(Chain<T>* chains, int gamma_i
     }
     const int q = pmap[p];
     const int j = jP;
-    const int s_start = c.s0[p];
+    const int s_start = s0_s[p];
+    const int dk = s_new - s_start + 2;   // index of lambda_new in the tables
     const bool to_start = (s_new == s_start);  // lambda_new = 0
     if (q < 0) {
       // first touch: gather s = G^0_{P,p}, w = G^0_{p,P}, G^0_pp
+      // (G = (N e^V - 1)/(e^V - 1) for old columns, Eq. NfromG; prep columns for new ones)
       for (int r = ht; r < j; r += 128) {
         const int pr = P_s[r];
-        sv[r] = g_int<A>(c, Nb, Gc, n_old, spin, pr, p);
-        wv[r] = g_int<A>(c, Nb, Gc, n_old, spin, p, pr);
+        const int kp = s0_s[p] + 2, kr = s0_s[pr] + 2;
+        sv[r] = (p < n_old)
+                    ? ((A)Nb[(long)p * ld + pr] * (A)ev_s[spin][kp] - (A)0) * (A)iem1_s[spin][kp]
+                    : (A)Gc[(long)(p - n_old) * ld + pr];
+        wv[r] = (pr < n_old)
+                    ? ((A)Nb[(long)pr * ld + p] * (A)ev_s[spin][kr] - (A)0) * (A)iem1_s[spin][kr]
+                    : (A)Gc[(long)(pr - n_old) * ld + p];
       }
       if (ht == 127) gpp_s[half] = g_int<A>(c, Nb, Gc, n_old, spin, p, p);
       __syncthreads();
-      // y = Gamma^{-1} s and the partial sums of w . y; z = w^T Gamma^{-1} is
-      // needed only on acceptance.  float64: four threads per row
-      // (interleaved columns, combined by shuffles) to shorten the chain of
-      // slow float64 operations; float32: one thread per row, two accumulators.
+      // y = Gamma^{-1} s and the partial sums of w . y (z = w^T Gamma^{-1} only
+      // on acceptance).  float64: four threads per row, combined by shuffles;
+      // float32: one thread per row, two accumulators.
       {
         A part = (A)0;
         if constexpr (sizeof(A) == 8) {
           const int quad = ht & 3;
           for (int r0 = 0; r0 < j; r0 += 32) {
+            if (r0 + (ht >> 2) - (lane >> 2) >= j) break;  // warp without rows (uniform)
             const int r = r0 + (ht >> 2);
             A acc = (A)0;
             if (r < j) {
@@ -562,33 +602,35 @@ __global__ void __launch_bounds__(256) k_proposals(Chain<T>* chains, int gamma_i
             part += wv[r] * y;
           }
         }
-        part = warp_sum_t(part);
-        if (lane == 0) red[half][hw] = part;
+        // warps that hold rows reduce their part; the others contribute 0
+        const bool has_rows = (sizeof(A) == 8) ? (hw * 8 < j) : (hw * 32 < j);
+        if (has_rows) part = warp_sum_t(part);
+        if (lane == 0) red[half][hw] = has_rows ? part : (A)0;
       }
       __syncthreads();
       if (ht == 0) {
-        const double lam_new = c.ev[spin][s_new - s_start + 2] - 1.0;
+        const double lam_new = ev_s[spin][dk] - 1.0;
         const A lam_a = (A)lam_new;
-        const A dd = gpp_s[half] - (A)c.glam[spin][s_new - s_start + 2];  // (1 + lambda) / lambda
+        const A dd = gpp_s[half] - glam_s[spin][dk];  // (1 + lambda) / lambda
         const A beta = dd - ((red[half][0] + red[half][1]) + (red[half][2] + red[half][3]));
         ratio_s[half] = (double)(-lam_a * beta);
-        scal_s[half] = (A)1 / beta;  // the bordered inverse's 1/beta
+        raw_s[half] = beta;
         lamn_s[half] = lam_new;
       }
     } else if (ht == 0) {
-      const double lam_new = c.ev[spin][s_new - s_start + 2] - 1.0;
+      const double lam_new = ev_s[spin][dk] - 1.0;
       const A lam_a = (A)lam_new;
-      const A lam_old = (A)lam[q];
+      const A ilo = (A)ilam[q];  // 1 / lambda of the slot's first change
       const A gqq = (A)G[(size_t)q * LG + q];
       A r;
       if (!to_start) {
-        const A delta = (A)1 / lam_old - (A)1 / lam_a;
-        r = (lam_a / lam_old) * ((A)1 + delta * gqq);
-        scal_s[half] = delta / ((A)1 + delta * gqq);  // Sherman-Morrison coefficient
+        const A delta = ilo - (A)iem1_s[spin][dk];  // 1/lambda_old - 1/lambda_new
+        r = (lam_a * ilo) * ((A)1 + delta * gqq);
+        raw_s[half] = delta;
       } else {
-        r = -gqq / lam_old;
-        scal_s[half] = (A)1 / gqq;  // Schur complement pivot
+        r = -gqq * ilo;
       }
+      gqq_s[half] = gqq;
       ratio_s[half] = (double)r;
       lamn_s[half] = lam_new;
     }
@@ -599,7 +641,7 @@ __global__ void __launch_bounds__(256) k_proposals(Chain<T>* chains, int gamma_i
       bool accept = dr.u_acc < pacc;
       bool finite = isfinite(R);
       if (!finite) accept = false;
-      const bool forced = (sizeof(T) == 4) && d.forced_t == t;
+      const bool forced = (sizeof(T) == 4) && forced_t == t;
       int dec;
       if (forced) {
         // decided in FP64 after the previous block stopped here (k_tie_refine)
@@ -607,8 +649,8 @@ __global__ void __launch_bounds__(256) k_proposals(Chain<T>* chains, int gamma_i
         R = d.forced_R;
         finite = true;
         dec = accept ? 1 : 0;
-      } else if (sizeof(T) == 4 && c.tie_guard > 0.0 && finite &&
-                 fabs(dr.u_acc - pacc) < c.tie_guard * fmax(dr.u_acc, pacc)) {
+      } else if (sizeof(T) == 4 && tie_guard > 0.0 && finite &&
+                 fabs(dr.u_acc - pacc) < tie_guard * fmax(dr.u_acc, pacc)) {
         // near tie in the float32 form: the block ends before this proposal,
         // which is decided in FP64 after the flush
         d.tie_pending = 1;
@@ -617,34 +659,26 @@ __global__ void __launch_bounds__(256) k_proposals(Chain<T>* chains, int gamma_i
         dec = 2;
       } else {
         dec = accept ? 1 : 0;
-      }
-      if (dec != 2) {
-        cnt_prop[move]++;
-        // algorithmic flops, both spins: y GEMV and the dot (first touch); on
-        // acceptance the z GEMV and the bordered update, or the rank-one update
-        const double jd = (double)j;
-        double fl = (q < 0) ? (2.0 * jd * jd + 2.0 * jd) : 4.0;
-        if (accept) fl += (q < 0) ? 2.0 * jd * jd + 3.0 * (jd + 1.0) * (jd + 1.0) : 3.0 * jd * jd;
-        flops += 2.0 * fl;
-        if (!finite) numeric++;
-        if (sizeof(T) == 4 && c.tie_guard == 0.0 && finite &&
+        if (sizeof(T) == 4 && tie_guard == 0.0 && finite &&
             fabs(dr.u_acc - pacc) < kTieGuard * fmax(dr.u_acc, pacc))
           ties++;  // detection only (FP64 re-evaluation off)
-        if (c.trace_cap > 0) {
-          TraceRec& rr = c.trace[(d.trace_written + jj) % c.trace_cap];
-          rr.t = t; rr.move = move; rr.n = nc;
-          rr.birth = birth[p]; rr.s_new = s_new; rr.accept = (accept ? 1 : 0) | (forced ? 2 : 0);
-          rr.ratio[0] = forced ? d.forced_ratio[0] : ratio_s[0];
-          rr.ratio[1] = forced ? d.forced_ratio[1] : ratio_s[1];
-          rr.R = R; rr.u = dr.u_acc;
-        }
-        if (forced) d.forced_t = -1;
-        if (accept) {
-          if (R < 0.0) sign_s = -sign_s;
-          cnt_acc[move]++;
-        }
       }
+      if (dec != 2) {
+        if (!finite) numeric++;
+        if (accept && R < 0.0) sign_s = -sign_s;
+        if (forced) d.forced_t = -1;
+      }
+      R_s = R;
+      fin_s = forced ? 1 : 0;
       dec_s = dec;
+    } else if ((tid == 32 || tid == 160) && q < 0) {
+      // 1 / beta of this spin, needed only on acceptance, beside the decision
+      scal_s[half] = (A)1 / raw_s[half];
+    } else if ((tid == 32 || tid == 160) && !to_start) {
+      const A delta = raw_s[half];
+      scal_s[half] = delta / ((A)1 + delta * gqq_s[half]);  // Sherman-Morrison coefficient
+    } else if (tid == 32 || tid == 160) {
+      scal_s[half] = (A)1 / gqq_s[half];  // Schur complement pivot
     }
     __syncthreads();
     const int dec = dec_s;
@@ -652,14 +686,36 @@ __global__ void __launch_bounds__(256) k_proposals(Chain<T>* chains, int gamma_i
       consumed = jj;
       break;
     }
+    if (tid == 64) {
+      // counters and the trace record, off the critical path
+      const bool accept = dec == 1;
+      cnt_prop[move]++;
+      if (accept) cnt_acc[move]++;
+      // algorithmic flops, both spins: y GEMV and the dot (first touch); on
+      // acceptance the z GEMV and the bordered update, or the rank-one update
+      const long long jl = j;
+      long long fl = (q < 0) ? (2 * jl * jl + 2 * jl) : 4;
+      if (accept) fl += (q < 0) ? 2 * jl * jl + 3 * (jl + 1) * (jl + 1) : 3 * jl * jl;
+      flops2 += fl;
+      if (trace_cap > 0) {
+        const bool forced = fin_s != 0;
+        TraceRec& rr = c.trace[(trace_base + jj) % trace_cap];
+        rr.t = t; rr.move = move; rr.n = nc;
+        rr.birth = birth[p]; rr.s_new = s_new; rr.accept = (accept ? 1 : 0) | (forced ? 2 : 0);
+        rr.ratio[0] = forced ? d.forced_ratio[0] : ratio_s[0];
+        rr.ratio[1] = forced ? d.forced_ratio[1] : ratio_s[1];
+        rr.R = R_s; rr.u = dr.u_acc;
+      }
+    }
     if (dec == 1) {
       const A sc = scal_s[half];
       if (q < 0) {
-        // z = w^T Gamma^{-1} (one column per thread), scaled by 1/beta, then the
-        // bordered inverse (Sec. III D): [[G + y z / beta, -y / beta], [-z / beta, 1 / beta]]
+        // z = w^T Gamma^{-1} (scaled by 1/beta), then the bordered inverse
+        // (Sec. III D): [[G + y z / beta, -y / beta], [-z / beta, 1 / beta]]
         if constexpr (sizeof(A) == 8) {
           const int quad = ht & 3;
           for (int c0 = 0; c0 < j; c0 += 32) {
+            if (c0 + (ht >> 2) - (lane >> 2) >= j) break;  // warp without columns (uniform)
             const int cc = c0 + (ht >> 2);
             A acc = (A)0;
             if (cc < j)
@@ -681,16 +737,23 @@ __global__ void __launch_bounds__(256) k_proposals(Chain<T>* chains, int gamma_i
           }
         }
         __syncthreads();
-        for (int e = ht; e < (j + 1) * (j + 1); e += 128) {
-          const int r = e / (j + 1), cc = e % (j + 1);
-          A v;
-          if (r < j && cc < j) v = (A)G[(size_t)r * LG + cc] + yv[r] * zv[cc];
-          else if (r < j) v = -yv[r] * sc;
-          else if (cc < j) v = -zv[cc];
-          else v = sc;
-          G[(size_t)r * LG + cc] = (T)v;
+        // (j+1) x (j+1) update: rows from ht / 16, columns from ht % 16 (no division)
+        const int j1 = j + 1;
+        for (int r = ht >> 4; r < j1; r += 8) {
+          const A yr = (r < j) ? yv[r] : (A)0;
+          for (int cc = ht & 15; cc < j1; cc += 16) {
+            A v;
+            if (r < j && cc < j) v = (A)G[(size_t)r * LG + cc] + yr * zv[cc];
+            else if (r < j) v = -yr * sc;
+            else if (cc < j) v = -zv[cc];
+            else v = sc;
+            G[(size_t)r * LG + cc] = (T)v;
+          }
         }
-        if (ht == 0) lam[j] = lamn_s[half];
+        if (ht == 0) {
+          lam[j] = lamn_s[half];
+          ilam[j] = iem1_s[spin][dk];
+        }
       } else if (!to_start) {
         // diagonal change delta of Gamma_qq: Sherman-Morrison on Gamma^{-1}
         for (int r = ht; r < j; r += 128) {
@@ -698,11 +761,13 @@ __global__ void __launch_bounds__(256) k_proposals(Chain<T>* chains, int gamma_i
           wv[r] = (A)G[(size_t)q * LG + r];
         }
         __syncthreads();
-        for (int e = ht; e < j * j; e += 128) {
-          const int r = e / j, cc = e % j;
-          G[(size_t)r * LG + cc] = (T)((A)G[(size_t)r * LG + cc] - sc * sv[r] * wv[cc]);
+        for (int r = ht >> 4; r < j; r += 8)
+          for (int cc = ht & 15; cc < j; cc += 16)
+            G[(size_t)r * LG + cc] = (T)((A)G[(size_t)r * LG + cc] - sc * sv[r] * wv[cc]);
+        if (ht == 0) {
+          lam[q] = lamn_s[half];
+          ilam[q] = iem1_s[spin][dk];
         }
-        if (ht == 0) lam[q] = lamn_s[half];
       } else {
         // back to the block-start spin: Schur complement removes q from P,
         // then the last entry of P moves into position q
@@ -711,10 +776,9 @@ __global__ void __launch_bounds__(256) k_proposals(Chain<T>* chains, int gamma_i
           wv[r] = (A)G[(size_t)q * LG + r];
         }
         __syncthreads();
-        for (int e = ht; e < j * j; e += 128) {
-          const int r = e / j, cc = e % j;
-          G[(size_t)r * LG + cc] = (T)((A)G[(size_t)r * LG + cc] - sv[r] * wv[cc] * sc);
-        }
+        for (int r = ht >> 4; r < j; r += 8)
+          for (int cc = ht & 15; cc < j; cc += 16)
+            G[(size_t)r * LG + cc] = (T)((A)G[(size_t)r * LG + cc] - sv[r] * wv[cc] * sc);
         __syncthreads();
         const int last = j - 1;
         if (q != last) {
@@ -726,6 +790,7 @@ __global__ void __launch_bounds__(256) k_proposals(Chain<T>* chains, int gamma_i
           if (ht == 0) {
             G[(size_t)q * LG + q] = G[(size_t)last * LG + last];
             lam[q] = lam[last];
+            ilam[q] = ilam[last];
           }
         }
       }
@@ -772,7 +837,7 @@ __global__ void __launch_bounds__(256) k_proposals(Chain<T>* chains, int gamma_i
     }
     d.numeric_rejects += numeric;
     d.near_ties += ties;
-    d.work_gamma += flops;
+    d.work_gamma += 2.0 * (double)flops2;
     if (c.trace_cap > 0) d.trace_written += consumed;
   }
 }
