@@ -390,8 +390,10 @@ constexpr double kTieGuard = 1e-4;
 // when it returns to its block-start spin (then ratio = -(Gamma^{-1})_qq / lambda).
 // Arithmetic in T (float64, or float32 in the mixed form, which counts near
 // ties of the accept decision).
-template <typename T>
-__global__ void __launch_bounds__(256) k_proposals(Chain<T>* chains, int gamma_in_smem) {
+template <typename T, bool GS>
+__global__ void __launch_bounds__(256) k_proposals(Chain<T>* chains) {
+  constexpr bool gamma_in_smem = GS;  // Gamma^{-1} in shared memory: known at compile time, so
+                                      // its accesses are shared-memory instructions
   using A = T;
   const Chain<T>& c = chains[blockIdx.x];
   Dyn& d = *c.dyn;
@@ -432,7 +434,9 @@ __global__ void __launch_bounds__(256) k_proposals(Chain<T>* chains, int gamma_i
   sp += sizeof(double) * 2 * KM;
   int8_t* s0_s = reinterpret_cast<int8_t*>(sp);     // block-start spins
 
-  T* G = gamma_in_smem ? (Gs + (size_t)spin * KM * LG) : c.Ginv[spin];
+  T* G;
+  if constexpr (GS) G = Gs + (size_t)spin * KM * LG;
+  else G = c.Ginv[spin];
   A* sv = vec + spin * 4 * KM;   // s (column of G^0 over P)
   A* wv = sv + KM;               // w (row of G^0 over P)
   A* yv = wv + KM;               // Gamma^{-1} s
@@ -1034,7 +1038,8 @@ void launch_block(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t st, Pha
   launch_gemm<T>(dchains, ls, PH_GCOL_NEW, st);
   pt->end(1, st, 3);
   pt->begin(2, st);
-  k_proposals<T><<<nch, 256, ls.prop_smem, st>>>(dchains, ls.gamma_in_smem);
+  if (ls.gamma_in_smem) k_proposals<T, true><<<nch, 256, ls.prop_smem, st>>>(dchains);
+  else k_proposals<T, false><<<nch, 256, ls.prop_smem, st>>>(dchains);
   pt->end(2, st, 1);
   bool tc = false;
   if constexpr (std::is_same<T, float>::value) tc = ls.use_tc != 0;
@@ -1061,7 +1066,10 @@ void launch_block(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t st, Pha
 
 template <typename T>
 cudaError_t configure_block_kernels(const LaunchShape& ls) {
-  return cudaFuncSetAttribute(k_proposals<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_proposals<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       ls.prop_smem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_proposals<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               ls.prop_smem);
 }
 
