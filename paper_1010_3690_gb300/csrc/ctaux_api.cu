@@ -138,6 +138,7 @@ ctaux_status build_chains(ctaux_ctx* ctx) {
   ls.meas_point_blocks = (max_pts + 255) / 256;
   ls.meas_lchunks = (max_ld + kMeasChunk - 1) / kMeasChunk;
   ls.meas_cb_blocks = (max_cls_bins + 255) / 256;
+  ls.meas_acc_blocks = (max_cls_bins + 7) / 8;
   ctx->max_ld = max_ld;
   // proposal kernel shared memory
   size_t fixed = ((sizeof(T) * 8 * max_k + 15) & ~size_t(15)) + sizeof(double) * 2 * max_k + sizeof(int) * max_k +

@@ -9,7 +9,11 @@ namespace ctaux {
 
 constexpr int kMaxPartials = 4096;  // split-K partial tiles per (chain, spin) and product
 constexpr int kTieSlices = 64;   // column slices of the near-tie matrix-vector products
-constexpr int kMeasChunk = 32;  // vertices per measurement evaluation chunk
+// vertices per measurement evaluation chunk: small orders get short chunks
+// (more work items for the GPU), large ones longer chunks (fewer partial sums)
+constexpr int kMeasChunk = 16;      // the shortest chunk (sizes the partial-sum buffers)
+constexpr int kMeasChunkMax = 32;
+__host__ __device__ inline int meas_chunk(int n) { return n <= 1024 ? kMeasChunk : kMeasChunkMax; }
 
 // tensor-core flush (mixed form): 128 x 128 output tiles, K chunks of 32 float32
 constexpr int kTcBM = 128, kTcBN = 128, kTcBK = 32, kTcStages = 3, kTcThreads = 384;
@@ -54,6 +58,7 @@ struct LaunchShape {
   int meas_point_blocks;
   int meas_lchunks;      // vertex chunks of the measurement evaluation
   int meas_cb_blocks;
+  int meas_acc_blocks;   // one warp per (class, bin) output
   int refresh_grid;
   int use_tc;            // mixed form: flush on the tensor cores
   int tc_tiles;          // bound on 128 x 128 flush tiles per (chain, spin)

@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(256) k_meas_gather(Chain<T>* chains) {
 }
 
 // Evaluation of the estimator, persistent over the (chain, spin, point block,
-// vertex chunk) items of all chains; partial sums over a chunk of kMeasChunk
+// vertex chunk) items of all chains; partial sums over a chunk of meas_chunk(n)
 // vertices go to Mpts[spin][chunk][(anchor * N_c + site) * B + bin].
 //
 // When the number of bins B is a multiple of the number of anchors A, every
@@ -57,16 +57,16 @@ __device__ __forceinline__ int meas_points(const Chain<T>& c) {
 template <typename T>
 __device__ __forceinline__ int meas_items(const Chain<T>& c, const Dyn& d) {
   if (d.status) return 0;
-  return 2 * ((meas_points(c) + 255) / 256) * max(1, (d.n + kMeasChunk - 1) / kMeasChunk);
+  return 2 * ((meas_points(c) + 255) / 256) * max(1, (d.n + meas_chunk(d.n) - 1) / meas_chunk(d.n));
 }
 
 // Per-chunk vertex data staged in shared memory by every CTA of an item:
 // tau_q, site_q and w_b(q) = (e^{V_q} - 1) v_b(q) for the anchors.
 template <typename A>
 struct MeasStage {
-  double tau[kMeasChunk];
-  int site[kMeasChunk];
-  A w[kMaxSharedAnchors][kMeasChunk];
+  double tau[kMeasChunkMax];
+  int site[kMeasChunkMax];
+  A w[kMaxSharedAnchors][kMeasChunkMax];
 };
 
 // Shared-anchor evaluation of one (site, tau_p) point over the staged chunk,
@@ -131,11 +131,12 @@ __global__ void __launch_bounds__(256) k_meas_eval(Chain<T>* chains, int n_chain
     const int n = d.n, buf = d.buf, A = c.n_anchors, B = c.n_bins;
     const int npts_out = A * c.n_c * B;
     const int npts = meas_points(c);
-    const int pblocks = (npts + 255) / 256, nchunks = max(1, (n + kMeasChunk - 1) / kMeasChunk);
+    const int chl = meas_chunk(n);
+    const int pblocks = (npts + 255) / 256, nchunks = max(1, (n + chl - 1) / chl);
     const int l = w - off[ci];
     const int spin = l / (pblocks * nchunks), r0 = l % (pblocks * nchunks);
     const int chunk = r0 / pblocks;
-    const int l0 = chunk * kMeasChunk, l1 = min(n, l0 + kMeasChunk);
+    const int l0 = chunk * chl, l1 = min(n, l0 + chl);
     const int nq = max(0, l1 - l0);
     const int pt = (r0 % pblocks) * blockDim.x + threadIdx.x;
     const bool shared = meas_shared(c);
@@ -200,35 +201,39 @@ __global__ void __launch_bounds__(256) k_meas_eval(Chain<T>* chains, int n_chain
   }
 }
 
-// Per (chain, spin, class, bin): fixed-order sum over vertex chunks, anchors
-// and sites.
+// Per (chain, spin, class, bin), one warp: the partial sums over vertex
+// chunks, anchors and the sites of the class are split over the lanes in a
+// fixed pattern and combined by a fixed shuffle tree (deterministic).
 template <typename T>
 __global__ void k_meas_accumulate(Chain<T>* chains) {
   const Chain<T>& c = chains[blockIdx.z];
   Dyn& d = *c.dyn;
   if (d.status) return;
-  const int spin = blockIdx.y, A = c.n_anchors, B = c.n_bins;
-  const int npts = A * c.n_c * B;
-  const int nchunks = max(1, (d.n + kMeasChunk - 1) / kMeasChunk);
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int spin = blockIdx.y, A = c.n_anchors, B = c.n_bins, nc = c.n_c;
+  const int npts = A * nc * B;
+  const int nchunks = max(1, (d.n + meas_chunk(d.n) - 1) / meas_chunk(d.n));
+  const int lane = threadIdx.x & 31;
+  const int e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);  // output of this warp
   if (e < c.n_classes * B) {
     const int cls = e / B, bin = e % B;
+    const double* Mp = c.Mpts[spin];
     double acc = 0.0;
-    for (int b = 0; b < A; ++b)
-      for (int xa = 0; xa < c.n_c; ++xa)
-        if (c.dx_class[xa * c.n_c] == cls) {
-          const int pt = (b * c.n_c + xa) * B + bin;
-          double v = 0.0;
-          for (int q = 0; q < nchunks; ++q) v += c.Mpts[spin][(size_t)q * npts + pt];
-          acc += v;
-        }
-    acc *= c.class_weight[cls];
-    const long o = ((long)spin * c.n_classes + cls) * B + bin;
-    c.Gmeas[o] = acc;
-    c.Gsum[o] += acc;
-    c.Gsq[o] += acc * acc;
+    const int terms = A * nc * nchunks;
+    for (int u = lane; u < terms; u += 32) {
+      const int q = u % nchunks, r = u / nchunks, xa = r % nc, b = r / nc;
+      if (c.dx_class[xa * nc] != cls) continue;
+      acc += Mp[(size_t)q * npts + (b * nc + xa) * B + bin];
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) {
+      acc *= c.class_weight[cls];
+      const long o = ((long)spin * c.n_classes + cls) * B + bin;
+      c.Gmeas[o] = acc;
+      c.Gsum[o] += acc;
+      c.Gsq[o] += acc * acc;
+    }
   }
-  if (e == 0 && spin == 0) {
+  if (blockIdx.x == 0 && threadIdx.x == 0 && spin == 0) {
     d.measurements += 1;
     d.order_sum += d.n;
     d.sign_sum += (double)d.sign;
@@ -262,7 +267,7 @@ void launch_measure(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t st, P
   k_meas_gather<T><<<dim3(ls.gather_slices, 2, nch), 256, 0, st>>>(dchains);
   launch_gemm<T>(dchains, ls, PH_MEAS, st);
   k_meas_eval<T><<<ls.persist_ctas, 256, 0, st>>>(dchains, nch);
-  k_meas_accumulate<T><<<dim3(ls.meas_cb_blocks, 2, nch), 256, 0, st>>>(dchains);
+  k_meas_accumulate<T><<<dim3(ls.meas_acc_blocks, 2, nch), 256, 0, st>>>(dchains);
   pt->end(5, st, 4);
 }
 
