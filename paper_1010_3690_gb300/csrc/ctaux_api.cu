@@ -95,7 +95,7 @@ ctaux_status build_chains(ctaux_ctx* ctx) {
   auto& hc = host_chains<T>(ctx);
   hc.resize(ctx->chains.size());
   cudaError_t err = cudaSuccess;
-  int max_ld = 0, max_k = 1, max_cls_bins = 1, max_pts = 1;
+  int max_ld = 0, max_k = 1, max_cls_bins = 1;
   // launch shape first (tile bounds and k splits from the capacities)
   const int items = 2 * (int)ctx->chains.size();
   for (size_t ci = 0; ci < ctx->chains.size(); ++ci) {
@@ -105,7 +105,6 @@ ctaux_status build_chains(ctaux_ctx* ctx) {
     max_ld = std::max(max_ld, ld);
     max_k = std::max(max_k, cp.k_max);
     max_cls_bins = std::max(max_cls_bins, cp.n_classes * P.n_tau_bins);
-    max_pts = std::max(max_pts, P.n_anchors * cp.n_c * P.n_tau_bins);
   }
   LaunchShape& ls = ctx->ls;
   ls.n_chains = (int)ctx->chains.size();
@@ -134,8 +133,6 @@ ctaux_status build_chains(ctaux_ctx* ctx) {
   }
   ls.persist_ctas = 8 * ctx->sm_count;   // 256-thread CTAs: up to 8 resident per SM
   ls.gather_slices = std::max(1, std::min(64, (2 * ctx->sm_count + items - 1) / items));
-  ls.y_blocks = (max_ld + 15) / 16;
-  ls.meas_point_blocks = (max_pts + 255) / 256;
   ls.meas_lchunks = (max_ld + kMeasChunk - 1) / kMeasChunk;
   ls.meas_cb_blocks = (max_cls_bins + 255) / 256;
   ls.meas_acc_blocks = (max_cls_bins + 7) / 8;
@@ -152,7 +149,6 @@ ctaux_status build_chains(ctaux_ctx* ctx) {
   ls.use_tc = mixed_tc ? 1 : 0;
   int max_rows = 128;
   for (const auto& cp : ctx->chains) max_rows = std::max(max_rows, round_up(cp.capacity + cp.k_max, 128));
-  ls.tc_tiles = (max_rows / 128) * (max_rows / 128);
   ls.tc_ctas = ctx->sm_count;
   ls.split_x_blocks = std::max(1, std::min(256, (max_rows + 7) / 8));
   if (mixed_tc) CUDA_TRY(ctx, configure_flush_tc());

@@ -52,16 +52,13 @@ struct LaunchShape {
   int tie_grid;          // cooperative grid of the near-tie refinement
   int tie_iters;         // most refinement iterations (0: every near tie takes the fallback)
   int refresh_df64;      // float32 form: refresh elimination in double-float
-  int y_blocks;
   int prop_smem;
   int gamma_in_smem;
-  int meas_point_blocks;
   int meas_lchunks;      // vertex chunks of the measurement evaluation
   int meas_cb_blocks;
   int meas_acc_blocks;   // one warp per (class, bin) output
   int refresh_grid;
   int use_tc;            // mixed form: flush on the tensor cores
-  int tc_tiles;          // bound on 128 x 128 flush tiles per (chain, spin)
   int tc_ctas;           // persistent grid of the tensor-core flush (one CTA per SM)
   int split_x_blocks;
 };

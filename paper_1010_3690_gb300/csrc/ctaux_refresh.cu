@@ -30,9 +30,9 @@ cudaError_t launch_refresh(Chain<T>* dchains, const LaunchShape& ls, int only_ch
   void* args[] = {&dchains, &nch, &only_chain, &filter};
   // double-float elimination only for the float32 form's own refreshes; the
   // near-tie fallback (filter 1) keeps float64, whose N it also stores
-  const void* fn = (std::is_same<T, float>::value && ls.refresh_df64 && filter == 0)
-                       ? (const void*)k_refresh<T, df64>
-                       : (const void*)k_refresh<T, double>;
+  const void* fn = (const void*)k_refresh<T, double>;
+  if constexpr (std::is_same<T, float>::value)
+    if (ls.refresh_df64 && filter == 0) fn = (const void*)k_refresh<T, df64>;
   e = cudaLaunchCooperativeKernel(fn, dim3(ls.refresh_grid), dim3(256), args, 0, st);
   if (e == cudaSuccess) {
     if (only_chain >= 0)
@@ -48,10 +48,14 @@ cudaError_t launch_refresh(Chain<T>* dchains, const LaunchShape& ls, int only_ch
 template <typename T>
 int refresh_blocks_per_sm() {
   // the grid must be co-resident for either element type
-  int nb = 0, nb2 = 0;
+  int nb = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_refresh<T, double>, 256, 0);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb2, k_refresh<T, df64>, 256, 0);
-  return nb < nb2 ? nb : nb2;
+  if constexpr (std::is_same<T, float>::value) {
+    int nb2 = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb2, k_refresh<T, df64>, 256, 0);
+    nb = nb < nb2 ? nb : nb2;
+  }
+  return nb;
 }
 
 template cudaError_t launch_refresh<double>(Chain<double>*, const LaunchShape&, int, cudaStream_t,
