@@ -24,7 +24,6 @@ struct ctaux_ctx {
   LaunchShape ls{};
   void* chains_dev = nullptr;        // Chain<double>[] or Chain<float>[]
   TcMaps* tc_maps_dev = nullptr;     // mixed form: TMA descriptors [chain][spin]
-  double* tie_part = nullptr;        // mixed form: per-CTA partials of the tie refinement
   std::vector<Chain<double>> hc64;   // host copies of the descriptors
   std::vector<Chain<float>> hc32;
   std::vector<void*> allocations;
@@ -157,7 +156,6 @@ ctaux_status build_chains(ctaux_ctx* ctx) {
     // barrier latency (which grows with the number of CTAs) dominates
     ls.tie_grid = ctx->sm_count;
     ls.tie_iters = P.tie_refine_iters == 0 ? 12 : std::max(0, P.tie_refine_iters);
-    ctx->tie_part = dalloc<double>(ctx, 4 * (size_t)ls.tie_grid + (size_t)2 * kTieSlices * max_ld, &err);
   }
   std::vector<TcMaps> host_maps(mixed_tc ? 2 * ctx->chains.size() : 0);
   ls.refresh_df64 = (sizeof(T) == 4 && P.refresh_df64) ? 1 : 0;
@@ -338,7 +336,7 @@ ctaux_status do_sweeps(ctaux_ctx* ctx, int n_sweeps, int measure, cudaStream_t s
     launch_block<T>(dc, ctx->ls, s, p, ctx->tc_maps_dev);
     if (!ties) return cudaSuccess;
     p->begin(7, s);
-    cudaError_t e = launch_tie_refine(reinterpret_cast<Chain<float>*>(dc), ctx->ls, ctx->tie_part, s);
+    cudaError_t e = launch_tie_refine(reinterpret_cast<Chain<float>*>(dc), ctx->ls, s);
     p->end(7, s, 1);
     return e;
   };

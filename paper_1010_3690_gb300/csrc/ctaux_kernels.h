@@ -125,9 +125,8 @@ void launch_measure(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t st, P
 template <typename T>
 cudaError_t launch_refresh(Chain<T>* dchains, const LaunchShape& ls, int only_chain,
                            cudaStream_t st, PhaseTimer* pt, int filter = 0);
-// part: 4*tie_grid + 2*kTieSlices*max_ld doubles of device scratch
-cudaError_t launch_tie_refine(Chain<float>* dchains, const LaunchShape& ls, double* part,
-                              cudaStream_t st);
+// scratch: each chain's refresh work area (both spins)
+cudaError_t launch_tie_refine(Chain<float>* dchains, const LaunchShape& ls, cudaStream_t st);
 template <typename T>
 void launch_reset_measure(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t st);
 int tc_smem_bytes();
