@@ -39,7 +39,7 @@ UNIT = "accepted updates/s"
 N_TAU_BINS, N_ANCHORS, REFRESH_EVERY = 32, 4, 32
 
 
-def workload(name, K, k_max, chain_id=0):
+def workload(name, K, k_max, chain_id=0, n_chains=8):
     from workloads import configs
     if name == "cube8":
         ch = configs.cube8(K=K, k_max=k_max, capacity=1024, seed=chain_id)
@@ -53,7 +53,7 @@ def workload(name, K, k_max, chain_id=0):
         # 8 independent chains; K-matched (K=5700: <n> ~ 7000) chains start from a
         # seeded configuration of that order instead of growing from n=0
         chs = [configs.cube100(K=K, k_max=k_max, capacity=9216, seed=8 * chain_id + i,
-                               chain_id=8 * chain_id + i) for i in range(8)]
+                               chain_id=8 * chain_id + i) for i in range(n_chains)]
         n_t = 7000 if K >= 4000 else 1400
         return chs, dict(n_target=n_t, start_order=n_t if K >= 4000 else 0)
     if name == "aim1":
@@ -216,6 +216,8 @@ def main():
     ap.add_argument("--workload", default="cube8")
     ap.add_argument("--K", type=float, default=256.0)
     ap.add_argument("--k-max", dest="k_max", type=int, default=64)
+    ap.add_argument("--chains", type=int, default=8,
+                    help="chains of the cube100 workload (a smaller case for profiling)")
     ap.add_argument("--thermalize", type=int, default=300)
     ap.add_argument("--refresh-every", dest="refresh_every", type=int, default=REFRESH_EVERY)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -246,7 +248,7 @@ def main():
         if rank == 0:
             run_k_sweep(args, pk, torch, local)
         return
-    chains, meta = workload(args.workload, args.K, args.k_max, chain_id=rank)
+    chains, meta = workload(args.workload, args.K, args.k_max, chain_id=rank, n_chains=args.chains)
     forms = ["fp64", "mixed", "mixed_df64"] if args.precision == "both" else [args.precision]
     results = {}
     for form in forms:

@@ -243,7 +243,8 @@ ctaux_status build_chains(ctaux_ctx* ctx) {
         if (err != cudaSuccess)
           return set_err(ctx, CTAUX_ENOMEM, "device allocation failed: %s", cudaGetErrorString(err));
         cudaError_t me = encode_tc_maps(&host_maps[2 * ci + spin], c.Yh[spin], c.Yl[spin], c.Xh[spin],
-                                        c.Xl[spin], rows, c.kp);
+                                        c.Xl[spin], rows, c.kp, reinterpret_cast<float*>(c.N[0][spin]),
+                                        reinterpret_cast<float*>(c.N[1][spin]), c.ld);
         if (me != cudaSuccess)
           return set_err(ctx, CTAUX_ECUDA, "tensor map encoding failed (%s)", cudaGetErrorString(me));
       }

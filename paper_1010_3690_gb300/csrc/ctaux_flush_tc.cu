@@ -12,18 +12,24 @@
 //
 // One persistent CTA per SM, warp-specialised, over the (chain, spin,
 // 128 x 128 tile) items of all chains:
-//   warp 0 (one thread): TMA producer into a ring of kTcStages 64 KB stages;
-//   warp 1 (one thread): MMA issuer, 12 tcgen05.mma per 32-wide K step into
+//   warp 0 (one thread): TMA producer into a ring of kTcStages 32 KB stages;
+//   warp 1 (one thread): MMA issuer, 6 tcgen05.mma per 16-wide K step into
 //     one of two 128-column TMEM accumulators, each stage released to the
 //     producer by tcgen05.commit when its MMAs are done;
+//   warp 3: loader of the epilogue input N[S_m][S_n]: the survivor rows
+//     S[m0] .. S[m0 + 127] of a tile are contiguous up to the few removed
+//     rows, so each of its 128 columns S[n] is a segment of kTcNsRows rows
+//     starting at S[m0] rounded down to 16 bytes, loaded by TMA in boxes of
+//     kTcNsGroup adjacent columns (a tile whose rows span more falls back to
+//     gathered global loads);
 //   warps 4-11: epilogue; warp w reads TMEM lane quarter w % 4 (64 of the 128
-//     columns), adds the gathered N[S_m][S_n] and writes the compacted N',
-//     then releases the accumulator, so that the epilogue of one tile overlaps
-//     the loads and MMAs of the next.
+//     columns), subtracts from the staged N[S_m][S_n] and writes the compacted
+//     N', then releases the accumulator and the staged input, so that the
+//     epilogue of one tile overlaps the loads and MMAs of the next.
 // Every mbarrier wait is bounded.  On timeout the chain's status gets
-// DS_TIMEOUT and every role stops; before the CTA exits, the producer waits
-// (bounded) for the copies it issued, the MMA thread for its MMAs, and the
-// TMEM is freed.
+// DS_TIMEOUT and every role stops; before the CTA exits, the copies issued
+// are waited for (bounded), the MMA thread waits for its MMAs, and the TMEM
+// is freed.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -34,8 +40,14 @@ namespace ctaux {
 
 namespace {
 
-constexpr int kTileBytes = kTcBM * kTcBK * 4;   // one 128 x 32 float32 operand tile
+constexpr int kRowBytes = kTcBK * 4;            // one K-major operand row
+constexpr int kTileBytes = kTcBM * kRowBytes;   // one 128 x 16 float32 operand tile
+static_assert(kRowBytes == 64 || kRowBytes == 128, "operand rows are one swizzle span");
 constexpr int kStageBytes = 4 * kTileBytes;     // Ah, Al, Bh, Bl
+constexpr int kNsSlotBytes = kTcNsRows * 4;     // one staged column segment
+constexpr int kNsBytes = kTcBN * kNsSlotBytes;  // the staged input of one tile
+static_assert(kNsSlotBytes % 128 == 0, "staged column segments must stay 128-byte aligned");
+static_assert(kTcBN % kTcNsGroup == 0 && kTcBN / kTcNsGroup <= 32, "one column group per lane");
 constexpr uint32_t kWaitLimit = 1u << 24;
 constexpr uint32_t kTmemCols = 2 * kTcBN;       // two accumulators
 
@@ -75,15 +87,15 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, rows of 128 B,
-// 8-row groups 1024 B apart.
+// Shared-memory matrix descriptor: K-major, rows of kRowBytes swizzled over
+// their own width (64- or 128-byte swizzle), 8-row groups 8 rows apart.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);   // start address
   d |= (uint64_t)(16u >> 4) << 16;            // leading byte offset (unused for this layout)
-  d |= (uint64_t)(1024u >> 4) << 32;          // stride byte offset
+  d |= (uint64_t)((8u * kRowBytes) >> 4) << 32;  // stride byte offset
   d |= (uint64_t)1 << 46;                     // descriptor version
-  d |= (uint64_t)2 << 61;                     // 128-byte swizzle
+  d |= (uint64_t)(kRowBytes == 128 ? 2 : 4) << 61;  // 128- or 64-byte swizzle
   return d;
 }
 
@@ -173,10 +185,21 @@ __device__ __forceinline__ TcItem tc_item(Chain<float>* chains, const int* off, 
   const int l = w - off[it.ci];
   it.spin = l / (tiles * tiles);
   const int tile = l % (tiles * tiles);
-  it.m0 = (tile / tiles) * kTcBM;
-  it.n0 = (tile % tiles) * kTcBN;
+  // consecutive items (processed at the same time by consecutive CTAs) share
+  // the column band and walk down the rows: their reads and writes of N are
+  // spread over the whole columns, not stacked at one row offset of many
+  // columns (which maps them onto few DRAM channels)
+  it.m0 = (tile % tiles) * kTcBM;
+  it.n0 = (tile / tiles) * kTcBN;
   it.nk = (d.k_acc + kTcBK - 1) / kTcBK;
   return it;
+}
+
+// Staged-input geometry of a tile: source row of its first row rounded down
+// to 16 bytes, and whether its rows fit one kTcNsRows segment.
+__device__ __forceinline__ bool ns_staged(const int* S, int m0, int nn, int& x0) {
+  x0 = __ldg(S + m0) & ~3;
+  return __ldg(S + min(m0 + kTcBM - 1, nn - 1)) - x0 < kTcNsRows;
 }
 
 // Barrier completion c (0-based) of an mbarrier has parity c & 1.
@@ -193,14 +216,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_flush_tc(Chain<float>* chains
   extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
       ((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* full = reinterpret_cast<uint64_t*>(base + kTcStages * kStageBytes);
+  float* ns = reinterpret_cast<float*>(base + kTcStages * kStageBytes);
+  uint64_t* full = reinterpret_cast<uint64_t*>(base + kTcStages * kStageBytes + kNsBytes);
   uint64_t* empty = full + kTcStages;
   uint64_t* accfull = empty + kTcStages;
   uint64_t* accempty = accfull + 2;
   uint64_t* drain = accempty + 2;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  uint64_t* nsfull = drain + 1;
+  uint64_t* nsempty = nsfull + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(nsempty + 1);
   volatile int* err_s = reinterpret_cast<volatile int*>(tmem_slot + 1);
   uint32_t* mma_taken = reinterpret_cast<uint32_t*>(tmem_slot + 2);  // stages the MMA thread waited for
+  uint32_t* ns_issued = reinterpret_cast<uint32_t*>(tmem_slot + 3);  // tiles the loader staged
 
   if (warp == 2) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -219,8 +246,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_flush_tc(Chain<float>* chains
       mbar_init(smem_u32(accempty + b), 8);  // one arrival per epilogue warp
     }
     mbar_init(smem_u32(drain), 1);
+    mbar_init(smem_u32(nsfull), 1);
+    mbar_init(smem_u32(nsempty), 8);
     *err_s = 0;
     *mma_taken = 0;
+    *ns_issued = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -295,10 +325,55 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_flush_tc(Chain<float>* chains
     // every MMA issued so far has completed before the TMEM can be freed
     mma_commit(smem_u32(drain));
     mbar_wait(smem_u32(drain), 0);
+  } else if (warp == 3) {
+    // ---- loader of the epilogue input, one tile ahead of the epilogue.  The
+    // 128 columns go in groups of kTcNsGroup: a group of adjacent source
+    // columns (no removed column inside) is one TMA box, any other group one
+    // box per column.  Indices are read before the buffer is free.
+    uint32_t nq = 0;
+    for (int w = blockIdx.x; w < total; w += gridDim.x) {
+      if (__any_sync(0xffffffffu, *err_s != 0)) break;
+      const TcItem t = tc_item(chains, off, n_chains, w);
+      const Chain<float>& c = chains[t.ci];
+      int x0;
+      const bool staged = ns_staged(c.S, t.m0, t.nn, x0);
+      const int cols = staged ? min(kTcBN, t.nn - t.n0) : 0;
+      const int g0 = lane * kTcNsGroup;  // lanes 0-15: one group each
+      int s_first = 0;
+      bool whole = false;
+      if (g0 < cols) {
+        s_first = __ldg(c.S + t.n0 + g0);
+        whole = g0 + kTcNsGroup <= cols &&
+                __ldg(c.S + t.n0 + g0 + kTcNsGroup - 1) - s_first == kTcNsGroup - 1;
+      }
+      const TcMaps& mp = maps[t.ci * 2 + t.spin];
+      const int buf = c.dyn->buf;
+      if (nq > 0 && !__all_sync(0xffffffffu, mbar_wait(smem_u32(nsempty), (nq - 1) & 1))) {
+        if (lane == 0) {
+          *err_s = 1;
+          atomicOr(&c.dyn->status, DS_TIMEOUT);
+        }
+        break;
+      }
+      if (lane == 0) mbar_expect_tx(smem_u32(nsfull), (uint32_t)(cols * kNsSlotBytes));
+      __syncwarp();
+      if (g0 < cols) {
+        const uint32_t dst = smem_u32(ns) + g0 * kNsSlotBytes;
+        if (whole) {
+          tma_load_2d(dst, &mp.nbg[buf], x0, s_first, smem_u32(nsfull));
+        } else {
+          for (int j = g0; j < min(g0 + kTcNsGroup, cols); ++j)
+            tma_load_2d(smem_u32(ns) + j * kNsSlotBytes, &mp.nb1[buf], x0, __ldg(c.S + t.n0 + j),
+                        smem_u32(nsfull));
+        }
+      }
+      ++nq;
+    }
+    if (lane == 0) *ns_issued = nq;
   } else if (warp >= 4) {
     // ---- epilogue: warp w, TMEM lanes 32 (w % 4) .. + 31, column half (w - 4) / 4
     const int quarter = warp & 3, colhalf = (warp - 4) >> 2;
-    uint32_t q = 0;
+    uint32_t q = 0, nq = 0;
     for (int w = blockIdx.x; w < total; w += gridDim.x) {
       if (__any_sync(0xffffffffu, *err_s != 0)) break;
       const TcItem t = tc_item(chains, off, n_chains, w);
@@ -310,13 +385,28 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_flush_tc(Chain<float>* chains
       const int* S = c.S;
       const int m = t.m0 + quarter * 32 + lane;
       const bool row_ok = m < nn;
-      const long srow = row_ok ? S[m] : 0;
+      int x0;
+      const bool staged = ns_staged(S, t.m0, nn, x0);
+      const int srow = row_ok ? __ldg(S + m) : x0;  // rows past the end read a valid slot
+      const float* nsrow = ns + (srow - x0);  // staged N[srow][S[n0 + j]] at nsrow[j * kTcNsRows]
+      if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(nsfull), nq & 1))) {
+        if (lane == 0) {
+          *err_s = 1;
+          atomicOr(&c.dyn->status, DS_TIMEOUT);
+        }
+        break;
+      }
+      ++nq;
       if (t.nk == 0) {  // no accepted change: the flush is a pure compaction
         if (row_ok)
           for (int j = colhalf * 64; j < colhalf * 64 + 64; ++j) {
             const int n = t.n0 + j;
-            if (n < nn) out[(long)n * ld + m] = Nb[(long)__ldg(S + n) * ld + srow];
+            if (n < nn)
+              out[(long)n * ld + m] =
+                  staged ? nsrow[j * kTcNsRows] : Nb[(long)__ldg(S + n) * ld + srow];
           }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(nsempty));
         continue;
       }
       const uint32_t b = q & 1, ub = q >> 1;
@@ -332,11 +422,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_flush_tc(Chain<float>* chains
       float v[32], cin[32];
 #pragma unroll 1
       for (int cc = colhalf * 2; cc < colhalf * 2 + 2; ++cc) {
-        // the 32 gathered inputs of this chunk: independent loads, issued first
+        if (staged) {
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int n = t.n0 + cc * 32 + j;
-          cin[j] = (row_ok && n < nn) ? Nb[(long)__ldg(S + n) * ld + srow] : 0.f;
+          for (int j = 0; j < 32; ++j) cin[j] = nsrow[(cc * 32 + j) * kTcNsRows];
+        } else {
+          // rows spanning more than one segment: gathered global loads
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int n = t.n0 + cc * 32 + j;
+            cin[j] = (row_ok && n < nn) ? Nb[(long)__ldg(S + n) * ld + srow] : 0.f;
+          }
         }
         tmem_ld32(tmem + b * kTcBN + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(cc * 32), v);
         if (row_ok) {
@@ -349,7 +444,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_flush_tc(Chain<float>* chains
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(accempty + b));
+      if (lane == 0) {
+        mbar_arrive(smem_u32(accempty + b));
+        mbar_arrive(smem_u32(nsempty));
+      }
       ++q;
     }
   }
@@ -358,6 +456,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_flush_tc(Chain<float>* chains
     // copies issued but never waited for (only after a timeout): let them land
     for (uint32_t i = *mma_taken; i < issued; ++i)
       mbar_wait(smem_u32(full + i % kTcStages), (i / kTcStages) & 1);
+    if (*ns_issued > 0) mbar_wait(smem_u32(nsfull), (*ns_issued - 1) & 1);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -368,7 +467,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_flush_tc(Chain<float>* chains
                  : "memory");
 }
 
-int tc_smem_bytes() { return kTcStages * kStageBytes + 1024 + 256; }
+int tc_smem_bytes() { return kTcStages * kStageBytes + kNsBytes + 1024 + 256; }
 
 cudaError_t configure_flush_tc() {
   return cudaFuncSetAttribute(k_flush_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -381,10 +480,12 @@ void launch_flush_tc(Chain<float>* dchains, const TcMaps* maps, const LaunchShap
   k_flush_tc<<<ls.tc_ctas, kTcThreads, tc_smem_bytes(), st>>>(dchains, ls.n_chains, maps);
 }
 
-// Host: the four TMA descriptors of one (chain, spin): K-major float32 buffers of
-// rows x kp, boxes of 128 rows x 32 float32 (128 bytes), 128-byte swizzle.
+// Host: the TMA descriptors of one (chain, spin): K-major float32 operand
+// buffers of rows x kp, boxes of 128 rows x kTcBK float32 swizzled over the
+// row width; and both buffers of N (ld x ld, column-major), boxes of one or
+// kTcNsGroup column segments of kTcNsRows rows, no swizzle.
 cudaError_t encode_tc_maps(TcMaps* out, float* yh, float* yl, float* xh, float* xl, int rows,
-                           int kp) {
+                           int kp, float* n0, float* n1, int ld) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
     cudaDriverEntryPointQueryResult q;
@@ -394,18 +495,36 @@ cudaError_t encode_tc_maps(TcMaps* out, float* yh, float* yl, float* xh, float* 
     if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
     encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   }
-  const cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
-  const cuuint64_t strides[1] = {(cuuint64_t)kp * sizeof(float)};
-  const cuuint32_t box[2] = {(cuuint32_t)kTcBK, (cuuint32_t)kTcBM};
   const cuuint32_t estr[2] = {1, 1};
-  float* ptrs[4] = {yh, yl, xh, xl};
-  CUtensorMap* maps[4] = {&out->yh, &out->yl, &out->xh, &out->xl};
-  for (int i = 0; i < 4; ++i) {
-    const CUresult r = encode(maps[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, ptrs[i], dims, strides,
-                              box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  {
+    const cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)kp * sizeof(float)};
+    const cuuint32_t box[2] = {(cuuint32_t)kTcBK, (cuuint32_t)kTcBM};
+    float* ptrs[4] = {yh, yl, xh, xl};
+    CUtensorMap* maps[4] = {&out->yh, &out->yl, &out->xh, &out->xl};
+    for (int i = 0; i < 4; ++i) {
+      const CUresult r = encode(maps[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, ptrs[i], dims, strides,
+                                box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                kRowBytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                                CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    }
+  }
+  {
+    const cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)ld};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(float)};
+    float* ptrs[2] = {n0, n1};
+    for (int g = 0; g < 2; ++g) {
+      const cuuint32_t box[2] = {(cuuint32_t)kTcNsRows, g ? (cuuint32_t)kTcNsGroup : 1u};
+      for (int i = 0; i < 2; ++i) {
+        const CUresult r = encode(g ? &out->nbg[i] : &out->nb1[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                                  ptrs[i], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+      }
+    }
   }
   return cudaSuccess;
 }

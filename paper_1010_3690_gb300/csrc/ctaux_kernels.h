@@ -15,12 +15,19 @@ constexpr int kMeasChunk = 16;      // the shortest chunk (sizes the partial-sum
 constexpr int kMeasChunkMax = 32;
 __host__ __device__ inline int meas_chunk(int n) { return n <= 1024 ? kMeasChunk : kMeasChunkMax; }
 
-// tensor-core flush (mixed form): 128 x 128 output tiles, K chunks of 32 float32
-constexpr int kTcBM = 128, kTcBN = 128, kTcBK = 32, kTcStages = 3, kTcThreads = 384;
+// tensor-core flush (mixed form): 128 x 128 output tiles, K chunks of 16 float32;
+// the gathered N[S_m][S_n] input of a tile is staged as 128 column segments of
+// kTcNsRows source rows
+constexpr int kTcBM = 128, kTcBN = 128, kTcBK = 16, kTcStages = 4, kTcThreads = 384;
+constexpr int kTcNsRows = 160;
 
-// TMA descriptors of one (chain, spin): split Y (rows a) and split X (rows b)
+// TMA descriptors of one (chain, spin): split Y (rows a), split X (rows b) and
+// both buffers of N, as column segments of kTcNsRows rows, one column (nb1)
+// or kTcNsGroup adjacent columns (nbg) per box
+constexpr int kTcNsGroup = 8;
 struct TcMaps {
   CUtensorMap yh, yl, xh, xl;
+  CUtensorMap nb1[2], nbg[2];
 };
 
 enum { PH_RTILDE = 0, PH_GCOL_OLD = 1, PH_GCOL_NEW = 2, PH_FLUSH = 3, PH_MEAS = 4, PH_COUNT = 5 };
@@ -134,7 +141,7 @@ cudaError_t configure_flush_tc();
 void launch_flush_tc(Chain<float>* dchains, const TcMaps* maps, const LaunchShape& ls,
                      cudaStream_t st);
 cudaError_t encode_tc_maps(TcMaps* out, float* yh, float* yl, float* xh, float* xl, int rows,
-                           int kp);
+                           int kp, float* n0, float* n1, int ld);
 void launch_philox_test(uint64_t seed, uint32_t chain, int64_t t0, int count, int purpose,
                         double* out, cudaStream_t st);
 
