@@ -186,9 +186,7 @@ __device__ __forceinline__ TcItem tc_item(Chain<float>* chains, const int* off, 
   it.spin = l / (tiles * tiles);
   const int tile = l % (tiles * tiles);
   // consecutive items (processed at the same time by consecutive CTAs) share
-  // the column band and walk down the rows: their reads and writes of N are
-  // spread over the whole columns, not stacked at one row offset of many
-  // columns (which maps them onto few DRAM channels)
+  // the column band, i.e. the X operand tile, and walk down the rows
   it.m0 = (tile % tiles) * kTcBM;
   it.n0 = (tile / tiles) * kTcBN;
   it.nk = (d.k_acc + kTcBK - 1) / kTcBK;
