@@ -37,6 +37,11 @@ if ROOT not in sys.path:
 METRIC = "CT-AUX accepted updates/s per GPU, mixed vs FP64 at |dN|<1e-8; flush %peak"
 UNIT = "accepted updates/s"
 N_TAU_BINS, N_ANCHORS, REFRESH_EVERY = 32, 4, 32
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# dominant kernel, from one ncu capture of the same workload in the state the
+# timed blocks run in (summaries under profiles/); an entry is removed when its
+# kernel changes
+DRAM_TRAFFIC = {("cube8", "fp64", "proposals"): 358144}
 
 
 def workload(name, K, k_max, chain_id=0, n_chains=8):
@@ -469,7 +474,8 @@ def measure_form(args, pk, torch, dist, chains, meta, form, local, world, with_e
     roofline = {"kernel": names[dom], "bound": r["bound"], "achieved": r["achieved"],
                 "peak": r["peak"], "unit": r["unit"],
                 "frac": r["achieved"] / r["peak"] if r["peak"] else None,
-                "traffic": None, "peak_source": r["peak_source"],
+                "traffic": DRAM_TRAFFIC.get((args.workload, form, names[dom])),
+                "peak_source": r["peak_source"],
                 "ms_per_step": phase_ms[dom] / prof_steps}
     fr = roof(names.index("flush_gemm"))
     flush_roof = {"bound": fr["bound"], "achieved": fr["achieved"], "peak": fr["peak"],
