@@ -391,7 +391,7 @@ constexpr double kTieGuard = 1e-4;
 // Arithmetic in T (float64, or float32 in the mixed form, which counts near
 // ties of the accept decision).
 template <typename T, bool GS>
-__global__ void __launch_bounds__(256) k_proposals(Chain<T>* chains) {
+__device__ __forceinline__ void proposals_body(Chain<T>* chains) {
   constexpr bool gamma_in_smem = GS;  // Gamma^{-1} in shared memory: known at compile time, so
                                       // its accesses are shared-memory instructions
   using A = T;
@@ -850,6 +850,19 @@ __global__ void __launch_bounds__(256) k_proposals(Chain<T>* chains) {
 // Survivor list S (slots with s != 0 after the block, in slot order) and the
 // compacted configuration in the other buffer (Sec. IV C: s=0 rows and
 // columns are deleted).
+
+template <typename T, bool GS>
+__global__ void __launch_bounds__(256) k_proposals(Chain<T>* chains) {
+  proposals_body<T, GS>(chains);
+}
+
+// The float32 chain with Gamma^{-1} in shared memory (whose size already
+// limits the CTAs per SM) runs faster with its registers unrationed.
+template <typename T>
+__global__ void __launch_bounds__(256, 1) k_proposals_smem(Chain<T>* chains) {
+  proposals_body<T, true>(chains);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(1024) k_survivors(Chain<T>* chains) {
   const Chain<T>& c = chains[blockIdx.x];
@@ -1038,7 +1051,8 @@ void launch_block(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t st, Pha
   launch_gemm<T>(dchains, ls, PH_GCOL_NEW, st);
   pt->end(1, st, 3);
   pt->begin(2, st);
-  if (ls.gamma_in_smem) k_proposals<T, true><<<nch, 256, ls.prop_smem, st>>>(dchains);
+  if (ls.gamma_in_smem && sizeof(T) == 4) k_proposals_smem<T><<<nch, 256, ls.prop_smem, st>>>(dchains);
+  else if (ls.gamma_in_smem) k_proposals<T, true><<<nch, 256, ls.prop_smem, st>>>(dchains);
   else k_proposals<T, false><<<nch, 256, ls.prop_smem, st>>>(dchains);
   pt->end(2, st, 1);
   bool tc = false;
@@ -1068,6 +1082,9 @@ template <typename T>
 cudaError_t configure_block_kernels(const LaunchShape& ls) {
   cudaError_t e = cudaFuncSetAttribute(k_proposals<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        ls.prop_smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_proposals_smem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           ls.prop_smem);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_proposals<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               ls.prop_smem);

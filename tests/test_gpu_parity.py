@@ -392,6 +392,57 @@ def test_mixed_near_tie_fallback_refresh_decides_in_fp64():
     assert n_fp64 >= 5 and st["tie_refreshes"] >= n_fp64
 
 
+@pytest.mark.parametrize("iters", [0, -1])
+def test_mixed_near_ties_of_many_chains_refined_together(iters):
+    """Several chains stop at near ties in the same blocks and are refined (or,
+    with iters=-1, refreshed) in one launch: each chain's trace is bit-identical
+    to the same chain run alone, and its accept sequence equals the FP64
+    oracle's."""
+    chs, cfgs = [], []
+    for i in range(3):
+        ch = configs.cube8(K=1.0, k_max=32, capacity=256, seed=10 + i)
+        ch.chain_id = i
+        chs.append(ch)
+        cfgs.append(configs.synthetic_configuration(ch, 120 + 10 * i, seed=3 + i))
+    n_sw = 12
+
+    def run(idx):
+        with pk.Context([chs[i] for i in idx], precision=pk.CTAUX_MIXED, trace_capacity=4096,
+                        refresh_every=8, tie_guard=0.5, tie_refine_iters=iters) as ctx:
+            for j, i in enumerate(idx):
+                c = cfgs[i]
+                ctx.set_config(j, c["tau"], c["site"], c["s"], c["birth"], c["t"])
+            ctx.sweep(n_sw)
+            ctx.synchronize()
+            return [(ctx.trace(j), ctx.stats(j)) for j in range(len(idx))]
+
+    together = run([0, 1, 2])
+    for i in range(3):
+        (tr, st), = run([i])
+        tt, stt = together[i]
+        np.testing.assert_array_equal(tr["accept"], tt["accept"])
+        np.testing.assert_array_equal(tr["ratio"], tt["ratio"])
+        assert st["near_ties"] == stt["near_ties"] and st["tie_refreshes"] == stt["tie_refreshes"]
+        oc = oracle_for(chs[i])
+        c = cfgs[i]
+        oc.set_config(c["tau"], c["site"], c["s"], c["birth"], c["t"])
+        recs = oc.run(len(tt))
+        n_fp64 = 0
+        for g, o in zip(tt, recs):
+            assert int(g["t"]) == o["t"] and int(g["move"]) == o["move"]
+            assert bool(int(g["accept"]) & 1) == o["accept"], (i, g, o)
+            if int(g["accept"]) & 2 and o["birth"] >= 0:
+                n_fp64 += 1
+                for s in (0, 1):
+                    ref = o["ratio"][s]
+                    assert abs(g["ratio"][s] - ref) <= 1e-9 * max(1.0, abs(ref)), (i, g, o)
+        assert n_fp64 >= 3
+        if iters < 0:
+            assert stt["tie_refreshes"] >= n_fp64
+        else:
+            assert stt["tie_refreshes"] == 0
+
+
 def test_set_kmax_between_sweeps_keeps_the_markov_chain():
     """k_max changed at run time (within the allocation): same proposals, decisions and
     ratios as the oracle, since every draw is keyed by the proposal counter."""
