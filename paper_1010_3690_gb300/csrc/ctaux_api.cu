@@ -159,8 +159,18 @@ ctaux_status build_chains(ctaux_ctx* ctx) {
   }
   std::vector<TcMaps> host_maps(mixed_tc ? 2 * ctx->chains.size() : 0);
   ls.refresh_df64 = (sizeof(T) == 4 && P.refresh_df64) ? 1 : 0;
+  // refresh grid: every resident CTA, except when even a refresh of every chain
+  // at its capacity is small (at most 4096 trailing-update tiles of 32 x 32 per
+  // panel): then its ~35 grid barriers per panel, not its work, set its time,
+  // and one CTA per SM makes each barrier shorter (measured: 0.081 -> 0.059 ms
+  // per block for one 2x2x2 chain at n ~ 400; 22 % slower at n ~ 2100)
   int nb = refresh_blocks_per_sm<T>();
-  ls.refresh_grid = std::max(1, nb) * ctx->sm_count;
+  long long cap_tiles = 0;
+  for (const auto& cp : ctx->chains) {
+    const long long tb = (cp.capacity + cp.k_max + 31) / 32;
+    cap_tiles += 2 * tb * tb;
+  }
+  ls.refresh_grid = (cap_tiles <= 4096 ? 1 : std::max(1, nb)) * ctx->sm_count;
 
   for (size_t ci = 0; ci < ctx->chains.size(); ++ci) {
     const ctaux_chain_params& cp = ctx->chains[ci];
