@@ -851,13 +851,15 @@ __device__ __forceinline__ void proposals_body(Chain<T>* chains) {
 // compacted configuration in the other buffer (Sec. IV C: s=0 rows and
 // columns are deleted).
 
-template <typename T, bool GS>
+// Gamma^{-1} in global memory (large k_max, large batches): registers held
+// to what lets several CTAs share an SM.
+template <typename T>
 __global__ void __launch_bounds__(256) k_proposals(Chain<T>* chains) {
-  proposals_body<T, GS>(chains);
+  proposals_body<T, false>(chains);
 }
 
-// The float32 chain with Gamma^{-1} in shared memory (whose size already
-// limits the CTAs per SM) runs faster with its registers unrationed.
+// Gamma^{-1} in shared memory, whose size already limits the CTAs per SM:
+// registers unrationed (4-6 % faster per block than at 64 registers).
 template <typename T>
 __global__ void __launch_bounds__(256, 1) k_proposals_smem(Chain<T>* chains) {
   proposals_body<T, true>(chains);
@@ -1051,9 +1053,8 @@ void launch_block(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t st, Pha
   launch_gemm<T>(dchains, ls, PH_GCOL_NEW, st);
   pt->end(1, st, 3);
   pt->begin(2, st);
-  if (ls.gamma_in_smem && sizeof(T) == 4) k_proposals_smem<T><<<nch, 256, ls.prop_smem, st>>>(dchains);
-  else if (ls.gamma_in_smem) k_proposals<T, true><<<nch, 256, ls.prop_smem, st>>>(dchains);
-  else k_proposals<T, false><<<nch, 256, ls.prop_smem, st>>>(dchains);
+  if (ls.gamma_in_smem) k_proposals_smem<T><<<nch, 256, ls.prop_smem, st>>>(dchains);
+  else k_proposals<T><<<nch, 256, ls.prop_smem, st>>>(dchains);
   pt->end(2, st, 1);
   bool tc = false;
   if constexpr (std::is_same<T, float>::value) tc = ls.use_tc != 0;
@@ -1080,13 +1081,10 @@ void launch_block(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t st, Pha
 
 template <typename T>
 cudaError_t configure_block_kernels(const LaunchShape& ls) {
-  cudaError_t e = cudaFuncSetAttribute(k_proposals<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_proposals_smem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        ls.prop_smem);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_proposals_smem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           ls.prop_smem);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_proposals<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(k_proposals<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               ls.prop_smem);
 }
 
