@@ -41,7 +41,7 @@ N_TAU_BINS, N_ANCHORS, REFRESH_EVERY = 32, 4, 32
 # dominant kernel, from one ncu capture of the same workload in the state the
 # timed blocks run in (summaries under profiles/); an entry is removed when its
 # kernel changes
-DRAM_TRAFFIC = {("cube8", "fp64", "proposals"): 358144}
+DRAM_TRAFFIC = {("cube8", "fp64", "proposals"): 398848}
 
 
 def workload(name, K, k_max, chain_id=0, n_chains=8):
