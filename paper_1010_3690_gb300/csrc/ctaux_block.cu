@@ -246,18 +246,49 @@ __global__ void __launch_bounds__(256) k_gemm(Chain<T>* chains, int n_chains, in
     for (int a = 0; a < TM; ++a)
 #pragma unroll
       for (int b = 0; b < TN; ++b) acc[a][b] = (T)0;
+    // the next K step's operands are loaded into registers while the current
+    // one is multiplied from shared memory (global latency off the FMA path)
+    constexpr int PA = (GBK * GBM + 255) / 256, PB = (GBK * GBN + 255) / 256;
+    T ra[PA], rb[PB];
+#pragma unroll
+    for (int q = 0; q < PA; ++q) {
+      const int e = threadIdx.x + 256 * q, ii = e % GBM, kk = e / GBM;
+      const int i = i0 + ii, k = kb + kk;
+      ra[q] = (e < GBK * GBM && i < g.M && k < ke) ? g.A.at(i, k) : (T)0;
+    }
+#pragma unroll
+    for (int q = 0; q < PB; ++q) {
+      const int e = threadIdx.x + 256 * q, kk = e % GBK, jj = e / GBK;
+      const int j = j0 + jj, k = kb + kk;
+      rb[q] = (e < GBK * GBN && j < g.Nn && k < ke) ? g.B.at(k, j) : (T)0;
+    }
     for (int k0 = kb; k0 < ke; k0 += GBK) {
-      for (int e = threadIdx.x; e < GBK * GBM; e += 256) {
-        const int ii = e % GBM, kk = e / GBM;
-        const int i = i0 + ii, k = k0 + kk;
-        As[kk][ii] = (i < g.M && k < ke) ? g.A.at(i, k) : (T)0;
+#pragma unroll
+      for (int q = 0; q < PA; ++q) {
+        const int e = threadIdx.x + 256 * q;
+        if (e < GBK * GBM) As[e / GBM][e % GBM] = ra[q];
       }
-      for (int e = threadIdx.x; e < GBK * GBN; e += 256) {
-        const int kk = e % GBK, jj = e / GBK;
-        const int j = j0 + jj, k = k0 + kk;
-        Bs[kk][jj] = (j < g.Nn && k < ke) ? g.B.at(k, j) : (T)0;
+#pragma unroll
+      for (int q = 0; q < PB; ++q) {
+        const int e = threadIdx.x + 256 * q;
+        if (e < GBK * GBN) Bs[e % GBK][e / GBK] = rb[q];
       }
       __syncthreads();
+      const int k1 = k0 + GBK;
+      if (k1 < ke) {
+#pragma unroll
+        for (int q = 0; q < PA; ++q) {
+          const int e = threadIdx.x + 256 * q, ii = e % GBM, kk = e / GBM;
+          const int i = i0 + ii, k = k1 + kk;
+          ra[q] = (e < GBK * GBM && i < g.M && k < ke) ? g.A.at(i, k) : (T)0;
+        }
+#pragma unroll
+        for (int q = 0; q < PB; ++q) {
+          const int e = threadIdx.x + 256 * q, kk = e % GBK, jj = e / GBK;
+          const int j = j0 + jj, k = k1 + kk;
+          rb[q] = (e < GBK * GBN && j < g.Nn && k < ke) ? g.B.at(k, j) : (T)0;
+        }
+      }
 #pragma unroll
       for (int kk = 0; kk < GBK; ++kk) {
         T av[TM], bv[TN];
