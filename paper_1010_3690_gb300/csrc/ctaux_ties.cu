@@ -76,16 +76,6 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return tot;
 }
 
-__device__ __forceinline__ double block_max(double v, double* red) {
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-  __syncthreads();
-  double mx = 0.0;
-  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, red[w]);
-  return mx;
-}
-
 // Fallback: decide from the FP64 N of a from-scratch refresh (N64).
 __device__ void tie_eval_chain(const Chain<float>& c) {
   Dyn& d = *c.dyn;
