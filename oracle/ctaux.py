@@ -35,6 +35,14 @@ Readings of the paper used here (it is silent or ambiguous on these):
       (t, chain, purpose); see oracle.philox.
   C9  G(dx, tau) estimator: G(a,b) = G0(a,b) + sum_lm G0(a,l) [(e^V-1)N]_lm G0(m,b),
       a = (x_a, tau_b + tau) and anchors b = (site 0, j beta / n_anchors).
+  C20 Matsubara and cluster-momentum estimator (Sec. IV D: measure directly in
+      cluster momenta and Matsubara frequencies): the Fourier transform
+      (1/beta) int int dtau dtau' e^{i w (tau - tau')} of the C9 estimator,
+          G_xy(iw) = G0_xy(iw) + (1/beta) sum_lm G0_{x x_l}(iw) e^{i w tau_l} M_lm
+                                                 e^{-i w tau_m} G0_{x_m y}(iw),
+      M = (e^V - 1) N, w_n = (2n+1) pi / beta, G0(iw) = int_0^beta e^{iw tau} G0(tau)
+      of the same (interpolated) G0 the weights use; cluster momenta by
+      G(K) = (1/N_c) sum_xy e^{-iK.(r_x - r_y)} G_xy.
 """
 from __future__ import annotations
 
@@ -46,6 +54,21 @@ from . import philox
 
 INSERT, REMOVE, FLIP = 0, 1, 2
 SIGMAS = (1.0, -1.0)
+
+
+def matsubara(beta, n_freq):
+    """Fermionic Matsubara frequencies w_n = (2n+1) pi / beta, n = 0 .. n_freq-1."""
+    return (2.0 * np.arange(n_freq) + 1.0) * math.pi / float(beta)
+
+
+def cluster_momenta(G_xy, sites, kvecs):
+    """G(K) = (1/N_c) sum_xy e^{-i K.(r_x - r_y)} G_xy (C20).
+
+    G_xy: [..., n_c, n_c, F]; sites: [n_c, d] positions; kvecs: [n_K, d].
+    Returns [..., n_K, F]."""
+    ph = np.exp(-1j * (np.asarray(kvecs, dtype=np.float64) @ np.asarray(sites, dtype=np.float64).T))
+    n_c = ph.shape[1]
+    return np.einsum("kx,...xyf,ky->...kf", ph, G_xy, ph.conj()) / n_c
 
 
 class OracleChain:
@@ -251,4 +274,41 @@ class OracleChain:
             per_site = val.sum(axis=0) / n_anchors                     # [site, bin]
             for x in range(self.n_c):
                 out[spin, cls_a[x]] += per_site[x] / count[cls_a[x]]
+        return out
+
+    def g0_matsubara(self, n_freq):
+        """G0_sigma,class(iw_n) = int_0^beta e^{iw tau} G0(tau) dtau of the interpolated
+        table, [2, n_classes, n_freq] complex (C20).  G0 is linear on every table
+        interval, so Simpson's rule on each interval (its midpoint added) leaves
+        only the (w dtau)^4 error of the smooth phase factor."""
+        w = matsubara(self.beta, n_freq)
+        t0 = np.arange(self.n_tau - 1) * self.dtau
+        tm = t0 + 0.5 * self.dtau
+        t1 = t0 + self.dtau
+        T = self.table
+        mid = 0.5 * (T[..., :-1] + T[..., 1:])
+        e0, em, e1 = (np.exp(1j * w[:, None] * t[None, :]) for t in (t0, tm, t1))  # [F, n_tau-1]
+        acc = (np.einsum("scj,fj->scf", T[..., :-1], e0) + 4.0 * np.einsum("scj,fj->scf", mid, em)
+               + np.einsum("scj,fj->scf", T[..., 1:], e1))
+        return acc * (self.dtau / 6.0)
+
+    def measure_G_matsubara(self, n_freq, g0_iw=None):
+        """Per-configuration G_sigma,xy(iw_n), [2, n_c, n_c, n_freq] complex (C20)."""
+        if g0_iw is None:
+            g0_iw = self.g0_matsubara(n_freq)
+        w = matsubara(self.beta, n_freq)
+        G0xy = g0_iw[:, self.dx_class, :]                         # [2, n_c, n_c, F]
+        out = np.array(G0xy, dtype=np.complex128)
+        n = self.order
+        if n == 0:
+            return out
+        sel = np.zeros((self.n_c, n))
+        sel[self.site, np.arange(n)] = 1.0                        # vertex l sits on site x_l
+        ph = np.exp(1j * w[:, None] * self.tau[None, :])          # [F, n]
+        for spin in (0, 1):
+            M = (self.exp_v(spin, self.s) - 1.0)[:, None] * self.N(spin)
+            # S_zw(iw) = sum_{l on z, m on w} e^{iw tau_l} M_lm e^{-iw tau_m}
+            S = np.einsum("zl,fl,lm,fm,wm->zwf", sel, ph, M, ph.conj(), sel)
+            G0s = G0xy[spin]
+            out[spin] += np.einsum("xzf,zwf,wyf->xyf", G0s, S, G0s) / self.beta
         return out

@@ -83,6 +83,17 @@ class AndersonED:
         return np.array([-_thermal_trace(self.E, self.V, self.beta, [(t, d), (0.0, d.T)])
                          for t in np.atleast_1d(taus)])
 
+    def G_matsubara(self, w, spin=0):
+        """G(iw) = int_0^beta e^{iw tau} G(tau) dtau by the Lehmann sum
+        (1/Z) sum_nm |<n|d|m>|^2 (e^{-beta E_n} + e^{-beta E_m}) / (iw + E_n - E_m)."""
+        A = self.V.T @ self.c[spin * self.no] @ self.V
+        Es = self.E - self.E.min()
+        bw = np.exp(-self.beta * Es)
+        num = (A ** 2) * (bw[:, None] + bw[None, :])
+        den = Es[:, None] - Es[None, :]
+        w = np.atleast_1d(np.asarray(w, dtype=np.float64))
+        return np.array([np.sum(num / (1j * wi + den)) for wi in w]) / bw.sum()
+
     def double_occupancy(self):
         return _thermal_trace(self.E, self.V, self.beta, [(0.0, self.nu @ self.nd)])
 
@@ -116,6 +127,13 @@ class SingleSpinFreeED:
         if tau > 0:
             return float(g0tables.fermion_g(E, tau, self.beta) @ w)
         return -float(g0tables.fermion_g(E, tau + self.beta, self.beta) @ w)
+
+    def g0_matsubara(self, w):
+        """G0(iw) = sum_k |U_0k|^2 / (iw - E_k) from the single-particle levels."""
+        E, U = np.linalg.eigh(self.h1)
+        wt = U[0, :] ** 2
+        w = np.atleast_1d(np.asarray(w, dtype=np.float64))
+        return (wt[None, :] / (1j * w[:, None] - E[None, :])).sum(axis=1)
 
     def _exp_n(self, v):
         # e^{v n} = 1 + (e^v - 1) n

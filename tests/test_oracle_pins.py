@@ -14,7 +14,7 @@ from scipy import integrate, linalg, stats
 
 from conftest import load_kat
 from oracle import philox
-from oracle.ctaux import FLIP, INSERT, REMOVE, OracleChain
+from oracle.ctaux import FLIP, INSERT, REMOVE, OracleChain, cluster_momenta, matsubara
 from oracle.ed import AndersonED, SingleSpinFreeED
 from workloads import configs, g0tables
 
@@ -279,26 +279,124 @@ def test_multi_change_ratio_equals_prod_lambda_det_gamma():
         assert np.allclose(Nw[np.ix_(keep, keep)], Nred, rtol=1e-8, atol=1e-9 * np.abs(Nred).max())
 
 
+# ------------------------------------------ Matsubara / momentum estimator
+def _simpson(f, x):
+    """Composite Simpson along the last axis (odd number of equally spaced points)."""
+    h = x[1] - x[0]
+    return (h / 3.0) * (f[..., 0] + f[..., -1] + 4.0 * f[..., 1:-1:2].sum(-1) + 2.0 * f[..., 2:-1:2].sum(-1))
+
+
+def test_g0_matsubara_against_quadrature_and_lehmann():
+    """The tabulated G0's transform: Simpson per table interval against an independent
+    fine quadrature of the interpolated G0 (C4, C20), and against the exact Lehmann
+    sum of the impurity (table interpolation error only)."""
+    oc = _aim_chain(n_tau=4001)
+    F = 6
+    w = matsubara(oc.beta, F)
+    g = oc.g0_matsubara(F)[0, 0]
+    tq = np.linspace(0.0, oc.beta, 300001)[1:-1]
+    vals = oc.g0(0, tq, np.zeros_like(tq, dtype=np.int64), 0.0, 0)
+    ref = np.trapezoid(np.exp(1j * w[:, None] * tq[None, :]) * vals[None, :], tq, axis=1)
+    assert np.allclose(g, ref, rtol=1e-6, atol=1e-7), (g, ref)
+    ed = SingleSpinFreeED(oc.beta)
+    assert np.allclose(g, ed.g0_matsubara(w), rtol=1e-5, atol=1e-6)
+
+
+def test_matsubara_estimator_is_fourier_transform_of_tau_estimator():
+    """C20 against the C9 estimator: the Fourier integrals of G0(tau - tau_l) and
+    G0(tau_m - tau') are done by quadrature of the tau-space G0 (split at the
+    jump), then assembled as (1/beta) sum_lm u_xl M_lm v_my; the estimator's closed
+    form (phases e^{+-iw tau} times G0(iw)) must agree.  A conjugated phase fails."""
+    ch = configs.cube8(K=4.0, k_max=16, capacity=128)
+    oc = OracleChain(ch.table, ch.dx_class, ch.beta, ch.U, ch.K, seed=3)
+    cfg = configs.synthetic_configuration(ch, 10, seed=5)
+    oc.set_config(cfg["tau"], cfg["site"], cfg["s"], cfg["birth"], cfg["t"])
+    F, n, n_c, beta = 3, oc.order, oc.n_c, oc.beta
+    w = matsubara(beta, F)
+    got = oc.measure_G_matsubara(F)
+    g0_iw = oc.g0_matsubara(F)
+    xs = np.arange(n_c)
+    for spin in (0, 1):
+        u = np.zeros((n_c, n, F), complex)     # int e^{iw tau} G0(x - x_l, tau - tau_l) dtau
+        v = np.zeros((n, n_c, F), complex)     # int e^{-iw t} G0(x_m - y, tau_m - t) dt
+        for l in range(n):
+            for lo, hi in ((0.0, oc.tau[l]), (oc.tau[l], beta)):
+                t = np.linspace(lo, hi, 20001)[None, :]
+                inner = t[:, 1:-1]
+                gu = oc.g0(spin, inner, xs[:, None], oc.tau[l], oc.site[l])      # [n_c, pts]
+                gv = oc.g0(spin, oc.tau[l], oc.site[l], inner, xs[:, None])      # [n_c, pts]
+                # endpoints: the one-sided limits of the piece
+                eps = 1e-12 * beta
+                e_lo = np.full((n_c, 1), lo + eps)
+                e_hi = np.full((n_c, 1), hi - eps)
+                gu = np.concatenate([oc.g0(spin, e_lo, xs[:, None], oc.tau[l], oc.site[l]), gu,
+                                     oc.g0(spin, e_hi, xs[:, None], oc.tau[l], oc.site[l])], axis=1)
+                gv = np.concatenate([oc.g0(spin, oc.tau[l], oc.site[l], e_lo, xs[:, None]), gv,
+                                     oc.g0(spin, oc.tau[l], oc.site[l], e_hi, xs[:, None])], axis=1)
+                tt = t[0]
+                u[:, l, :] += _simpson(np.exp(1j * w[None, :, None] * tt) * gu[:, None, :], tt)
+                v[l, :, :] += _simpson(np.exp(-1j * w[None, :, None] * tt) * gv[:, None, :], tt)
+        M = (oc.exp_v(spin, oc.s) - 1.0)[:, None] * oc.N(spin)
+        ref = g0_iw[spin][oc.dx_class] + np.einsum("xlf,lm,myf->xyf", u, M, v) / beta
+        assert np.allclose(got[spin], ref, rtol=1e-6, atol=1e-8), np.abs(got[spin] - ref).max()
+        # the closed form of one factor, and a planted conjugated phase
+        G0xy = g0_iw[spin][oc.dx_class]
+        u_closed = G0xy[:, oc.site, :] * np.exp(1j * w[None, None, :] * oc.tau[None, :, None])
+        assert np.allclose(u, u_closed, rtol=1e-6, atol=1e-9)
+        u_bad = G0xy[:, oc.site, :] * np.exp(-1j * w[None, None, :] * oc.tau[None, :, None])
+        bad = G0xy + np.einsum("xlf,lm,myf->xyf", u_bad, M, v) / beta
+        assert np.abs(bad - ref).max() > 1e3 * np.abs(got[spin] - ref).max() + 1e-6
+
+
+def test_cluster_momenta_of_the_free_cluster():
+    """With no vertices the estimator is G0; its cluster-momentum transform equals the
+    coarse-grained lattice sum (1/N_p) sum_k~ 1/(iw - eps(K + k~)) that generated the
+    table (cube8, half filling), up to the table's interpolation error."""
+    ch = configs.cube8(K=4.0, k_max=16, capacity=128)
+    oc = OracleChain(ch.table, ch.dx_class, ch.beta, ch.U, ch.K, seed=0)
+    F = 5
+    w = matsubara(oc.beta, F)
+    G = oc.measure_G_matsubara(F)                      # n = 0: G = G0
+    cl = configs.cluster(8)
+    GK = cluster_momenta(G, cl.sites, cl.K)            # [2, n_K, F]
+    kt = g0tables._patch_offsets(cl, 12)
+    for iK, K in enumerate(cl.K):
+        xi = g0tables.dispersion(K[None, :] + kt)      # mu = 0 at half filling
+        ref = (1.0 / (1j * w[None, :] - xi[:, None])).mean(axis=0)
+        for spin in (0, 1):
+            assert np.allclose(GK[spin, iK], ref, rtol=2e-5, atol=1e-6), (iK, GK[spin, iK], ref)
+    # and back: sum_K e^{iK.(r_x - r_y)} G(K) / N_c returns G_xy
+    ph = np.exp(1j * (cl.sites.astype(float) @ cl.K.T))
+    back = np.einsum("xk,skf,yk->sxyf", ph, GK, ph.conj()) / 8
+    assert np.allclose(back, G, atol=1e-12)
+
+
 # ------------------------------------------------------- interacting ED
 @pytest.mark.slow
 def test_oracle_montecarlo_matches_exact_diagonalisation():
-    """Anderson impurity + 3 bath levels: <order> = K + beta U (1/2 - d) and G(tau) vs ED."""
+    """Anderson impurity + 3 bath levels: <order> = K + beta U (1/2 - d), and G(tau) and
+    G(iw_n) vs ED."""
     beta, U, K = 5.0, 4.0, 1.0
     ch = configs.aim_ed(beta=beta, U=U, K=K, n_tau=4001)
     oc = OracleChain(ch.table, ch.dx_class, beta, U, K, seed=11)
     ed = AndersonED(beta, U)
     d = ed.double_occupancy()
     nb, n_batch, per_batch, k = 10, 12, 160, 8
+    F = 4
+    g0_iw = oc.g0_matsubara(F)
     oc.run(1500)
-    Gs, orders = [], []
+    Gs, orders, Gw = [], [], []
     for _ in range(n_batch):
         acc = np.zeros((2, 1, nb))
+        accw = np.zeros((2, F), complex)
         o = 0.0
         for _ in range(per_batch):
             oc.run(k)
             acc += oc.measure_G(nb, 16)
+            accw += oc.measure_G_matsubara(F, g0_iw)[:, 0, 0, :]
             o += oc.order
         Gs.append(acc / per_batch)
+        Gw.append(accw / per_batch)
         orders.append(o / per_batch)
     Gs = np.array(Gs)
     mean = Gs.mean(axis=0)
@@ -312,6 +410,14 @@ def test_oracle_montecarlo_matches_exact_diagonalisation():
     o_mean = np.mean(orders)
     o_err = np.std(orders, ddof=1) / math.sqrt(n_batch)
     assert abs(o_mean - (K + beta * U * (0.5 - d))) < 4.0 * o_err + 0.05
+    # Matsubara estimator (C20) against the Lehmann sum, real and imaginary parts
+    Gw = np.array(Gw)
+    ref_w = ed.G_matsubara(matsubara(beta, F))
+    for part in (np.real, np.imag):
+        m_w = part(Gw).mean(axis=0)
+        e_w = part(Gw).std(axis=0, ddof=1) / math.sqrt(n_batch)
+        zw = (m_w - part(ref_w)[None, :]) / np.maximum(e_w, 1e-12)
+        assert np.all(np.abs(zw) < 4.0), zw
 
 
 # -------------------------------------------- planted mistakes are caught
