@@ -7,8 +7,9 @@
 //
 // Operands are K-major split buffers written by the flush preparation kernels
 // (Yh/Yl: rows a, Xh/Xl: rows b, KP = k_max rounded up to 32 float32 per row,
-// zero beyond k_acc), loaded by TMA into 128-byte-swizzled shared memory (one
-// TMA load per 128 x 32 tile, no multicast).
+// zero beyond k_acc), loaded by TMA into shared memory swizzled over the
+// 64-byte row of one 16-wide K chunk (one TMA load per 128 x 16 tile, no
+// multicast).
 //
 // One persistent CTA per SM, warp-specialised, over the (chain, spin,
 // 128 x 128 tile) items of all chains:
