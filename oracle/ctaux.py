@@ -167,6 +167,17 @@ class OracleChain:
             self._draw_base = base
         return tuple(float(v) for v in self._draw_tab[t - base])
 
+    def move_factor(self, move, n):
+        """Proposal-probability factor of a move from order n (Eq. insprob): an
+        insertion picks tau, site and s with density K-normalised over n+1
+        vertices, K/(n+1); a removal, its inverse from order n, n/K; a spin flip
+        keeps n, 1."""
+        if move == INSERT:
+            return self.K / (n + 1)
+        if move == REMOVE:
+            return n / self.K
+        return 1.0
+
     def step(self):
         """One Metropolis proposal (index self.t).  Returns its trace record."""
         t = self.t
@@ -185,7 +196,7 @@ class OracleChain:
             s_new = 1 if u_spin < 0.5 else -1
             new = (np.append(self.tau, tau_new), np.append(self.site, site_new),
                    np.append(self.s, s_new), np.append(self.birth, t))
-            f = self.K / (n + 1)
+            f = self.move_factor(INSERT, n)
             rec.update(birth=t, s_new=s_new)
         else:
             if n == 0:
@@ -197,13 +208,13 @@ class OracleChain:
             if move == REMOVE:
                 keep = np.arange(n) != idx
                 new = (self.tau[keep], self.site[keep], self.s[keep], self.birth[keep])
-                f = n / self.K
+                f = self.move_factor(REMOVE, n)
                 rec.update(s_new=0)
             else:
                 s2 = self.s.copy()
                 s2[idx] = -s2[idx]
                 new = (self.tau, self.site, s2, self.birth)
-                f = 1.0
+                f = self.move_factor(FLIP, n)
                 rec.update(s_new=int(s2[idx]))
         ratios = []
         dets = []

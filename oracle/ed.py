@@ -119,15 +119,6 @@ class SingleSpinFreeED:
         self.n = c[0].T @ c[0]
         self.h1 = h1
 
-    def g0_exact(self, tau):
-        """G0(tau) for tau in (-beta, beta), from the single-particle levels."""
-        E, U = np.linalg.eigh(self.h1)
-        w = U[0, :] ** 2
-        tau = float(tau)
-        if tau > 0:
-            return float(g0tables.fermion_g(E, tau, self.beta) @ w)
-        return -float(g0tables.fermion_g(E, tau + self.beta, self.beta) @ w)
-
     def g0_matsubara(self, w):
         """G0(iw) = sum_k |U_0k|^2 / (iw - E_k) from the single-particle levels."""
         E, U = np.linalg.eigh(self.h1)

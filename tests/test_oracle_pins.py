@@ -2,9 +2,11 @@
 
 Each test checks the oracle against a value the paper or the mathematics fixes:
 published Philox vectors, operator-algebra traces (exact diagonalisation),
-closed forms (first insertion, U -> 0), detailed balance of insertion/removal,
+closed forms (first insertion, U -> 0), detailed balance of insertion/removal
+and of spin-flip pairs driven through OracleChain.step with planted uniforms,
 the determinant identities of Secs. III-IV, and the interacting impurity
-solved by exact diagonalisation.
+solved by exact diagonalisation.  Planted mistakes in the oracle (move factors,
+the equal-time convention) fail their pins.
 """
 import math
 
@@ -173,40 +175,157 @@ def test_first_insertion_closed_form(maker):
         oc.t += 1
 
 
+def _plant(oc, script):
+    """Replace the Philox draws of proposals t in `script` by the given uniforms
+    (u_move, u_acc, u_tau, u_site, u_spin, u_idx); other proposals keep theirs."""
+    drawn = oc.draws
+    oc.draws = lambda t: script[t] if t in script else drawn(t)
+
+
+def _u_insert(oc):
+    return 0.5 * oc.p_insert
+
+
+def _u_remove(oc):
+    return oc.p_insert + 0.5 * oc.p_remove
+
+
+def _u_flip(oc):
+    return oc.p_insert + oc.p_remove + 0.5 * oc.p_flip
+
+
+def _u_pick(i, n):
+    """u with floor(u n) = i: the i-th interacting vertex in birth order."""
+    return (i + 0.5) / n
+
+
+def _insert_then_remove(oc, u_tau, u_site, u_spin):
+    """Drive OracleChain.step through an accepted insertion and the removal of the
+    same vertex (u_acc = 0 accepts any |R| > 0).  Returns both trace records."""
+    n, t = oc.order, oc.t
+    _plant(oc, {t: (_u_insert(oc), 0.0, u_tau, u_site, u_spin, 0.5),
+                t + 1: (_u_remove(oc), 0.0, 0.5, 0.5, 0.5, _u_pick(n, n + 1))})
+    return oc.step(), oc.step()
+
+
+def _flip_twice(oc, i):
+    n, t = oc.order, oc.t
+    u = (_u_flip(oc), 0.0, 0.5, 0.5, 0.5, _u_pick(i, n))
+    _plant(oc, {t: u, t + 1: u})
+    return oc.step(), oc.step()
+
+
 def test_insert_remove_detailed_balance():
-    """R_insert(c -> c') * R_remove(c' -> c) = 1 for any pair (Eq. insprob and its inverse)."""
+    """An accepted insertion c -> c' and the removal of the same vertex c' -> c,
+    both through OracleChain.step: R_ins(c -> c') R_rem(c' -> c) = 1 (Eq. insprob
+    and its inverse move), and the chain returns to c with its determinants."""
     ch = configs.cube8(K=2.0)
     oc = OracleChain(ch.table, ch.dx_class, ch.beta, ch.U, ch.K, seed=5)
     oc.run(300)
-    n = oc.order
-    assert n > 2
+    assert oc.order > 2
     rng = np.random.default_rng(0)
     for _ in range(5):
-        tau_new, site_new, s_new = rng.uniform(0, oc.beta), int(rng.integers(ch.n_c)), 1
-        c = (oc.tau, oc.site, oc.s)
-        c2 = (np.append(oc.tau, tau_new), np.append(oc.site, site_new), np.append(oc.s, s_new))
-        r = 1.0
+        before = (oc.tau.copy(), oc.s.copy(), list(oc._logdet))
+        n = oc.order
+        r_ins, r_rem = _insert_then_remove(oc, *rng.uniform(0.0, 1.0, 3))
+        assert r_ins["move"] == INSERT and r_rem["move"] == REMOVE
+        assert r_ins["accept"] and r_rem["accept"] and r_rem["birth"] == r_ins["birth"]
+        assert r_ins["n"] == n and r_rem["n"] == n + 1
+        assert r_ins["R"] * r_rem["R"] == pytest.approx(1.0, rel=1e-10)
+        np.testing.assert_array_equal(oc.tau, before[0])
+        np.testing.assert_array_equal(oc.s, before[1])
+        assert oc._logdet == pytest.approx(before[2], rel=1e-12, abs=1e-10)
+
+
+def test_flip_pair_detailed_balance():
+    """A spin flip and the flip back, through OracleChain.step with p_flip > 0:
+    R_flip(c -> c') R_flip(c' -> c) = 1, and each flip ratio is the ratio of the
+    two configurations' dense determinants."""
+    ch = configs.cube8(K=2.0)
+    oc = OracleChain(ch.table, ch.dx_class, ch.beta, ch.U, ch.K, seed=6, p_insert=0.4,
+                     p_flip=0.3)
+    oc.run(300)
+    n = oc.order
+    assert n > 4
+    for i in (0, n // 2, n - 1):
+        s_before = oc.s.copy()
+        r1, r2 = _flip_twice(oc, i)
+        assert r1["move"] == FLIP and r2["move"] == FLIP
+        assert r1["accept"] and r2["accept"] and r1["birth"] == r2["birth"] == oc.birth[i]
+        assert r1["s_new"] == -s_before[i] and r2["s_new"] == s_before[i]
+        assert r1["R"] * r2["R"] == pytest.approx(1.0, rel=1e-10)
+        np.testing.assert_array_equal(oc.s, s_before)
+        s2 = s_before.copy()
+        s2[i] = -s2[i]
+        want = 1.0
         for spin in (0, 1):
-            s1, l1 = oc.slogdet(spin, *c)
-            s2, l2 = oc.slogdet(spin, *c2)
-            r *= s1 * s2 * math.exp(l2 - l1)
-        R_ins = oc.K / (n + 1) * r
-        R_rem = (n + 1) / oc.K / r
-        assert R_ins * R_rem == pytest.approx(1.0, rel=1e-12)
+            A0 = oc.ninv(spin, oc.tau, oc.site, s_before)
+            A1 = oc.ninv(spin, oc.tau, oc.site, s2)
+            want *= np.linalg.det(A1) / np.linalg.det(A0)
+        assert r1["R"] == pytest.approx(want, rel=1e-9)
 
 
-def test_U_to_zero_limit():
-    """U -> 0: gamma -> 0, every determinant ratio is 1, G = G0, and n ~ Poisson(K)."""
+def test_flip_ratio_equals_ratio_of_operator_traces():
+    """The flip branch's R against exact diagonalisation: det N^{-1} =
+    prod e^{V_i} <T prod e^{-V_i n(tau_i)}>_0 per spin (Eq. Zn_div_Z0), so a flip of
+    vertex i changes the weight by the ratio of two operator traces."""
+    ch = configs.aim_ed(beta=5.0, U=4.0, K=1.0, n_tau=20001)
+    oc = OracleChain(ch.table, ch.dx_class, ch.beta, ch.U, ch.K, p_insert=0.3, p_flip=0.4)
+    ed = SingleSpinFreeED(oc.beta)
+    rng = np.random.default_rng(8)
+    for _ in range(4):
+        n = int(rng.integers(2, 6))
+        taus = rng.choice(oc.n_tau - 1, size=n, replace=False) * oc.dtau   # on the grid: exact
+        s = rng.choice([-1, 1], size=n)
+        oc.set_config(taus, np.zeros(n, np.int64), s, np.arange(n), 100)
+        i = int(rng.integers(n))
+        _plant(oc, {100: (_u_flip(oc), 0.0, 0.5, 0.5, 0.5, _u_pick(i, n))})
+        rec = oc.step()
+        s2 = s.copy()
+        s2[i] = -s2[i]
+        want = 1.0
+        for spin in (0, 1):
+            sig = 1.0 if spin == 0 else -1.0
+            V0, V1 = oc.gamma * sig * s, oc.gamma * sig * s2
+            w0 = np.prod(np.exp(V0)) * ed.weight(taus, -V0)
+            w1 = np.prod(np.exp(V1)) * ed.weight(taus, -V1)
+            want *= w1 / w0
+        assert rec["move"] == FLIP and rec["birth"] == i
+        assert rec["R"] == pytest.approx(want, rel=1e-10)
+
+
+def test_removal_from_empty_configuration_rejects():
+    """n = 0: a removal (or flip) is rejected without a ratio, the counter advances
+    and the configuration stays empty (reading C7)."""
+    ch = configs.cube8(K=2.0)
+    oc = OracleChain(ch.table, ch.dx_class, ch.beta, ch.U, ch.K, p_insert=0.4, p_flip=0.3)
+    for u_move in (_u_remove(oc), _u_flip(oc)):
+        t = oc.t
+        _plant(oc, {t: (u_move, 0.0, 0.5, 0.5, 0.5, 0.5)})
+        rec = oc.step()
+        assert not rec["accept"] and rec["birth"] == -1 and rec["R"] == 0.0
+        assert oc.t == t + 1 and oc.order == 0
+
+
+@pytest.mark.parametrize("p_flip", [0.0, 0.3])
+def test_U_to_zero_limit(p_flip):
+    """U -> 0: gamma -> 0, every determinant ratio (insertion, removal and spin
+    flip) is 1, G = G0, and n ~ Poisson(K) whatever share of the moves are flips."""
     ch = configs.cube8(K=3.0)
-    oc = OracleChain(ch.table, ch.dx_class, ch.beta, 0.0, ch.K, seed=2)
+    p_ins = 0.5 * (1.0 - p_flip)
+    oc = OracleChain(ch.table, ch.dx_class, ch.beta, 0.0, ch.K, seed=2, p_insert=p_ins,
+                     p_flip=p_flip)
     assert oc.gamma == 0.0
     orders = []
-    for _ in range(600):
+    n_flips = 0
+    for _ in range(600 if p_flip == 0.0 else 900):
         for rec in oc.run(8):
             if rec["n"] > 0 or rec["move"] == INSERT:
                 assert rec["ratio"][0] == pytest.approx(1.0, abs=1e-12)
                 assert rec["ratio"][1] == pytest.approx(1.0, abs=1e-12)
+                n_flips += rec["move"] == FLIP and rec["accept"]
         orders.append(oc.order)
+    assert (n_flips > 500) == (p_flip > 0.0)
     G = oc.measure_G(n_bins=5, n_anchors=2)
     tau_c = (np.arange(5) + 0.5) * oc.beta / 5
     for cls in range(ch.n_c):
@@ -441,9 +560,35 @@ def test_planted_equal_time_mistake_fails_weight_pin():
     assert abs(np.linalg.det(A_bad) / ref - 1.0) > 1e-3
 
 
-def test_planted_removal_factor_mistake_fails_detailed_balance():
-    """A removal factor n/K computed with the post-move order breaks R_ins R_rem = 1."""
-    n, K, r = 7, 2.0, 0.37
-    R_ins = K / (n + 1) * r
-    assert R_ins * ((n + 1) / K / r) == pytest.approx(1.0)
-    assert abs(R_ins * (n / K / r) - 1.0) > 0.1
+@pytest.mark.parametrize("wrong", ["removal_post_move_order", "insertion_pre_move_order"])
+def test_planted_move_factor_mistake_fails_detailed_balance(wrong):
+    """A move factor taken at the wrong order (n - 1 after a removal, or n before
+    an insertion), planted in the oracle, breaks R_ins R_rem = 1 through step()."""
+    ch = configs.cube8(K=2.0)
+    oc = OracleChain(ch.table, ch.dx_class, ch.beta, ch.U, ch.K, seed=5)
+    oc.run(300)
+    right = oc.move_factor
+
+    def planted(move, n):
+        if wrong == "removal_post_move_order" and move == REMOVE:
+            return (n - 1) / oc.K
+        if wrong == "insertion_pre_move_order" and move == INSERT:
+            return oc.K / n
+        return right(move, n)
+    oc.move_factor = planted
+    r_ins, r_rem = _insert_then_remove(oc, 0.3, 0.6, 0.2)
+    assert r_ins["accept"] and r_rem["accept"]
+    assert abs(r_ins["R"] * r_rem["R"] - 1.0) > 1e-3
+
+
+def test_planted_flip_factor_mistake_fails_flip_balance():
+    """A flip that reuses the removal factor n/K, planted in the oracle, breaks
+    R_flip R_flip' = 1."""
+    ch = configs.cube8(K=2.0)
+    oc = OracleChain(ch.table, ch.dx_class, ch.beta, ch.U, ch.K, seed=6, p_insert=0.4,
+                     p_flip=0.3)
+    oc.run(300)
+    right = oc.move_factor
+    oc.move_factor = lambda move, n: n / oc.K if move == FLIP else right(move, n)
+    r1, r2 = _flip_twice(oc, oc.order // 2)
+    assert abs(r1["R"] * r2["R"] - 1.0) > 1e-3
