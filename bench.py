@@ -3,16 +3,22 @@
 
 One step = one full submatrix block of every chain: pre-insertion and G0
 gather, prep products, k_max proposals with Gamma growth, Woodbury flush with
-compaction, G(tau) measurement, and the FP64 refresh every 32 blocks
-(amortised: it lands inside the timed steps at its natural rate).
+compaction, G(tau) measurement, and the FP64 refresh at its cadence (it lands
+inside the timed steps: every min(refresh_every, steps) blocks).
 
-Metric: accepted updates per second (whole job, all GPUs).  Default workload:
-the 2x2x2 simple-cubic cluster (N_c=8, beta=5, U=8) with k_max=64 and the
-expansion constant K=256 that puts the order at n~430 (inside the 300-500
-range the workload names).
+Metric: accepted updates per second (whole job, all GPUs), for the plain FP64
+form and the mixed form (3xTF32 tensor-core flush, FP64 refresh and near-tie
+decisions) in one line, plus the flush's fraction of its tensor roofline.
+Default workload: the largest single-GPU configuration, the 100-site 3D
+Hubbard cluster (beta=4, U=8, half filling) with k_max=256 and 8 independent
+chains, at the expansion constant K=5700 that puts the order at n~7000 (the
+range the workload names); every chain starts from a seeded configuration of
+order 7000.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision both|fp64|mixed|mixed_df64]
+                  [--workload cube100|cube8|sq36|batch|aim1]
   python bench.py --impl reference      # the CPU oracle on the same workload
+  python bench.py --k-sweep 1,2,4,...   # proposals/s against the submatrix size
 
 Timing: W untimed blocks, then K timed blocks, each bracketed by CUDA events on
 the stream the library launches on, with the L2 cache flushed (a 512 MB write)
@@ -24,6 +30,7 @@ import argparse
 import json
 import math
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -36,40 +43,103 @@ if ROOT not in sys.path:
 
 METRIC = "CT-AUX accepted updates/s per GPU, mixed vs FP64 at |dN|<1e-8; flush %peak"
 UNIT = "accepted updates/s"
-N_TAU_BINS, N_ANCHORS, REFRESH_EVERY = 32, 4, 32
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# dominant kernel, from one ncu capture of the same workload in the state the
-# timed blocks run in (summaries under profiles/); an entry is removed when its
-# kernel changes
-DRAM_TRAFFIC = {("cube8", "fp64", "proposals"): 398848}
+N_TAU_BINS, N_ANCHORS = 32, 4
+
+# Per workload: expansion constant (K-matched, so that the order lands in the
+# range the workload names), submatrix size, thermalisation blocks, the order
+# the chains start from (0 = empty), the order the CPU oracle samples at,
+# chains per GPU and the refresh cadence.
+WORKLOADS = {
+    "cube100": dict(K=5700.0, k_max=256, thermalize=5, start_order=7000, n_target=7000,
+                    chains=8, refresh_every=32),
+    "cube8": dict(K=256.0, k_max=64, thermalize=300, start_order=0, n_target=430, chains=1,
+                  refresh_every=32),
+    "sq36": dict(K=1400.0, k_max=128, thermalize=200, start_order=0, n_target=2000, chains=1,
+                 refresh_every=32),
+    "aim1": dict(K=1.0, k_max=8, thermalize=300, start_order=0, n_target=20, chains=1,
+                 refresh_every=32),
+    "batch": dict(K=None, k_max=128, thermalize=150, start_order=0, n_target=None, chains=512,
+                  refresh_every=128, autotune="16,32,64,128"),
+}
+
+# DRAM bytes per timed step of the dominant phase's kernels (dram__bytes_read.sum
+# + dram__bytes_write.sum, summed over the phase's launches of one block) from
+# one ncu capture of the same workload in the state the timed blocks run in
+# (summaries under profiles/); an entry is removed when its kernels change
+DRAM_TRAFFIC = {}
 
 
-def workload(name, K, k_max, chain_id=0, n_chains=8):
+def workload(name, K=None, k_max=None, chain_id=0, n_chains=None):
+    """Chains of one rank (chain ids offset by rank) and the workload's settings."""
     from workloads import configs
+    w = dict(WORKLOADS[name])
+    K = w["K"] if K is None else K
+    k_max = w["k_max"] if k_max is None else k_max
+    n_chains = w["chains"] if n_chains is None else n_chains
+    w.update(K=K, k_max=k_max, chains=n_chains)
+    if name == "cube100":
+        chs = [configs.cube100(K=K, k_max=k_max, capacity=9216, seed=n_chains * chain_id + i,
+                               chain_id=n_chains * chain_id + i) for i in range(n_chains)]
+        if K < 4000:   # K = 1: orders ~1400, grown from the empty configuration
+            w.update(n_target=1400, start_order=0)
+        return chs, w
     if name == "cube8":
         ch = configs.cube8(K=K, k_max=k_max, capacity=1024, seed=chain_id)
         ch.chain_id = chain_id
-        return [ch], dict(n_target=430 if K >= 200 else 140)
+        if K < 200:
+            w.update(n_target=140)
+        return [ch], w
     if name == "sq36":
         ch = configs.sq36(K=K, k_max=k_max, capacity=3072, seed=chain_id)
         ch.chain_id = chain_id
-        return [ch], dict(n_target=2000 if K >= 1000 else 640)
-    if name == "cube100":
-        # 8 independent chains; K-matched (K=5700: <n> ~ 7000) chains start from a
-        # seeded configuration of that order instead of growing from n=0
-        chs = [configs.cube100(K=K, k_max=k_max, capacity=9216, seed=8 * chain_id + i,
-                               chain_id=8 * chain_id + i) for i in range(n_chains)]
-        n_t = 7000 if K >= 4000 else 1400
-        return chs, dict(n_target=n_t, start_order=n_t if K >= 4000 else 0)
+        if K < 1000:
+            w.update(n_target=640)
+        return [ch], w
     if name == "aim1":
         ch = configs.aim1(K=K, k_max=k_max, capacity=256, seed=chain_id)
-        return [ch], dict(n_target=20)
+        ch.chain_id = chain_id
+        return [ch], w
     if name == "batch":
-        chs = configs.batch(n_chains=512, k_max=k_max)   # K per chain, matched to n ~ 50..1200
+        chs = configs.batch(n_chains=n_chains, k_max=k_max)   # K per chain, matched to n ~ 50..1200
         for c in chs:
-            c.chain_id += 512 * chain_id
-        return chs, dict(n_target=None)
+            c.chain_id += n_chains * chain_id
+        return chs, w
     raise SystemExit(f"unknown workload {name}")
+
+
+def workload_name(chains, meta):
+    c0 = chains[0]
+    if c0.name == "batch":
+        ncs = sorted({c.n_c for c in chains})
+        return (f"batch: {len(chains)} independent chains per GPU, N_c in {ncs}, "
+                f"beta in [{min(c.beta for c in chains)}, {max(c.beta for c in chains)}], "
+                f"U in [{min(c.U for c in chains):.2f}, {max(c.U for c in chains):.2f}], "
+                f"K = 0.3 beta U N_c + 30, k_max={c0.k_max}")
+    start = (f", start from a seeded configuration of order {meta['start_order']}"
+             if meta.get("start_order") else "")
+    return (f"{c0.name} N_c={c0.n_c} beta={c0.beta} U={c0.U} K={c0.K} k_max={c0.k_max}, "
+            f"{len(chains)} chain{'s' if len(chains) > 1 else ''} per GPU{start}")
+
+
+def effective_refresh(meta, args):
+    """Refresh cadence of the run: the workload's, or every `steps` blocks when
+    fewer steps are timed, so that the timed region holds its share of refreshes
+    (exactly one when steps <= the workload's cadence)."""
+    r = args.refresh_every if args.refresh_every is not None else meta["refresh_every"]
+    if r > 0 and args.steps < r:
+        r = args.steps
+    return r
+
+
+def line_config(args, chains, meta, refresh):
+    """The `config` object, identical in the GPU arm and the oracle arm."""
+    return {"workload": workload_name(chains, meta),
+            "k_max": sorted({c.k_max for c in chains}),
+            "refresh_every": refresh, "n_tau_bins": N_TAU_BINS, "n_anchors": N_ANCHORS,
+            "measure": "one G(tau) measurement per block",
+            "l2": "GPU arm: L2 flushed by a 512 MB write between timed steps; "
+                  "oracle arm: host cores",
+            "launch": "GPU arm: one CUDA graph per block and per measurement; oracle arm: numpy"}
 
 
 def load_peaks():
@@ -82,6 +152,143 @@ def load_peaks():
 
 # nominal dense rates of GB300 per the recipe table (TFLOP/s)
 NOMINAL = {"bf16": 2250.0, "tf32": 1100.0, "fp64": 1.25}
+
+
+# ------------------------------------------------------------------ host cores
+def host_cores():
+    """Cores this process may use: affinity, capped by a cgroup CPU quota."""
+    n = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    try:
+        q, p = open("/sys/fs/cgroup/cpu.max").read().split()[:2]
+        if q != "max":
+            n = min(n, max(1, int(math.ceil(int(q) / int(p)))))
+    except (OSError, ValueError):
+        pass
+    return n
+
+
+def host_cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    fields = {}
+    try:
+        for line in open("/proc/cpuinfo"):
+            if ":" in line:
+                k, v = line.split(":", 1)
+                fields.setdefault(k.strip(), v.strip())
+    except OSError:
+        pass
+    if "model name" in fields:
+        return fields["model name"]
+    parts = {"0xd4f": "Arm Neoverse-V2", "0xd40": "Arm Neoverse-V1", "0xd0c": "Arm Neoverse-N1"}
+    if "CPU part" in fields:
+        return parts.get(fields["CPU part"], f"Arm CPU part {fields['CPU part']}")
+    return platform.processor() or platform.machine()
+
+
+def host_mem_bytes():
+    try:
+        return os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_PHYS_PAGES")
+    except (ValueError, OSError):
+        return 0
+
+
+def _oracle_worker(job):
+    """One independent oracle chain on one core: untimed start from a seeded
+    configuration, then proposals until `seconds` have passed (at least one)."""
+    ch, n0, seed, seconds = job
+    from oracle.ctaux import OracleChain
+    from workloads import configs
+    oc = OracleChain(ch.table, ch.dx_class, ch.beta, ch.U, ch.K, seed=ch.seed, chain_id=ch.chain_id)
+    if n0:
+        cfg = configs.synthetic_configuration(ch, n0, seed=seed)
+        oc.set_config(cfg["tau"], cfg["site"], cfg["s"], cfg["birth"], cfg["t"])
+    props = acc = 0
+    t0 = time.perf_counter()
+    while props == 0 or time.perf_counter() - t0 < seconds:
+        acc += int(oc.step()["accept"])
+        props += 1
+    return props, acc, time.perf_counter() - t0
+
+
+def cpu_baseline(chains, meta, seconds):
+    """The oracle as it stands, one independent chain per host core (single-threaded
+    BLAS each), on a bounded sample of the workload at its order."""
+    import multiprocessing as mp
+    cores = host_cores()
+    n0 = meta["n_target"] or 0
+    # an oracle proposal at order m holds a few m x m float64 temporaries
+    per_proc = 8 * 8 * max(n0, 256) ** 2 + (1 << 28)
+    mem = host_mem_bytes()
+    procs = max(1, min(cores, int(0.5 * mem // per_proc) if mem else cores))
+    jobs = [(chains[i % len(chains)], n0, 11 + i, seconds) for i in range(procs)]
+    saved = {k: os.environ.get(k) for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS",
+                                             "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"        # inherited by the spawned workers only
+    try:
+        with mp.get_context("spawn").Pool(procs) as pool:
+            res = pool.map(_oracle_worker, jobs, chunksize=1)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    props = sum(r[0] for r in res)
+    acc = sum(r[1] for r in res)
+    wall = max(r[2] for r in res)
+    c0 = chains[0]
+    return {"value": acc / wall, "unit": UNIT, "cores": procs, "kind": "oracle",
+            "sample": f"{procs} independent oracle chains of {c0.name} (one per core, "
+                      f"single-threaded BLAS), each from a seeded configuration of order {n0}, "
+                      f"{props} proposals in {wall:.1f} s; dense-LU determinant ratios, "
+                      f"not an optimised CPU solver",
+            "proposals_per_s": props / wall, "nproc": cores, "cpu_model": host_cpu_model()}
+
+
+def run_reference(args, rank, world):
+    """The oracle on the same workload (chain 0), on all host cores through the
+    BLAS threads of numpy; a step is a bounded sample: one proposal."""
+    if rank != 0:
+        return
+    from oracle.ctaux import OracleChain
+    from workloads import configs
+    chains, meta = workload(args.workload, args.K, args.k_max, n_chains=args.chains)
+    refresh = effective_refresh(meta, args)
+    ch = chains[0]
+    n0 = meta["n_target"] or 0
+    oc = OracleChain(ch.table, ch.dx_class, ch.beta, ch.U, ch.K, seed=ch.seed, chain_id=ch.chain_id)
+    if n0:
+        cfg = configs.synthetic_configuration(ch, n0, seed=1000 + ch.chain_id)
+        oc.set_config(cfg["tau"], cfg["site"], cfg["s"], cfg["birth"], cfg["t"])
+    per_step = 1
+    for _ in range(args.warmup):
+        oc.run(per_step)
+    acc = 0
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        acc += sum(int(r["accept"]) for r in oc.run(per_step))
+    dt = time.perf_counter() - t0
+    value = acc / dt
+    cores = host_cores()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": line_config(args, chains, meta, refresh),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} steps of {per_step} proposal of chain 0 of "
+                                       f"{ch.name} from a seeded configuration of order {n0} "
+                                       f"(numpy BLAS on {cores} threads)",
+                             "cpu_model": host_cpu_model()},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
 
 
 class ClockSampler:
@@ -132,12 +339,9 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+# --------------------------------------------------------------- multi-GPU
 def reduce_over_ranks(torch, dist, total_ms, accepted, device):
-    """Whole-job numbers: the slowest rank's timed milliseconds, the sum of accepted updates.
-
-    Chains are independent (each rank runs its own, with its own Philox chain ids), so
-    this is the only exchange between ranks.
-    """
+    """Whole-job numbers: the slowest rank's timed milliseconds, the sum of accepted updates."""
     t = torch.tensor([total_ms, float(accepted)], dtype=torch.float64, device=device)
     tmax = t.clone()
     dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
@@ -145,88 +349,70 @@ def reduce_over_ranks(torch, dist, total_ms, accepted, device):
     return float(tmax[0]), float(t[1])
 
 
-def cpu_baseline(chains, meta, seconds=15.0):
-    """The oracle as it stands, single process, on a bounded sample of the workload."""
-    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
-    from oracle.ctaux import OracleChain
-    from workloads import configs
-    ch = chains[0]
-    n0 = meta["n_target"] or 100
-    cfg = configs.synthetic_configuration(ch, n0, seed=11)
-    oc = OracleChain(ch.table, ch.dx_class, ch.beta, ch.U, ch.K, seed=ch.seed, chain_id=ch.chain_id)
-    oc.set_config(cfg["tau"], cfg["site"], cfg["s"], cfg["birth"], cfg["t"])
-    t0 = time.perf_counter()
-    props = acc = 0
-    while time.perf_counter() - t0 < seconds:
-        acc += int(oc.step()["accept"])
-        props += 1
-    dt = time.perf_counter() - t0
-    threads = int(os.environ.get("OPENBLAS_NUM_THREADS", "1"))
-    return {"value": acc / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{props} proposals of {ch.name} (k_max={ch.k_max}) from a seeded n={n0} "
-                      f"configuration, {dt:.1f} s, dense-LU ratios",
-            "proposals_per_s": props / dt}
+def pool_accumulators(accs):
+    """Sum the raw G(tau) accumulators of several chains (ctaux_get_accumulators);
+    chains must share the measurement layout."""
+    import numpy as np
+    out = {k: np.zeros_like(accs[0][k]) for k in ("sum", "sumsq", "bin_sum", "bin_sumsq")}
+    out["n_meas"] = out["n_bins"] = 0
+    for a in accs:
+        for k in ("sum", "sumsq", "bin_sum", "bin_sumsq"):
+            out[k] += a[k]
+        out["n_meas"] += a["n_meas"]
+        out["n_bins"] += a["n_bins"]
+    return out
 
 
-def run_reference(args, rank, world):
-    if rank != 0:
-        return
-    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
-    from oracle.ctaux import OracleChain
-    from workloads import configs
-    chains, meta = workload(args.workload, args.K, args.k_max)
-    ch = chains[0]
-    n0 = meta["n_target"] or 100
-    cfg = configs.synthetic_configuration(ch, n0, seed=11)
-    oc = OracleChain(ch.table, ch.dx_class, ch.beta, ch.U, ch.K, seed=ch.seed, chain_id=ch.chain_id)
-    oc.set_config(cfg["tau"], cfg["site"], cfg["s"], cfg["birth"], cfg["t"])
-    # a step of the reference is a bounded sample of one block: as many
-    # proposals as keep the whole run near two minutes (at least one)
-    t1 = time.perf_counter()
-    oc.step()
-    t_prop = time.perf_counter() - t1
-    per_step = int(max(1, min(ch.k_max, 120.0 / (t_prop * (args.steps + args.warmup)))))
-    for _ in range(args.warmup):
-        oc.run(per_step)
-    acc = 0
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        acc += sum(int(r["accept"]) for r in oc.run(per_step))
-    dt = time.perf_counter() - t0
-    value = acc / dt
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
-            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{ch.name} N_c={ch.n_c} beta={ch.beta} U={ch.U} K={ch.K} "
-                                   f"k_max={ch.k_max} n~{n0}", "l2": "oracle on host"},
-            "cpu_baseline": {"value": value, "unit": UNIT,
-                             "cores": int(os.environ.get("OPENBLAS_NUM_THREADS", "1")),
-                             "kind": "oracle",
-                             "sample": f"{args.steps} steps of {per_step} proposals from a seeded "
-                                       f"n={n0} configuration"},
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
+def merge_accumulators(torch, dist, acc, device):
+    """The measurement exchange of the multi-GPU path (chains shard by rank): an
+    all-reduce (sum) of the G(tau) sums, squares, bin sums and counts, then the
+    pooled mean and its binned standard error."""
+    import numpy as np
+    shape = acc["sum"].shape
+    flat = np.concatenate([acc[k].ravel() for k in ("sum", "sumsq", "bin_sum", "bin_sumsq")]
+                          + [np.array([acc["n_meas"], acc["n_bins"]], dtype=np.float64)])
+    t = torch.tensor(flat, dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    v = t.cpu().numpy()
+    size = int(np.prod(shape))
+    parts = [v[i * size:(i + 1) * size].reshape(shape) for i in range(4)]
+    n_meas, n_bins = float(v[4 * size]), float(v[4 * size + 1])
+    return pooled_estimate(parts[0], parts[2], parts[3], n_meas, n_bins)
 
 
+def pooled_estimate(s, bs, bq, n_meas, n_bins):
+    """Mean = sum / measurements; error = spread of the bin means / sqrt(bins)."""
+    import numpy as np
+    mean = s / max(n_meas, 1.0)
+    if n_bins >= 2:
+        bm = bs / n_bins
+        var = np.maximum(bq / n_bins - bm * bm, 0.0) * n_bins / (n_bins - 1.0)
+        err = np.sqrt(var / n_bins)
+    else:
+        err = np.full_like(mean, np.nan)
+    return mean, err, n_meas, n_bins
+
+
+# ------------------------------------------------------------------- main
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["both", "fp64", "mixed", "mixed_df64"], default="both",
                     help="both = fp64, mixed and mixed_df64 (the mixed form with its refresh "
                          "eliminating in double-float on the float32 pipe)")
-    ap.add_argument("--workload", default="cube8")
-    ap.add_argument("--K", type=float, default=256.0)
-    ap.add_argument("--k-max", dest="k_max", type=int, default=64)
-    ap.add_argument("--chains", type=int, default=8,
-                    help="chains of the cube100 workload (a smaller case for profiling)")
-    ap.add_argument("--thermalize", type=int, default=300)
-    ap.add_argument("--refresh-every", dest="refresh_every", type=int, default=REFRESH_EVERY)
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--workload", default="cube100", choices=sorted(WORKLOADS))
+    ap.add_argument("--K", type=float, default=None)
+    ap.add_argument("--k-max", dest="k_max", type=int, default=None)
+    ap.add_argument("--chains", type=int, default=None,
+                    help="chains per GPU (cube100: 8; fewer for a smaller profiling case)")
+    ap.add_argument("--thermalize", type=int, default=None)
+    ap.add_argument("--refresh-every", dest="refresh_every", type=int, default=None)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", dest="no_graph", action="store_true",
                     help="direct kernel launches instead of one CUDA graph per block")
     ap.add_argument("--autotune", default=None,
@@ -235,6 +421,8 @@ def main():
     ap.add_argument("--k-sweep", dest="k_sweep", default=None,
                     help="comma-separated k_max values: print proposals/s per k instead")
     args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -254,21 +442,36 @@ def main():
             run_k_sweep(args, pk, torch, local)
         return
     chains, meta = workload(args.workload, args.K, args.k_max, chain_id=rank, n_chains=args.chains)
+    if args.autotune is None and meta.get("autotune"):
+        args.autotune = meta["autotune"]
+    if args.thermalize is None:
+        args.thermalize = meta["thermalize"]
+    refresh = effective_refresh(meta, args)
     forms = ["fp64", "mixed", "mixed_df64"] if args.precision == "both" else [args.precision]
     results = {}
     for form in forms:
-        results[form] = measure_form(args, pk, torch, dist, chains, meta, form, local, world,
-                                     with_e2e=(form == forms[0]))
+        results[form] = measure_form(args, pk, torch, dist, chains, meta, refresh, form, local,
+                                     world, with_e2e=(form == forms[0]) and not args.no_e2e)
     prim = results[forms[0]]
     line = dict(prim["line"])
+    line["config"] = line_config(args, chains, meta, refresh)
     for form in forms[1:]:
         sec = results[form]
         line[form] = {k: sec["line"][k] for k in ("value", "ms_per_step", "dtype", "roofline",
                                                  "flush_roofline", "phase_ms_per_step",
-                                                 "drift_max_last_refresh", "near_ties",
-                                                 "tie_refreshes", "gpu_launches", "clocks")}
+                                                 "drift_max_last_refresh", "order_n",
+                                                 "near_ties", "tie_refreshes", "gpu_launches",
+                                                 "refreshes_in_timed_region", "clocks")}
         line[f"{form}_vs_fp64"] = sec["line"]["value"] / prim["line"]["value"]
         line["gpu_launches"] += sec["line"]["gpu_launches"]
+    if "mixed" in results:
+        line["flush_tensor_frac"] = results["mixed"]["line"]["flush_roofline"]["frac"]
+        line["mixed_precision_note"] = (
+            "|dN| < 1e-8 after refresh: the FP64 form's drift at a refresh is reported as "
+            "drift_max_last_refresh; in the mixed forms the refresh's float64 result is stored "
+            "in float32 (relative rounding 6e-8), and drift_max_last_refresh is the float32 "
+            "chain's drift before the refresh, so the condition holds for the refresh result, "
+            "not for the float32 N the mixed chain continues from")
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(chains, meta, args.cpu_seconds)
     if rank == 0:
@@ -290,10 +493,12 @@ def run_k_sweep(args, pk, torch, local):
     ks = [int(x) for x in args.k_sweep.split(",")]
     forms = ["fp64", "mixed"] if args.precision == "both" else [args.precision]
     rows = []
+    meta0 = None
     for form in forms:
         precision = pk.CTAUX_MIXED if form == "mixed" else pk.CTAUX_FP64
         for k in ks:
-            chains, meta = workload(args.workload, args.K, k)
+            chains, meta = workload(args.workload, args.K, k, n_chains=args.chains)
+            meta0 = meta
             ctx = pk.Context(chains, precision=precision, refresh_every=0,
                              n_tau_bins=N_TAU_BINS, n_anchors=N_ANCHORS, device=local)
             n0 = meta["n_target"] or 100
@@ -322,7 +527,8 @@ def run_k_sweep(args, pk, torch, local):
                          "accepted_per_s": acc / (ms / 1e3), "us_per_proposal": ms * 1e3 / (steps * k)})
             ctx.close()
     out = {"metric": "CT-AUX proposals/s against submatrix size k (k=1: rank-one updates)",
-           "workload": workload_name(workload(args.workload, args.K, ks[0])[0]),
+           "workload": workload_name(workload(args.workload, args.K, ks[0], n_chains=args.chains)[0],
+                                     meta0),
            "note": "no measurement, no refresh, no L2 flush; 4096 proposals per k after 512 "
                    "relaxation proposals from a seeded configuration", "rows": rows}
     for form in forms:
@@ -333,24 +539,9 @@ def run_k_sweep(args, pk, torch, local):
     print(json.dumps(out), flush=True)
 
 
-def workload_name(chains):
-    c0 = chains[0]
-    if len(chains) == 1:
-        return f"{c0.name} N_c={c0.n_c} beta={c0.beta} U={c0.U} K={c0.K} k_max={c0.k_max}, 1 chain per GPU"
-    if all(c.name == c0.name and c.n_c == c0.n_c and c.beta == c0.beta and c.U == c0.U and c.K == c0.K
-           for c in chains):
-        return (f"{c0.name} N_c={c0.n_c} beta={c0.beta} U={c0.U} K={c0.K} k_max={c0.k_max}, "
-                f"{len(chains)} chains per GPU")
-    ncs = sorted({c.n_c for c in chains})
-    return (f"{c0.name}: {len(chains)} independent chains per GPU, N_c in {ncs}, "
-            f"beta in [{min(c.beta for c in chains)}, {max(c.beta for c in chains)}], "
-            f"U in [{min(c.U for c in chains):.2f}, {max(c.U for c in chains):.2f}], "
-            f"K = 0.3 beta U N_c + 30, k_max={c0.k_max}")
-
-
-def measure_form(args, pk, torch, dist, chains, meta, form, local, world, with_e2e):
+def measure_form(args, pk, torch, dist, chains, meta, refresh, form, local, world, with_e2e):
     precision = pk.CTAUX_FP64 if form == "fp64" else pk.CTAUX_MIXED
-    ctx = pk.Context(chains, precision=precision, refresh_every=args.refresh_every,
+    ctx = pk.Context(chains, precision=precision, refresh_every=refresh,
                      n_tau_bins=N_TAU_BINS, n_anchors=N_ANCHORS, device=local,
                      refresh_df64=int(form == "mixed_df64"), use_graph=int(not args.no_graph))
     stream = torch.cuda.current_stream()
@@ -366,18 +557,39 @@ def measure_form(args, pk, torch, dist, chains, meta, form, local, world, with_e
         cand = [int(x) for x in args.autotune.split(",")]
         ks, _ = ctx.autotune_k(candidates=cand, n_blocks=8)
         k_tuned = {str(k): int((ks == k).sum()) for k in sorted(set(ks.tolist()))}
-    for _ in range(max(3, args.warmup)):
+    ctx.recompute()   # fresh N; the refresh cadence counts from here
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    # phase breakdown first: a profiled pass (CUDA events around every phase,
+    # direct launches) over one refresh period, which ends with a refresh
+    prof_steps = refresh if refresh > 0 else 16
+    work0 = ctx.work()
+    ms0, _ = ctx.phase_times()
+    ctx.set_profiling(True)
+    for i in range(prof_steps):
+        flush.zero_()
+        ctx.sweep(1, measure=True, stream=sh)
+    ctx.synchronize()
+    ctx.set_profiling(False)
+    ms1, _ = ctx.phase_times()
+    work1 = ctx.work()
+    phase_ms = ms1 - ms0
+
+    for _ in range(args.warmup):
         ctx.sweep(1, measure=True, stream=sh)
     ctx.synchronize()
 
     def accepted_total():
         return sum(sum(ctx.stats(i)["accepted"]) for i in range(len(chains)))
 
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    def refreshes_total():
+        return sum(ctx.stats(i)["refreshes"] for i in range(len(chains)))
+
     steps = args.steps
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     acc0 = accepted_total()
+    ref0 = refreshes_total()
     _, kern0 = ctx.phase_times()
     ties0 = sum(ctx.stats(i)["near_ties"] for i in range(len(chains)))
     # timed region: no phase events (and CUDA-graph launches unless --no-graph)
@@ -397,30 +609,21 @@ def measure_form(args, pk, torch, dist, chains, meta, form, local, world, with_e
     clk = clocks.stop()
     total_ms = sum(s_.elapsed_time(e_) for s_, e_ in zip(starts, ends))
     acc = accepted_total() - acc0
+    n_refreshes = (refreshes_total() - ref0) // max(1, len(chains))
     _, kern1 = ctx.phase_times()
     kernels = int((kern1 - kern0).sum())
     ties = sum(ctx.stats(i)["near_ties"] for i in range(len(chains))) - ties0
     tie_refreshes = sum(ctx.stats(i)["tie_refreshes"] for i in range(len(chains)))
+    measurement = None
     if world > 1:
         total_ms, acc = reduce_over_ranks(torch, dist, total_ms, acc, "cuda")
+        # the measurement exchange: every rank's chains pooled into one estimate
+        mean, err, n_meas, n_bins = merge_accumulators(
+            torch, dist, pool_accumulators([ctx.accumulators(i) for i in range(len(chains))]),
+            "cuda")
+        measurement = {"pooled_measurements": n_meas, "pooled_bins": n_bins,
+                       "G_local_tau0": float(mean[0, 0, 0]), "err": float(err[0, 0, 0])}
     value = acc / (total_ms / 1e3)
-
-    # phase breakdown: a further profiled pass (CUDA events around every phase,
-    # direct launches) over a whole number of refresh periods
-    prof_steps = args.refresh_every if args.refresh_every > 0 else 32
-    while prof_steps < 16:
-        prof_steps += args.refresh_every
-    work0 = ctx.work()
-    ms0, _ = ctx.phase_times()
-    ctx.set_profiling(True)
-    for i in range(prof_steps):
-        flush.zero_()
-        ctx.sweep(1, measure=True, stream=sh)
-    ctx.synchronize()
-    ctx.set_profiling(False)
-    ms1, _ = ctx.phase_times()
-    work1 = ctx.work()
-    phase_ms = ms1 - ms0
 
     # ---------------- rooflines (live CUDA-event phase times, algorithmic work from the device)
     peaks, peak_kind = load_peaks()
@@ -433,50 +636,69 @@ def measure_form(args, pk, torch, dist, chains, meta, form, local, world, with_e
                else "FP32 = 152 SMs x 128 lanes x 2 x 2.07 GHz")
     dw = {k: work1[k] - work0[k] for k in work1}
     n_sm = min(152, len(chains))   # one CTA (one SM) per chain for the Gamma growth
+    elem = 8 if precision == pk.CTAUX_FP64 else 4
 
     def roof(phase):
         sec = phase_ms[phase] / 1e3
         nm = names[phase]
         if nm == "flush_gemm":
+            r = dict(achieved=dw["flush_flop"] / sec / 1e12, unit="TFLOP/s",
+                     alg_bytes_per_step=dw["flush_bytes"] / prof_steps)
             if precision == pk.CTAUX_MIXED:
-                return dict(bound="tensor", achieved=dw["flush_flop"] / sec / 1e12, peak=tf32x3_peak,
-                            unit="TFLOP/s",
-                            peak_source=f"3xTF32 = bf16 {peak_kind} x 1100/2250 / 3 products")
-            return dict(bound="alu", achieved=dw["flush_flop"] / sec / 1e12, peak=alu_peak,
-                        unit="TFLOP/s", peak_source=alu_src)
+                r.update(bound="tensor", peak=tf32x3_peak,
+                         peak_source=f"3xTF32 = bf16 {peak_kind} x 1100/2250 / 3 products")
+            else:
+                r.update(bound="alu", peak=alu_peak, peak_source=alu_src)
+            return r
         if nm == "prep":
+            # N is read by the R~ and the G_{old,new} products: one read per spin is
+            # the algorithmic minimum
+            n_mean = meta_order_mean[0]
             return dict(bound="alu", achieved=dw["prep_flop"] / sec / 1e12, peak=alu_peak,
-                        unit="TFLOP/s", peak_source=alu_src)
+                        unit="TFLOP/s", peak_source=alu_src,
+                        alg_bytes_per_step=2.0 * elem * n_mean * n_mean * len(chains))
         if nm == "proposals":
-            return dict(bound="alu", achieved=dw["gamma_flop"] / sec / 1e12,
-                        peak=alu_peak * n_sm / 152.0, unit="TFLOP/s",
-                        peak_source=alu_src + f", {n_sm} of 152 SMs (one CTA per chain)")
+            a = dw["gamma_flop"] / sec / 1e12
+            return dict(bound="alu", achieved=a, peak=alu_peak, unit="TFLOP/s",
+                        peak_source=alu_src + "; whole GPU (the Gamma chain of a chain runs on "
+                                              "one SM: frac_of_active_sms is against the "
+                                              f"{n_sm} SMs in use)",
+                        frac_of_active_sms=a / (alu_peak * n_sm / 152.0))
         if nm == "measure":
             return dict(bound="alu", achieved=dw["meas_flop"] / sec / 1e12, peak=alu_peak,
-                        unit="TFLOP/s", peak_source=alu_src + " (estimator flops, interpolations not counted)")
+                        unit="TFLOP/s",
+                        peak_source=alu_src + " (estimator flops, interpolations not counted)")
         if nm == "refresh":
             if form == "mixed_df64":
                 # one compensated double-float multiply-add of the trailing update
                 # is 12 float32 operations (TwoProd 2, cross terms 2, TwoSum 6, 2 adds)
-                return dict(bound="alu", achieved=dw["refresh_flop"] / sec / 1e12, peak=fp32_peak / 12.0,
-                            unit="TFLOP/s",
-                            peak_source="double-float = FP32 peak / 12 float32 operations per multiply-add "
-                                        "(2 m^3 per spin)")
+                return dict(bound="alu", achieved=dw["refresh_flop"] / sec / 1e12,
+                            peak=fp32_peak / 12.0, unit="TFLOP/s",
+                            peak_source="double-float = FP32 peak / 12 float32 operations per "
+                                        "multiply-add (2 m^3 per spin)")
             return dict(bound="alu", achieved=dw["refresh_flop"] / sec / 1e12, peak=fp64_peak,
-                        unit="TFLOP/s", peak_source=f"FP64 = bf16 {peak_kind} x 1.25/2250 (2 m^3 per spin)")
+                        unit="TFLOP/s",
+                        peak_source=f"FP64 = bf16 {peak_kind} x 1.25/2250 (2 m^3 per spin)")
         # plan/gather and flush support: latency-bound, no algorithmic roofline
         return dict(bound="latency", achieved=None, peak=None, unit=None, peak_source=None)
 
+    orders = [ctx.stats(i)["n"] for i in range(len(chains))]
+    meta_order_mean = [sum(orders) / len(orders)]
     # dominant among the phases of every block; the near-tie refinement (rare by
     # construction) is reported in phase_ms_per_step only
     dom = int(phase_ms[:names.index("tie_refine")].argmax())
     r = roof(dom)
+    traffic = DRAM_TRAFFIC.get((args.workload, form, names[dom]))
     roofline = {"kernel": names[dom], "bound": r["bound"], "achieved": r["achieved"],
                 "peak": r["peak"], "unit": r["unit"],
                 "frac": r["achieved"] / r["peak"] if r["peak"] else None,
-                "traffic": DRAM_TRAFFIC.get((args.workload, form, names[dom])),
-                "peak_source": r["peak_source"],
+                "traffic": traffic, "peak_source": r["peak_source"],
                 "ms_per_step": phase_ms[dom] / prof_steps}
+    for key in ("frac_of_active_sms", "alg_bytes_per_step"):
+        if key in r:
+            roofline[key] = r[key]
+    if traffic and r.get("alg_bytes_per_step"):
+        roofline["traffic_over_alg_bytes"] = traffic / r["alg_bytes_per_step"]
     fr = roof(names.index("flush_gemm"))
     flush_roof = {"bound": fr["bound"], "achieved": fr["achieved"], "peak": fr["peak"],
                   "unit": fr["unit"], "frac": fr["achieved"] / fr["peak"],
@@ -484,46 +706,46 @@ def measure_form(args, pk, torch, dist, chains, meta, form, local, world, with_e
 
     e2e = None
     if with_e2e:
-        e2e_steps = max(5, min(steps, 50))
+        # through the public API with the result read back to the host every step:
+        # the chains' state (tables, configurations, N) stays resident by design,
+        # so no per-step input crosses to the device
+        e2e_steps = steps
         acc_e0 = accepted_total()
         t_e2e = 0.0
         d2h = 0
         for _ in range(e2e_steps):
             t0 = time.perf_counter()
             ctx.sweep(1, measure=True, stream=sh)
-            G, E, nm_ = ctx.measure_G(0)
-            ctx.stats(0)
+            nb = 0
+            for i in range(len(chains)):
+                G, E, nm_ = ctx.measure_G(i)
+                nb += 4 * G.nbytes + 3 * 8       # sums, squares, bin sums and squares, counts
             t_e2e += time.perf_counter() - t0
-            d2h = 2 * G.nbytes + 512   # sums and squares of G(tau), plus the counters
+            d2h = nb
         acc_e = accepted_total() - acc_e0
         e2e = {"value": acc_e / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 0,
                "d2h_bytes_per_step": d2h}
 
-    st = ctx.stats(0)
-    orders = [ctx.stats(i)["n"] for i in range(len(chains))]
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
             "warmup": args.warmup, "ms_per_step": total_ms / steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if precision == pk.CTAUX_FP64 else "f32",
             "data": "synthetic",
-            "config": {"workload": workload_name(chains),
-                       "order_n": st["n"] if len(chains) == 1 else
-                       {"mean": sum(orders) / len(orders), "min": int(min(orders)), "max": int(max(orders))},
-                       "precision": form,
-                       "l2": "flushed between timed steps (512 MB write)",
-                       "launch": "direct" if args.no_graph else "one CUDA graph per block and per measurement",
-                       "refresh_every": args.refresh_every, "n_tau_bins": N_TAU_BINS,
-                       "n_anchors": N_ANCHORS,
-                       "k_max": ({"autotuned (chains per k)": k_tuned} if k_tuned
-                                 else sorted({c.k_max for c in chains}))},
+            "precision": form,
+            "order_n": {"mean": sum(orders) / len(orders), "min": int(min(orders)),
+                        "max": int(max(orders))},
+            "k_autotuned": k_tuned,
             "roofline": roofline, "flush_roofline": flush_roof,
             "phase_ms_per_step": {names[i]: phase_ms[i] / prof_steps for i in range(len(names))},
             "phase_pass_steps": prof_steps,
+            "refreshes_in_timed_region": int(n_refreshes),
             "gpu_launches": kernels,
             "accept_rate": acc / max(1, steps * sum(c.k_max for c in chains) * world),
-            "drift_max_last_refresh": st["last_drift_max"], "near_ties": ties,
-            "tie_refreshes": tie_refreshes,
+            "drift_max_last_refresh": max(ctx.stats(i)["last_drift_max"] for i in range(len(chains))),
+            "near_ties": ties, "tie_refreshes": tie_refreshes,
             "clocks": clk}
+    if measurement is not None:
+        line["measurement"] = measurement
     if e2e is not None:
         line["e2e"] = e2e
     ctx.close()

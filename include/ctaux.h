@@ -111,6 +111,8 @@ typedef struct {
                                          GB300 runs 64x faster than float64; 0 = float64.  The
                                          matrix N^{-1} is built in float64 either way, and the
                                          near-tie fallback always eliminates in float64 */
+  int meas_bin_size;                  /* measurements per bin of the binned error of
+                                         ctaux_measure_G; 0 = 16 */
 } ctaux_params;
 
 typedef struct {
@@ -161,11 +163,28 @@ ctaux_status ctaux_init(const ctaux_params *params, ctaux_ctx **out);
  * blocks a from-scratch FP64 recomputation of N. */
 ctaux_status ctaux_sweep(ctaux_ctx *ctx, int n_sweeps, int measure, void *cuda_stream);
 
-/* Mean and naive standard error of G_sigma(class, tau bin) over the
- * measurements of one chain since the last reset; arrays [2][n_classes][n_tau_bins].
- * err_out may be NULL.  Synchronises the context's stream. */
+/* G(tau) measurement of one chain (Sec. IV D; the estimator is the row of an
+ * s=0 vertex of the extended N of Sec. IV A contracted with G0, averaged over
+ * anchor times and the sites of each displacement class).  Mean of
+ * G_sigma(class, tau bin) over the measurements since the last reset, arrays
+ * [2][n_classes][n_tau_bins], and its standard error: the spread of the means of
+ * completed bins of meas_bin_size consecutive measurements once two bins are
+ * complete (Markov-chain samples are correlated), before that the naive error
+ * of single measurements.  err_out and n_meas_out may be NULL.  Synchronises the
+ * context's stream. */
 ctaux_status ctaux_measure_G(ctaux_ctx *ctx, int chain, double *G_out, double *err_out,
                              int64_t *n_meas_out);
+
+/* Raw measurement accumulators of one chain, for merging chains or ranks:
+ * running sums of the per-measurement G estimates and of their squares, sums of
+ * the completed bin means and of their squares (arrays [2][n_classes][n_tau_bins],
+ * host, caller-owned, any may be NULL) and counts_out[3] = {measurements,
+ * completed bins, bin size} (may be NULL).  Pooled over chains or ranks by plain
+ * sums, the mean is sum/measurements and the binned error follows from the bin
+ * sums as in ctaux_measure_G.  Synchronises the context's stream. */
+ctaux_status ctaux_get_accumulators(ctaux_ctx *ctx, int chain, double *sum_out, double *sumsq_out,
+                                    double *bin_sum_out, double *bin_sumsq_out,
+                                    int64_t *counts_out);
 
 /* Zero every chain's measurement accumulators (asynchronous). */
 ctaux_status ctaux_reset_measurements(ctaux_ctx *ctx);

@@ -273,6 +273,10 @@ ctaux_status build_chains(ctaux_ctx* ctx) {
     const size_t gb = (size_t)2 * cp.n_classes * P.n_tau_bins;
     c.Gsum = dalloc<double>(ctx, gb, &err);
     c.Gsq = dalloc<double>(ctx, gb, &err);
+    c.Gbin = dalloc<double>(ctx, gb, &err);
+    c.Gbsum = dalloc<double>(ctx, gb, &err);
+    c.Gbsq = dalloc<double>(ctx, gb, &err);
+    c.bin_size = P.meas_bin_size > 0 ? P.meas_bin_size : 16;
     c.Gmeas = dalloc<double>(ctx, gb, &err);
     c.trace = dalloc<TraceRec>(ctx, std::max(1, P.trace_capacity), &err);
     c.dyn = dalloc<Dyn>(ctx, 1, &err);
@@ -417,7 +421,7 @@ ctaux_status ctaux_init(const ctaux_params* params, ctaux_ctx** out) {
     return CTAUX_EINVAL;
   if (!(params->tie_guard >= 0.0) || params->tie_guard >= 1.0) return CTAUX_EINVAL;
   if (params->n_tau_bins < 1 || params->n_anchors < 1 || params->n_anchors > 64 ||
-      params->trace_capacity < 0 || params->refresh_every < 0)
+      params->trace_capacity < 0 || params->refresh_every < 0 || params->meas_bin_size < 0)
     return CTAUX_EINVAL;
   for (int i = 0; i < params->n_chains; ++i) {
     const ctaux_chain_params& c = params->chains[i];
@@ -476,30 +480,57 @@ ctaux_status ctaux_synchronize(ctaux_ctx* ctx) {
   return check_device_status(ctx);
 }
 
-ctaux_status ctaux_measure_G(ctaux_ctx* ctx, int chain, double* G_out, double* err_out,
-                             int64_t* n_meas_out) {
-  if (!ctx || chain < 0 || chain >= (int)ctx->chains.size() || !G_out) return CTAUX_EINVAL;
+ctaux_status ctaux_get_accumulators(ctaux_ctx* ctx, int chain, double* sum_out, double* sumsq_out,
+                                    double* bin_sum_out, double* bin_sumsq_out, int64_t* counts_out) {
+  if (!ctx || chain < 0 || chain >= (int)ctx->chains.size()) return CTAUX_EINVAL;
   CUDA_TRY(ctx, cudaStreamSynchronize(ctx->last_stream));
   const ctaux_chain_params& cp = ctx->chains[chain];
   const size_t nb = (size_t)2 * cp.n_classes * ctx->params.n_tau_bins;
-  std::vector<double> sum(nb), sq(nb);
-  const double* ds = is_mixed(ctx) ? ctx->hc32[chain].Gsum : ctx->hc64[chain].Gsum;
-  const double* dq = is_mixed(ctx) ? ctx->hc32[chain].Gsq : ctx->hc64[chain].Gsq;
-  CUDA_TRY(ctx, cudaMemcpy(sum.data(), ds, nb * sizeof(double), cudaMemcpyDeviceToHost));
-  CUDA_TRY(ctx, cudaMemcpy(sq.data(), dq, nb * sizeof(double), cudaMemcpyDeviceToHost));
-  Dyn d;
-  ctaux_status r = read_dyn(ctx, chain, &d);
+  const bool mx = is_mixed(ctx);
+  const double* src[4] = {mx ? ctx->hc32[chain].Gsum : ctx->hc64[chain].Gsum,
+                          mx ? ctx->hc32[chain].Gsq : ctx->hc64[chain].Gsq,
+                          mx ? ctx->hc32[chain].Gbsum : ctx->hc64[chain].Gbsum,
+                          mx ? ctx->hc32[chain].Gbsq : ctx->hc64[chain].Gbsq};
+  double* dst[4] = {sum_out, sumsq_out, bin_sum_out, bin_sumsq_out};
+  for (int k = 0; k < 4; ++k)
+    if (dst[k]) CUDA_TRY(ctx, cudaMemcpy(dst[k], src[k], nb * sizeof(double), cudaMemcpyDeviceToHost));
+  if (counts_out) {
+    Dyn d;
+    ctaux_status r = read_dyn(ctx, chain, &d);
+    if (r != CTAUX_OK) return r;
+    counts_out[0] = d.measurements;
+    counts_out[1] = d.meas_bins;
+    counts_out[2] = mx ? ctx->hc32[chain].bin_size : ctx->hc64[chain].bin_size;
+  }
+  return CTAUX_OK;
+}
+
+ctaux_status ctaux_measure_G(ctaux_ctx* ctx, int chain, double* G_out, double* err_out,
+                             int64_t* n_meas_out) {
+  if (!ctx || chain < 0 || chain >= (int)ctx->chains.size() || !G_out) return CTAUX_EINVAL;
+  const ctaux_chain_params& cp = ctx->chains[chain];
+  const size_t nb = (size_t)2 * cp.n_classes * ctx->params.n_tau_bins;
+  std::vector<double> sum(nb), sq(nb), bs(nb), bq(nb);
+  int64_t cnt[3];
+  ctaux_status r = ctaux_get_accumulators(ctx, chain, sum.data(), sq.data(), bs.data(), bq.data(), cnt);
   if (r != CTAUX_OK) return r;
-  const double nm = (double)d.measurements;
+  const double nm = (double)cnt[0], nbins = (double)cnt[1];
   for (size_t i = 0; i < nb; ++i) {
     const double mean = nm > 0 ? sum[i] / nm : 0.0;
     G_out[i] = mean;
     if (err_out) {
-      const double var = nm > 1 ? std::max(0.0, sq[i] / nm - mean * mean) * nm / (nm - 1.0) : 0.0;
-      err_out[i] = nm > 1 ? std::sqrt(var / nm) : 0.0;
+      if (nbins >= 2) {
+        // spread of the completed bin means (binning analysis)
+        const double bm = bs[i] / nbins;
+        const double var = std::max(0.0, bq[i] / nbins - bm * bm) * nbins / (nbins - 1.0);
+        err_out[i] = std::sqrt(var / nbins);
+      } else {
+        const double var = nm > 1 ? std::max(0.0, sq[i] / nm - mean * mean) * nm / (nm - 1.0) : 0.0;
+        err_out[i] = nm > 1 ? std::sqrt(var / nm) : 0.0;
+      }
     }
   }
-  if (n_meas_out) *n_meas_out = d.measurements;
+  if (n_meas_out) *n_meas_out = cnt[0];
   return CTAUX_OK;
 }
 

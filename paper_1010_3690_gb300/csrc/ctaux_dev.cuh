@@ -60,6 +60,7 @@ struct Dyn {
   int64_t t;    // next proposal counter
   int64_t proposals[3], accepted[3];
   int64_t sweeps, measurements, order_sum;
+  int64_t meas_bins;       // completed bins of Chain::bin_size measurements
   double sign_sum;
   int64_t numeric_rejects;
   int64_t near_ties;      // mixed form: accept decisions within the guard band
@@ -135,6 +136,10 @@ struct Chain {
   double* work_logdet;       // refresh: [spin]
   double* Gsum;              // [2][n_classes][n_bins] running sums
   double* Gsq;
+  double* Gbin;              // sum over the measurements of the open bin
+  double* Gbsum;             // sums of completed bin means and of their squares
+  double* Gbsq;
+  int bin_size;              // measurements per bin of the binned error
   double* Gmeas;             // last measurement
   TraceRec* trace;
   Dyn* dyn;

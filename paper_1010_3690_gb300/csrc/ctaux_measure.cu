@@ -19,9 +19,19 @@ namespace ctaux {
 template <typename T>
 __global__ void __launch_bounds__(256) k_meas_gather(Chain<T>* chains) {
   const Chain<T>& c = chains[blockIdx.z];
-  const Dyn& d = *c.dyn;
+  Dyn& d = *c.dyn;
   if (d.status) return;
   const int spin = blockIdx.y, n = d.n, buf = d.buf, A = c.n_anchors;
+  if (blockIdx.x == 0 && spin == 0 && threadIdx.x == 0) {
+    // counters of this measurement (read by the accumulation kernel that follows)
+    d.measurements += 1;
+    d.order_sum += n;
+    d.sign_sum += (double)d.sign;
+    // both spins: v_b = N g_b (2 n^2 per anchor) and the contraction with
+    // G0(a, l) (2 flops per point, vertex and anchor)
+    const double nd = (double)n;
+    d.work_meas += 2.0 * (2.0 * nd * nd * A + 2.0 * A * (double)c.n_c * c.n_bins * nd);
+  }
   const long total = (long)n * A;
   for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (long)gridDim.x * blockDim.x) {
@@ -203,12 +213,16 @@ __global__ void __launch_bounds__(256) k_meas_eval(Chain<T>* chains, int n_chain
 
 // Per (chain, spin, class, bin), one warp: the partial sums over vertex
 // chunks, anchors and the sites of the class are split over the lanes in a
-// fixed pattern and combined by a fixed shuffle tree (deterministic).
+// fixed pattern and combined by a fixed shuffle tree (deterministic).  Besides
+// the running sums, consecutive measurements are grouped in bins of
+// Chain::bin_size; each completed bin adds its mean and the mean's square to
+// the bin accumulators (error bars of correlated Markov-chain samples).
 template <typename T>
 __global__ void k_meas_accumulate(Chain<T>* chains) {
   const Chain<T>& c = chains[blockIdx.z];
   Dyn& d = *c.dyn;
   if (d.status) return;
+  const bool closes_bin = (d.measurements % c.bin_size) == 0;  // counted by k_meas_gather
   const int spin = blockIdx.y, A = c.n_anchors, B = c.n_bins, nc = c.n_c;
   const int npts = A * nc * B;
   const int nchunks = max(1, (d.n + meas_chunk(d.n) - 1) / meas_chunk(d.n));
@@ -231,17 +245,18 @@ __global__ void k_meas_accumulate(Chain<T>* chains) {
       c.Gmeas[o] = acc;
       c.Gsum[o] += acc;
       c.Gsq[o] += acc * acc;
+      const double open = c.Gbin[o] + acc;
+      if (closes_bin) {
+        const double mean = open / (double)c.bin_size;
+        c.Gbsum[o] += mean;
+        c.Gbsq[o] += mean * mean;
+        c.Gbin[o] = 0.0;
+      } else {
+        c.Gbin[o] = open;
+      }
     }
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0 && spin == 0) {
-    d.measurements += 1;
-    d.order_sum += d.n;
-    d.sign_sum += (double)d.sign;
-    // both spins: v_b = N g_b (2 n^2 per anchor) and the contraction with
-    // G0(a, l) (2 flops per point, vertex and anchor)
-    const double n = (double)d.n;
-    d.work_meas += 2.0 * (2.0 * n * n * A + 2.0 * A * (double)c.n_c * B * n);
-  }
+  if (closes_bin && blockIdx.x == 0 && threadIdx.x == 0 && spin == 0) d.meas_bins += 1;
 }
 
 template <typename T>
@@ -252,9 +267,13 @@ __global__ void k_meas_reset(Chain<T>* chains) {
     c.Gsum[e] = 0.0;
     c.Gsq[e] = 0.0;
     c.Gmeas[e] = 0.0;
+    c.Gbin[e] = 0.0;
+    c.Gbsum[e] = 0.0;
+    c.Gbsq[e] = 0.0;
   }
   if (e == 0) {
     c.dyn->measurements = 0;
+    c.dyn->meas_bins = 0;
     c.dyn->order_sum = 0;
     c.dyn->sign_sum = 0.0;
   }

@@ -37,7 +37,7 @@ class Params(C.Structure):
                 ("trace_capacity", C.c_int), ("device", C.c_int),
                 ("mixed_flush_tc", C.c_int), ("tie_guard", C.c_double),
                 ("tie_refine_iters", C.c_int), ("use_graph", C.c_int),
-                ("refresh_df64", C.c_int)]
+                ("refresh_df64", C.c_int), ("meas_bin_size", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -80,6 +80,8 @@ def _load():
         "ctaux_init": (C.c_int, [P(Params), P(vp)]),
         "ctaux_sweep": (C.c_int, [vp, C.c_int, C.c_int, vp]),
         "ctaux_measure_G": (C.c_int, [vp, C.c_int, P(C.c_double), P(C.c_double), P(C.c_int64)]),
+        "ctaux_get_accumulators": (C.c_int, [vp, C.c_int, P(C.c_double), P(C.c_double),
+                                            P(C.c_double), P(C.c_double), P(C.c_int64)]),
         "ctaux_reset_measurements": (C.c_int, [vp]),
         "ctaux_recompute": (C.c_int, [vp, P(C.c_double)]),
         "ctaux_get_stats": (C.c_int, [vp, C.c_int, P(Stats)]),
@@ -111,7 +113,8 @@ def _load():
 
 
 lib = _load()
-EXPORTED = ("ctaux_init", "ctaux_sweep", "ctaux_measure_G", "ctaux_reset_measurements",
+EXPORTED = ("ctaux_init", "ctaux_sweep", "ctaux_measure_G", "ctaux_get_accumulators",
+            "ctaux_reset_measurements",
             "ctaux_recompute", "ctaux_get_stats", "ctaux_get_trace", "ctaux_get_config",
             "ctaux_set_config", "ctaux_get_N", "ctaux_set_profiling", "ctaux_get_phase_times",
             "ctaux_get_work", "ctaux_philox_uniforms", "ctaux_synchronize", "ctaux_destroy",
@@ -161,7 +164,8 @@ class Context:
 
     def __init__(self, chains, precision=CTAUX_FP64, refresh_every=32, p_insert=0.5, p_flip=0.0,
                  n_tau_bins=32, n_anchors=4, trace_capacity=0, device=0, mixed_flush_tc=1,
-                 tie_guard=1e-4, tie_refine_iters=0, refresh_df64=0, use_graph=0):
+                 tie_guard=1e-4, tie_refine_iters=0, refresh_df64=0, use_graph=0,
+                 meas_bin_size=0):
         self._keep = []
         cps = (ChainParams * len(chains))()
         self.chain_inputs = list(chains)
@@ -175,7 +179,8 @@ class Context:
                                  int(ch.chain_id))
         self.params = Params(len(chains), cps, precision, refresh_every, p_insert, p_flip,
                              n_tau_bins, n_anchors, trace_capacity, device, mixed_flush_tc,
-                             tie_guard, tie_refine_iters, int(use_graph), int(refresh_df64))
+                             tie_guard, tie_refine_iters, int(use_graph), int(refresh_df64),
+                             int(meas_bin_size))
         self.n_tau_bins = n_tau_bins
         self.trace_capacity = trace_capacity
         h = C.c_void_p()
@@ -218,6 +223,18 @@ class Context:
         nm = C.c_int64()
         self._check(lib.ctaux_measure_G(self.h, chain, _dp(G), _dp(E), C.byref(nm)), "measure_G")
         return G, E, nm.value
+
+    def accumulators(self, chain=0):
+        """Raw sums for merging chains or ranks: dict of sum, sumsq, bin_sum,
+        bin_sumsq ([2, n_classes, n_tau_bins]) and n_meas, n_bins, bin_size."""
+        ch = self.chain_inputs[chain]
+        shape = (2, np.asarray(ch.table).shape[1], self.n_tau_bins)
+        arrs = [np.empty(shape) for _ in range(4)]
+        cnt = np.zeros(3, np.int64)
+        self._check(lib.ctaux_get_accumulators(self.h, chain, *(_dp(a) for a in arrs), _lp(cnt)),
+                    "get_accumulators")
+        return dict(sum=arrs[0], sumsq=arrs[1], bin_sum=arrs[2], bin_sumsq=arrs[3],
+                    n_meas=int(cnt[0]), n_bins=int(cnt[1]), bin_size=int(cnt[2]))
 
     def reset_measurements(self):
         self._check(lib.ctaux_reset_measurements(self.h), "reset_measurements")
