@@ -260,6 +260,8 @@ def run_reference(args, rank, world):
     from oracle.ctaux import OracleChain
     from workloads import configs
     chains, meta = workload(args.workload, args.K, args.k_max, n_chains=args.chains)
+    if args.order is not None:
+        meta.update(start_order=args.order, n_target=args.order)
     refresh = effective_refresh(meta, args)
     ch = chains[0]
     n0 = meta["n_target"] or 0
@@ -409,6 +411,9 @@ def main():
     ap.add_argument("--chains", type=int, default=None,
                     help="chains per GPU (cube100: 8; fewer for a smaller profiling case)")
     ap.add_argument("--thermalize", type=int, default=None)
+    ap.add_argument("--order", type=int, default=None,
+                    help="start order of the chains (and of the oracle's sample); a smaller "
+                         "case for profiling")
     ap.add_argument("--refresh-every", dest="refresh_every", type=int, default=None)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -442,6 +447,8 @@ def main():
             run_k_sweep(args, pk, torch, local)
         return
     chains, meta = workload(args.workload, args.K, args.k_max, chain_id=rank, n_chains=args.chains)
+    if args.order is not None:
+        meta.update(start_order=args.order, n_target=args.order)
     if args.autotune is None and meta.get("autotune"):
         args.autotune = meta["autotune"]
     if args.thermalize is None:
