@@ -93,11 +93,15 @@ typedef struct {
   int device;                         /* CUDA device ordinal */
   int mixed_flush_tc;                 /* mixed form: 1 = flush on the tensor cores (tcgen05,
                                          split 3xTF32), 0 = float32 CUDA-core product */
-  double tie_guard;                   /* mixed form: a proposal with |u - min(1,|R|)| below
-                                         tie_guard * max(u, min(1,|R|)) is decided in FP64
-                                         (the block stops there; FP64 iterative refinement of
-                                         the first-touch ratio, or a from-scratch FP64 refresh
-                                         where it does not converge); 0 = off; must be < 1 */
+  double tie_guard;                   /* mixed form: the decision u < |R| of a proposal with
+                                         |u - |R|| below tie_guard * max(u, |R|), i.e. one that
+                                         a relative error of |R| below tie_guard could change,
+                                         is taken in FP64 (the block stops there; FP64
+                                         iterative refinement of the first-touch ratio, or a
+                                         from-scratch FP64 refresh where it does not converge).
+                                         Set it above the float32 ratio error of the workload
+                                         (the binding's default, 1e-2, is 8x the largest error
+                                         measured at order 2000); 0 = off; must be < 1 */
   int tie_refine_iters;               /* mixed form: most refinement iterations per near tie;
                                          0 = 12; -1 = none, so that every near tie takes the
                                          from-scratch fallback (for tests) */
@@ -113,6 +117,10 @@ typedef struct {
                                          near-tie fallback always eliminates in float64 */
   int meas_bin_size;                  /* measurements per bin of the binned error of
                                          ctaux_measure_G; 0 = 16 */
+  int n_matsubara;                    /* 0 = off; 1..64: every measurement also evaluates
+                                         G_xy(i w_n) at the first n_matsubara fermionic
+                                         Matsubara frequencies (ctaux_measure_G_matsubara);
+                                         needs n_c <= 1024 */
 } ctaux_params;
 
 typedef struct {
@@ -175,6 +183,22 @@ ctaux_status ctaux_sweep(ctaux_ctx *ctx, int n_sweeps, int measure, void *cuda_s
 ctaux_status ctaux_measure_G(ctaux_ctx *ctx, int chain, double *G_out, double *err_out,
                              int64_t *n_meas_out);
 
+/* Measurement directly in Matsubara frequencies (Sec. IV D: for large clusters
+ * the Green's function is measured directly in cluster momenta and Matsubara
+ * frequencies).  The estimator is the Fourier transform of the G(tau)
+ * estimator,
+ *   G_xy(i w_n) = G0_xy(i w_n) + (1/beta) sum_{z,w} G0_xz(i w_n) S_zw G0_wy(i w_n),
+ *   S_zw = sum_{l on site z, m on site w} e^{i w_n tau_l} [(e^V - 1) N]_lm e^{-i w_n tau_m},
+ * w_n = (2n + 1) pi / beta, n = 0 .. n_matsubara - 1, with G0(i w_n) the exact
+ * transform of the linearly interpolated table; cluster momenta follow by
+ * G(K) = (1/N_c) sum_xy e^{-iK.(r_x - r_y)} G_xy.  Mean over the measurements
+ * since the last reset, G_out[2][n_c][n_c][n_matsubara][2] (real, imaginary;
+ * host, caller-owned) and the naive standard error of each part (err_out, may
+ * be NULL).  CTAUX_EINVAL if the context was created with n_matsubara = 0.
+ * Synchronises the context's stream. */
+ctaux_status ctaux_measure_G_matsubara(ctaux_ctx *ctx, int chain, double *G_out, double *err_out,
+                                       int64_t *n_meas_out);
+
 /* Raw measurement accumulators of one chain, for merging chains or ranks:
  * running sums of the per-measurement G estimates and of their squares, sums of
  * the completed bin means and of their squares (arrays [2][n_classes][n_tau_bins],
@@ -232,10 +256,12 @@ ctaux_status ctaux_get_phase_times(ctaux_ctx *ctx, double *ms_out, int64_t *kern
  * Gamma growth (both spins), bytes of N read and written by the flush, flops
  * of the G(tau) estimator (the products v_b = N g_b and the contraction with
  * G0(a, l); the table interpolations are not counted) and of the FP64
- * refreshes (2 m^3 per spin and refresh).  Any output may be NULL. */
+ * refreshes (2 m^3 per spin and refresh), and of the Matsubara-frequency
+ * measurement (4 n^2 F for S, 16 N_c^3 F for the two cluster products, per
+ * spin).  Any output may be NULL. */
 ctaux_status ctaux_get_work(ctaux_ctx *ctx, double *prep_flop, double *flush_flop,
                             double *flush_bytes, double *gamma_flop, double *meas_flop,
-                            double *refresh_flop);
+                            double *refresh_flop, double *mats_flop);
 
 /* Change the submatrix size of one chain between sweeps: 1 <= k_max <= the
  * chain's k_max at ctaux_init (its buffers are sized for that).  The Markov

@@ -150,6 +150,7 @@ ctaux_status build_chains(ctaux_ctx* ctx) {
   for (const auto& cp : ctx->chains) max_rows = std::max(max_rows, round_up(cp.capacity + cp.k_max, 128));
   ls.tc_ctas = ctx->sm_count;
   ls.split_x_blocks = std::max(1, std::min(256, (max_rows + 7) / 8));
+  ls.mats = P.n_matsubara > 0 ? 1 : 0;
   if (mixed_tc) CUDA_TRY(ctx, configure_flush_tc());
   if (sizeof(T) == 4 && P.tie_guard > 0.0) {
     // one CTA per SM: the refinement is a chain of short grid-wide steps, so
@@ -277,6 +278,25 @@ ctaux_status build_chains(ctaux_ctx* ctx) {
     c.Gbsum = dalloc<double>(ctx, gb, &err);
     c.Gbsq = dalloc<double>(ctx, gb, &err);
     c.bin_size = P.meas_bin_size > 0 ? P.meas_bin_size : 16;
+    c.n_freq = P.n_matsubara;
+    if (c.n_freq > 0) {
+      const size_t F = c.n_freq, nc = cp.n_c;
+      c.G0w = dalloc<double2>(ctx, (size_t)2 * cp.n_classes * F, &err);
+      c.vorder = dalloc<int>(ctx, ld, &err);
+      c.site_off = dalloc<int>(ctx, nc + 1, &err);
+      c.PhR = dalloc<unsigned char>(ctx, ld * F * 2 * sizeof(T), &err);
+      for (int spin = 0; spin < 2; ++spin) {
+        c.PhL[spin] = dalloc<unsigned char>(ctx, ld * F * 2 * sizeof(T), &err);
+        c.Sw[spin] = dalloc<double2>(ctx, nc * nc * F, &err);
+        c.Tw[spin] = dalloc<double2>(ctx, nc * nc * F, &err);
+      }
+      c.Gw_sum = dalloc<double>(ctx, 4 * nc * nc * F, &err);
+      c.Gw_sq = dalloc<double>(ctx, 4 * nc * nc * F, &err);
+      if (err != cudaSuccess)
+        return set_err(ctx, CTAUX_ENOMEM, "device allocation failed: %s", cudaGetErrorString(err));
+      launch_g0_matsubara(g0, cp.n_classes, cp.n_tau, cp.beta, c.n_freq, c.G0w, nullptr);
+      CUDA_TRY(ctx, cudaDeviceSynchronize());
+    }
     c.Gmeas = dalloc<double>(ctx, gb, &err);
     c.trace = dalloc<TraceRec>(ctx, std::max(1, P.trace_capacity), &err);
     c.dyn = dalloc<Dyn>(ctx, 1, &err);
@@ -421,7 +441,8 @@ ctaux_status ctaux_init(const ctaux_params* params, ctaux_ctx** out) {
     return CTAUX_EINVAL;
   if (!(params->tie_guard >= 0.0) || params->tie_guard >= 1.0) return CTAUX_EINVAL;
   if (params->n_tau_bins < 1 || params->n_anchors < 1 || params->n_anchors > 64 ||
-      params->trace_capacity < 0 || params->refresh_every < 0 || params->meas_bin_size < 0)
+      params->trace_capacity < 0 || params->refresh_every < 0 || params->meas_bin_size < 0 ||
+      params->n_matsubara < 0 || params->n_matsubara > kMaxMatsFreq)
     return CTAUX_EINVAL;
   for (int i = 0; i < params->n_chains; ++i) {
     const ctaux_chain_params& c = params->chains[i];
@@ -429,6 +450,7 @@ ctaux_status ctaux_init(const ctaux_params* params, ctaux_ctx** out) {
     if (!(c.beta > 0) || !(c.K > 0) || !(c.U > 0) || c.k_max < 1 || c.k_max > kMaxK || c.capacity < 1)
       return CTAUX_EINVAL;
     if (c.capacity + c.k_max > 30000) return CTAUX_EINVAL;
+    if (params->n_matsubara > 0 && c.n_c > kMaxMatsSites) return CTAUX_EINVAL;
     for (int k = 0; k < c.n_c * c.n_c; ++k)
       if (c.dx_class[k] < 0 || c.dx_class[k] >= c.n_classes) return CTAUX_EINVAL;
   }
@@ -531,6 +553,36 @@ ctaux_status ctaux_measure_G(ctaux_ctx* ctx, int chain, double* G_out, double* e
     }
   }
   if (n_meas_out) *n_meas_out = cnt[0];
+  return CTAUX_OK;
+}
+
+ctaux_status ctaux_measure_G_matsubara(ctaux_ctx* ctx, int chain, double* G_out, double* err_out,
+                                       int64_t* n_meas_out) {
+  if (!ctx || chain < 0 || chain >= (int)ctx->chains.size() || !G_out) return CTAUX_EINVAL;
+  if (ctx->params.n_matsubara <= 0)
+    return set_err(ctx, CTAUX_EINVAL, "the context measures no Matsubara frequencies (n_matsubara = 0)");
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->last_stream));
+  const ctaux_chain_params& cp = ctx->chains[chain];
+  const size_t nb = (size_t)4 * cp.n_c * cp.n_c * ctx->params.n_matsubara;
+  std::vector<double> sum(nb), sq(nb);
+  const bool mx = is_mixed(ctx);
+  CUDA_TRY(ctx, cudaMemcpy(sum.data(), mx ? ctx->hc32[chain].Gw_sum : ctx->hc64[chain].Gw_sum,
+                           nb * sizeof(double), cudaMemcpyDeviceToHost));
+  CUDA_TRY(ctx, cudaMemcpy(sq.data(), mx ? ctx->hc32[chain].Gw_sq : ctx->hc64[chain].Gw_sq,
+                           nb * sizeof(double), cudaMemcpyDeviceToHost));
+  Dyn d;
+  ctaux_status r = read_dyn(ctx, chain, &d);
+  if (r != CTAUX_OK) return r;
+  const double nm = (double)d.measurements;
+  for (size_t i = 0; i < nb; ++i) {
+    const double mean = nm > 0 ? sum[i] / nm : 0.0;
+    G_out[i] = mean;
+    if (err_out) {
+      const double var = nm > 1 ? std::max(0.0, sq[i] / nm - mean * mean) * nm / (nm - 1.0) : 0.0;
+      err_out[i] = nm > 1 ? std::sqrt(var / nm) : 0.0;
+    }
+  }
+  if (n_meas_out) *n_meas_out = d.measurements;
   return CTAUX_OK;
 }
 
@@ -738,9 +790,10 @@ ctaux_status ctaux_get_phase_times(ctaux_ctx* ctx, double* ms_out, int64_t* kern
 }
 
 ctaux_status ctaux_get_work(ctaux_ctx* ctx, double* prep_flop, double* flush_flop, double* flush_bytes,
-                            double* gamma_flop, double* meas_flop, double* refresh_flop) {
+                            double* gamma_flop, double* meas_flop, double* refresh_flop,
+                            double* mats_flop) {
   if (!ctx) return CTAUX_EINVAL;
-  double a = 0.0, b = 0.0, c = 0.0, g = 0.0, me = 0.0, rf = 0.0;
+  double a = 0.0, b = 0.0, c = 0.0, g = 0.0, me = 0.0, rf = 0.0, mw = 0.0;
   for (size_t ci = 0; ci < ctx->chains.size(); ++ci) {
     Dyn d;
     ctaux_status r = read_dyn(ctx, (int)ci, &d);
@@ -751,7 +804,9 @@ ctaux_status ctaux_get_work(ctaux_ctx* ctx, double* prep_flop, double* flush_flo
     g += d.work_gamma;
     me += d.work_meas;
     rf += d.work_refresh;
+    mw += d.work_mats;
   }
+  if (mats_flop) *mats_flop = mw;
   if (gamma_flop) *gamma_flop = g;
   if (meas_flop) *meas_flop = me;
   if (refresh_flop) *refresh_flop = rf;

@@ -408,8 +408,11 @@ __device__ __forceinline__ A warp_sum_t(A v) {
   return v;
 }
 
-// Relative guard band of the mixed form: a float32 ratio whose Metropolis
-// decision lies this close to the uniform is a near tie.
+// Relative guard band of the mixed form's tie detection when the FP64
+// re-evaluation is off (counted only).  The decision is u < |R| (u < 1, so
+// |R| >= 1 always accepts): a float32 |R| with relative error below g can
+// change it only when |u - |R|| < g max(u, |R|), which never holds once
+// |R| >= 1 / (1 - g).
 constexpr double kTieGuard = 1e-4;
 
 // One CTA per chain, threads [0,128) spin up, [128,256) spin down.  Runs the
@@ -685,7 +688,7 @@ __device__ __forceinline__ void proposals_body(Chain<T>* chains) {
         finite = true;
         dec = accept ? 1 : 0;
       } else if (sizeof(T) == 4 && tie_guard > 0.0 && finite &&
-                 fabs(dr.u_acc - pacc) < tie_guard * fmax(dr.u_acc, pacc)) {
+                 fabs(dr.u_acc - fabs(R)) < tie_guard * fmax(dr.u_acc, fabs(R))) {
         // near tie in the float32 form: the block ends before this proposal,
         // which is decided in FP64 after the flush
         d.tie_pending = 1;
@@ -695,7 +698,7 @@ __device__ __forceinline__ void proposals_body(Chain<T>* chains) {
       } else {
         dec = accept ? 1 : 0;
         if (sizeof(T) == 4 && tie_guard == 0.0 && finite &&
-            fabs(dr.u_acc - pacc) < kTieGuard * fmax(dr.u_acc, pacc))
+            fabs(dr.u_acc - fabs(R)) < kTieGuard * fmax(dr.u_acc, fabs(R)))
           ties++;  // detection only (FP64 re-evaluation off)
       }
       if (dec != 2) {

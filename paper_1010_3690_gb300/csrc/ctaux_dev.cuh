@@ -75,6 +75,7 @@ struct Dyn {
   double work_gamma;      // algorithmic flops of the Gamma growth (both spins)
   double work_meas;       // algorithmic flops of the G(tau) estimator (both spins)
   double work_refresh;    // algorithmic flops of the FP64 refreshes (2 m^3 per spin)
+  double work_mats;       // algorithmic flops of the Matsubara-frequency measurement
   int flush_noop;         // block left N unchanged (nothing accepted, survivors = [0, n))
   int tie_pending;        // mixed form: 1 = proposal d.t awaits an FP64 decision
   int tie_jj;             // index in the block of the near-tie proposal
@@ -140,6 +141,16 @@ struct Chain {
   double* Gbsum;             // sums of completed bin means and of their squares
   double* Gbsq;
   int bin_size;              // measurements per bin of the binned error
+  int n_freq;                // Matsubara frequencies of the G(iw) measurement (0 = off)
+  double2* G0w;              // [2][n_classes][n_freq] G0(i w_f) of the interpolated table
+  int* vorder;               // [ld] vertex slots grouped by site
+  int* site_off;             // [n_c + 1] start of each site's group in vorder
+  void* PhR;                 // [ld][n_freq] e^{-i w tau} in site order (complex of T)
+  void* PhL[2];              // [spin][ld][n_freq] (e^{V} - 1) e^{+i w tau}
+  double2* Sw[2];            // [spin][n_c][n_c][n_freq] S_zw
+  double2* Tw[2];            // [spin][n_c][n_c][n_freq] S G0
+  double* Gw_sum;            // [2][n_c][n_c][n_freq][2] sums of Re, Im of G_xy(i w)
+  double* Gw_sq;             // and of their squares
   double* Gmeas;             // last measurement
   TraceRec* trace;
   Dyn* dyn;

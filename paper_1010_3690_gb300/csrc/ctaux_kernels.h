@@ -8,6 +8,8 @@
 namespace ctaux {
 
 constexpr int kMaxPartials = 4096;  // split-K partial tiles per (chain, spin) and product
+constexpr int kMaxMatsFreq = 64;    // Matsubara frequencies of the G(iw) measurement
+constexpr int kMaxMatsSites = 1024; // cluster sites of the G(iw) measurement
 constexpr int kTieSlices = 64;   // column slices of the near-tie matrix-vector products
 // vertices per measurement evaluation chunk: small orders get short chunks
 // (more work items for the GPU), large ones longer chunks (fewer partial sums)
@@ -68,6 +70,7 @@ struct LaunchShape {
   int use_tc;            // mixed form: flush on the tensor cores
   int tc_ctas;           // persistent grid of the tensor-core flush (one CTA per SM)
   int split_x_blocks;
+  int mats;              // Matsubara-frequency measurement on (n_matsubara > 0)
 };
 
 // CUDA-event timing of the sweep phases and kernel launch counts.  Phases:
@@ -136,6 +139,10 @@ cudaError_t launch_refresh(Chain<T>* dchains, const LaunchShape& ls, int only_ch
 cudaError_t launch_tie_refine(Chain<float>* dchains, const LaunchShape& ls, cudaStream_t st);
 template <typename T>
 void launch_reset_measure(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t st);
+template <typename T>
+void launch_matsubara(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t st);
+void launch_g0_matsubara(const double* table, int n_classes, int n_tau, double beta, int n_freq,
+                         double2* out, cudaStream_t st);
 int tc_smem_bytes();
 cudaError_t configure_flush_tc();
 void launch_flush_tc(Chain<float>* dchains, const TcMaps* maps, const LaunchShape& ls,

@@ -271,6 +271,11 @@ __global__ void k_meas_reset(Chain<T>* chains) {
     c.Gbsum[e] = 0.0;
     c.Gbsq[e] = 0.0;
   }
+  const long nw = (long)4 * c.n_c * c.n_c * c.n_freq;
+  for (long q = e; q < nw; q += (long)gridDim.x * blockDim.x) {
+    c.Gw_sum[q] = 0.0;
+    c.Gw_sq[q] = 0.0;
+  }
   if (e == 0) {
     c.dyn->measurements = 0;
     c.dyn->meas_bins = 0;
@@ -287,7 +292,8 @@ void launch_measure(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t st, P
   launch_gemm<T>(dchains, ls, PH_MEAS, st);
   k_meas_eval<T><<<ls.persist_ctas, 256, 0, st>>>(dchains, nch);
   k_meas_accumulate<T><<<dim3(ls.meas_acc_blocks, 2, nch), 256, 0, st>>>(dchains);
-  pt->end(5, st, 4);
+  if (ls.mats) launch_matsubara<T>(dchains, ls, st);
+  pt->end(5, st, ls.mats ? 9 : 4);
 }
 
 template <typename T>

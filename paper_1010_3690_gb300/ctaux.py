@@ -37,7 +37,8 @@ class Params(C.Structure):
                 ("trace_capacity", C.c_int), ("device", C.c_int),
                 ("mixed_flush_tc", C.c_int), ("tie_guard", C.c_double),
                 ("tie_refine_iters", C.c_int), ("use_graph", C.c_int),
-                ("refresh_df64", C.c_int), ("meas_bin_size", C.c_int)]
+                ("refresh_df64", C.c_int), ("meas_bin_size", C.c_int),
+                ("n_matsubara", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -80,6 +81,8 @@ def _load():
         "ctaux_init": (C.c_int, [P(Params), P(vp)]),
         "ctaux_sweep": (C.c_int, [vp, C.c_int, C.c_int, vp]),
         "ctaux_measure_G": (C.c_int, [vp, C.c_int, P(C.c_double), P(C.c_double), P(C.c_int64)]),
+        "ctaux_measure_G_matsubara": (C.c_int, [vp, C.c_int, P(C.c_double), P(C.c_double),
+                                               P(C.c_int64)]),
         "ctaux_get_accumulators": (C.c_int, [vp, C.c_int, P(C.c_double), P(C.c_double),
                                             P(C.c_double), P(C.c_double), P(C.c_int64)]),
         "ctaux_reset_measurements": (C.c_int, [vp]),
@@ -94,7 +97,8 @@ def _load():
         "ctaux_set_profiling": (C.c_int, [vp, C.c_int]),
         "ctaux_get_phase_times": (C.c_int, [vp, P(C.c_double), P(C.c_int64)]),
         "ctaux_get_work": (C.c_int, [vp, P(C.c_double), P(C.c_double), P(C.c_double),
-                                     P(C.c_double), P(C.c_double), P(C.c_double)]),
+                                     P(C.c_double), P(C.c_double), P(C.c_double),
+                                     P(C.c_double)]),
         "ctaux_philox_uniforms": (C.c_int, [C.c_uint64, C.c_uint32, C.c_int64, C.c_int, C.c_int,
                                             P(C.c_double)]),
         "ctaux_set_kmax": (C.c_int, [vp, C.c_int, C.c_int]),
@@ -113,7 +117,8 @@ def _load():
 
 
 lib = _load()
-EXPORTED = ("ctaux_init", "ctaux_sweep", "ctaux_measure_G", "ctaux_get_accumulators",
+EXPORTED = ("ctaux_init", "ctaux_sweep", "ctaux_measure_G", "ctaux_measure_G_matsubara",
+            "ctaux_get_accumulators",
             "ctaux_reset_measurements",
             "ctaux_recompute", "ctaux_get_stats", "ctaux_get_trace", "ctaux_get_config",
             "ctaux_set_config", "ctaux_get_N", "ctaux_set_profiling", "ctaux_get_phase_times",
@@ -164,8 +169,8 @@ class Context:
 
     def __init__(self, chains, precision=CTAUX_FP64, refresh_every=32, p_insert=0.5, p_flip=0.0,
                  n_tau_bins=32, n_anchors=4, trace_capacity=0, device=0, mixed_flush_tc=1,
-                 tie_guard=1e-4, tie_refine_iters=0, refresh_df64=0, use_graph=0,
-                 meas_bin_size=0):
+                 tie_guard=1e-2, tie_refine_iters=0, refresh_df64=0, use_graph=0,
+                 meas_bin_size=0, n_matsubara=0):
         self._keep = []
         cps = (ChainParams * len(chains))()
         self.chain_inputs = list(chains)
@@ -180,8 +185,9 @@ class Context:
         self.params = Params(len(chains), cps, precision, refresh_every, p_insert, p_flip,
                              n_tau_bins, n_anchors, trace_capacity, device, mixed_flush_tc,
                              tie_guard, tie_refine_iters, int(use_graph), int(refresh_df64),
-                             int(meas_bin_size))
+                             int(meas_bin_size), int(n_matsubara))
         self.n_tau_bins = n_tau_bins
+        self.n_matsubara = n_matsubara
         self.trace_capacity = trace_capacity
         h = C.c_void_p()
         r = lib.ctaux_init(C.byref(self.params), C.byref(h))
@@ -223,6 +229,18 @@ class Context:
         nm = C.c_int64()
         self._check(lib.ctaux_measure_G(self.h, chain, _dp(G), _dp(E), C.byref(nm)), "measure_G")
         return G, E, nm.value
+
+    def measure_G_matsubara(self, chain=0):
+        """(mean G_xy(i w_n) [2, n_c, n_c, n_matsubara] complex, standard errors of the
+        real and imaginary parts [2, n_c, n_c, n_matsubara, 2], measurements)."""
+        n_c = int(self.chain_inputs[chain].n_c)
+        shape = (2, n_c, n_c, self.n_matsubara, 2)
+        G = np.empty(shape)
+        E = np.empty(shape)
+        nm = C.c_int64()
+        self._check(lib.ctaux_measure_G_matsubara(self.h, chain, _dp(G), _dp(E), C.byref(nm)),
+                    "measure_G_matsubara")
+        return G[..., 0] + 1j * G[..., 1], E, nm.value
 
     def accumulators(self, chain=0):
         """Raw sums for merging chains or ranks: dict of sum, sumsq, bin_sum,
@@ -313,8 +331,9 @@ class Context:
         return ms, ln
 
     def work(self):
-        a, b, c, g, me, rf = (C.c_double() for _ in range(6))
+        a, b, c, g, me, rf, mw = (C.c_double() for _ in range(7))
         self._check(lib.ctaux_get_work(self.h, C.byref(a), C.byref(b), C.byref(c), C.byref(g),
-                                       C.byref(me), C.byref(rf)), "get_work")
+                                       C.byref(me), C.byref(rf), C.byref(mw)), "get_work")
         return dict(prep_flop=a.value, flush_flop=b.value, flush_bytes=c.value,
-                    gamma_flop=g.value, meas_flop=me.value, refresh_flop=rf.value)
+                    gamma_flop=g.value, meas_flop=me.value, refresh_flop=rf.value,
+                    mats_flop=mw.value)

@@ -35,7 +35,8 @@ def _start(ctx, chains, order, seed0=1000):
 
 
 def _check_N_is_inverse(ctx, chain, oc_like, rtol):
-    """N of the chain's current configuration against inverse(N^{-1}(config))."""
+    """Property check at any size: the chain's N against the inverse of N^{-1}
+    built (Eq. Nmatrix) from the configuration the chain ends in."""
     cfg = ctx.get_config(chain)
     worst = 0.0
     for spin in (0, 1):
@@ -97,7 +98,11 @@ def test_sq36_full_size_block_parity(name, prec, rtol):
         recs = oc.run(len(tr))
         worst = compare_traces(tr, recs, rtol)
         compare_config(ctx, 0, oc)
-        nerr = _check_N_is_inverse(ctx, 0, oc, 1e-8 if prec == 0 else 1e-4)
+        nerr = 0.0
+        for spin in (0, 1):
+            No = oc.N(spin)
+            nerr = max(nerr, np.abs(ctx.get_N(0, spin) - No).max() / np.abs(No).max())
+        assert nerr <= (1e-8 if prec == 0 else 1e-4), nerr
         st = ctx.stats(0)
         print(f"sq36 {name}: {len(tr)} proposals, worst ratio error {worst:.2e}, "
               f"near ties {st['near_ties']}, N error {nerr:.2e}, sign {st['sign']}")
@@ -106,20 +111,25 @@ def test_sq36_full_size_block_parity(name, prec, rtol):
 @pytest.mark.parametrize("prec", [0, 1])
 def test_k256_whole_blocks_against_oracle(prec):
     """k_max = 256 (Gamma^{-1} of 2 x 256 x 257 entries, kept in global memory)
-    over two whole blocks of the 2x2x2 cluster at order 430."""
+    over three blocks of the 2x2x2 cluster at order 430.  In the mixed form a
+    block ends early at a near tie (decided in FP64 and applied by the next
+    block), so its trace holds at most 3 x 256 records."""
     ch = configs.cube8(K=256.0, k_max=256, capacity=1024)
     cfg = configs.synthetic_configuration(ch, 430, seed=5)
     oc = oracle_for(ch)
     oc.set_config(cfg["tau"], cfg["site"], cfg["s"], cfg["birth"], cfg["t"])
-    with pk.Context([ch], precision=prec, trace_capacity=512, refresh_every=0) as ctx:
+    with pk.Context([ch], precision=prec, trace_capacity=768, refresh_every=0) as ctx:
         ctx.set_config(0, cfg["tau"], cfg["site"], cfg["s"], cfg["birth"], cfg["t"])
-        ctx.sweep(2)
+        ctx.sweep(3)
         ctx.synchronize()
         tr = ctx.trace(0)
-        assert len(tr) == 512
-        worst = compare_traces(tr, oc.run(512), RTOL64 if prec == 0 else RTOL_MIXED)
+        st = ctx.stats(0)
+        assert len(tr) == 768 if prec == 0 else 256 < len(tr) <= 768
+        worst = compare_traces(tr, oc.run(len(tr)), RTOL64 if prec == 0 else RTOL_MIXED)
+        assert st["t"] == oc.t
         compare_config(ctx, 0, oc)
-        print(f"cube8 k=256 precision {prec}: worst ratio error {worst:.2e}")
+        print(f"cube8 k=256 precision {prec}: {len(tr)} proposals, worst ratio error {worst:.2e}, "
+              f"near ties {st['near_ties']}")
 
 
 def test_batch_chains_of_every_cluster_size_against_oracle():
@@ -179,7 +189,7 @@ def test_measurement_above_1024_vertices(prec):
         ctx.sweep(1, measure=True)
         G, E, nm = ctx.measure_G(0)
         assert nm == 1
-        oc.run(ch.k_max)
+        oc.run(ctx.stats(0)["t"] - oc.t)   # a near tie can end the block early
         compare_config(ctx, 0, oc)
         assert oc.order > 1024
         ref = oc.measure_G(12, 3)
