@@ -121,6 +121,16 @@ typedef struct {
                                          G_xy(i w_n) at the first n_matsubara fermionic
                                          Matsubara frequencies (ctaux_measure_G_matsubara);
                                          needs n_c <= 1024 */
+  double drift_limit;                 /* > 0: a from-scratch recomputation whose drift
+                                         max |N_run - N_fresh| / max |N_fresh| exceeds it makes
+                                         the next synchronous call return CTAUX_EDRIFT once (the
+                                         chain continues from the fresh N); 0 = off */
+  int tc_wait_limit;                  /* mixed form, tensor-core flush: most polls of one
+                                         pipeline wait before the kernel stops with
+                                         CTAUX_ETIMEOUT; 0 = 2^24 (seconds).  A negative value
+                                         is a test of that path: the MMA issuer first waits
+                                         -tc_wait_limit polls on a barrier that nothing
+                                         completes, so every flush reports CTAUX_ETIMEOUT */
 } ctaux_params;
 
 typedef struct {
@@ -140,6 +150,7 @@ typedef struct {
   int64_t refreshes;
   double last_drift_max;     /* max |N_run - N_fresh| at the last refresh (both spins) */
   double last_drift_fro;     /* Frobenius norm of the same difference */
+  double last_drift_rel;     /* last_drift_max / max |N_fresh| */
   double logdet[2];          /* log|det N_sigma^{-1}| at the last refresh */
   int sign;                  /* current walker sign */
   int status;                /* device fault bits (0 = none) */

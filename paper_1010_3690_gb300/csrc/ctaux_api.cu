@@ -151,6 +151,7 @@ ctaux_status build_chains(ctaux_ctx* ctx) {
   ls.tc_ctas = ctx->sm_count;
   ls.split_x_blocks = std::max(1, std::min(256, (max_rows + 7) / 8));
   ls.mats = P.n_matsubara > 0 ? 1 : 0;
+  ls.tc_wait_limit = P.tc_wait_limit;
   if (mixed_tc) CUDA_TRY(ctx, configure_flush_tc());
   if (sizeof(T) == 4 && P.tie_guard > 0.0) {
     // one CTA per SM: the refinement is a chain of short grid-wide steps, so
@@ -269,7 +270,8 @@ ctaux_status build_chains(ctaux_ctx* ctx) {
     c.pcol = dalloc<int>(ctx, 2 * ld, &err);
     if (c.pcol) CUDA_TRY(ctx, cudaMemset(c.pcol, 0xFF, 2 * ld * sizeof(int)));
     c.pkeys = dalloc<unsigned long long>(ctx, 2 * ld, &err);
-    c.work_drift = dalloc<double>(ctx, 2, &err);
+    c.work_drift = dalloc<double>(ctx, 3, &err);
+    c.drift_limit = P.drift_limit;
     c.work_logdet = dalloc<double>(ctx, 2, &err);
     const size_t gb = (size_t)2 * cp.n_classes * P.n_tau_bins;
     c.Gsum = dalloc<double>(ctx, gb, &err);
@@ -326,6 +328,8 @@ ctaux_status build_chains(ctaux_ctx* ctx) {
 
 ctaux_status check_device_status(ctaux_ctx* ctx) {
   const bool mixed = is_mixed(ctx);
+  int drift_chain = -1;
+  double drift_rel = 0.0;
   for (size_t ci = 0; ci < ctx->chains.size(); ++ci) {
     Dyn* dp = mixed ? ctx->hc32[ci].dyn : ctx->hc64[ci].dyn;
     int st = 0;
@@ -335,8 +339,23 @@ ctaux_status check_device_status(ctaux_ctx* ctx) {
     if (st & DS_SINGULAR)
       return set_err(ctx, CTAUX_ESINGULAR, "chain %zu: zero pivot in the FP64 recomputation", ci);
     if (st & DS_INDEX) return set_err(ctx, CTAUX_EINVAL, "chain %zu: vertex selection out of range", ci);
+    if (st & DS_TIMEOUT)
+      return set_err(ctx, CTAUX_ETIMEOUT, "chain %zu: a bounded wait of the tensor-core flush gave up", ci);
     if (st) return set_err(ctx, CTAUX_ENUMERIC, "chain %zu: device status %d", ci, st);
+    int ex = 0;
+    CUDA_TRY(ctx, cudaMemcpy(&ex, &dp->drift_exceeded, sizeof(int), cudaMemcpyDeviceToHost));
+    if (ex && drift_chain < 0) {
+      drift_chain = (int)ci;
+      CUDA_TRY(ctx, cudaMemcpy(&drift_rel, &dp->drift_rel, sizeof(double), cudaMemcpyDeviceToHost));
+    }
+    if (ex) {
+      const int zero = 0;   // reported once
+      CUDA_TRY(ctx, cudaMemcpy(&dp->drift_exceeded, &zero, sizeof(int), cudaMemcpyHostToDevice));
+    }
   }
+  if (drift_chain >= 0)
+    return set_err(ctx, CTAUX_EDRIFT, "chain %d: relative drift %.3e at a refresh above the limit %.3e",
+                   drift_chain, drift_rel, ctx->params.drift_limit);
   return CTAUX_OK;
 }
 
@@ -442,7 +461,8 @@ ctaux_status ctaux_init(const ctaux_params* params, ctaux_ctx** out) {
   if (!(params->tie_guard >= 0.0) || params->tie_guard >= 1.0) return CTAUX_EINVAL;
   if (params->n_tau_bins < 1 || params->n_anchors < 1 || params->n_anchors > 64 ||
       params->trace_capacity < 0 || params->refresh_every < 0 || params->meas_bin_size < 0 ||
-      params->n_matsubara < 0 || params->n_matsubara > kMaxMatsFreq)
+      params->n_matsubara < 0 || params->n_matsubara > kMaxMatsFreq ||
+      !(params->drift_limit >= 0.0))
     return CTAUX_EINVAL;
   for (int i = 0; i < params->n_chains; ++i) {
     const ctaux_chain_params& c = params->chains[i];
@@ -637,6 +657,7 @@ ctaux_status ctaux_get_stats(ctaux_ctx* ctx, int chain, ctaux_stats* out) {
   out->refreshes = d.refreshes;
   out->last_drift_max = d.drift_max;
   out->last_drift_fro = d.drift_fro;
+  out->last_drift_rel = d.drift_rel;
   out->logdet[0] = d.logdet[0];
   out->logdet[1] = d.logdet[1];
   out->sign = d.sign;
@@ -741,6 +762,11 @@ ctaux_status ctaux_set_config(ctaux_ctx* ctx, int chain, const double* tau, cons
   ctaux_status r = is_mixed(ctx) ? do_refresh<float>(ctx, chain, ctx->last_stream)
                                  : do_refresh<double>(ctx, chain, ctx->last_stream);
   if (r != CTAUX_OK) return r;
+  // the drift of this refresh compares N of the previous configuration with the
+  // new one: it is not a drift of the chain
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->last_stream));
+  const int zero = 0;
+  CUDA_TRY(ctx, cudaMemcpy(&dyn_of(ctx, chain)->drift_exceeded, &zero, sizeof(int), cudaMemcpyHostToDevice));
   return ctaux_synchronize(ctx);
 }
 

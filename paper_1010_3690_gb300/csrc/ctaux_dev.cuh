@@ -66,6 +66,8 @@ struct Dyn {
   int64_t near_ties;      // mixed form: accept decisions within the guard band
   int64_t refreshes;
   double drift_max, drift_fro;
+  double drift_rel;       // drift_max / max |N_fresh| at the last refresh
+  int drift_exceeded;     // a refresh saw drift_rel above Chain::drift_limit (not yet reported)
   double logdet[2];
   int64_t trace_written;  // total records written
   int64_t trace_read;     // records handed to the host
@@ -133,7 +135,8 @@ struct Chain {
   int8_t* used;              // refresh pivot flags [spin][ld]
   int* pcol;                 // refresh: column at which a row was pivoted, -1 if not [spin][ld]
   unsigned long long* pkeys; // refresh pivot keys [spin][ld]
-  double* work_drift;        // refresh: max, sum of squares
+  double* work_drift;        // refresh: max, sum of squares of the drift, max |N_fresh|
+  double drift_limit;        // relative drift that a refresh reports as CTAUX_EDRIFT (0 = off)
   double* work_logdet;       // refresh: [spin]
   double* Gsum;              // [2][n_classes][n_bins] running sums
   double* Gsq;

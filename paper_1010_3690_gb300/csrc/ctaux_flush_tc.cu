@@ -27,10 +27,13 @@
 //     columns), subtracts from the staged N[S_m][S_n] and writes the compacted
 //     N', then releases the accumulator and the staged input, so that the
 //     epilogue of one tile overlaps the loads and MMAs of the next.
-// Every mbarrier wait is bounded.  On timeout the chain's status gets
-// DS_TIMEOUT and every role stops; before the CTA exits, the copies issued
-// are waited for (bounded), the MMA thread waits for its MMAs, and the TMEM
-// is freed.
+// Every mbarrier wait is bounded: the pipeline roles poll at most `wl` times
+// (a launch argument, 2^24 unless the context sets a smaller limit), the
+// final drains always 2^24 times.  On timeout the chain's status gets
+// DS_TIMEOUT (CTAUX_ETIMEOUT) and every role stops; before the CTA exits, the
+// copies issued are waited for, the MMA thread waits for its MMAs, and the
+// TMEM is freed.  With `stall` set (a test of this path) the MMA issuer first
+// waits on a barrier that nothing completes, so every launch times out.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -66,8 +69,8 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes)
                : "memory");
 }
-__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity) {
-  for (uint32_t i = 0; i < kWaitLimit; ++i) {
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, uint32_t limit = kWaitLimit) {
+  for (uint32_t i = 0; i < limit; ++i) {
     uint32_t ok;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -203,7 +206,8 @@ __device__ __forceinline__ bool ns_staged(const int* S, int m0, int nn, int& x0)
 
 // Barrier completion c (0-based) of an mbarrier has parity c & 1.
 __global__ void __launch_bounds__(kTcThreads, 1) k_flush_tc(Chain<float>* chains, int n_chains,
-                                                            const TcMaps* maps) {
+                                                            const TcMaps* maps, uint32_t wl,
+                                                            int stall) {
   __shared__ int off[kMaxChains + 1];
   for (int ci = threadIdx.x; ci < n_chains; ci += blockDim.x) off[ci] = tc_items(*chains[ci].dyn);
   __syncthreads();
@@ -223,7 +227,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_flush_tc(Chain<float>* chains
   uint64_t* drain = accempty + 2;
   uint64_t* nsfull = drain + 1;
   uint64_t* nsempty = nsfull + 1;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(nsempty + 1);
+  uint64_t* never = nsempty + 1;  // completed by nothing (the test stall)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(never + 1);
   volatile int* err_s = reinterpret_cast<volatile int*>(tmem_slot + 1);
   uint32_t* mma_taken = reinterpret_cast<uint32_t*>(tmem_slot + 2);  // stages the MMA thread waited for
   uint32_t* ns_issued = reinterpret_cast<uint32_t*>(tmem_slot + 3);  // tiles the loader staged
@@ -247,6 +252,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_flush_tc(Chain<float>* chains
     mbar_init(smem_u32(drain), 1);
     mbar_init(smem_u32(nsfull), 1);
     mbar_init(smem_u32(nsempty), 8);
+    mbar_init(smem_u32(never), 1);
     *err_s = 0;
     *mma_taken = 0;
     *ns_issued = 0;
@@ -267,7 +273,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_flush_tc(Chain<float>* chains
       const TcMaps& mp = maps[t.ci * 2 + t.spin];
       for (int kc = 0; kc < t.nk; ++kc) {
         const uint32_t stage = issued % kTcStages, use = issued / kTcStages;
-        if (use > 0 && !mbar_wait(smem_u32(empty + stage), (use - 1) & 1)) {
+        if (use > 0 && !mbar_wait(smem_u32(empty + stage), (use - 1) & 1, wl)) {
           *err_s = 1;
           atomicOr(&chains[t.ci].dyn->status, DS_TIMEOUT);
           break;
@@ -285,16 +291,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_flush_tc(Chain<float>* chains
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer
     uint32_t taken = 0, q = 0;
+    if (stall && !mbar_wait(smem_u32(never), 0, wl)) {
+      // test of the bounded waits: a barrier that nothing completes
+      *err_s = 1;
+      atomicOr(&chains[find_chain(off, n_chains, blockIdx.x)].dyn->status, DS_TIMEOUT);
+    }
     for (int w = blockIdx.x; w < total && !*err_s; w += gridDim.x) {
       const TcItem t = tc_item(chains, off, n_chains, w);
       if (t.nk == 0) continue;
       const uint32_t b = q & 1, ub = q >> 1;
-      bool ok = ub == 0 || mbar_wait(smem_u32(accempty + b), (ub - 1) & 1);
+      bool ok = ub == 0 || mbar_wait(smem_u32(accempty + b), (ub - 1) & 1, wl);
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t acc = tmem + b * kTcBN;
       for (int kc = 0; kc < t.nk && ok; ++kc) {
         const uint32_t stage = taken % kTcStages, use = taken / kTcStages;
-        if (!mbar_wait(smem_u32(full + stage), use & 1)) {
+        if (!mbar_wait(smem_u32(full + stage), use & 1, wl)) {
           ok = false;
           break;
         }
@@ -347,7 +358,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_flush_tc(Chain<float>* chains
       }
       const TcMaps& mp = maps[t.ci * 2 + t.spin];
       const int buf = c.dyn->buf;
-      if (nq > 0 && !__all_sync(0xffffffffu, mbar_wait(smem_u32(nsempty), (nq - 1) & 1))) {
+      if (nq > 0 && !__all_sync(0xffffffffu, mbar_wait(smem_u32(nsempty), (nq - 1) & 1, wl))) {
         if (lane == 0) {
           *err_s = 1;
           atomicOr(&c.dyn->status, DS_TIMEOUT);
@@ -388,7 +399,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_flush_tc(Chain<float>* chains
       const bool staged = ns_staged(S, t.m0, nn, x0);
       const int srow = row_ok ? __ldg(S + m) : x0;  // rows past the end read a valid slot
       const float* nsrow = ns + (srow - x0);  // staged N[srow][S[n0 + j]] at nsrow[j * kTcNsRows]
-      if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(nsfull), nq & 1))) {
+      if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(nsfull), nq & 1, wl))) {
         if (lane == 0) {
           *err_s = 1;
           atomicOr(&c.dyn->status, DS_TIMEOUT);
@@ -409,7 +420,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_flush_tc(Chain<float>* chains
         continue;
       }
       const uint32_t b = q & 1, ub = q >> 1;
-      const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(accfull + b), ub & 1));
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(accfull + b), ub & 1, wl));
       if (!ok) {
         if (lane == 0) {
           *err_s = 1;
@@ -476,7 +487,10 @@ cudaError_t configure_flush_tc() {
 void launch_flush_tc(Chain<float>* dchains, const TcMaps* maps, const LaunchShape& ls,
                      cudaStream_t st) {
   k_flush_split_x<<<dim3(ls.split_x_blocks, 2, ls.n_chains), 256, 0, st>>>(dchains);
-  k_flush_tc<<<ls.tc_ctas, kTcThreads, tc_smem_bytes(), st>>>(dchains, ls.n_chains, maps);
+  const int lim = ls.tc_wait_limit;
+  const uint32_t wl = lim > 0 ? (uint32_t)lim : lim < 0 ? (uint32_t)(-(int64_t)lim) : kWaitLimit;
+  k_flush_tc<<<ls.tc_ctas, kTcThreads, tc_smem_bytes(), st>>>(dchains, ls.n_chains, maps, wl,
+                                                              lim < 0 ? 1 : 0);
 }
 
 // Host: the TMA descriptors of one (chain, spin): K-major float32 operand

@@ -71,6 +71,7 @@ struct LaunchShape {
   int tc_ctas;           // persistent grid of the tensor-core flush (one CTA per SM)
   int split_x_blocks;
   int mats;              // Matsubara-frequency measurement on (n_matsubara > 0)
+  int tc_wait_limit;     // polls of a tensor-core flush pipeline wait (0: 2^24)
 };
 
 // CUDA-event timing of the sweep phases and kernel launch counts.  Phases:

@@ -126,7 +126,7 @@ __device__ void refresh_body(Chain<T>* chains, int n_chains, int only_chain, int
   __shared__ int max_m_s;
   __shared__ E Ps[32][kPB + 1];
   __shared__ E Rs[kPB][33];
-  __shared__ double red[2][8];
+  __shared__ double red[3][8];
 
   if (threadIdx.x == 0) max_m_s = 0;
   __syncthreads();
@@ -299,7 +299,7 @@ __device__ void refresh_body(Chain<T>* chains, int n_chains, int only_chain, int
     T* Nr = c.N[buf][spin];
     double* N64 = (filter == 1) ? c.N64[spin] : nullptr;
     const int pj = perm[j];
-    double dmax = 0.0, dsq = 0.0;
+    double dmax = 0.0, dsq = 0.0, nmax = 0.0;
     for (int cc = threadIdx.x; cc < m; cc += blockDim.x) {
       const double v = el_to(X[(size_t)j * ld + perm[cc]]);  // N[cc][perm[j]]
       const long o = (long)pj * ld + cc;
@@ -307,28 +307,36 @@ __device__ void refresh_body(Chain<T>* chains, int n_chains, int only_chain, int
       const double diff = fabs((double)Nr[o] - v);
       dmax = fmax(dmax, diff);
       dsq += diff * diff;
+      nmax = fmax(nmax, fabs(v));
       Nr[o] = (T)v;
     }
     for (int o = 16; o > 0; o >>= 1) {
       dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
       dsq += __shfl_xor_sync(0xffffffffu, dsq, o);
+      nmax = fmax(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
     }
     __syncthreads();
     if ((threadIdx.x & 31) == 0) {
       red[0][threadIdx.x >> 5] = dmax;
       red[1][threadIdx.x >> 5] = dsq;
+      red[2][threadIdx.x >> 5] = nmax;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-      double bm = 0.0, bs = 0.0;
+      double bm = 0.0, bs = 0.0, bn = 0.0;
       for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
         bm = fmax(bm, red[0][w]);
         bs += red[1][w];
+        bn = fmax(bn, red[2][w]);
       }
+      // non-negative doubles order like their bit patterns
       if (bm > 0.0)
         atomicMax(reinterpret_cast<unsigned long long*>(&c.work_drift[0]),
                   (unsigned long long)__double_as_longlong(bm));
       if (bs > 0.0) atomicAdd(&c.work_drift[1], bs);
+      if (bn > 0.0)
+        atomicMax(reinterpret_cast<unsigned long long*>(&c.work_drift[2]),
+                  (unsigned long long)__double_as_longlong(bn));
     }
   }
   grid.sync();  // every column has read perm before the flags are cleared
@@ -351,8 +359,11 @@ __device__ __forceinline__ void refresh_finish_one(const Chain<T>& c, int filter
   d.work_refresh += 4.0 * (double)d.n * (double)d.n * (double)d.n;  // 2 m^3 per spin
   d.drift_max = c.work_drift[0];
   d.drift_fro = sqrt(c.work_drift[1]);
+  d.drift_rel = c.work_drift[2] > 0.0 ? c.work_drift[0] / c.work_drift[2] : 0.0;
+  if (c.drift_limit > 0.0 && d.drift_rel > c.drift_limit) d.drift_exceeded = 1;
   c.work_drift[0] = 0.0;
   c.work_drift[1] = 0.0;
+  c.work_drift[2] = 0.0;
   for (int spin = 0; spin < 2; ++spin) d.logdet[spin] = c.work_logdet[spin];
 }
 
