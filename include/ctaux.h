@@ -99,9 +99,10 @@ typedef struct {
                                          is taken in FP64 (the block stops there; FP64
                                          iterative refinement of the first-touch ratio, or a
                                          from-scratch FP64 refresh where it does not converge).
-                                         Set it above the float32 ratio error of the workload
-                                         (the binding's default, 1e-2, is 8x the largest error
-                                         measured at order 2000); 0 = off; must be < 1 */
+                                         Each chain widens its band to 16x the largest float32
+                                         ratio error that its FP64 near-tie decisions have
+                                         shown (at most 0.05; ctaux_stats.tie_guard_eff);
+                                         0 = off; must be < 1 */
   int tie_refine_iters;               /* mixed form: most refinement iterations per near tie;
                                          0 = 12; -1 = none, so that every near tie takes the
                                          from-scratch fallback (for tests) */
@@ -125,6 +126,11 @@ typedef struct {
                                          max |N_run - N_fresh| / max |N_fresh| exceeds it makes
                                          the next synchronous call return CTAUX_EDRIFT once (the
                                          chain continues from the fresh N); 0 = off */
+  int mixed_prep_tc;                  /* mixed form with mixed_flush_tc: 1 = the prep products
+                                         (rows of the extended N and G columns of the new
+                                         vertices, Sec. IV A) on the tensor cores, split 3xTF32;
+                                         the flush and the refresh then also keep N^T; 0 =
+                                         float32 CUDA-core products.  Needs capacity + k_max > 96 */
   int tc_wait_limit;                  /* mixed form, tensor-core flush: most polls of one
                                          pipeline wait before the kernel stops with
                                          CTAUX_ETIMEOUT; 0 = 2^24 (seconds).  A negative value
@@ -154,6 +160,11 @@ typedef struct {
   double logdet[2];          /* log|det N_sigma^{-1}| at the last refresh */
   int sign;                  /* current walker sign */
   int status;                /* device fault bits (0 = none) */
+  double tie_err_max;        /* mixed form: largest relative error of a float32 R against its
+                                FP64 value, over the near ties decided in FP64 */
+  double tie_guard_eff;      /* mixed form: the chain's guard band now, max(tie_guard,
+                                min(0.05, 16 tie_err_max)): it widens when a near tie shows a
+                                float32 ratio error above 1/16 of it */
 } ctaux_stats;
 
 typedef struct {

@@ -153,6 +153,12 @@ ctaux_status build_chains(ctaux_ctx* ctx) {
   ls.mats = P.n_matsubara > 0 ? 1 : 0;
   ls.tc_wait_limit = P.tc_wait_limit;
   if (mixed_tc) CUDA_TRY(ctx, configure_flush_tc());
+  // prep products on the tensor cores: the flush keeps N^T for them; every
+  // chain's N must hold one 128-row TMA box
+  bool prep_tc = mixed_tc && P.mixed_prep_tc != 0;
+  for (const auto& cp : ctx->chains) prep_tc = prep_tc && round_up(cp.capacity + cp.k_max, 32) >= 128;
+  ls.prep_tc = prep_tc ? 1 : 0;
+  if (prep_tc) CUDA_TRY(ctx, configure_prep_tc());
   if (sizeof(T) == 4 && P.tie_guard > 0.0) {
     // one CTA per SM: the refinement is a chain of short grid-wide steps, so
     // barrier latency (which grows with the number of CTAs) dominates
@@ -228,10 +234,12 @@ ctaux_status build_chains(ctaux_ctx* ctx) {
       c.birth[b] = dalloc<int64_t>(ctx, ld, &err);
     }
     c.s0 = dalloc<int8_t>(ctx, ld, &err);
+    // panel rows: k_max, or whole 128-row TMA boxes for the tensor-core prep
+    const size_t KR = prep_tc ? (size_t)round_up(std::max(cp.k_max, 128), 128) : K;
     for (int spin = 0; spin < 2; ++spin) {
-      c.Cpan[spin] = dalloc<T>(ctx, K * ld, &err);
-      c.Bpan[spin] = dalloc<T>(ctx, ld * K, &err);
-      c.Gcol[spin] = dalloc<T>(ctx, ld * K, &err);
+      c.Cpan[spin] = dalloc<T>(ctx, KR * ld, &err);
+      c.Bpan[spin] = dalloc<T>(ctx, ld * KR, &err);
+      c.Gcol[spin] = dalloc<T>(ctx, ld * KR, &err);
       c.Ginv[spin] = dalloc<T>(ctx, K * (K + 1), &err);
       c.lam[spin] = dalloc<double>(ctx, K, &err);
       c.Y[spin] = dalloc<T>(ctx, ld * K, &err);
@@ -259,6 +267,17 @@ ctaux_status build_chains(ctaux_ctx* ctx) {
                                         reinterpret_cast<float*>(c.N[1][spin]), c.ld);
         if (me != cudaSuccess)
           return set_err(ctx, CTAUX_ECUDA, "tensor map encoding failed (%s)", cudaGetErrorString(me));
+        if (prep_tc) {
+          for (int b = 0; b < 2; ++b) c.NT[b][spin] = dalloc<float>(ctx, ld * ld, &err);
+          if (err != cudaSuccess)
+            return set_err(ctx, CTAUX_ENOMEM, "device allocation failed: %s", cudaGetErrorString(err));
+          me = encode_prep_maps(&host_maps[2 * ci + spin], reinterpret_cast<float*>(c.Cpan[spin]),
+                                reinterpret_cast<float*>(c.Bpan[spin]), reinterpret_cast<float*>(c.Gcol[spin]),
+                                (int)KR, reinterpret_cast<float*>(c.N[0][spin]),
+                                reinterpret_cast<float*>(c.N[1][spin]), c.NT[0][spin], c.NT[1][spin], c.ld);
+          if (me != cudaSuccess)
+            return set_err(ctx, CTAUX_ECUDA, "prep tensor map encoding failed (%s)", cudaGetErrorString(me));
+        }
       }
     }
     c.P = dalloc<int>(ctx, K, &err);
@@ -308,6 +327,7 @@ ctaux_status build_chains(ctaux_ctx* ctx) {
     std::memset(&d0, 0, sizeof(d0));
     d0.sign = 1;
     d0.forced_t = -1;
+    d0.guard_eff = c.tie_guard;
     CUDA_TRY(ctx, cudaMemcpy(c.dyn, &d0, sizeof(Dyn), cudaMemcpyHostToDevice));
   }
   if (mixed_tc) {
@@ -658,6 +678,8 @@ ctaux_status ctaux_get_stats(ctaux_ctx* ctx, int chain, ctaux_stats* out) {
   out->last_drift_max = d.drift_max;
   out->last_drift_fro = d.drift_fro;
   out->last_drift_rel = d.drift_rel;
+  out->tie_err_max = d.tie_err_max;
+  out->tie_guard_eff = d.guard_eff;
   out->logdet[0] = d.logdet[0];
   out->logdet[1] = d.logdet[1];
   out->sign = d.sign;

@@ -529,7 +529,7 @@ __device__ __forceinline__ void proposals_body(Chain<T>* chains) {
   for (int e = tid; e < KM; e += 256) bd_s[e] = c.draws[e];
   // read once: the decision of a near tie taken in FP64 after the previous block
   const int64_t forced_t = (sizeof(T) == 4) ? d.forced_t : -1;
-  const double tie_guard = c.tie_guard;
+  const double tie_guard = (sizeof(T) == 4 && c.tie_guard > 0.0) ? d.guard_eff : 0.0;
   const int trace_cap = c.trace_cap;
   const int64_t trace_base = d.trace_written;
   __syncthreads();
@@ -693,6 +693,7 @@ __device__ __forceinline__ void proposals_body(Chain<T>* chains) {
         // which is decided in FP64 after the flush
         d.tie_pending = 1;
         d.tie_jj = jj;
+        d.tie_R32 = R;
         ties++;
         dec = 2;
       } else {
@@ -1082,10 +1083,17 @@ void launch_block(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t st, Pha
   k_gather<T><<<dim3(ls.gather_slices, 2, nch), 256, 0, st>>>(dchains);
   pt->end(0, st, 2);
   pt->begin(1, st);
-  launch_gemm<T>(dchains, ls, PH_RTILDE, st);
-  launch_gemm<T>(dchains, ls, PH_GCOL_OLD, st);
-  launch_gemm<T>(dchains, ls, PH_GCOL_NEW, st);
-  pt->end(1, st, 3);
+  bool prep_tc = false;
+  if constexpr (std::is_same<T, float>::value) prep_tc = ls.prep_tc != 0;
+  if (prep_tc) {
+    if constexpr (std::is_same<T, float>::value) launch_prep_tc(dchains, maps, ls, st);
+    pt->end(1, st, 2);
+  } else {
+    launch_gemm<T>(dchains, ls, PH_RTILDE, st);
+    launch_gemm<T>(dchains, ls, PH_GCOL_OLD, st);
+    launch_gemm<T>(dchains, ls, PH_GCOL_NEW, st);
+    pt->end(1, st, 3);
+  }
   pt->begin(2, st);
   if (ls.gamma_in_smem) k_proposals_smem<T><<<nch, 256, ls.prop_smem, st>>>(dchains);
   else k_proposals<T><<<nch, 256, ls.prop_smem, st>>>(dchains);

@@ -86,6 +86,9 @@ struct Dyn {
   int64_t tie_refreshes;  // near ties decided through a from-scratch refresh (refinement failed)
   double forced_ratio[2];
   double forced_R;
+  double tie_R32;         // mixed form: float32 R of the pending near tie
+  double tie_err_max;     // largest |R_float32 - R_FP64| / |R_FP64| seen at near ties
+  double guard_eff;       // the chain's guard band: max(tie_guard, min(0.05, 16 tie_err_max))
 };
 
 template <typename T>
@@ -107,6 +110,7 @@ struct Chain {
   const int* dx_class;       // [n_c][n_c]
   const double* class_weight;  // [n_classes] 1/(n_anchors * #sites of the class)
   T* N[2][2];                // [buf][spin]
+  float* NT[2][2];           // mixed form with the tensor-core prep: N^T [buf][spin], ld x ld
   double* tau[2];
   int* site[2];
   int8_t* s[2];

@@ -39,115 +39,22 @@
 
 #include "ctaux_dev.cuh"
 #include "ctaux_kernels.h"
+#include "ctaux_tc.cuh"
 
 namespace ctaux {
 
 namespace {
 
-constexpr int kRowBytes = kTcBK * 4;            // one K-major operand row
-constexpr int kTileBytes = kTcBM * kRowBytes;   // one 128 x 16 float32 operand tile
-static_assert(kRowBytes == 64 || kRowBytes == 128, "operand rows are one swizzle span");
+using namespace tc;
 constexpr int kStageBytes = 4 * kTileBytes;     // Ah, Al, Bh, Bl
 constexpr int kNsSlotBytes = kTcNsRows * 4;     // one staged column segment
 constexpr int kNsBytes = kTcBN * kNsSlotBytes;  // the staged input of one tile
+static_assert(kTcBK == kBK && kTcBM == 128 && kTcBN == 128, "the shared descriptors' tile");
 static_assert(kNsSlotBytes % 128 == 0, "staged column segments must stay 128-byte aligned");
 static_assert(kTcBN % kTcNsGroup == 0 && kTcBN / kTcNsGroup <= 32, "one column group per lane");
-constexpr uint32_t kWaitLimit = 1u << 24;
 constexpr uint32_t kTmemCols = 2 * kTcBN;       // two accumulators
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t a) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, uint32_t limit = kWaitLimit) {
-  for (uint32_t i = 0; i < limit; ++i) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (ok) return true;
-  }
-  return false;
-}
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
-                                            uint32_t mbar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-          dst),
-      "l"((uint64_t)map), "r"(x), "r"(y), "r"(mbar)
-      : "memory");
-}
-
-// Shared-memory matrix descriptor: K-major, rows of kRowBytes swizzled over
-// their own width (64- or 128-byte swizzle), 8-row groups 8 rows apart.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);   // start address
-  d |= (uint64_t)(16u >> 4) << 16;            // leading byte offset (unused for this layout)
-  d |= (uint64_t)((8u * kRowBytes) >> 4) << 32;  // stride byte offset
-  d |= (uint64_t)1 << 46;                     // descriptor version
-  d |= (uint64_t)(kRowBytes == 128 ? 2 : 4) << 61;  // 128- or 64-byte swizzle
-  return d;
-}
-
-// Instruction descriptor, kind::tf32: D float32, A and B tf32, both K-major,
-// N = 128, M = 128.
-constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTcBN >> 3) << 17) |
-                            ((uint32_t)(kTcBM >> 4) << 24);
-
-__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-      "l"(a), "l"(b), "r"(kIdesc), "r"(acc)
-      : "memory");
-}
-__device__ __forceinline__ void mma_commit(uint32_t mbar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                   mbar)
-               : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
-      "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
-      "%30, %31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
 }  // namespace
-
-// float32 -> (hi, lo) tf32 pair, hi rounded to nearest (cvt.rna.tf32.f32).
-__device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
-  uint32_t h, l;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
-  hi = __uint_as_float(h);
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(x - hi));
-  lo = __uint_as_float(l);
-}
 
 // X = N[P, S] as K-major split rows: Xh/Xl[b * KP + r], zero for r >= k_acc.
 // One warp per output row b.
@@ -392,6 +299,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_flush_tc(Chain<float>* chains
       const int ld = c.ld, nn = t.nn;
       const float* Nb = c.N[d.buf][t.spin];
       float* out = c.N[1 - d.buf][t.spin];
+      float* outT = c.NT[1 - d.buf][t.spin];  // N'^T for the tensor-core prep (or null)
       const int* S = c.S;
       const int m = t.m0 + quarter * 32 + lane;
       const bool row_ok = m < nn;
@@ -411,9 +319,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_flush_tc(Chain<float>* chains
         if (row_ok)
           for (int j = colhalf * 64; j < colhalf * 64 + 64; ++j) {
             const int n = t.n0 + j;
-            if (n < nn)
-              out[(long)n * ld + m] =
-                  staged ? nsrow[j * kTcNsRows] : Nb[(long)__ldg(S + n) * ld + srow];
+            if (n < nn) {
+              const float val = staged ? nsrow[j * kTcNsRows] : Nb[(long)__ldg(S + n) * ld + srow];
+              out[(long)n * ld + m] = val;
+              if (outT) outT[(long)m * ld + n] = val;
+            }
           }
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(nsempty));
@@ -447,8 +357,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_flush_tc(Chain<float>* chains
         if (row_ok) {
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
+            v[j] = cin[j] - v[j];
             const int n = t.n0 + cc * 32 + j;
-            if (n < nn) out[(long)n * ld + m] = cin[j] - v[j];
+            if (n < nn) out[(long)n * ld + m] = v[j];
+          }
+          if (outT) {
+            // row m of N' is a contiguous run of N'^T: 128 bytes per thread
+            const int nb0 = t.n0 + cc * 32;
+            float* dstT = outT + (long)m * ld + nb0;
+            if (nb0 + 32 <= nn) {
+#pragma unroll
+              for (int q4 = 0; q4 < 8; ++q4)
+                reinterpret_cast<float4*>(dstT)[q4] =
+                    make_float4(v[4 * q4], v[4 * q4 + 1], v[4 * q4 + 2], v[4 * q4 + 3]);
+            } else {
+#pragma unroll
+              for (int j = 0; j < 32; ++j)
+                if (nb0 + j < nn) dstT[j] = v[j];
+            }
           }
         }
       }
@@ -491,6 +417,44 @@ void launch_flush_tc(Chain<float>* dchains, const TcMaps* maps, const LaunchShap
   const uint32_t wl = lim > 0 ? (uint32_t)lim : lim < 0 ? (uint32_t)(-(int64_t)lim) : kWaitLimit;
   k_flush_tc<<<ls.tc_ctas, kTcThreads, tc_smem_bytes(), st>>>(dchains, ls.n_chains, maps, wl,
                                                               lim < 0 ? 1 : 0);
+}
+
+namespace {
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                     cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return nullptr;
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  return encode;
+}
+}  // namespace
+
+// Host: the prep's TMA descriptors of one (chain, spin): rows of ld float32
+// (the panels C, B and the G columns with panel_rows rows; both buffers of N
+// and of N^T with ld rows), boxes of 128 rows x kTcBK float32, 64-byte swizzle.
+cudaError_t encode_prep_maps(TcMaps* out, float* cpan, float* bpan, float* gcol, int panel_rows,
+                             float* n0, float* n1, float* nt0, float* nt1, int ld) {
+  PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+  if (!encode) return cudaErrorNotSupported;
+  const cuuint32_t estr[2] = {1, 1};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)kTcBK, 128u};
+  float* ptrs[7] = {cpan, bpan, gcol, n0, n1, nt0, nt1};
+  CUtensorMap* maps[7] = {&out->cpan, &out->bpan, &out->gcol, &out->nb[0], &out->nb[1],
+                          &out->nt[0], &out->nt[1]};
+  for (int i = 0; i < 7; ++i) {
+    const cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)(i < 3 ? panel_rows : ld)};
+    const CUresult r = encode(maps[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, ptrs[i], dims, strides,
+                              box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  }
+  return cudaSuccess;
 }
 
 // Host: the TMA descriptors of one (chain, spin): K-major float32 operand

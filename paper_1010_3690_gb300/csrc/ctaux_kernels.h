@@ -30,6 +30,9 @@ constexpr int kTcNsGroup = 8;
 struct TcMaps {
   CUtensorMap yh, yl, xh, xl;
   CUtensorMap nb1[2], nbg[2];
+  // tensor-core prep: the panels' rows and N, N^T as K-major rows (boxes of
+  // 128 rows x kTcBK float32, 64-byte swizzle)
+  CUtensorMap cpan, bpan, gcol, nb[2], nt[2];
 };
 
 enum { PH_RTILDE = 0, PH_GCOL_OLD = 1, PH_GCOL_NEW = 2, PH_FLUSH = 3, PH_MEAS = 4, PH_COUNT = 5 };
@@ -72,6 +75,7 @@ struct LaunchShape {
   int split_x_blocks;
   int mats;              // Matsubara-frequency measurement on (n_matsubara > 0)
   int tc_wait_limit;     // polls of a tensor-core flush pipeline wait (0: 2^24)
+  int prep_tc;           // mixed form: prep products on the tensor cores
 };
 
 // CUDA-event timing of the sweep phases and kernel launch counts.  Phases:
@@ -145,6 +149,11 @@ void launch_matsubara(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t st)
 void launch_g0_matsubara(const double* table, int n_classes, int n_tau, double beta, int n_freq,
                          double2* out, cudaStream_t st);
 int tc_smem_bytes();
+cudaError_t configure_prep_tc();
+void launch_prep_tc(Chain<float>* dchains, const TcMaps* maps, const LaunchShape& ls,
+                    cudaStream_t st);
+cudaError_t encode_prep_maps(TcMaps* out, float* cpan, float* bpan, float* gcol, int panel_rows,
+                             float* n0, float* n1, float* nt0, float* nt1, int ld);
 cudaError_t configure_flush_tc();
 void launch_flush_tc(Chain<float>* dchains, const TcMaps* maps, const LaunchShape& ls,
                      cudaStream_t st);

@@ -27,10 +27,13 @@ static_assert(kScratchBytes <= CTAUX_NOALLOC_SCRATCH_BYTES, "scratch size in the
 // Shared by every call on a device; held by each device that loads the library.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[CTAUX_NOALLOC_SCRATCH_BYTES];
 
+// Pivot key: the upper 32 bits of |v|'s float64 pattern (sign 0, the whole
+// exponent, 20 significand bits) order like |v| for every non-negative double,
+// so any normal entry, however small, beats an exact zero; ties within 2^-20
+// go to the lower row.
 __device__ __forceinline__ unsigned long long na_pivot_key(double v, int row) {
-  const float a = (float)fabs(v);
-  return ((unsigned long long)__float_as_uint(a) << 32) |
-         (unsigned long long)(0xffffffffu - (unsigned)row);
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(fabs(v));
+  return (bits & 0xffffffff00000000ull) | (unsigned long long)(0xffffffffu - (unsigned)row);
 }
 __device__ __forceinline__ int na_key_row(unsigned long long k) {
   return (int)(0xffffffffu - (unsigned)(k & 0xffffffffull));

@@ -17,8 +17,8 @@
 // After all panels, N[c][perm[j]] = X[perm[c]][j] and
 // log|det N^{-1}| = sum_c log|pivot_c|.
 // Pivots: the largest |value| over rows not yet pivoted, folded while the
-// previous step writes that column: atomicMax of a 64-bit key (float
-// magnitude, ties to the lower row) per (chain, spin, column).
+// previous step writes that column: atomicMax of a 64-bit key (the upper half
+// of the float64 magnitude, ties to the lower row) per (chain, spin, column).
 #pragma once
 
 #include <cooperative_groups.h>
@@ -31,8 +31,13 @@ namespace ctaux {
 
 namespace cg = cooperative_groups;
 
-__device__ __forceinline__ unsigned long long pivot_key_mag(float a, int row) {
-  return ((unsigned long long)__float_as_uint(a) << 32) | (unsigned long long)(0xffffffffu - (unsigned)row);
+// Pivot key: the upper 32 bits of the float64 pattern of a magnitude (sign 0,
+// the whole exponent, 20 significand bits) order like the magnitude for every
+// non-negative double, so a normal entry, however small, beats an exact zero;
+// ties within 2^-20 go to the lower row.
+__device__ __forceinline__ unsigned long long pivot_key_mag(double a, int row) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(a);
+  return (bits & 0xffffffff00000000ull) | (unsigned long long)(0xffffffffu - (unsigned)row);
 }
 
 // Element arithmetic of the elimination: float64, or double-float (df64, the
@@ -51,10 +56,10 @@ __device__ __forceinline__ df64 el_neg(df64 a) { return df_neg(a); }
 __device__ __forceinline__ double el_recip(double a) { return 1.0 / a; }
 __device__ __forceinline__ df64 el_recip(df64 a) { return df_recip(a); }
 __device__ __forceinline__ unsigned long long pivot_key(double v, int row) {
-  return pivot_key_mag((float)fabs(v), row);
+  return pivot_key_mag(fabs(v), row);
 }
 __device__ __forceinline__ unsigned long long pivot_key(df64 v, int row) {
-  return pivot_key_mag(fabsf(v.hi), row);
+  return pivot_key_mag(fabs((double)v.hi), row);
 }
 template <typename E>
 __device__ __forceinline__ E el_zero() {
@@ -297,6 +302,7 @@ __device__ void refresh_body(Chain<T>* chains, int n_chains, int only_chain, int
     const E* X = reinterpret_cast<const E*>(c.work + (size_t)spin * refresh_work_per_spin(ld));
     const int* perm = c.perm + spin * ld;
     T* Nr = c.N[buf][spin];
+    float* NTr = c.NT[buf][spin];   // N^T kept for the tensor-core prep (mixed form), or null
     double* N64 = (filter == 1) ? c.N64[spin] : nullptr;
     const int pj = perm[j];
     double dmax = 0.0, dsq = 0.0, nmax = 0.0;
@@ -309,6 +315,7 @@ __device__ void refresh_body(Chain<T>* chains, int n_chains, int only_chain, int
       dsq += diff * diff;
       nmax = fmax(nmax, fabs(v));
       Nr[o] = (T)v;
+      if (NTr) NTr[(long)cc * ld + pj] = (float)v;
     }
     for (int o = 16; o > 0; o >>= 1) {
       dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));

@@ -64,6 +64,14 @@ __device__ __forceinline__ void set_forced(const Chain<float>& c, Dyn& d, const 
   d.forced_R = R;
   d.forced_t = d.t;
   d.tie_pending = 0;
+  // the float32 ratio this proposal had against its FP64 value: a sample of
+  // the form's ratio error, from which the chain's guard band follows
+  // (16 x the largest error seen, at least the configured guard, at most 0.05)
+  if (!q.none && finite && fabs(R) > 0.0 && isfinite(d.tie_R32)) {
+    const double err = fabs(d.tie_R32 - R) / fabs(R);
+    d.tie_err_max = fmax(d.tie_err_max, err);
+    d.guard_eff = fmax(c.tie_guard, fmin(0.05, 16.0 * d.tie_err_max));
+  }
 }
 
 __device__ __forceinline__ double block_sum(double v, double* red) {

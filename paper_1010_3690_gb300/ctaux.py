@@ -39,7 +39,7 @@ class Params(C.Structure):
                 ("tie_refine_iters", C.c_int), ("use_graph", C.c_int),
                 ("refresh_df64", C.c_int), ("meas_bin_size", C.c_int),
                 ("n_matsubara", C.c_int), ("drift_limit", C.c_double),
-                ("tc_wait_limit", C.c_int)]
+                ("mixed_prep_tc", C.c_int), ("tc_wait_limit", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -51,7 +51,8 @@ class Stats(C.Structure):
                 ("refreshes", C.c_int64),
                 ("last_drift_max", C.c_double), ("last_drift_fro", C.c_double),
                 ("last_drift_rel", C.c_double),
-                ("logdet", C.c_double * 2), ("sign", C.c_int), ("status", C.c_int)]
+                ("logdet", C.c_double * 2), ("sign", C.c_int), ("status", C.c_int),
+                ("tie_err_max", C.c_double), ("tie_guard_eff", C.c_double)]
 
     def as_dict(self):
         d = {}
@@ -171,8 +172,9 @@ class Context:
 
     def __init__(self, chains, precision=CTAUX_FP64, refresh_every=32, p_insert=0.5, p_flip=0.0,
                  n_tau_bins=32, n_anchors=4, trace_capacity=0, device=0, mixed_flush_tc=1,
-                 tie_guard=1e-2, tie_refine_iters=0, refresh_df64=0, use_graph=0,
-                 meas_bin_size=0, n_matsubara=0, drift_limit=0.0, tc_wait_limit=0):
+                 tie_guard=1e-4, tie_refine_iters=0, refresh_df64=0, use_graph=0,
+                 meas_bin_size=0, n_matsubara=0, drift_limit=0.0, mixed_prep_tc=1,
+                 tc_wait_limit=0):
         self._keep = []
         cps = (ChainParams * len(chains))()
         self.chain_inputs = list(chains)
@@ -188,7 +190,7 @@ class Context:
                              n_tau_bins, n_anchors, trace_capacity, device, mixed_flush_tc,
                              tie_guard, tie_refine_iters, int(use_graph), int(refresh_df64),
                              int(meas_bin_size), int(n_matsubara), float(drift_limit),
-                             int(tc_wait_limit))
+                             int(mixed_prep_tc), int(tc_wait_limit))
         self.n_tau_bins = n_tau_bins
         self.n_matsubara = n_matsubara
         self.trace_capacity = trace_capacity

@@ -519,3 +519,28 @@ def test_graph_launches_equal_direct_launches(precision):
         np.testing.assert_array_equal(c0[key], c1[key])
     np.testing.assert_array_equal(g0, g1)
     assert s0["t"] == s1["t"] and s0["refreshes"] == s1["refreshes"]
+
+
+@pytest.mark.parametrize("n0,k", [(430, 64), (1000, 128), (60, 32), (300, 256)])
+def test_mixed_tensor_core_prep_matches_oracle_and_cuda_core_prep(n0, k):
+    """The prep products on the tensor cores (split 3xTF32, N^T kept by the flush
+    and the refresh) and on the CUDA cores give the same chain as the FP64
+    oracle, ratios within the mixed tolerance; their ratios agree closely."""
+    ch = configs.cube8(K=256.0, k_max=k, capacity=1536)
+    cfg = configs.synthetic_configuration(ch, n0, seed=13)
+    out = {}
+    for prep in (1, 0):
+        with pk.Context([ch], precision=pk.CTAUX_MIXED, trace_capacity=4 * k, refresh_every=2,
+                        mixed_prep_tc=prep) as ctx:
+            ctx.set_config(0, cfg["tau"], cfg["site"], cfg["s"], cfg["birth"], cfg["t"])
+            ctx.sweep(4)
+            ctx.synchronize()
+            out[prep] = (ctx.trace(0), ctx.get_config(0))
+    oc = oracle_for(ch)
+    oc.set_config(cfg["tau"], cfg["site"], cfg["s"], cfg["birth"], cfg["t"])
+    recs = oc.run(max(len(out[0][0]), len(out[1][0])))
+    for prep in (1, 0):
+        tr = out[prep][0]
+        worst = compare_traces(tr, recs[:len(tr)], RTOL_MIXED)
+        print(f"n0={n0} k={k} prep on {'tensor' if prep else 'CUDA'} cores: "
+              f"{len(tr)} proposals, worst ratio error {worst:.2e}")

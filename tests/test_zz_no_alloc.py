@@ -60,3 +60,40 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     a = torch.zeros(1, dtype=torch.float64, device="cuda")
     r = ctaux.ctaux_invert_noalloc(a.data_ptr(), m, a.data_ptr(), m, m)
     assert r == 4   # CTAUX_ECAPACITY, returned before any launch
+
+
+@pytest.mark.parametrize("case", ["lda_above_m", "m_at_the_limit", "tiny_scale_with_zero"])
+def test_noalloc_leading_dimensions_limit_and_scale(case):
+    """Padded leading dimensions, the largest supported order, and a matrix
+    scaled far below float32 range whose first column starts with an exact
+    zero (the pivot search orders float64 magnitudes), against numpy."""
+    from paper_1010_3690_gb300 import ctaux
+    ch = configs.cube8(K=16.0, k_max=32, capacity=600)
+    n = {"lda_above_m": 200, "m_at_the_limit": 512, "tiny_scale_with_zero": 150}[case]
+    cfg = configs.synthetic_configuration(ch, n, seed=11)
+    oc = oracle_for(ch)
+    oc.set_config(cfg["tau"], cfg["site"], cfg["s"], cfg["birth"], cfg["t"])
+    A = oc.ninv(0)
+    scale = 1.0
+    if case == "tiny_scale_with_zero":
+        A = A.copy()
+        A[0, 0] = 0.0
+        scale = 1e-300
+    A = A * scale
+    lda = n + 37 if case == "lda_above_m" else n
+    ldi = n + 5 if case == "lda_above_m" else n
+    host = np.zeros((n, lda))          # column j of A in host[j, :n]
+    host[:, :n] = A.T
+    a = torch.tensor(host, dtype=torch.float64, device="cuda")
+    out = torch.full((n, ldi), float("nan"), dtype=torch.float64, device="cuda")
+    logdet = torch.zeros(1, dtype=torch.float64, device="cuda")
+    r = ctaux.ctaux_invert_noalloc(a.data_ptr(), lda, out.data_ptr(), ldi, n, logdet.data_ptr(),
+                                   torch.cuda.current_stream().cuda_stream)
+    assert r == 0
+    torch.cuda.synchronize()
+    inv = out.cpu().numpy()[:, :n].T
+    ref = np.linalg.inv(A)
+    assert np.all(np.isfinite(inv))
+    np.testing.assert_allclose(inv, ref, rtol=1e-8, atol=1e-10 * np.abs(ref).max())
+    sign, ld_ref = np.linalg.slogdet(A)
+    assert float(logdet.item()) == pytest.approx(ld_ref, rel=1e-10, abs=1e-8)
