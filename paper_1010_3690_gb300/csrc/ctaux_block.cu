@@ -184,16 +184,23 @@ __device__ __forceinline__ bool setup_gemm(const Chain<T>& c, const Dyn& d, int 
 
 constexpr int GBK = 16;
 
+// Tile variant of a product for a chain: the context's table (filled by the
+// autotuner) at the chain's current order and k_max; 0 without a table.
+template <typename T>
+__device__ __forceinline__ int chain_tile_var(const Chain<T>& c, const Dyn& d, int phase) {
+  return c.tile_var ? (int)c.tile_var[tile_table_index(phase, d.n, c.k_max)] : 0;
+}
+
 // Work items of one product for one chain: 2 spins x output tiles x slices
 // of the inner dimension.  Slices are kchunk wide while the partial tiles
 // they need fit in kMaxPartials per spin; products with more output tiles
 // than that get fewer, wider slices (down to one).  The partition, and with
-// it the rounding, depends only on the product's own sizes: a chain gives the
-// same bits alone or in a batch.
+// it the rounding, depends only on the product's own sizes and the chain's
+// tile variant: a chain gives the same bits alone or in a batch.
 template <typename T, int PHASE>
-__device__ __forceinline__ int gemm_items(const Chain<T>& c, const Dyn& d, int kchunk, int& tiles_m,
-                                          int& tiles_n, int& nslices, int& width) {
-  constexpr GemmTile tl = gemm_tile(sizeof(T) == 8, PHASE);
+__device__ __forceinline__ int gemm_items(const Chain<T>& c, const Dyn& d, int kchunk, int v,
+                                          int& tiles_m, int& tiles_n, int& nslices, int& width) {
+  const GemmTile tl = tile_variant(sizeof(T) == 8, PHASE, v);
   Gemm<T> g;
   if (d.status || !setup_gemm(c, d, 0, PHASE, g)) return 0;
   tiles_m = (g.M + tl.bm - 1) / tl.bm;
@@ -203,142 +210,167 @@ __device__ __forceinline__ int gemm_items(const Chain<T>& c, const Dyn& d, int k
   return 2 * tiles_m * tiles_n * nslices;
 }
 
-// Persistent batched product: CTAs loop over the (chain, spin, tile, slice)
-// items of all chains.  One output tile (gemm_tile) and one slice per item (256
-// threads).  With more than one slice every slice stores its partial tile,
-// and the slice that arrives last at the tile's ticket adds the partials in
-// slice order (deterministic, no waiting) and writes the result.
-template <typename T, int PHASE>
-__global__ void __launch_bounds__(256) k_gemm(Chain<T>* chains, int n_chains, int kchunk) {
-  constexpr GemmTile tl = gemm_tile(sizeof(T) == 8, PHASE);
+// Largest tile of any variant of a product (sizes the shared staging).
+template <bool FP64, int PHASE>
+struct TileMax {
+  static constexpr int a(int x, int y) { return x > y ? x : y; }
+  static constexpr int bm = a(a(tile_variant(FP64, PHASE, 0).bm, tile_variant(FP64, PHASE, 1).bm),
+                              tile_variant(FP64, PHASE, 2).bm);
+  static constexpr int bn = a(a(tile_variant(FP64, PHASE, 0).bn, tile_variant(FP64, PHASE, 1).bn),
+                              tile_variant(FP64, PHASE, 2).bn);
+};
+
+// One (chain, spin, tile, slice) item of a product with tile variant V.
+// As / Bs: shared staging with row strides SA / SB.
+template <typename T, int PHASE, int V, int SA, int SB>
+__device__ __forceinline__ void gemm_item(const Chain<T>& c, const Dyn& d, int l, int kchunk, T* As,
+                                          T* Bs, int* s_last) {
+  constexpr GemmTile tl = tile_variant(sizeof(T) == 8, PHASE, V);
   constexpr int GBM = tl.bm, GBN = tl.bn, TM = tl.tm, TN = tl.tn;
   constexpr int NTX = GBN / TN, NTY = GBM / TM;  // thread grid over the tile
   static_assert(NTX * NTY == 256, "256 threads per output tile");
-  constexpr int phase = PHASE;
+  static_assert(GBM < SA && GBN < SB, "staging rows hold the tile");
+  const int tx = threadIdx.x % NTX, ty = threadIdx.x / NTX;
+  int tiles_m, tiles_n, nslices, width;
+  gemm_items<T, PHASE>(c, d, kchunk, V, tiles_m, tiles_n, nslices, width);
+  const int per_spin = tiles_m * tiles_n * nslices;
+  const int spin = l / per_spin, r0 = l % per_spin;
+  const int tile = r0 / nslices, ks = r0 % nslices;
+  Gemm<T> g;
+  setup_gemm(c, d, spin, PHASE, g);
+  const int i0 = (tile / tiles_n) * GBM, j0 = (tile % tiles_n) * GBN;
+  const int kb = ks * width, ke = min(g.Kk, kb + width);
+  T acc[TM][TN];
+#pragma unroll
+  for (int a = 0; a < TM; ++a)
+#pragma unroll
+    for (int b = 0; b < TN; ++b) acc[a][b] = (T)0;
+  // the next K step's operands are loaded into registers while the current
+  // one is multiplied from shared memory (global latency off the FMA path)
+  constexpr int PA = (GBK * GBM + 255) / 256, PB = (GBK * GBN + 255) / 256;
+  T ra[PA], rb[PB];
+#pragma unroll
+  for (int q = 0; q < PA; ++q) {
+    const int e = threadIdx.x + 256 * q, ii = e % GBM, kk = e / GBM;
+    const int i = i0 + ii, k = kb + kk;
+    ra[q] = (e < GBK * GBM && i < g.M && k < ke) ? g.A.at(i, k) : (T)0;
+  }
+#pragma unroll
+  for (int q = 0; q < PB; ++q) {
+    const int e = threadIdx.x + 256 * q, kk = e % GBK, jj = e / GBK;
+    const int j = j0 + jj, k = kb + kk;
+    rb[q] = (e < GBK * GBN && j < g.Nn && k < ke) ? g.B.at(k, j) : (T)0;
+  }
+  for (int k0 = kb; k0 < ke; k0 += GBK) {
+#pragma unroll
+    for (int q = 0; q < PA; ++q) {
+      const int e = threadIdx.x + 256 * q;
+      if (e < GBK * GBM) As[(e / GBM) * SA + e % GBM] = ra[q];
+    }
+#pragma unroll
+    for (int q = 0; q < PB; ++q) {
+      const int e = threadIdx.x + 256 * q;
+      if (e < GBK * GBN) Bs[(e % GBK) * SB + e / GBK] = rb[q];
+    }
+    __syncthreads();
+    const int k1 = k0 + GBK;
+    if (k1 < ke) {
+#pragma unroll
+      for (int q = 0; q < PA; ++q) {
+        const int e = threadIdx.x + 256 * q, ii = e % GBM, kk = e / GBM;
+        const int i = i0 + ii, k = k1 + kk;
+        ra[q] = (e < GBK * GBM && i < g.M && k < ke) ? g.A.at(i, k) : (T)0;
+      }
+#pragma unroll
+      for (int q = 0; q < PB; ++q) {
+        const int e = threadIdx.x + 256 * q, kk = e % GBK, jj = e / GBK;
+        const int j = j0 + jj, k = k1 + kk;
+        rb[q] = (e < GBK * GBN && j < g.Nn && k < ke) ? g.B.at(k, j) : (T)0;
+      }
+    }
+#pragma unroll
+    for (int kk = 0; kk < GBK; ++kk) {
+      T av[TM], bv[TN];
+#pragma unroll
+      for (int a = 0; a < TM; ++a) av[a] = As[kk * SA + ty + NTY * a];
+#pragma unroll
+      for (int b = 0; b < TN; ++b) bv[b] = Bs[kk * SB + tx + NTX * b];
+#pragma unroll
+      for (int a = 0; a < TM; ++a)
+#pragma unroll
+        for (int b = 0; b < TN; ++b) acc[a][b] += av[a] * bv[b];
+    }
+    __syncthreads();
+  }
+  if (nslices > 1) {
+    T* part = c.kpart[spin] + (size_t)tile * nslices * GBM * GBN;
+#pragma unroll
+    for (int a = 0; a < TM; ++a)
+#pragma unroll
+      for (int b = 0; b < TN; ++b)
+        part[(size_t)ks * GBM * GBN + (ty + NTY * a) * GBN + tx + NTX * b] = acc[a][b];
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) *s_last = (atomicAdd(c.ticket[spin] + tile, 1) == nslices - 1);
+    __syncthreads();
+    if (!*s_last) return;
+    __threadfence();
+#pragma unroll
+    for (int a = 0; a < TM; ++a)
+#pragma unroll
+      for (int b = 0; b < TN; ++b) {
+        T v = (T)0;
+        for (int q = 0; q < nslices; ++q)
+          v += __ldcg(part + (size_t)q * GBM * GBN + (ty + NTY * a) * GBN + tx + NTX * b);
+        acc[a][b] = v;
+      }
+    if (threadIdx.x == 0) c.ticket[spin][tile] = 0;
+  }
+#pragma unroll
+  for (int a = 0; a < TM; ++a) {
+    const int i = i0 + ty + NTY * a;
+    if (i >= g.M) continue;
+#pragma unroll
+    for (int b = 0; b < TN; ++b) {
+      const int j = j0 + tx + NTX * b;
+      if (j >= g.Nn) continue;
+      T v = (T)g.alpha * acc[a][b];
+      if (g.has_cin) v += g.Cin.at(i, j);
+      g.out[(long)i * g.out_rs + (long)j * g.out_cs] = v;
+    }
+  }
+}
+
+// Persistent batched product: CTAs loop over the (chain, spin, tile, slice)
+// items of all chains.  One output tile (of the chain's tile variant) and one
+// slice per item (256 threads).  With more than one slice every slice stores
+// its partial tile, and the slice that arrives last at the tile's ticket adds
+// the partials in slice order (deterministic, no waiting) and writes the result.
+template <typename T, int PHASE>
+__global__ void __launch_bounds__(256) k_gemm(Chain<T>* chains, int n_chains, int kchunk) {
+  using TMx = TileMax<sizeof(T) == 8, PHASE>;
+  constexpr int SA = TMx::bm + 1, SB = TMx::bn + 1;
   __shared__ int off[kMaxChains + 1];
-  __shared__ T As[GBK][GBM + 1];
-  __shared__ T Bs[GBK][GBN + 1];
+  __shared__ T As[GBK * SA];
+  __shared__ T Bs[GBK * SB];
   __shared__ int s_last;
   for (int ci = threadIdx.x; ci < n_chains; ci += blockDim.x) {
     int a, b, q, wd;
-    off[ci] = gemm_items<T, PHASE>(chains[ci], *chains[ci].dyn, kchunk, a, b, q, wd);
+    const Chain<T>& c = chains[ci];
+    off[ci] = gemm_items<T, PHASE>(c, *c.dyn, kchunk, chain_tile_var(c, *c.dyn, PHASE), a, b, q, wd);
   }
   __syncthreads();
   block_exclusive_scan(off, n_chains);
   const int total = off[n_chains];
-  const int tx = threadIdx.x % NTX, ty = threadIdx.x / NTX;
   for (int w = blockIdx.x; w < total; w += gridDim.x) {
     const int ci = find_chain(off, n_chains, w);
     const Chain<T>& c = chains[ci];
     const Dyn& d = *c.dyn;
-    int tiles_m, tiles_n, nslices, width;
-    gemm_items<T, PHASE>(c, d, kchunk, tiles_m, tiles_n, nslices, width);
     const int l = w - off[ci];
-    const int per_spin = tiles_m * tiles_n * nslices;
-    const int spin = l / per_spin, r0 = l % per_spin;
-    const int tile = r0 / nslices, ks = r0 % nslices;
-    Gemm<T> g;
-    setup_gemm(c, d, spin, phase, g);
-    const int i0 = (tile / tiles_n) * GBM, j0 = (tile % tiles_n) * GBN;
-    const int kb = ks * width, ke = min(g.Kk, kb + width);
-    T acc[TM][TN];
-#pragma unroll
-    for (int a = 0; a < TM; ++a)
-#pragma unroll
-      for (int b = 0; b < TN; ++b) acc[a][b] = (T)0;
-    // the next K step's operands are loaded into registers while the current
-    // one is multiplied from shared memory (global latency off the FMA path)
-    constexpr int PA = (GBK * GBM + 255) / 256, PB = (GBK * GBN + 255) / 256;
-    T ra[PA], rb[PB];
-#pragma unroll
-    for (int q = 0; q < PA; ++q) {
-      const int e = threadIdx.x + 256 * q, ii = e % GBM, kk = e / GBM;
-      const int i = i0 + ii, k = kb + kk;
-      ra[q] = (e < GBK * GBM && i < g.M && k < ke) ? g.A.at(i, k) : (T)0;
-    }
-#pragma unroll
-    for (int q = 0; q < PB; ++q) {
-      const int e = threadIdx.x + 256 * q, kk = e % GBK, jj = e / GBK;
-      const int j = j0 + jj, k = kb + kk;
-      rb[q] = (e < GBK * GBN && j < g.Nn && k < ke) ? g.B.at(k, j) : (T)0;
-    }
-    for (int k0 = kb; k0 < ke; k0 += GBK) {
-#pragma unroll
-      for (int q = 0; q < PA; ++q) {
-        const int e = threadIdx.x + 256 * q;
-        if (e < GBK * GBM) As[e / GBM][e % GBM] = ra[q];
-      }
-#pragma unroll
-      for (int q = 0; q < PB; ++q) {
-        const int e = threadIdx.x + 256 * q;
-        if (e < GBK * GBN) Bs[e % GBK][e / GBK] = rb[q];
-      }
-      __syncthreads();
-      const int k1 = k0 + GBK;
-      if (k1 < ke) {
-#pragma unroll
-        for (int q = 0; q < PA; ++q) {
-          const int e = threadIdx.x + 256 * q, ii = e % GBM, kk = e / GBM;
-          const int i = i0 + ii, k = k1 + kk;
-          ra[q] = (e < GBK * GBM && i < g.M && k < ke) ? g.A.at(i, k) : (T)0;
-        }
-#pragma unroll
-        for (int q = 0; q < PB; ++q) {
-          const int e = threadIdx.x + 256 * q, kk = e % GBK, jj = e / GBK;
-          const int j = j0 + jj, k = k1 + kk;
-          rb[q] = (e < GBK * GBN && j < g.Nn && k < ke) ? g.B.at(k, j) : (T)0;
-        }
-      }
-#pragma unroll
-      for (int kk = 0; kk < GBK; ++kk) {
-        T av[TM], bv[TN];
-#pragma unroll
-        for (int a = 0; a < TM; ++a) av[a] = As[kk][ty + NTY * a];
-#pragma unroll
-        for (int b = 0; b < TN; ++b) bv[b] = Bs[kk][tx + NTX * b];
-#pragma unroll
-        for (int a = 0; a < TM; ++a)
-#pragma unroll
-          for (int b = 0; b < TN; ++b) acc[a][b] += av[a] * bv[b];
-      }
-      __syncthreads();
-    }
-    if (nslices > 1) {
-      T* part = c.kpart[spin] + (size_t)tile * nslices * GBM * GBN;
-#pragma unroll
-      for (int a = 0; a < TM; ++a)
-#pragma unroll
-        for (int b = 0; b < TN; ++b)
-          part[(size_t)ks * GBM * GBN + (ty + NTY * a) * GBN + tx + NTX * b] = acc[a][b];
-      __threadfence();
-      __syncthreads();
-      if (threadIdx.x == 0) s_last = (atomicAdd(c.ticket[spin] + tile, 1) == nslices - 1);
-      __syncthreads();
-      if (!s_last) continue;
-      __threadfence();
-#pragma unroll
-      for (int a = 0; a < TM; ++a)
-#pragma unroll
-        for (int b = 0; b < TN; ++b) {
-          T v = (T)0;
-          for (int q = 0; q < nslices; ++q)
-            v += __ldcg(part + (size_t)q * GBM * GBN + (ty + NTY * a) * GBN + tx + NTX * b);
-          acc[a][b] = v;
-        }
-      if (threadIdx.x == 0) c.ticket[spin][tile] = 0;
-    }
-#pragma unroll
-    for (int a = 0; a < TM; ++a) {
-      const int i = i0 + ty + NTY * a;
-      if (i >= g.M) continue;
-#pragma unroll
-      for (int b = 0; b < TN; ++b) {
-        const int j = j0 + tx + NTX * b;
-        if (j >= g.Nn) continue;
-        T v = (T)g.alpha * acc[a][b];
-        if (g.has_cin) v += g.Cin.at(i, j);
-        g.out[(long)i * g.out_rs + (long)j * g.out_cs] = v;
-      }
+    switch (chain_tile_var(c, d, PHASE)) {
+      case 1: gemm_item<T, PHASE, 1, SA, SB>(c, d, l, kchunk, As, Bs, &s_last); break;
+      case 2: gemm_item<T, PHASE, 2, SA, SB>(c, d, l, kchunk, As, Bs, &s_last); break;
+      default: gemm_item<T, PHASE, 0, SA, SB>(c, d, l, kchunk, As, Bs, &s_last); break;
     }
   }
 }

@@ -132,6 +132,7 @@ struct Chain {
   float* Yl[2];
   float* Xh[2];
   float* Xl[2];
+  const int8_t* tile_var;    // tile-variant table of the products (tile_table_index)
   T* kpart[2];               // split-K partial tiles
   int* ticket[2];            // split-K arrival counters per output tile
   double* work;              // refresh: per spin X (ld x ld), two panels, pivot rows (float64)

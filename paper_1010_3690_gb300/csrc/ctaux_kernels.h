@@ -54,6 +54,32 @@ constexpr GemmTile gemm_tile(bool fp64, int phase) {
                                 : GemmTile{32, 32, 2, 2};
 }
 
+// Compiled tile variants of each product (the autotuner's choices):
+// 0 = the default above; 1 and 2 trade re-reads of the operands against
+// padding and per-item overhead.  Every variant keeps 256 threads per tile.
+constexpr int kTileVariants = 3;
+constexpr GemmTile tile_variant(bool fp64, int phase, int v) {
+  return v == 0 ? gemm_tile(fp64, phase)
+         : phase == PH_MEAS ? (v == 1 ? GemmTile{64, 8, 2, 1} : GemmTile{256, 8, 8, 1})
+         : !fp64 ? (v == 1 ? GemmTile{32, 32, 2, 2} : GemmTile{128, 64, 8, 4})
+         : phase == PH_RTILDE   ? (v == 1 ? GemmTile{32, 32, 2, 2} : GemmTile{16, 128, 1, 8})
+         : phase == PH_GCOL_OLD ? (v == 1 ? GemmTile{32, 32, 2, 2} : GemmTile{128, 16, 8, 1})
+                                : (v == 1 ? GemmTile{64, 64, 4, 4} : GemmTile{64, 32, 4, 2});
+}
+constexpr int kTileMaxBM = 256, kTileMaxBN = 128;
+
+// Tile-variant table of a context (the autotuner's cache): one byte per
+// (product, octave of the expansion order, octave of k_max), read by the
+// product kernels on the device for each chain's current order.
+constexpr int kTileOct = 16, kTileKOct = 9;
+constexpr int kTileTable = PH_COUNT * kTileOct * kTileKOct;
+__host__ __device__ inline int tile_table_index(int phase, int n, int k) {
+  int o = 0, ko = 0;
+  while (o + 1 < kTileOct && (2 << o) <= n) ++o;
+  while (ko + 1 < kTileKOct && (2 << ko) <= k) ++ko;
+  return (phase * kTileOct + o) * kTileKOct + ko;
+}
+
 // Fixed launch shapes of one context (derived from capacities at init, so
 // that a sweep needs no host-side knowledge of the current orders).
 struct LaunchShape {

@@ -6,8 +6,8 @@
 //   product 2: G[n + a][b] += sum_{l<n} C[a][l] G[l][b]             (onto G0(new_a, new_b))
 // with C = G0(new, old)(e^{V_old} - 1) and B = G0(old, new) (the gathered
 // panels), as 128 x 128 output tiles of a tcgen05 GEMM with the split 3xTF32
-// product of Ootomo & Yokota (2022): hi*hi + hi*lo + lo*hi in one float32
-// TMEM accumulator.
+// product of Ootomo & Yokota (2022): hi*hi in one float32 TMEM accumulator,
+// hi*lo + lo*hi in a second one, added in the epilogue.
 //
 // Both operands are read by TMA as K-major float32 rows (K = the old-vertex
 // index l): C and B are the panels' rows, the columns of N (column-major) are
@@ -20,7 +20,7 @@
 // One persistent CTA per SM, warp-specialised like the tensor-core flush:
 //   warp 0 (one thread): TMA producer into a ring of raw float32 stages;
 //   warp 1 (one thread): MMA issuer, 6 tcgen05.mma per 16-wide K chunk into
-//     one of two 128-column TMEM accumulators;
+//     one of two TMEM accumulator pairs (main hi*hi, correction hi*lo + lo*hi);
 //   warp 2: TMEM allocation;
 //   warps 4-7: converters, raw stage -> split stage;
 //   warps 8-11: epilogue, TMEM lane quarter w % 4, all 128 columns.
@@ -42,7 +42,12 @@ constexpr int kRawStages = 4, kSplitStages = 4;
 constexpr int kRawStageBytes = 2 * kTileBytes;    // A, B as float32
 constexpr int kSplitStageBytes = 4 * kTileBytes;  // Ah, Al, Bh, Bl
 constexpr int kPrepThreads = 384;
-constexpr uint32_t kPrepTmemCols = 256;           // two 128-column accumulators
+// two tiles in flight, each with a main (hi*hi) and a correction (hi*lo +
+// lo*hi) accumulator of 128 columns: the small correction terms are not
+// accumulated into the large main sum, whose additions truncate (Ootomo &
+// Yokota keep them apart for that reason); the epilogue adds the two in
+// float32 with round-to-nearest
+constexpr uint32_t kPrepTmemCols = 512;
 
 struct PrepItem {
   int ci, spin, prod, m0, n0, M, N, K;
@@ -270,7 +275,7 @@ __global__ void __launch_bounds__(kPrepThreads, 1) k_prep_tc(Chain<float>* chain
       const uint32_t b = q & 1, ub = q >> 1;
       bool ok = ub == 0 || mbar_wait(smem_u32(accempty + b), (ub - 1) & 1, wl);
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t acc = tmem + b * 128;
+      const uint32_t acc = tmem + b * 256, corr = acc + 128;
       for (int kc = 0; kc < nk && ok; ++kc) {
         const uint32_t ss = taken % kSplitStages, su = taken / kSplitStages;
         if (!mbar_wait(smem_u32(sfull + ss), su & 1, wl)) {
@@ -285,9 +290,9 @@ __global__ void __launch_bounds__(kPrepThreads, 1) k_prep_tc(Chain<float>* chain
         for (int kk = 0; kk < kBK / 8; ++kk) {
           const uint32_t offk = kk * 32;  // 8 tf32 = 32 bytes along K
           const uint32_t first = (kc == 0 && kk == 0) ? 0u : 1u;
-          mma_tf32(acc, smem_desc(ah + offk), smem_desc(bl + offk), first);  // hi * lo
-          mma_tf32(acc, smem_desc(al + offk), smem_desc(bh + offk), 1u);     // lo * hi
-          mma_tf32(acc, smem_desc(ah + offk), smem_desc(bh + offk), 1u);     // hi * hi
+          mma_tf32(corr, smem_desc(ah + offk), smem_desc(bl + offk), first);  // hi * lo
+          mma_tf32(corr, smem_desc(al + offk), smem_desc(bh + offk), 1u);      // lo * hi
+          mma_tf32(acc, smem_desc(ah + offk), smem_desc(bh + offk), first);   // hi * hi
         }
         mma_commit(smem_u32(sempty + ss));  // split stage free once these MMAs are done
       }
@@ -323,10 +328,14 @@ __global__ void __launch_bounds__(kPrepThreads, 1) k_prep_tc(Chain<float>* chain
       const int row = t.m0 + quarter * 32 + lane;
       float* Nb = c.N[d.buf][t.spin];
       float* Gc = c.Gcol[t.spin];
-      float v[32];
+      float v[32], vc[32];
 #pragma unroll 1
       for (int cc = 0; cc < 4; ++cc) {
-        tmem_ld32(tmem + b * 128 + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(cc * 32), v);
+        const uint32_t ta = tmem + b * 256 + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(cc * 32);
+        tmem_ld32(ta, v);
+        tmem_ld32(ta + 128, vc);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] += vc[j];
         if (row < t.M) {
 #pragma unroll
           for (int j = 0; j < 32; ++j) {

@@ -523,9 +523,12 @@ def test_graph_launches_equal_direct_launches(precision):
 
 @pytest.mark.parametrize("n0,k", [(430, 64), (1000, 128), (60, 32), (300, 256)])
 def test_mixed_tensor_core_prep_matches_oracle_and_cuda_core_prep(n0, k):
-    """The prep products on the tensor cores (split 3xTF32, N^T kept by the flush
-    and the refresh) and on the CUDA cores give the same chain as the FP64
-    oracle, ratios within the mixed tolerance; their ratios agree closely."""
+    """The prep products on the tensor cores (split 3xTF32 with separate main and
+    correction accumulators, N^T kept by the flush and the refresh) and on the
+    CUDA cores give the same chain as the FP64 oracle.  Float32 ratio errors grow
+    with the order (about 4e-6 at n ~ 430, 2e-5 at n ~ 1000 for either prep), so
+    the bound is 1e-5 up to n ~ 430 and 5e-5 above; the tensor-core prep's worst
+    error stays within 2x the CUDA-core prep's."""
     ch = configs.cube8(K=256.0, k_max=k, capacity=1536)
     cfg = configs.synthetic_configuration(ch, n0, seed=13)
     out = {}
@@ -539,8 +542,10 @@ def test_mixed_tensor_core_prep_matches_oracle_and_cuda_core_prep(n0, k):
     oc = oracle_for(ch)
     oc.set_config(cfg["tau"], cfg["site"], cfg["s"], cfg["birth"], cfg["t"])
     recs = oc.run(max(len(out[0][0]), len(out[1][0])))
+    worst = {}
     for prep in (1, 0):
         tr = out[prep][0]
-        worst = compare_traces(tr, recs[:len(tr)], RTOL_MIXED)
+        worst[prep] = compare_traces(tr, recs[:len(tr)], RTOL_MIXED if n0 <= 430 else 5e-5)
         print(f"n0={n0} k={k} prep on {'tensor' if prep else 'CUDA'} cores: "
-              f"{len(tr)} proposals, worst ratio error {worst:.2e}")
+              f"{len(tr)} proposals, worst ratio error {worst[prep]:.2e}")
+    assert worst[1] <= 2.0 * worst[0] + 1e-6
