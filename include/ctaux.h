@@ -306,6 +306,31 @@ ctaux_status ctaux_set_kmax(ctaux_ctx *ctx, int chain, int k_max);
 ctaux_status ctaux_autotune_k(ctaux_ctx *ctx, const int *candidates, int n_candidates,
                               int n_blocks, int *k_out, double *rate_out);
 
+/* Tile shapes of the CUDA-core products (the prep products, the flush of the
+ * FP64 form, the measurement product).  Each product has CTAUX_TILE_VARIANTS
+ * compiled output-tile shapes; a table of one byte per (product, octave of the
+ * chain's current order n, octave of its k_max),
+ *   index = (product * 16 + min(floor(log2 n), 15)) * 9 + min(floor(log2 k_max), 8),
+ * products 0 R~, 1 G_{old,new}, 2 G_{new,new}, 3 flush, 4 measurement, picks the
+ * shape each chain uses (the table is read on the device for every chain's
+ * current order, so chains of different sizes in one launch use different
+ * shapes).  A new context starts with all zeros (the default shapes).
+ * ctaux_autotune_tiles times the variants on the context's own chains: per
+ * product first one variant for every table slot, then the slots holding at
+ * least a tenth of the chains (at most four, most populated first) one by one,
+ * keeping a change only if it makes the product's time per algorithmic flop
+ * more than 2 % lower; each trial is one untimed and n_blocks timed blocks
+ * (CUDA events, direct launches, no refresh), real Markov-chain steps; a
+ * from-scratch refresh ends it.  table_out (may be NULL) receives the table,
+ * *gain_out (may be NULL) the summed time per flop of the default shapes over
+ * that of the chosen ones.  ctaux_get_tile_table / ctaux_set_tile_table move a
+ * table between contexts (a cache of tuned shapes).  Synchronous. */
+#define CTAUX_TILE_VARIANTS 3
+#define CTAUX_TILE_TABLE_SIZE 720
+ctaux_status ctaux_autotune_tiles(ctaux_ctx *ctx, int n_blocks, int8_t *table_out, double *gain_out);
+ctaux_status ctaux_get_tile_table(ctaux_ctx *ctx, int8_t *table_out);
+ctaux_status ctaux_set_tile_table(ctaux_ctx *ctx, const int8_t *table);
+
 /* Philox-4x32-10 on the device: for counters (t0 + i, chain, purpose), i <
  * count, write the two 53-bit uniforms of each draw to out[2*i], out[2*i+1].
  * A check of the device generator; allocates and frees a small buffer. */

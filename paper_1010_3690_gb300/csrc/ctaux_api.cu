@@ -39,6 +39,9 @@ struct ctaux_ctx {
   cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
   long long graph_kernels[2][PhaseTimer::kPhases] = {};
   bool graph_failed = false;
+  // tile-variant table of the products (the autotuner's cache), host copy
+  std::vector<int8_t> tile_table = std::vector<int8_t>(kTileTable, 0);
+  int8_t* tile_table_dev = nullptr;
 };
 
 namespace {
@@ -120,17 +123,26 @@ ctaux_status build_chains(ctaux_ctx* ctx) {
     const long rows[PH_COUNT] = {k, cap_m, k, cap_m, cap_m};
     const long cols[PH_COUNT] = {cap_m, k, k, cap_m, P.n_anchors};
     size_t need = 1;  // elements
-    for (int ph = 0; ph < PH_COUNT; ++ph) {
-      const GemmTile tl = gemm_tile(sizeof(T) == 8, ph);
-      const long tiles = ((rows[ph] + tl.bm - 1) / tl.bm) * ((cols[ph] + tl.bn - 1) / tl.bn);
-      const long k_inner = ph == PH_FLUSH ? k : cap_m;
-      const long ks = std::max<long>(1, (k_inner + ls.kchunk - 1) / ls.kchunk);
-      if (ks > 1)
-        need = std::max(need, (size_t)std::min<long>(kMaxPartials, tiles * ks) * tl.bm * tl.bn);
-    }
+    for (int ph = 0; ph < PH_COUNT; ++ph)
+      for (int v = 0; v < kTileVariants; ++v) {
+        const GemmTile tl = tile_variant(sizeof(T) == 8, ph, v);
+        const long tiles = ((rows[ph] + tl.bm - 1) / tl.bm) * ((cols[ph] + tl.bn - 1) / tl.bn);
+        const long k_inner = ph == PH_FLUSH ? k : cap_m;
+        const long ks = std::max<long>(1, (k_inner + ls.kchunk - 1) / ls.kchunk);
+        if (ks > 1)
+          need = std::max(need, (size_t)std::min<long>(kMaxPartials, tiles * ks) * tl.bm * tl.bn);
+      }
     kpart_of[ci] = need;
   }
   ls.persist_ctas = 8 * ctx->sm_count;   // 256-thread CTAs: up to 8 resident per SM
+  for (int ph = 0; ph < PH_COUNT; ++ph) ls.tile_mask[ph] = 1;   // variant 0 until tuned
+  {
+    void* tt = nullptr;
+    CUDA_TRY(ctx, cudaMalloc(&tt, kTileTable));
+    ctx->allocations.push_back(tt);
+    CUDA_TRY(ctx, cudaMemset(tt, 0, kTileTable));
+    ctx->tile_table_dev = reinterpret_cast<int8_t*>(tt);
+  }
   ls.gather_slices = std::max(1, std::min(64, (2 * ctx->sm_count + items - 1) / items));
   ls.meas_lchunks = (max_ld + kMeasChunk - 1) / kMeasChunk;
   ls.meas_cb_blocks = (max_cls_bins + 255) / 256;
@@ -208,6 +220,7 @@ ctaux_status build_chains(ctaux_ctx* ctx) {
     c.ld = round_up(c.cap_m, 32);
     c.seed = cp.seed;
     c.chain_id = cp.chain_id;
+    c.tile_var = ctx->tile_table_dev;
     c.trace_cap = P.trace_capacity;
     c.n_bins = P.n_tau_bins;
     c.n_anchors = P.n_anchors;
@@ -996,6 +1009,132 @@ ctaux_status ctaux_autotune_k(ctaux_ctx* ctx, const int* candidates, int n_candi
     if (k_out) k_out[c] = k;
   }
   if (rate_out) *rate_out = best;
+  // the trials ran without refreshes: start from a fresh N
+  return ctaux_recompute(ctx, nullptr);
+}
+
+ctaux_status ctaux_set_tile_table(ctaux_ctx* ctx, const int8_t* table) {
+  if (!ctx || !table) return CTAUX_EINVAL;
+  for (int i = 0; i < kTileTable; ++i)
+    if (table[i] < 0 || table[i] >= kTileVariants) return CTAUX_EINVAL;
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->last_stream));
+  std::copy(table, table + kTileTable, ctx->tile_table.begin());
+  CUDA_TRY(ctx, cudaMemcpy(ctx->tile_table_dev, table, kTileTable, cudaMemcpyHostToDevice));
+  for (int ph = 0; ph < PH_COUNT; ++ph) {
+    int mask = 0;
+    for (int i = 0; i < kTileOct * kTileKOct; ++i) mask |= 1 << table[ph * kTileOct * kTileKOct + i];
+    ctx->ls.tile_mask[ph] = mask;
+  }
+  // captured graphs hold the old set of launches
+  for (int w = 0; w < 2; ++w)
+    if (ctx->graph_exec[w]) {
+      cudaGraphExecDestroy(ctx->graph_exec[w]);
+      ctx->graph_exec[w] = nullptr;
+    }
+  return CTAUX_OK;
+}
+
+ctaux_status ctaux_get_tile_table(ctaux_ctx* ctx, int8_t* table_out) {
+  if (!ctx || !table_out) return CTAUX_EINVAL;
+  std::copy(ctx->tile_table.begin(), ctx->tile_table.end(), table_out);
+  return CTAUX_OK;
+}
+
+ctaux_status ctaux_autotune_tiles(ctaux_ctx* ctx, int n_blocks, int8_t* table_out, double* gain_out) {
+  if (!ctx || n_blocks < 1) return CTAUX_EINVAL;
+  const int nch = (int)ctx->chains.size();
+  const bool mixed = is_mixed(ctx);
+  // products this context launches on the CUDA cores, with the phase timer and
+  // work counter that measure them (0 prep, 1 flush, 2 measurement)
+  std::vector<std::pair<int, int>> prods;
+  if (!(mixed && ctx->ls.prep_tc))
+    for (int ph : {PH_RTILDE, PH_GCOL_OLD, PH_GCOL_NEW}) prods.push_back({ph, 0});
+  if (!(mixed && ctx->ls.use_tc)) prods.push_back({PH_FLUSH, 1});
+  prods.push_back({PH_MEAS, 2});
+  const int timer_phase[3] = {1, 3, 5};
+  // groups: (octave of the current order, octave of k_max) slots of the table
+  std::vector<int> slot_pop(kTileOct * kTileKOct, 0);
+  for (int c = 0; c < nch; ++c) {
+    Dyn d;
+    ctaux_status r = read_dyn(ctx, c, &d);
+    if (r != CTAUX_OK) return r;
+    const int kmax = mixed ? ctx->hc32[c].k_max : ctx->hc64[c].k_max;
+    slot_pop[tile_table_index(0, d.n, kmax)] += 1;
+  }
+  std::vector<int> slots;
+  for (int i = 0; i < (int)slot_pop.size(); ++i)
+    if (slot_pop[i] * 10 >= nch) slots.push_back(i);
+  std::sort(slots.begin(), slots.end(), [&](int a, int b) { return slot_pop[a] > slot_pop[b]; });
+  if (slots.size() > 4) slots.resize(4);
+  const int saved_refresh = ctx->params.refresh_every;
+  const bool saved_prof = ctx->profiling;
+  ctx->params.refresh_every = 0;  // no refresh inside the timed trials
+  ctaux_set_profiling(ctx, 1);
+  std::vector<int8_t> table = ctx->tile_table;
+  double first_total = 0.0, best_total = 0.0;
+  ctaux_status status = CTAUX_OK;
+  // milliseconds per algorithmic flop of product p's phase over n_blocks blocks
+  auto score = [&](int kind, double* out) -> ctaux_status {
+    ctaux_status r = ctaux_set_tile_table(ctx, table.data());
+    if (r != CTAUX_OK) return r;
+    if ((r = ctaux_sweep(ctx, 1, kind == 2, ctx->last_stream)) != CTAUX_OK) return r;  // untimed
+    if ((r = ctaux_synchronize(ctx)) != CTAUX_OK) return r;
+    double ms0[PhaseTimer::kPhases], ms1[PhaseTimer::kPhases], w0[7], w1[7];
+    ctaux_get_phase_times(ctx, ms0, nullptr);
+    ctaux_get_work(ctx, &w0[0], &w0[1], &w0[2], &w0[3], &w0[4], &w0[5], &w0[6]);
+    if ((r = ctaux_sweep(ctx, n_blocks, kind == 2, ctx->last_stream)) != CTAUX_OK) return r;
+    if ((r = ctaux_synchronize(ctx)) != CTAUX_OK) return r;
+    ctaux_get_phase_times(ctx, ms1, nullptr);
+    ctaux_get_work(ctx, &w1[0], &w1[1], &w1[2], &w1[3], &w1[4], &w1[5], &w1[6]);
+    const int wi = kind == 0 ? 0 : kind == 1 ? 1 : 4;
+    const double work = w1[wi] - w0[wi];
+    const double ms = ms1[timer_phase[kind]] - ms0[timer_phase[kind]];
+    *out = work > 0.0 ? ms / work : ms;
+    return CTAUX_OK;
+  };
+  for (const auto& pk : prods) {
+    const int ph = pk.first, kind = pk.second;
+    auto set_all = [&](int v) {
+      for (int i = 0; i < kTileOct * kTileKOct; ++i) table[ph * kTileOct * kTileKOct + i] = (int8_t)v;
+    };
+    // 1) one variant for every slot; 2) per populated slot, keep a change
+    // only if it gains more than 2 %
+    double best = 0.0, s0 = 0.0;
+    int best_v = 0;
+    for (int v = 0; v < kTileVariants && status == CTAUX_OK; ++v) {
+      set_all(v);
+      double sc = 0.0;
+      status = score(kind, &sc);
+      if (v == 0) s0 = sc;
+      if (status == CTAUX_OK && (v == 0 || sc < best)) {
+        best = sc;
+        best_v = v;
+      }
+    }
+    if (status != CTAUX_OK) break;
+    set_all(best_v);
+    for (int slot : slots) {
+      const int idx = ph * kTileOct * kTileKOct + slot;
+      for (int v = 0; v < kTileVariants && status == CTAUX_OK; ++v) {
+        if (v == table[idx]) continue;
+        const int8_t keep = table[idx];
+        table[idx] = (int8_t)v;
+        double sc = 0.0;
+        status = score(kind, &sc);
+        if (status == CTAUX_OK && sc < 0.98 * best) best = sc;
+        else table[idx] = keep;
+      }
+    }
+    first_total += s0;
+    best_total += best;
+  }
+  ctx->params.refresh_every = saved_refresh;
+  ctaux_set_profiling(ctx, saved_prof ? 1 : 0);
+  if (status != CTAUX_OK) return status;
+  ctaux_status r = ctaux_set_tile_table(ctx, table.data());
+  if (r != CTAUX_OK) return r;
+  if (table_out) std::copy(table.begin(), table.end(), table_out);
+  if (gain_out) *gain_out = best_total > 0.0 ? first_total / best_total : 1.0;
   // the trials ran without refreshes: start from a fresh N
   return ctaux_recompute(ctx, nullptr);
 }

@@ -210,16 +210,6 @@ __device__ __forceinline__ int gemm_items(const Chain<T>& c, const Dyn& d, int k
   return 2 * tiles_m * tiles_n * nslices;
 }
 
-// Largest tile of any variant of a product (sizes the shared staging).
-template <bool FP64, int PHASE>
-struct TileMax {
-  static constexpr int a(int x, int y) { return x > y ? x : y; }
-  static constexpr int bm = a(a(tile_variant(FP64, PHASE, 0).bm, tile_variant(FP64, PHASE, 1).bm),
-                              tile_variant(FP64, PHASE, 2).bm);
-  static constexpr int bn = a(a(tile_variant(FP64, PHASE, 0).bn, tile_variant(FP64, PHASE, 1).bn),
-                              tile_variant(FP64, PHASE, 2).bn);
-};
-
 // One (chain, spin, tile, slice) item of a product with tile variant V.
 // As / Bs: shared staging with row strides SA / SB.
 template <typename T, int PHASE, int V, int SA, int SB>
@@ -342,14 +332,15 @@ __device__ __forceinline__ void gemm_item(const Chain<T>& c, const Dyn& d, int l
 }
 
 // Persistent batched product: CTAs loop over the (chain, spin, tile, slice)
-// items of all chains.  One output tile (of the chain's tile variant) and one
-// slice per item (256 threads).  With more than one slice every slice stores
-// its partial tile, and the slice that arrives last at the tile's ticket adds
-// the partials in slice order (deterministic, no waiting) and writes the result.
-template <typename T, int PHASE>
+// items of the chains whose tile variant for this product is V (one launch
+// per variant in use).  One output tile and one slice per item (256
+// threads).  With more than one slice every slice stores its partial tile,
+// and the slice that arrives last at the tile's ticket adds the partials in
+// slice order (deterministic, no waiting) and writes the result.
+template <typename T, int PHASE, int V>
 __global__ void __launch_bounds__(256) k_gemm(Chain<T>* chains, int n_chains, int kchunk) {
-  using TMx = TileMax<sizeof(T) == 8, PHASE>;
-  constexpr int SA = TMx::bm + 1, SB = TMx::bn + 1;
+  constexpr GemmTile tl = tile_variant(sizeof(T) == 8, PHASE, V);
+  constexpr int SA = tl.bm + 1, SB = tl.bn + 1;
   __shared__ int off[kMaxChains + 1];
   __shared__ T As[GBK * SA];
   __shared__ T Bs[GBK * SB];
@@ -357,35 +348,41 @@ __global__ void __launch_bounds__(256) k_gemm(Chain<T>* chains, int n_chains, in
   for (int ci = threadIdx.x; ci < n_chains; ci += blockDim.x) {
     int a, b, q, wd;
     const Chain<T>& c = chains[ci];
-    off[ci] = gemm_items<T, PHASE>(c, *c.dyn, kchunk, chain_tile_var(c, *c.dyn, PHASE), a, b, q, wd);
+    off[ci] = (chain_tile_var(c, *c.dyn, PHASE) == V)
+                  ? gemm_items<T, PHASE>(c, *c.dyn, kchunk, V, a, b, q, wd)
+                  : 0;
   }
   __syncthreads();
   block_exclusive_scan(off, n_chains);
   const int total = off[n_chains];
   for (int w = blockIdx.x; w < total; w += gridDim.x) {
     const int ci = find_chain(off, n_chains, w);
-    const Chain<T>& c = chains[ci];
-    const Dyn& d = *c.dyn;
-    const int l = w - off[ci];
-    switch (chain_tile_var(c, d, PHASE)) {
-      case 1: gemm_item<T, PHASE, 1, SA, SB>(c, d, l, kchunk, As, Bs, &s_last); break;
-      case 2: gemm_item<T, PHASE, 2, SA, SB>(c, d, l, kchunk, As, Bs, &s_last); break;
-      default: gemm_item<T, PHASE, 0, SA, SB>(c, d, l, kchunk, As, Bs, &s_last); break;
-    }
+    gemm_item<T, PHASE, V, SA, SB>(chains[ci], *chains[ci].dyn, w - off[ci], kchunk, As, Bs,
+                                   &s_last);
   }
 }
 
-template <typename T>
-void launch_gemm(Chain<T>* dchains, const LaunchShape& ls, int phase, cudaStream_t st) {
+template <typename T, int PHASE>
+void launch_gemm_variants(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t st) {
   const dim3 grid(ls.persist_ctas);
-  const int n = ls.n_chains, kc = ls.kchunk;
+  const int n = ls.n_chains, kc = ls.kchunk, mask = ls.tile_mask[PHASE];
+  if (mask & 1) k_gemm<T, PHASE, 0><<<grid, 256, 0, st>>>(dchains, n, kc);
+  if (mask & 2) k_gemm<T, PHASE, 1><<<grid, 256, 0, st>>>(dchains, n, kc);
+  if (mask & 4) k_gemm<T, PHASE, 2><<<grid, 256, 0, st>>>(dchains, n, kc);
+}
+
+// One product for every chain: one launch per tile variant the context's
+// table holds for it (only variant 0 without a tuned table).
+template <typename T>
+int launch_gemm(Chain<T>* dchains, const LaunchShape& ls, int phase, cudaStream_t st) {
   switch (phase) {
-    case PH_RTILDE: k_gemm<T, PH_RTILDE><<<grid, 256, 0, st>>>(dchains, n, kc); break;
-    case PH_GCOL_OLD: k_gemm<T, PH_GCOL_OLD><<<grid, 256, 0, st>>>(dchains, n, kc); break;
-    case PH_GCOL_NEW: k_gemm<T, PH_GCOL_NEW><<<grid, 256, 0, st>>>(dchains, n, kc); break;
-    case PH_FLUSH: k_gemm<T, PH_FLUSH><<<grid, 256, 0, st>>>(dchains, n, kc); break;
-    default: k_gemm<T, PH_MEAS><<<grid, 256, 0, st>>>(dchains, n, kc); break;
+    case PH_RTILDE: launch_gemm_variants<T, PH_RTILDE>(dchains, ls, st); break;
+    case PH_GCOL_OLD: launch_gemm_variants<T, PH_GCOL_OLD>(dchains, ls, st); break;
+    case PH_GCOL_NEW: launch_gemm_variants<T, PH_GCOL_NEW>(dchains, ls, st); break;
+    case PH_FLUSH: launch_gemm_variants<T, PH_FLUSH>(dchains, ls, st); break;
+    default: launch_gemm_variants<T, PH_MEAS>(dchains, ls, st); break;
   }
+  return __builtin_popcount(ls.tile_mask[phase]);
 }
 
 // ------------------------------------------------------------ proposals
@@ -1121,10 +1118,10 @@ void launch_block(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t st, Pha
     if constexpr (std::is_same<T, float>::value) launch_prep_tc(dchains, maps, ls, st);
     pt->end(1, st, 2);
   } else {
-    launch_gemm<T>(dchains, ls, PH_RTILDE, st);
-    launch_gemm<T>(dchains, ls, PH_GCOL_OLD, st);
-    launch_gemm<T>(dchains, ls, PH_GCOL_NEW, st);
-    pt->end(1, st, 3);
+    int nk = launch_gemm<T>(dchains, ls, PH_RTILDE, st);
+    nk += launch_gemm<T>(dchains, ls, PH_GCOL_OLD, st);
+    nk += launch_gemm<T>(dchains, ls, PH_GCOL_NEW, st);
+    pt->end(1, st, nk);
   }
   pt->begin(2, st);
   if (ls.gamma_in_smem) k_proposals_smem<T><<<nch, 256, ls.prop_smem, st>>>(dchains);
@@ -1146,8 +1143,7 @@ void launch_block(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t st, Pha
     if constexpr (std::is_same<T, float>::value) launch_flush_tc(dchains, maps, ls, st);
     pt->end(3, st, 2);
   } else {
-    launch_gemm<T>(dchains, ls, PH_FLUSH, st);
-    pt->end(3, st, 1);
+    pt->end(3, st, launch_gemm<T>(dchains, ls, PH_FLUSH, st));
   }
   k_finish_block<T><<<(nch + 127) / 128, 128, 0, st>>>(dchains, nch);
   pt->kernels[4] += 1;
@@ -1162,8 +1158,8 @@ cudaError_t configure_block_kernels(const LaunchShape& ls) {
                               ls.prop_smem);
 }
 
-template void launch_gemm<double>(Chain<double>*, const LaunchShape&, int, cudaStream_t);
-template void launch_gemm<float>(Chain<float>*, const LaunchShape&, int, cudaStream_t);
+template int launch_gemm<double>(Chain<double>*, const LaunchShape&, int, cudaStream_t);
+template int launch_gemm<float>(Chain<float>*, const LaunchShape&, int, cudaStream_t);
 template void launch_block<double>(Chain<double>*, const LaunchShape&, cudaStream_t, PhaseTimer*,
                                    const TcMaps*);
 template void launch_block<float>(Chain<float>*, const LaunchShape&, cudaStream_t, PhaseTimer*,

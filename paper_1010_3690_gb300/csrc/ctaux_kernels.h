@@ -66,13 +66,13 @@ constexpr GemmTile tile_variant(bool fp64, int phase, int v) {
          : phase == PH_GCOL_OLD ? (v == 1 ? GemmTile{32, 32, 2, 2} : GemmTile{128, 16, 8, 1})
                                 : (v == 1 ? GemmTile{64, 64, 4, 4} : GemmTile{64, 32, 4, 2});
 }
-constexpr int kTileMaxBM = 256, kTileMaxBN = 128;
 
 // Tile-variant table of a context (the autotuner's cache): one byte per
 // (product, octave of the expansion order, octave of k_max), read by the
 // product kernels on the device for each chain's current order.
 constexpr int kTileOct = 16, kTileKOct = 9;
 constexpr int kTileTable = PH_COUNT * kTileOct * kTileKOct;
+static_assert(kTileTable == 720 && kTileVariants == 3, "table size and variants in include/ctaux.h");
 __host__ __device__ inline int tile_table_index(int phase, int n, int k) {
   int o = 0, ko = 0;
   while (o + 1 < kTileOct && (2 << o) <= n) ++o;
@@ -102,6 +102,7 @@ struct LaunchShape {
   int mats;              // Matsubara-frequency measurement on (n_matsubara > 0)
   int tc_wait_limit;     // polls of a tensor-core flush pipeline wait (0: 2^24)
   int prep_tc;           // mixed form: prep products on the tensor cores
+  int tile_mask[PH_COUNT];  // tile variants in the context's table, per product (bit v)
 };
 
 // CUDA-event timing of the sweep phases and kernel launch counts.  Phases:
@@ -157,7 +158,7 @@ void launch_block(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t st, Pha
 template <typename T>
 cudaError_t configure_block_kernels(const LaunchShape& ls);
 template <typename T>
-void launch_gemm(Chain<T>* dchains, const LaunchShape& ls, int phase, cudaStream_t st);
+int launch_gemm(Chain<T>* dchains, const LaunchShape& ls, int phase, cudaStream_t st);
 template <typename T>
 int refresh_blocks_per_sm();
 size_t refresh_work_doubles(int ld);

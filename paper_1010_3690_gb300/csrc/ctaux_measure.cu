@@ -289,11 +289,11 @@ void launch_measure(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t st, P
   const int nch = ls.n_chains;
   pt->begin(5, st);
   k_meas_gather<T><<<dim3(ls.gather_slices, 2, nch), 256, 0, st>>>(dchains);
-  launch_gemm<T>(dchains, ls, PH_MEAS, st);
+  const int ng = launch_gemm<T>(dchains, ls, PH_MEAS, st);
   k_meas_eval<T><<<ls.persist_ctas, 256, 0, st>>>(dchains, nch);
   k_meas_accumulate<T><<<dim3(ls.meas_acc_blocks, 2, nch), 256, 0, st>>>(dchains);
   if (ls.mats) launch_matsubara<T>(dchains, ls, st);
-  pt->end(5, st, ls.mats ? 9 : 4);
+  pt->end(5, st, 3 + ng + (ls.mats ? 5 : 0));
 }
 
 template <typename T>

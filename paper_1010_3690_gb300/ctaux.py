@@ -108,6 +108,9 @@ def _load():
         "ctaux_autotune_k": (C.c_int, [vp, P(C.c_int), C.c_int, C.c_int, P(C.c_int),
                                        P(C.c_double)]),
         "ctaux_synchronize": (C.c_int, [vp]),
+        "ctaux_autotune_tiles": (C.c_int, [vp, C.c_int, P(C.c_int8), P(C.c_double)]),
+        "ctaux_get_tile_table": (C.c_int, [vp, P(C.c_int8)]),
+        "ctaux_set_tile_table": (C.c_int, [vp, P(C.c_int8)]),
         "ctaux_invert_noalloc": (C.c_int, [vp, C.c_int, vp, C.c_int, C.c_int, vp, vp]),
         "ctaux_destroy": (None, [vp]),
         "ctaux_last_error": (C.c_char_p, [vp]),
@@ -126,7 +129,8 @@ EXPORTED = ("ctaux_init", "ctaux_sweep", "ctaux_measure_G", "ctaux_measure_G_mat
             "ctaux_recompute", "ctaux_get_stats", "ctaux_get_trace", "ctaux_get_config",
             "ctaux_set_config", "ctaux_get_N", "ctaux_set_profiling", "ctaux_get_phase_times",
             "ctaux_get_work", "ctaux_philox_uniforms", "ctaux_synchronize", "ctaux_destroy",
-            "ctaux_set_kmax", "ctaux_autotune_k",
+            "ctaux_set_kmax", "ctaux_autotune_k", "ctaux_autotune_tiles", "ctaux_get_tile_table",
+            "ctaux_set_tile_table",
             "ctaux_last_error", "ctaux_invert_noalloc")
 
 
@@ -321,6 +325,29 @@ class Context:
         self._check(lib.ctaux_autotune_k(self.h, _ip(cand), len(cand), int(n_blocks), _ip(k),
                                          C.byref(rate)), "autotune_k")
         return k, rate.value
+
+    TILE_TABLE_SIZE = 720
+
+    def autotune_tiles(self, n_blocks=4):
+        """Tile shape per (product, order octave, k octave) timed on the device;
+        returns (table [720] int8, gain of the chosen shapes over the defaults)."""
+        t = np.zeros(self.TILE_TABLE_SIZE, np.int8)
+        g = C.c_double()
+        self._check(lib.ctaux_autotune_tiles(self.h, int(n_blocks),
+                                             t.ctypes.data_as(C.POINTER(C.c_int8)), C.byref(g)),
+                    "autotune_tiles")
+        return t, g.value
+
+    def tile_table(self):
+        t = np.zeros(self.TILE_TABLE_SIZE, np.int8)
+        self._check(lib.ctaux_get_tile_table(self.h, t.ctypes.data_as(C.POINTER(C.c_int8))),
+                    "get_tile_table")
+        return t
+
+    def set_tile_table(self, table):
+        t = np.ascontiguousarray(table, dtype=np.int8)
+        self._check(lib.ctaux_set_tile_table(self.h, t.ctypes.data_as(C.POINTER(C.c_int8))),
+                    "set_tile_table")
 
     def set_profiling(self, on=True):
         self._check(lib.ctaux_set_profiling(self.h, int(bool(on))), "set_profiling")

@@ -549,3 +549,65 @@ def test_mixed_tensor_core_prep_matches_oracle_and_cuda_core_prep(n0, k):
         print(f"n0={n0} k={k} prep on {'tensor' if prep else 'CUDA'} cores: "
               f"{len(tr)} proposals, worst ratio error {worst[prep]:.2e}")
     assert worst[1] <= 2.0 * worst[0] + 1e-6
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("variant", [1, 2])
+def test_every_tile_variant_follows_the_oracle(precision, variant):
+    """Every compiled tile shape of the CUDA-core products (a table that selects
+    it for all products and orders) gives the oracle's chain: FP64 ratios within
+    1e-10, mixed within 1e-5 (prep and flush on the CUDA cores)."""
+    ch = configs.cube8(K=256.0, k_max=64, capacity=1024)
+    cfg = configs.synthetic_configuration(ch, 430, seed=17)
+    prec = pk.CTAUX_MIXED if precision == "mixed" else pk.CTAUX_FP64
+    with pk.Context([ch], precision=prec, trace_capacity=512, refresh_every=2, mixed_flush_tc=0,
+                    mixed_prep_tc=0, n_tau_bins=12, n_anchors=3) as ctx:
+        ctx.set_tile_table(np.full(720, variant, np.int8))
+        ctx.set_config(0, cfg["tau"], cfg["site"], cfg["s"], cfg["birth"], cfg["t"])
+        ctx.reset_measurements()
+        ctx.sweep(3, measure=True)
+        ctx.synchronize()
+        tr = ctx.trace(0)
+        G, E, nm = ctx.measure_G(0)
+        assert nm == 3 and np.all(np.isfinite(G))
+        oc = oracle_for(ch)
+        oc.set_config(cfg["tau"], cfg["site"], cfg["s"], cfg["birth"], cfg["t"])
+        compare_traces(tr, oc.run(len(tr)), RTOL64 if precision == "fp64" else RTOL_MIXED)
+        compare_config(ctx, 0, oc)
+
+
+def test_tile_autotuner_keeps_chains_on_the_oracle_and_batch_bits():
+    """The tile tuner on a batch of uneven chains: a valid table, chains still on
+    the oracle's path afterwards, and a chain run alone with the same table
+    gives the same bits as in the batch."""
+    pool = configs.batch(n_chains=24, k_max=32, n_tau=512)
+    chs = pool[:6]
+    with pk.Context(chs, trace_capacity=4096, refresh_every=8) as ctx:
+        ctx.sweep(6)
+        table, gain = ctx.autotune_tiles(n_blocks=2)
+        assert table.shape == (720,) and table.min() >= 0 and table.max() <= 2
+        assert gain > 0
+        ctx.synchronize()
+        t_tuned = [ctx.stats(i)["t"] for i in range(len(chs))]
+        for i in range(len(chs)):
+            ctx.trace(i)
+        ctx.sweep(4)
+        ctx.synchronize()
+        together = [ctx.trace(i) for i in range(len(chs))]
+        for i, ch in enumerate(chs):
+            oc = oracle_for(ch)
+            oc.run(t_tuned[i])
+            compare_traces(together[i], oc.run(len(together[i])), RTOL64)
+            compare_config(ctx, i, oc)
+    print(f"tile table variants used: {np.bincount(table, minlength=3)}, gain {gain:.3f}")
+    # with the tuned table from the start, a chain alone gives the bits it gives
+    # in the batch (the shape follows the chain's own order and k)
+    runs = []
+    for members in (chs, [chs[2]]):
+        with pk.Context(members, trace_capacity=4096, refresh_every=8) as ctx:
+            ctx.set_tile_table(table)
+            ctx.sweep(8)
+            ctx.synchronize()
+            runs.append(ctx.trace(members.index(chs[2])))
+    np.testing.assert_array_equal(runs[0]["ratio"], runs[1]["ratio"])
+    np.testing.assert_array_equal(runs[0]["accept"], runs[1]["accept"])
