@@ -59,7 +59,7 @@ WORKLOADS = {
     "aim1": dict(K=1.0, k_max=8, thermalize=300, start_order=0, n_target=20, chains=1,
                  refresh_every=32),
     "batch": dict(K=None, k_max=128, thermalize=150, start_order=0, n_target=None, chains=512,
-                  refresh_every=128, autotune="16,32,64,128"),
+                  refresh_every=128, autotune="16,32,64,128", autotune_tiles=True),
 }
 
 # DRAM bytes per timed step of the dominant phase's kernels (dram__bytes_read.sum
@@ -423,6 +423,9 @@ def main():
     ap.add_argument("--autotune", default=None,
                     help="comma-separated k candidates: choose k_max per chain on the device "
                          "(ctaux_autotune_k) after thermalisation; --k-max is the allocation")
+    ap.add_argument("--autotune-tiles", dest="autotune_tiles", action="store_true",
+                    help="choose the CUDA-core products' tile shapes per (order, k) octave on the "
+                         "device (ctaux_autotune_tiles) after the k tuning")
     ap.add_argument("--k-sweep", dest="k_sweep", default=None,
                     help="comma-separated k_max values: print proposals/s per k instead")
     args = ap.parse_args()
@@ -451,6 +454,8 @@ def main():
         meta.update(start_order=args.order, n_target=args.order)
     if args.autotune is None and meta.get("autotune"):
         args.autotune = meta["autotune"]
+    if meta.get("autotune_tiles"):
+        args.autotune_tiles = True
     if args.thermalize is None:
         args.thermalize = meta["thermalize"]
     refresh = effective_refresh(meta, args)
@@ -564,6 +569,12 @@ def measure_form(args, pk, torch, dist, chains, meta, refresh, form, local, worl
         cand = [int(x) for x in args.autotune.split(",")]
         ks, _ = ctx.autotune_k(candidates=cand, n_blocks=8)
         k_tuned = {str(k): int((ks == k).sum()) for k in sorted(set(ks.tolist()))}
+    tiles_tuned = None
+    if args.autotune_tiles:
+        import numpy as np
+        table, gain = ctx.autotune_tiles(n_blocks=3)
+        tiles_tuned = {"variants_in_table": np.bincount(table, minlength=3).tolist(),
+                       "gain_over_default_shapes": gain}
     ctx.recompute()   # fresh N; the refresh cadence counts from here
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
@@ -742,6 +753,7 @@ def measure_form(args, pk, torch, dist, chains, meta, refresh, form, local, worl
             "order_n": {"mean": sum(orders) / len(orders), "min": int(min(orders)),
                         "max": int(max(orders))},
             "k_autotuned": k_tuned,
+            "tiles_autotuned": tiles_tuned,
             "roofline": roofline, "flush_roofline": flush_roof,
             "phase_ms_per_step": {names[i]: phase_ms[i] / prof_steps for i in range(len(names))},
             "phase_pass_steps": prof_steps,
