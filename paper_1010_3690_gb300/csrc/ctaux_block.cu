@@ -1142,6 +1142,11 @@ void launch_block(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t st, Pha
   if (tc) {
     if constexpr (std::is_same<T, float>::value) launch_flush_tc(dchains, maps, ls, st);
     pt->end(3, st, 2);
+    if (ls.prep_tc) {   // N'^T for the next block's prep, timed as flush support
+      pt->begin(4, st);
+      if constexpr (std::is_same<T, float>::value) launch_transpose_n(dchains, ls, st);
+      pt->end(4, st, 1);
+    }
   } else {
     pt->end(3, st, launch_gemm<T>(dchains, ls, PH_FLUSH, st));
   }

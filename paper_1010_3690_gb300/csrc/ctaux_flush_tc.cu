@@ -299,7 +299,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_flush_tc(Chain<float>* chains
       const int ld = c.ld, nn = t.nn;
       const float* Nb = c.N[d.buf][t.spin];
       float* out = c.N[1 - d.buf][t.spin];
-      float* outT = c.NT[1 - d.buf][t.spin];  // N'^T for the tensor-core prep (or null)
       const int* S = c.S;
       const int m = t.m0 + quarter * 32 + lane;
       const bool row_ok = m < nn;
@@ -319,11 +318,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_flush_tc(Chain<float>* chains
         if (row_ok)
           for (int j = colhalf * 64; j < colhalf * 64 + 64; ++j) {
             const int n = t.n0 + j;
-            if (n < nn) {
-              const float val = staged ? nsrow[j * kTcNsRows] : Nb[(long)__ldg(S + n) * ld + srow];
-              out[(long)n * ld + m] = val;
-              if (outT) outT[(long)m * ld + n] = val;
-            }
+            if (n < nn)
+              out[(long)n * ld + m] = staged ? nsrow[j * kTcNsRows] : Nb[(long)__ldg(S + n) * ld + srow];
           }
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(nsempty));
@@ -357,24 +353,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_flush_tc(Chain<float>* chains
         if (row_ok) {
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
-            v[j] = cin[j] - v[j];
             const int n = t.n0 + cc * 32 + j;
-            if (n < nn) out[(long)n * ld + m] = v[j];
-          }
-          if (outT) {
-            // row m of N' is a contiguous run of N'^T: 128 bytes per thread
-            const int nb0 = t.n0 + cc * 32;
-            float* dstT = outT + (long)m * ld + nb0;
-            if (nb0 + 32 <= nn) {
-#pragma unroll
-              for (int q4 = 0; q4 < 8; ++q4)
-                reinterpret_cast<float4*>(dstT)[q4] =
-                    make_float4(v[4 * q4], v[4 * q4 + 1], v[4 * q4 + 2], v[4 * q4 + 3]);
-            } else {
-#pragma unroll
-              for (int j = 0; j < 32; ++j)
-                if (nb0 + j < nn) dstT[j] = v[j];
-            }
+            if (n < nn) out[(long)n * ld + m] = cin[j] - v[j];
           }
         }
       }
@@ -403,6 +383,43 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_flush_tc(Chain<float>* chains
                  : "memory");
 }
 
+// N'^T for the tensor-core prep (its G_{old,new} = N B reads rows of N as
+// K-major rows): 32 x 32 tiles of the flushed N' through shared memory, all
+// chains, both spins; nothing to do for a block that left N unchanged.
+__global__ void __launch_bounds__(256) k_transpose_n(Chain<float>* chains, int n_chains) {
+  __shared__ float tile[32][33];
+  __shared__ int off[kMaxChains + 1];
+  for (int ci = threadIdx.x; ci < n_chains; ci += blockDim.x) {
+    const Dyn& d = *chains[ci].dyn;
+    const int tb = (d.n_new + 31) / 32;
+    off[ci] = (d.status || d.flush_noop || !chains[ci].NT[0][0]) ? 0 : 2 * tb * tb;
+  }
+  __syncthreads();
+  block_exclusive_scan(off, n_chains);
+  const int total = off[n_chains];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  for (int w = blockIdx.x; w < total; w += gridDim.x) {
+    const int ci = find_chain(off, n_chains, w);
+    const Chain<float>& c = chains[ci];
+    const Dyn& d = *c.dyn;
+    const int nn = d.n_new, tb = (nn + 31) / 32, l = w - off[ci];
+    const int spin = l / (tb * tb), t = l % (tb * tb);
+    const int i0 = (t % tb) * 32, j0 = (t / tb) * 32, ld = c.ld;
+    const float* src = c.N[1 - d.buf][spin];   // the flush wrote the other buffer
+    float* dst = c.NT[1 - d.buf][spin];
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+      const int i = i0 + tx, j = j0 + r;
+      tile[r][tx] = (i < nn && j < nn) ? src[(long)j * ld + i] : 0.f;   // N'[i][j]
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+      const int i = i0 + r, j = j0 + tx;
+      if (i < nn && j < nn) dst[(long)i * ld + j] = tile[tx][r];      // N'^T[j][i] = N'[i][j]
+    }
+  }
+}
+
 int tc_smem_bytes() { return kTcStages * kStageBytes + kNsBytes + 1024 + 256; }
 
 cudaError_t configure_flush_tc() {
@@ -417,6 +434,10 @@ void launch_flush_tc(Chain<float>* dchains, const TcMaps* maps, const LaunchShap
   const uint32_t wl = lim > 0 ? (uint32_t)lim : lim < 0 ? (uint32_t)(-(int64_t)lim) : kWaitLimit;
   k_flush_tc<<<ls.tc_ctas, kTcThreads, tc_smem_bytes(), st>>>(dchains, ls.n_chains, maps, wl,
                                                               lim < 0 ? 1 : 0);
+}
+
+void launch_transpose_n(Chain<float>* dchains, const LaunchShape& ls, cudaStream_t st) {
+  k_transpose_n<<<ls.persist_ctas, 256, 0, st>>>(dchains, ls.n_chains);
 }
 
 namespace {

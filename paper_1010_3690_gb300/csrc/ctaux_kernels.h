@@ -184,6 +184,7 @@ cudaError_t encode_prep_maps(TcMaps* out, float* cpan, float* bpan, float* gcol,
 cudaError_t configure_flush_tc();
 void launch_flush_tc(Chain<float>* dchains, const TcMaps* maps, const LaunchShape& ls,
                      cudaStream_t st);
+void launch_transpose_n(Chain<float>* dchains, const LaunchShape& ls, cudaStream_t st);
 cudaError_t encode_tc_maps(TcMaps* out, float* yh, float* yl, float* xh, float* xl, int rows,
                            int kp, float* n0, float* n1, int ld);
 void launch_philox_test(uint64_t seed, uint32_t chain, int64_t t0, int count, int purpose,

@@ -23,7 +23,9 @@
 //     one of two TMEM accumulator pairs (main hi*hi, correction hi*lo + lo*hi);
 //   warp 2: TMEM allocation;
 //   warps 4-7: converters, raw stage -> split stage;
-//   warps 8-11: epilogue, TMEM lane quarter w % 4, all 128 columns.
+//   warps 8-11: epilogue, TMEM lane quarter w % 4, all 128 columns: adds each
+//     segment's partial tile to the float32 tile accumulator in shared memory
+//     and writes the tile after the last segment.
 // Every mbarrier wait is bounded; on timeout the chain's status gets
 // DS_TIMEOUT and every role stops, the copies issued are drained, the MMA
 // thread waits for its MMAs and the TMEM is freed.
@@ -38,7 +40,12 @@ namespace ctaux {
 namespace {
 
 using namespace tc;
-constexpr int kRawStages = 4, kSplitStages = 4;
+constexpr int kRawStages = 3, kSplitStages = 3;
+// K chunks accumulated in TMEM before the epilogue adds the partial tile to a
+// float32 accumulator in shared memory (round to nearest): the tensor cores'
+// own additions truncate, so long inner dimensions are summed in segments
+constexpr int kSegChunks = 8;
+constexpr int kAccBytes = 128 * 128 * 4;          // the output tile, column-major
 constexpr int kRawStageBytes = 2 * kTileBytes;    // A, B as float32
 constexpr int kSplitStageBytes = 4 * kTileBytes;  // Ah, Al, Bh, Bl
 constexpr int kPrepThreads = 384;
@@ -147,7 +154,8 @@ __global__ void __launch_bounds__(kPrepThreads, 1) k_prep_tc(Chain<float>* chain
       ((uintptr_t)prep_smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* raw = base;                                          // kRawStages x 16 KB
   unsigned char* split = base + kRawStages * kRawStageBytes;         // kSplitStages x 32 KB
-  uint64_t* rfull = reinterpret_cast<uint64_t*>(split + kSplitStages * kSplitStageBytes);
+  float* acc_s = reinterpret_cast<float*>(split + kSplitStages * kSplitStageBytes);  // 64 KB
+  uint64_t* rfull = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(acc_s) + kAccBytes);
   uint64_t* rempty = rfull + kRawStages;
   uint64_t* sfull = rempty + kRawStages;
   uint64_t* sempty = sfull + kSplitStages;
@@ -267,42 +275,46 @@ __global__ void __launch_bounds__(kPrepThreads, 1) k_prep_tc(Chain<float>* chain
     }
     if (threadIdx.x == 128) *conv_taken = taken;
   } else if (warp == 1 && lane == 0) {
-    // ---- MMA issuer
+    // ---- MMA issuer: each segment of kSegChunks K chunks into the next free
+    // accumulator pair
     uint32_t taken = 0, q = 0;
-    for (int w = blockIdx.x; w < total && !*err_s; w += gridDim.x) {
+    bool ok = true;
+    for (int w = blockIdx.x; w < total && ok && !*err_s; w += gridDim.x) {
       const PrepItem t = prep_item(chains, off, n_chains, p_lo, p_hi, w);
       const int nk = (t.K + kBK - 1) / kBK;
-      const uint32_t b = q & 1, ub = q >> 1;
-      bool ok = ub == 0 || mbar_wait(smem_u32(accempty + b), (ub - 1) & 1, wl);
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t acc = tmem + b * 256, corr = acc + 128;
-      for (int kc = 0; kc < nk && ok; ++kc) {
-        const uint32_t ss = taken % kSplitStages, su = taken / kSplitStages;
-        if (!mbar_wait(smem_u32(sfull + ss), su & 1, wl)) {
-          ok = false;
+      for (int k0 = 0; k0 < nk && ok; k0 += kSegChunks) {
+        const uint32_t b = q & 1, ub = q >> 1;
+        ok = ub == 0 || mbar_wait(smem_u32(accempty + b), (ub - 1) & 1, wl);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t acc = tmem + b * 256, corr = acc + 128;
+        for (int kc = k0; kc < min(nk, k0 + kSegChunks) && ok; ++kc) {
+          const uint32_t ss = taken % kSplitStages, su = taken / kSplitStages;
+          if (!mbar_wait(smem_u32(sfull + ss), su & 1, wl)) {
+            ok = false;
+            break;
+          }
+          ++taken;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t ah = smem_u32(split + ss * kSplitStageBytes), al = ah + kTileBytes,
+                         bh = ah + 2 * kTileBytes, bl = ah + 3 * kTileBytes;
+#pragma unroll
+          for (int kk = 0; kk < kBK / 8; ++kk) {
+            const uint32_t offk = kk * 32;  // 8 tf32 = 32 bytes along K
+            const uint32_t first = (kc == k0 && kk == 0) ? 0u : 1u;
+            mma_tf32(corr, smem_desc(ah + offk), smem_desc(bl + offk), first);  // hi * lo
+            mma_tf32(corr, smem_desc(al + offk), smem_desc(bh + offk), 1u);      // lo * hi
+            mma_tf32(acc, smem_desc(ah + offk), smem_desc(bh + offk), first);   // hi * hi
+          }
+          mma_commit(smem_u32(sempty + ss));  // split stage free once these MMAs are done
+        }
+        if (!ok) {
+          *err_s = 1;
+          atomicOr(&chains[t.ci].dyn->status, DS_TIMEOUT);
           break;
         }
-        ++taken;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t ah = smem_u32(split + ss * kSplitStageBytes), al = ah + kTileBytes,
-                       bh = ah + 2 * kTileBytes, bl = ah + 3 * kTileBytes;
-#pragma unroll
-        for (int kk = 0; kk < kBK / 8; ++kk) {
-          const uint32_t offk = kk * 32;  // 8 tf32 = 32 bytes along K
-          const uint32_t first = (kc == 0 && kk == 0) ? 0u : 1u;
-          mma_tf32(corr, smem_desc(ah + offk), smem_desc(bl + offk), first);  // hi * lo
-          mma_tf32(corr, smem_desc(al + offk), smem_desc(bh + offk), 1u);      // lo * hi
-          mma_tf32(acc, smem_desc(ah + offk), smem_desc(bh + offk), first);   // hi * hi
-        }
-        mma_commit(smem_u32(sempty + ss));  // split stage free once these MMAs are done
+        mma_commit(smem_u32(accfull + b));
+        ++q;
       }
-      if (!ok) {
-        *err_s = 1;
-        atomicOr(&chains[t.ci].dyn->status, DS_TIMEOUT);
-        break;
-      }
-      mma_commit(smem_u32(accfull + b));
-      ++q;
     }
     mma_commit(smem_u32(drain));   // every MMA issued so far completes before the TMEM is freed
     mbar_wait(smem_u32(drain), 0);
@@ -316,41 +328,55 @@ __global__ void __launch_bounds__(kPrepThreads, 1) k_prep_tc(Chain<float>* chain
       const Chain<float>& c = chains[t.ci];
       const Dyn& d = *c.dyn;
       const int ld = c.ld, n = d.n;
-      const uint32_t b = q & 1, ub = q >> 1;
-      if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(accfull + b), ub & 1, wl))) {
+      const int rl = quarter * 32 + lane;      // the tile row of this thread
+      const int row = t.m0 + rl;
+      const int nk = (t.K + kBK - 1) / kBK;
+      bool ok = true;
+      for (int k0 = 0; k0 < nk; k0 += kSegChunks) {
+        const uint32_t b = q & 1, ub = q >> 1;
+        if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(accfull + b), ub & 1, wl))) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        float v[32], vc[32];
+#pragma unroll 1
+        for (int cc = 0; cc < 4; ++cc) {
+          const uint32_t ta = tmem + b * 256 + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(cc * 32);
+          tmem_ld32(ta, v);
+          tmem_ld32(ta + 128, vc);
+          float* a = acc_s + (cc * 32) * 128 + rl;   // column-major: [column][row]
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const float seg = v[j] + vc[j];
+            a[j * 128] = (k0 == 0) ? seg : a[j * 128] + seg;
+          }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(accempty + b));
+        ++q;
+      }
+      if (!ok) {
         if (lane == 0) {
           *err_s = 1;
           atomicOr(&c.dyn->status, DS_TIMEOUT);
         }
         break;
       }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int row = t.m0 + quarter * 32 + lane;
       float* Nb = c.N[d.buf][t.spin];
       float* Gc = c.Gcol[t.spin];
-      float v[32], vc[32];
-#pragma unroll 1
-      for (int cc = 0; cc < 4; ++cc) {
-        const uint32_t ta = tmem + b * 256 + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(cc * 32);
-        tmem_ld32(ta, v);
-        tmem_ld32(ta + 128, vc);
-#pragma unroll
-        for (int j = 0; j < 32; ++j) v[j] += vc[j];
-        if (row < t.M) {
-#pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int col = t.n0 + cc * 32 + j;
-            if (col >= t.N) continue;
-            if (t.prod == 0) Nb[(long)col * ld + n + row] = v[j];
-            else if (t.prod == 1) Gc[(long)col * ld + row] = v[j];
-            else Gc[(long)col * ld + n + row] += v[j];
-          }
+      if (row < t.M) {
+        for (int j = 0; j < 128; ++j) {
+          const int col = t.n0 + j;
+          if (col >= t.N) break;
+          const float v = acc_s[j * 128 + rl];
+          if (t.prod == 0) Nb[(long)col * ld + n + row] = v;
+          else if (t.prod == 1) Gc[(long)col * ld + row] = v;
+          else Gc[(long)col * ld + n + row] += v;
         }
       }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(accempty + b));
-      ++q;
     }
   }
   __syncthreads();
@@ -369,7 +395,7 @@ __global__ void __launch_bounds__(kPrepThreads, 1) k_prep_tc(Chain<float>* chain
 }
 
 int prep_tc_smem_bytes() {
-  return kRawStages * kRawStageBytes + kSplitStages * kSplitStageBytes + 1024 + 256;
+  return kRawStages * kRawStageBytes + kSplitStages * kSplitStageBytes + kAccBytes + 1024 + 256;
 }
 
 cudaError_t configure_prep_tc() {

@@ -603,11 +603,11 @@ def test_tile_autotuner_keeps_chains_on_the_oracle_and_batch_bits():
     # with the tuned table from the start, a chain alone gives the bits it gives
     # in the batch (the shape follows the chain's own order and k)
     runs = []
-    for members in (chs, [chs[2]]):
+    for members, idx in ((chs, 2), ([chs[2]], 0)):
         with pk.Context(members, trace_capacity=4096, refresh_every=8) as ctx:
             ctx.set_tile_table(table)
             ctx.sweep(8)
             ctx.synchronize()
-            runs.append(ctx.trace(members.index(chs[2])))
+            runs.append(ctx.trace(idx))
     np.testing.assert_array_equal(runs[0]["ratio"], runs[1]["ratio"])
     np.testing.assert_array_equal(runs[0]["accept"], runs[1]["accept"])
