@@ -426,6 +426,10 @@ def main():
     ap.add_argument("--autotune-tiles", dest="autotune_tiles", action="store_true",
                     help="choose the CUDA-core products' tile shapes per (order, k) octave on the "
                          "device (ctaux_autotune_tiles) after the k tuning")
+    ap.add_argument("--cpu-k-sweep", dest="cpu_k_sweep", default=None,
+                    help="comma-separated k_max values: rank-one against submatrix updates on one "
+                         "host core (the paper's CPU comparison, Sec. V A) at --cpu-orders")
+    ap.add_argument("--cpu-orders", dest="cpu_orders", default="512,1024,2048")
     ap.add_argument("--k-sweep", dest="k_sweep", default=None,
                     help="comma-separated k_max values: print proposals/s per k instead")
     args = ap.parse_args()
@@ -437,6 +441,8 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.cpu_k_sweep:
+        return run_cpu_k_sweep(args) if rank == 0 else None
 
     import torch
     import torch.distributed as dist
@@ -490,6 +496,35 @@ def main():
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_cpu_k_sweep(args):
+    """Proposals/s of rank-one and submatrix updates on one host core, the same
+    Markov chain from the same seeded configuration (bench_cpu.py), on the
+    2x2x2 cluster table at the orders of the paper's comparison (Sec. V A, Fig. 2:
+    about 8x at orders 512-2048 on CPUs)."""
+    for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    import bench_cpu
+    from workloads import configs
+    ks = [int(x) for x in args.cpu_k_sweep.split(",")]
+    orders = [int(x) for x in args.cpu_orders.split(",")]
+    ch = configs.cube8(K=256.0, k_max=max(ks), capacity=max(orders) + 1024)
+    rows = []
+    for n0 in orders:
+        rows += bench_cpu.time_algorithms(ch, n0, ks, n_props=max(256, 2 * max(ks)))
+    out = {"metric": "CT-AUX proposals/s on one host core: submatrix against rank-one updates",
+           "workload": f"cube8 table (N_c=8, beta=5, U=8, K=256), seeded configurations of orders {orders}",
+           "cpu_model": host_cpu_model(), "threads": 1,
+           "note": "float64, numpy with BLAS products; the same Markov chain for every algorithm",
+           "rows": rows, "speedup": {}}
+    for n0 in orders:
+        r1 = next(r for r in rows if r["order_n0"] == n0 and r["algorithm"] == "rank_one")
+        best = max((r for r in rows if r["order_n0"] == n0 and r["algorithm"] == "submatrix"),
+                   key=lambda r: r["proposals_per_s"])
+        out["speedup"][str(n0)] = {"k_best": best["k_max"],
+                                   "submatrix_over_rank_one": best["proposals_per_s"] / r1["proposals_per_s"]}
+    print(json.dumps(out), flush=True)
 
 
 def run_k_sweep(args, pk, torch, local):

@@ -50,16 +50,17 @@ class Model:
         ti, xi, tj, xj = np.broadcast_arrays(np.asarray(ti, float), np.asarray(xi, np.int64),
                                              np.asarray(tj, float), np.asarray(xj, np.int64))
         dt = ti - tj
-        rows = self.table[spin][self.dx_class[xi, xj]]
+        flat = self.table[spin].reshape(-1)
+        base = self.dx_class[xi, xj] * self.n_tau
         neg = dt < 0.0
         x = np.where(neg, dt + self.beta, dt) * self.inv_dtau
         idx = np.clip(np.floor(x).astype(np.int64), 0, self.n_tau - 2)
         f = x - idx
-        lo = np.take_along_axis(rows, idx[..., None], axis=-1)[..., 0]
-        hi = np.take_along_axis(rows, idx[..., None] + 1, axis=-1)[..., 0]
+        lo = flat[base + idx]
+        hi = flat[base + idx + 1]
         v = lo + f * (hi - lo)
         v = np.where(neg, -v, v)
-        return np.where(dt == 0.0, -rows[..., -1], v)
+        return np.where(dt == 0.0, -flat[base + self.n_tau - 1], v)
 
     def ev(self, spin, s):
         return np.exp(self.gamma * SIGMAS[spin] * np.asarray(s, float))
@@ -110,23 +111,64 @@ class _Chain:
 
 
 class RankOne(_Chain):
-    """Rank-one (fast) updates: one O(n^2) update per accepted proposal."""
+    """Rank-one (fast) updates: one O(n^2) update per accepted proposal, in place
+    through BLAS (dgemv, dger) on a capacity-sized Fortran array; vertices live
+    in slots [0, n), a removal moves the last slot into the freed one, and a list
+    keeps the birth order the proposals index."""
+
+    def set_config(self, tau, site, s, t):
+        from scipy.linalg import blas
+        self.blas = blas
+        super().set_config(tau, site, s, t)
+        n = len(self.tau)
+        self.n = n
+        self.order = list(range(n))     # slots in birth order
+        self.N = [np.asfortranarray(self.N[spin]) for spin in (0, 1)]
+        self.cap = n
+        self._grow()
+
+    def _grow(self):
+        """Capacity of 64 more slots (the BLAS calls run over the whole array, so
+        it stays a little above the order)."""
+        n, cap = self.n, self.cap + 64
+        pad = lambda a, dt: np.concatenate([a[:n], np.zeros(cap - n, dt)])
+        self.tau, self.site, self.s = pad(self.tau, float), pad(self.site, np.int64), pad(self.s, np.int64)
+        for spin in (0, 1):
+            F = np.zeros((cap, cap), order="F")
+            F[:n, :n] = self.N[spin][:n, :n]
+            self.N[spin] = F
+        self.cap = cap
+
+    def matrices(self):
+        """N in birth order (for checks)."""
+        o = np.array(self.order, np.int64)
+        return [F[np.ix_(o, o)] for F in self.N]
+
+    def config(self):
+        o = np.array(self.order, np.int64)
+        return self.tau[o], self.site[o], self.s[o]
 
     def step(self):
+        blas, cap = self.blas, self.cap
         move, u, tau, site, s_new, u_idx = self.proposal(self.t)
-        n = len(self.tau)
+        n = self.n
         rec = {"t": self.t, "move": move, "n": n}
         self.t += 1
         if move == INSERT:
+            if n + 1 >= cap:
+                self._grow()
+                cap = self.cap
             f = self.m.K / (n + 1)
             parts = []
             for spin in (0, 1):
                 e_new = float(self.m.ev(spin, s_new))
-                e_old = self.m.ev(spin, self.s)
-                b = -self.m.g0(spin, self.tau, self.site, tau, site) * (e_new - 1.0)
-                c = -self.m.g0(spin, tau, site, self.tau, self.site) * (e_old - 1.0)
+                b = np.zeros(cap)
+                c = np.zeros(cap)
+                e_old = self.m.ev(spin, self.s[:n])
+                b[:n] = -self.m.g0(spin, self.tau[:n], self.site[:n], tau, site) * (e_new - 1.0)
+                c[:n] = -self.m.g0(spin, tau, site, self.tau[:n], self.site[:n]) * (e_old - 1.0)
                 d = e_new - float(self.m.g0(spin, tau, site, tau, site)) * (e_new - 1.0)
-                Nb = self.N[spin] @ b
+                Nb = blas.dgemv(1.0, self.N[spin], b)
                 parts.append((d - c @ Nb, Nb, c))
             R = f * parts[0][0] * parts[1][0]
             rec["ratio"] = (parts[0][0], parts[1][0])
@@ -134,34 +176,44 @@ class RankOne(_Chain):
             if acc:
                 for spin in (0, 1):
                     S, Nb, c = parts[spin]
-                    cN = c @ self.N[spin]
-                    N = self.N[spin]
-                    Nn = np.empty((n + 1, n + 1))
-                    Nn[:n, :n] = N + np.outer(Nb, cN) / S
-                    Nn[:n, n] = -Nb / S
-                    Nn[n, :n] = -cN / S
-                    Nn[n, n] = 1.0 / S
-                    self.N[spin] = Nn
-                self.tau = np.append(self.tau, tau)
-                self.site = np.append(self.site, site)
-                self.s = np.append(self.s, s_new)
+                    F = self.N[spin]
+                    cN = blas.dgemv(1.0, F, c, trans=1)
+                    blas.dger(1.0 / S, Nb, cN, a=F, overwrite_a=1)
+                    F[:n, n] = -Nb[:n] / S
+                    F[n, :n] = -cN[:n] / S
+                    F[n, n] = 1.0 / S
+                self.tau[n], self.site[n], self.s[n] = tau, site, s_new
+                self.order.append(n)
+                self.n = n + 1
         else:
             if n == 0:
                 rec.update(ratio=(0.0, 0.0), accept=False)
                 self.trace.append(rec)
                 return rec
-            p = min(int(u_idx * n), n - 1)
+            i = min(int(u_idx * n), n - 1)
+            p = self.order[i]
             f = n / self.m.K
             r = (self.N[0][p, p], self.N[1][p, p])
             rec["ratio"] = r
             acc = u < min(1.0, abs(f * r[0] * r[1]))
             if acc:
-                keep = np.arange(n) != p
+                last = n - 1
                 for spin in (0, 1):
-                    N = self.N[spin]
-                    N = N - np.outer(N[:, p], N[p, :]) / N[p, p]
-                    self.N[spin] = N[np.ix_(keep, keep)]
-                self.tau, self.site, self.s = self.tau[keep], self.site[keep], self.s[keep]
+                    F = self.N[spin]
+                    col = F[:, p].copy()
+                    row = F[p, :].copy()
+                    blas.dger(-1.0 / col[p], col, row, a=F, overwrite_a=1)
+                    if p != last:          # the last slot moves into the freed one
+                        F[p, :n] = F[last, :n]
+                        F[:n, p] = F[:n, last]
+                        F[p, p] = F[last, last]
+                    F[last, :n] = 0.0
+                    F[:n, last] = 0.0
+                del self.order[i]
+                if p != last:
+                    self.tau[p], self.site[p], self.s[p] = self.tau[last], self.site[last], self.s[last]
+                    self.order[self.order.index(last)] = p
+                self.n = last
         rec["accept"] = bool(acc)
         self.trace.append(rec)
         return rec
@@ -349,7 +401,8 @@ def time_algorithms(chain_input, n0, ks, n_props, seed=7):
                 acc += sum(int(r["accept"]) for r in c.trace[before:])
                 done += k
         dt = time.perf_counter() - t0
-        rows.append({"algorithm": name, "k_max": k, "order_n0": n0, "order_end": len(c.tau),
+        n_end = c.n if name == "rank_one" else len(c.tau)
+        rows.append({"algorithm": name, "k_max": k, "order_n0": n0, "order_end": n_end,
                      "proposals": done, "seconds": dt, "proposals_per_s": done / dt,
                      "accepted_per_s": acc / dt})
     return rows

@@ -19,19 +19,19 @@ def _setup(n0, K):
     return ch, cfg, oc, model, draws
 
 
-def _compare(trace, recs, cpu_chain, oc):
+def _compare(trace, recs, tau, s, Ns, oc):
     assert len(trace) == len(recs)
     for g, o in zip(trace, recs):
         assert g["t"] == o["t"] and g["move"] == o["move"] and g["n"] == o["n"]
         assert g["accept"] == o["accept"], (g, o)
         if o.get("birth", -1) >= 0:
-            for s in (0, 1):
-                assert g["ratio"][s] == pytest.approx(o["ratio"][s], rel=1e-9, abs=1e-12)
-    np.testing.assert_allclose(cpu_chain.tau, oc.tau, rtol=0, atol=0)
-    np.testing.assert_array_equal(cpu_chain.s, oc.s)
+            for sp in (0, 1):
+                assert g["ratio"][sp] == pytest.approx(o["ratio"][sp], rel=1e-9, abs=1e-12)
+    np.testing.assert_allclose(tau, oc.tau, rtol=0, atol=0)
+    np.testing.assert_array_equal(s, oc.s)
     for spin in (0, 1):
         No = oc.N(spin)
-        np.testing.assert_allclose(cpu_chain.N[spin], No, rtol=1e-8, atol=1e-10 * np.abs(No).max())
+        np.testing.assert_allclose(Ns[spin], No, rtol=1e-8, atol=1e-10 * np.abs(No).max())
 
 
 @pytest.mark.parametrize("n0,K", [(0, 4.0), (120, 64.0)])
@@ -41,7 +41,8 @@ def test_rank_one_follows_the_oracle(n0, K):
     c.set_config(cfg["tau"], cfg["site"], cfg["s"], cfg["t"])
     for _ in range(200):
         c.step()
-    _compare(c.trace, oc.run(200), c, oc)
+    tau, site, s = c.config()
+    _compare(c.trace, oc.run(200), tau, s, c.matrices(), oc)
 
 
 @pytest.mark.parametrize("n0,K,k", [(0, 4.0, 8), (120, 64.0, 32), (60, 16.0, 64)])
@@ -51,4 +52,4 @@ def test_submatrix_follows_the_oracle(n0, K, k):
     c.set_config(cfg["tau"], cfg["site"], cfg["s"], cfg["t"])
     for _ in range(256 // k):
         c.block()
-    _compare(c.trace, oc.run(len(c.trace)), c, oc)
+    _compare(c.trace, oc.run(len(c.trace)), c.tau, c.s, c.N, oc)
