@@ -136,10 +136,14 @@ def line_config(args, chains, meta, refresh):
     return {"workload": workload_name(chains, meta),
             "k_max": sorted({c.k_max for c in chains}),
             "refresh_every": refresh, "n_tau_bins": N_TAU_BINS, "n_anchors": N_ANCHORS,
+            "gamma": getattr(args, "gamma", "inverse"),
             "measure": "one G(tau) measurement per block",
             "l2": "GPU arm: L2 flushed by a 512 MB write between timed steps; "
                   "oracle arm: host cores",
             "launch": "GPU arm: one CUDA graph per block and per measurement; oracle arm: numpy"}
+
+
+GAMMA_FORMS = {"inverse": 0, "lu": 1}   # CTAUX_GAMMA_INVERSE, CTAUX_GAMMA_LU
 
 
 def load_peaks():
@@ -430,6 +434,8 @@ def main():
                     help="comma-separated k_max values: rank-one against submatrix updates on one "
                          "host core (the paper's CPU comparison, Sec. V A) at --cpu-orders")
     ap.add_argument("--cpu-orders", dest="cpu_orders", default="512,1024,2048")
+    ap.add_argument("--gamma", choices=["inverse", "lu"], default="inverse",
+                    help="how a block keeps Gamma: partitioned inverse or L U (Sec. III D)")
     ap.add_argument("--k-sweep", dest="k_sweep", default=None,
                     help="comma-separated k_max values: print proposals/s per k instead")
     args = ap.parse_args()
@@ -547,7 +553,8 @@ def run_k_sweep(args, pk, torch, local):
             chains, meta = workload(args.workload, args.K, k, n_chains=args.chains)
             meta0 = meta
             ctx = pk.Context(chains, precision=precision, refresh_every=0,
-                             n_tau_bins=N_TAU_BINS, n_anchors=N_ANCHORS, device=local)
+                             n_tau_bins=N_TAU_BINS, n_anchors=N_ANCHORS, device=local,
+                             gamma_form=GAMMA_FORMS[args.gamma])
             n0 = meta["n_target"] or 100
             for i, ch in enumerate(chains):
                 cfg = configs.synthetic_configuration(ch, n0, seed=1000 + ch.chain_id)
@@ -590,7 +597,8 @@ def measure_form(args, pk, torch, dist, chains, meta, refresh, form, local, worl
     precision = pk.CTAUX_FP64 if form == "fp64" else pk.CTAUX_MIXED
     ctx = pk.Context(chains, precision=precision, refresh_every=refresh,
                      n_tau_bins=N_TAU_BINS, n_anchors=N_ANCHORS, device=local,
-                     refresh_df64=int(form == "mixed_df64"), use_graph=int(not args.no_graph))
+                     refresh_df64=int(form == "mixed_df64"), use_graph=int(not args.no_graph),
+                     gamma_form=GAMMA_FORMS[args.gamma])
     stream = torch.cuda.current_stream()
     sh = stream.cuda_stream
     if meta.get("start_order"):

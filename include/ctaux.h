@@ -59,6 +59,15 @@ enum {
   CTAUX_MIXED = 1       /* N, Gamma^{-1} in float32; FP64 refresh and near-tie accepts */
 };
 
+/* How a block keeps Gamma (Sec. III D). */
+enum {
+  CTAUX_GAMMA_INVERSE = 0,  /* Gamma^{-1} grown by partitioning (Eq. ratS) */
+  CTAUX_GAMMA_LU = 1        /* Gamma = L U grown by bordering (triangular solves per proposal,
+                               Eqs. lineq1-detrat); a slot changed twice re-factorises by
+                               Bennett's rank-one update; the flush takes Gamma^{-1}
+                               formed from L U after the block's proposals */
+};
+
 /* Move types (trace records). */
 enum { CTAUX_INSERT = 0, CTAUX_REMOVE = 1, CTAUX_FLIP = 2 };
 
@@ -137,6 +146,9 @@ typedef struct {
                                          is a test of that path: the MMA issuer first waits
                                          -tc_wait_limit polls on a barrier that nothing
                                          completes, so every flush reports CTAUX_ETIMEOUT */
+  int gamma_form;                     /* CTAUX_GAMMA_INVERSE (0) or CTAUX_GAMMA_LU (1); the
+                                         same Markov chain either way (ratios equal up to
+                                         rounding) */
 } ctaux_params;
 
 typedef struct {

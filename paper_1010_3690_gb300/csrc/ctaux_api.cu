@@ -151,10 +151,12 @@ ctaux_status build_chains(ctaux_ctx* ctx) {
   // proposal kernel shared memory
   size_t fixed = ((sizeof(T) * 8 * max_k + 15) & ~size_t(15)) + sizeof(double) * 2 * max_k + sizeof(int) * max_k +
                  sizeof(short) * ((max_ld + 7) & ~7) + sizeof(uint32_t) * ((max_ld + 31) / 32) +
-                 sizeof(double) * 2 * max_k + ((max_ld + 15) & ~15) + 64;
+                 sizeof(double) * 2 * max_k + sizeof(double) * 2 * max_k + ((max_ld + 15) & ~15) + 64;
   size_t gam = ((sizeof(T) * 2 * (size_t)max_k * (max_k + 1)) + 15) & ~size_t(15);
   ls.gamma_in_smem = (fixed + gam <= 200 * 1024) ? 1 : 0;
   ls.prop_smem = (int)(fixed + (ls.gamma_in_smem ? gam : 0));
+  ls.gamma_lu = P.gamma_form == CTAUX_GAMMA_LU ? 1 : 0;
+  ls.max_k = max_k;
   CUDA_TRY(ctx, configure_block_kernels<T>(ls));
   const bool mixed_tc = (sizeof(T) == 4) && P.mixed_flush_tc != 0;
   ls.use_tc = mixed_tc ? 1 : 0;
@@ -164,6 +166,7 @@ ctaux_status build_chains(ctaux_ctx* ctx) {
   ls.split_x_blocks = std::max(1, std::min(256, (max_rows + 7) / 8));
   ls.mats = P.n_matsubara > 0 ? 1 : 0;
   ls.tc_wait_limit = P.tc_wait_limit;
+
   if (mixed_tc) CUDA_TRY(ctx, configure_flush_tc());
   // prep products on the tensor cores: the flush keeps N^T for them; every
   // chain's N must hold one 128-row TMA box
@@ -254,6 +257,7 @@ ctaux_status build_chains(ctaux_ctx* ctx) {
       c.Bpan[spin] = dalloc<T>(ctx, ld * KR, &err);
       c.Gcol[spin] = dalloc<T>(ctx, ld * KR, &err);
       c.Ginv[spin] = dalloc<T>(ctx, K * (K + 1), &err);
+      if (P.gamma_form == CTAUX_GAMMA_LU) c.Glu[spin] = dalloc<T>(ctx, K * (K + 1), &err);
       c.lam[spin] = dalloc<double>(ctx, K, &err);
       c.Y[spin] = dalloc<T>(ctx, ld * K, &err);
       c.Mg[spin] = dalloc<T>(ctx, ld * P.n_anchors, &err);
@@ -262,6 +266,7 @@ ctaux_status build_chains(ctaux_ctx* ctx) {
       c.kpart[spin] = dalloc<T>(ctx, kpart_of[ci], &err);
       c.ticket[spin] = dalloc<int>(ctx, kMaxPartials, &err);
     }
+    c.gamma_lu = P.gamma_form == CTAUX_GAMMA_LU ? 1 : 0;
     c.kp = round_up(cp.k_max, 32);
     c.tie_guard = (sizeof(T) == 4) ? P.tie_guard : 0.0;
     if (c.tie_guard > 0.0)
@@ -492,6 +497,8 @@ ctaux_status ctaux_init(const ctaux_params* params, ctaux_ctx** out) {
   if (params->p_insert < 0 || params->p_flip < 0 || params->p_insert + params->p_flip > 1.0)
     return CTAUX_EINVAL;
   if (!(params->tie_guard >= 0.0) || params->tie_guard >= 1.0) return CTAUX_EINVAL;
+  if (params->gamma_form != CTAUX_GAMMA_INVERSE && params->gamma_form != CTAUX_GAMMA_LU)
+    return CTAUX_EINVAL;
   if (params->n_tau_bins < 1 || params->n_anchors < 1 || params->n_anchors > 64 ||
       params->trace_capacity < 0 || params->refresh_every < 0 || params->meas_bin_size < 0 ||
       params->n_matsubara < 0 || params->n_matsubara > kMaxMatsFreq ||

@@ -444,6 +444,87 @@ __device__ __forceinline__ A warp_sum_t(A v) {
 // |R| >= 1 / (1 - g).
 constexpr double kTieGuard = 1e-4;
 
+// ---- Gamma kept as L U (Sec. III D, the factorisation variant) ----
+// L (unit lower, strictly-lower part stored) and U (upper, diagonal included)
+// share one j x j array with row stride LG; iu[i] = 1 / U_ii.  Every function
+// below is called by both spin halves of the CTA with the same j and start
+// index, so the CTA-wide barriers inside match.
+
+// In place: y <- L^{-1} y (Eq. lineq1) and x <- U^{-T} x (Eq. lineq2) over
+// rows [r_start, j), entries below r_start being zero.  Blocks of 32 rows: a
+// diagonal block is solved by one warp with shuffles (warp 0 of the half for
+// y, warp 1 for x), then the 128 threads of the half subtract its
+// contribution from the rows below.
+template <typename T, typename A>
+__device__ __forceinline__ void lu_solve_pair(const T* G, int LG, const A* iu, A* y, A* x, int r_start,
+                                              int j, int ht, int hw, int lane) {
+  for (int r0 = r_start & ~31; r0 < j; r0 += 32) {
+    const int r1 = min(j, r0 + 32), nb = r1 - r0, r = r0 + lane;
+    if (hw == 0) {
+      A v = (r < r1) ? y[r] : (A)0;
+      for (int t = 0; t < nb - 1; ++t) {
+        const A yt = __shfl_sync(0xffffffffu, v, t);
+        if (lane > t && r < r1) v -= (A)G[(size_t)r * LG + r0 + t] * yt;
+      }
+      if (r < r1) y[r] = v;
+    } else if (hw == 1) {
+      A v = (r < r1) ? x[r] : (A)0;
+      for (int t = 0; t < nb - 1; ++t) {
+        const A xt = __shfl_sync(0xffffffffu, v, t) * iu[r0 + t];
+        if (lane > t && r < r1) v -= (A)G[(size_t)(r0 + t) * LG + r] * xt;
+      }
+      if (r < r1) x[r] = v * iu[r];
+    }
+    __syncthreads();
+    if (r1 < j) {
+      // rows below the block: y_r -= L[r, blk] y_blk, x_r -= U[blk, r]^T x_blk
+      for (int e = ht; e < 2 * (j - r1); e += 128) {
+        const int rr = r1 + (e >> 1);
+        A acc = (A)0;
+        if (e & 1) {
+          for (int t = r0; t < r1; ++t) acc += (A)G[(size_t)t * LG + rr] * x[t];
+          x[rr] -= acc;
+        } else {
+          const T* Lr = G + (size_t)rr * LG;
+          for (int t = r0; t < r1; ++t) acc += (A)Lr[t] * y[t];
+          y[rr] -= acc;
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Bennett's update of L U to the factors of L U + xb yb^T, touching pivots
+// [i0, j) (xb and yb are zero below i0; both are overwritten).  Step i: U_ii
+// += xb_i yb_i, c = yb_i / U_ii; for r > i: xb_r -= xb_i L_ri, L_ri += c xb_r;
+// U_ir += xb_i yb_r, yb_r -= c U_ir.
+template <typename T, typename A>
+__device__ __forceinline__ void lu_rank_one(T* G, int LG, A* iu, A* xb, A* yb, int i0, int j, int ht,
+                                            A* coef) {
+  for (int i = i0; i < j; ++i) {
+    if (ht == 0) {
+      const T uii = (T)((A)G[(size_t)i * LG + i] + xb[i] * yb[i]);
+      G[(size_t)i * LG + i] = uii;
+      const A inv = (A)1 / (A)uii;
+      iu[i] = inv;
+      *coef = yb[i] * inv;
+    }
+    __syncthreads();
+    const A xi = xb[i], cf = *coef;
+    for (int r = i + 1 + ht; r < j; r += 128) {
+      const A lri = (A)G[(size_t)r * LG + i];
+      const A xr = xb[r] - xi * lri;
+      xb[r] = xr;
+      G[(size_t)r * LG + i] = (T)(lri + cf * xr);
+      const A uir = (A)G[(size_t)i * LG + r] + xi * yb[r];
+      G[(size_t)i * LG + r] = (T)uir;
+      yb[r] -= cf * uir;
+    }
+    __syncthreads();
+  }
+}
+
 // One CTA per chain, threads [0,128) spin up, [128,256) spin down.  Runs the
 // k_max proposals of the block in order; Gamma^{-1} (row-major, row stride
 // k_max + 1) is grown by partitioning (Sec. III D): beta = d - w^T Gamma^{-1} s,
@@ -452,8 +533,14 @@ constexpr double kTieGuard = 1e-4;
 // (Eq. Gamma): Sherman-Morrison on Gamma^{-1}, or removal of the slot from P
 // when it returns to its block-start spin (then ratio = -(Gamma^{-1})_qq / lambda).
 // Arithmetic in T (float64, or float32 in the mixed form, which counts near
-// ties of the accept decision).
-template <typename T, bool GS>
+// ties of the accept decision).  LU: Gamma = L U instead (Eqs. lineq1-detrat):
+// beta = d - x^T y with y = L^{-1} s, x = U^{-T} w; an accepted first touch
+// appends x^T to L and (y, beta) to U; (Gamma^{-1})_qq of a re-touched slot is
+// x^T y for s = w = e_q; accepted re-touches re-factorise by Bennett's update
+// (diagonal change: xb = delta e_q, yb = e_q; return to the block-start spin:
+// row and column q deleted, which leaves the outer product of q's old L column
+// and U row).
+template <typename T, bool GS, bool LU>
 __device__ __forceinline__ void proposals_body(Chain<T>* chains) {
   constexpr bool gamma_in_smem = GS;  // Gamma^{-1} in shared memory: known at compile time, so
                                       // its accesses are shared-memory instructions
@@ -495,11 +582,14 @@ __device__ __forceinline__ void proposals_body(Chain<T>* chains) {
   sp = reinterpret_cast<unsigned char*>(((uintptr_t)sp + 15) & ~(uintptr_t)15);
   double* ilam_s = reinterpret_cast<double*>(sp);   // 1/lambda of the slots in P, per spin
   sp += sizeof(double) * 2 * KM;
+  A* iu_s = reinterpret_cast<A*>(sp);               // LU form: 1 / U_ii, per spin
+  sp += sizeof(double) * 2 * KM;
   int8_t* s0_s = reinterpret_cast<int8_t*>(sp);     // block-start spins
 
   T* G;
   if constexpr (GS) G = Gs + (size_t)spin * KM * LG;
-  else G = c.Ginv[spin];
+  else G = LU ? c.Glu[spin] : c.Ginv[spin];
+  A* iu = iu_s + spin * KM;
   A* sv = vec + spin * 4 * KM;   // s (column of G^0 over P)
   A* wv = sv + KM;               // w (row of G^0 over P)
   A* yv = wv + KM;               // Gamma^{-1} s
@@ -514,6 +604,7 @@ __device__ __forceinline__ void proposals_body(Chain<T>* chains) {
   __shared__ A raw_s[2];        // per spin: beta (first touch), delta or Gamma^{-1}_qq (re-touch)
   __shared__ A gqq_s[2];
   __shared__ A scal_s[2];       // per spin: 1/beta, Sherman-Morrison coefficient or Schur pivot
+  __shared__ A coef_s[2];       // LU form: Bennett coefficient of the current pivot
   __shared__ double lamn_s[2];  // per spin: lambda of the proposed change
   __shared__ double ev_s[2][5], iem1_s[2][5];
   __shared__ A glam_s[2][5];
@@ -632,6 +723,14 @@ __device__ __forceinline__ void proposals_body(Chain<T>* chains) {
       }
       if (ht == 127) gpp_s[half] = g_int<A>(c, Nb, Gc, n_old, spin, p, p);
       __syncthreads();
+      if constexpr (LU) {
+        // s -> y = L^{-1} s, w -> x = U^{-T} w, partial sums of x . y
+        lu_solve_pair<T, A>(G, LG, iu, sv, wv, 0, j, ht, hw, lane);
+        A part = (A)0;
+        for (int r = ht; r < j; r += 128) part += sv[r] * wv[r];
+        part = warp_sum_t(part);
+        if (lane == 0) red[half][hw] = part;
+      } else
       // y = Gamma^{-1} s and the partial sums of w . y (z = w^T Gamma^{-1} only
       // on acceptance).  float64: four threads per row, combined by shuffles;
       // float32: one thread per row, two accumulators.
@@ -684,11 +783,24 @@ __device__ __forceinline__ void proposals_body(Chain<T>* chains) {
         raw_s[half] = beta;
         lamn_s[half] = lam_new;
       }
-    } else if (ht == 0) {
+    } else {
+      if constexpr (LU) {
+        // (Gamma^{-1})_qq = x^T y with y = L^{-1} e_q, x = U^{-T} e_q
+        for (int r = ht; r < j; r += 128) sv[r] = wv[r] = (r == q) ? (A)1 : (A)0;
+        __syncthreads();
+        lu_solve_pair<T, A>(G, LG, iu, sv, wv, q, j, ht, hw, lane);
+        A part = (A)0;
+        for (int r = q + ht; r < j; r += 128) part += sv[r] * wv[r];
+        part = warp_sum_t(part);
+        if (lane == 0) red[half][hw] = part;
+        __syncthreads();
+      }
+      if (ht == 0) {
       const double lam_new = ev_s[spin][dk] - 1.0;
       const A lam_a = (A)lam_new;
       const A ilo = (A)ilam[q];  // 1 / lambda of the slot's first change
-      const A gqq = (A)G[(size_t)q * LG + q];
+      const A gqq = LU ? (red[half][0] + red[half][1]) + (red[half][2] + red[half][3])
+                       : (A)G[(size_t)q * LG + q];
       A r;
       if (!to_start) {
         const A delta = ilo - (A)iem1_s[spin][dk];  // 1/lambda_old - 1/lambda_new
@@ -700,6 +812,7 @@ __device__ __forceinline__ void proposals_body(Chain<T>* chains) {
       gqq_s[half] = gqq;
       ratio_s[half] = (double)r;
       lamn_s[half] = lam_new;
+      }
     }
     __syncthreads();
     if (tid == 0) {
@@ -762,8 +875,17 @@ __device__ __forceinline__ void proposals_body(Chain<T>* chains) {
       // algorithmic flops, both spins: y GEMV and the dot (first touch); on
       // acceptance the z GEMV and the bordered update, or the rank-one update
       const long long jl = j;
-      long long fl = (q < 0) ? (2 * jl * jl + 2 * jl) : 4;
-      if (accept) fl += (q < 0) ? 2 * jl * jl + 3 * (jl + 1) * (jl + 1) : 3 * jl * jl;
+      long long fl;
+      if constexpr (LU) {
+        // two triangular solves and the dot (over rows >= q for a re-touch);
+        // Bennett's update on an accepted re-touch, the append costs nothing
+        const long long jq = (q < 0) ? jl : jl - q;
+        fl = 2 * jq * jq + 2 * jq;
+        if (accept && q >= 0) fl += 3 * jq * jq;
+      } else {
+        fl = (q < 0) ? (2 * jl * jl + 2 * jl) : 4;
+        if (accept) fl += (q < 0) ? 2 * jl * jl + 3 * (jl + 1) * (jl + 1) : 3 * jl * jl;
+      }
       flops2 += fl;
       if (trace_cap > 0) {
         const bool forced = fin_s != 0;
@@ -775,7 +897,74 @@ __device__ __forceinline__ void proposals_body(Chain<T>* chains) {
         rr.R = R_s; rr.u = dr.u_acc;
       }
     }
-    if (dec == 1) {
+    if (dec == 1 && LU) {
+      if (q < 0) {
+        // bordering: L gains the row x^T, U the column (y, beta)
+        for (int l = ht; l < j; l += 128) {
+          G[(size_t)j * LG + l] = (T)wv[l];
+          G[(size_t)l * LG + j] = (T)sv[l];
+        }
+        if (ht == 0) {
+          G[(size_t)j * LG + j] = (T)raw_s[half];
+          iu[j] = scal_s[half];
+          lam[j] = lamn_s[half];
+          ilam[j] = iem1_s[spin][dk];
+        }
+      } else if (!to_start) {
+        // Gamma_qq += delta: Bennett with xb = delta e_q, yb = e_q
+        const A delta = raw_s[half];
+        for (int r = ht; r < j; r += 128) {
+          sv[r] = (r == q) ? delta : (A)0;
+          wv[r] = (r == q) ? (A)1 : (A)0;
+        }
+        __syncthreads();
+        lu_rank_one<T, A>(G, LG, iu, sv, wv, q, j, ht, &coef_s[half]);
+        if (ht == 0) {
+          lam[q] = lamn_s[half];
+          ilam[q] = iem1_s[spin][dk];
+        }
+      } else {
+        // delete row and column q; what remains is L'U' + (L[>q, q]) (U[q, >q])^T
+        for (int r = q + 1 + ht; r < j; r += 128) {
+          sv[r - 1] = (A)G[(size_t)r * LG + q];
+          wv[r - 1] = (A)G[(size_t)q * LG + r];
+        }
+        __syncthreads();
+        for (int r = ht; r < j; r += 128)
+          for (int cc = q; cc < j - 1; ++cc) G[(size_t)r * LG + cc] = G[(size_t)r * LG + cc + 1];
+        __syncthreads();
+        for (int cc = ht; cc < j - 1; cc += 128)
+          for (int r = q; r < j - 1; ++r) G[(size_t)r * LG + cc] = G[(size_t)(r + 1) * LG + cc];
+        if (ht == 0)
+          for (int l = q; l < j - 1; ++l) {
+            lam[l] = lam[l + 1];
+            ilam[l] = ilam[l + 1];
+          }
+        __syncthreads();
+        lu_rank_one<T, A>(G, LG, iu, sv, wv, q, j - 1, ht, &coef_s[half]);
+      }
+      __syncthreads();
+      if (tid == 0) {
+        if (q < 0) {
+          P_s[j] = p;
+          pmap[p] = (short)j;
+          jP = j + 1;
+        } else if (to_start) {
+          // later entries of P move down one place (the factors' order)
+          for (int l = q; l < j - 1; ++l) {
+            P_s[l] = P_s[l + 1];
+            pmap[P_s[l]] = (short)l;
+          }
+          pmap[p] = -1;
+          jP = j - 1;
+        }
+        s_cur[p] = (int8_t)s_new;
+        if (s_new == 0) alive[p >> 5] &= ~(1u << (p & 31));
+        else alive[p >> 5] |= (1u << (p & 31));
+        if (move == MV_INSERT) n_cur = nc + 1;
+        else if (move == MV_REMOVE) n_cur = nc - 1;
+      }
+    } else if (dec == 1) {
       const A sc = scal_s[half];
       if (q < 0) {
         // z = w^T Gamma^{-1} (scaled by 1/beta), then the bordered inverse
@@ -889,9 +1078,10 @@ __device__ __forceinline__ void proposals_body(Chain<T>* chains) {
   // write back Gamma^{-1}, lambda, P
   const int jf = jP;
   if (gamma_in_smem) {
+    T* dst = LU ? c.Glu[spin] : c.Ginv[spin];
     for (int e = ht; e < jf * jf; e += 128) {
       const int r = e / jf, cc = e % jf;
-      c.Ginv[spin][(size_t)r * LG + cc] = G[(size_t)r * LG + cc];
+      dst[(size_t)r * LG + cc] = G[(size_t)r * LG + cc];
     }
   }
   for (int r = ht; r < jf; r += 128) c.lam[spin][r] = lam[r];
@@ -917,16 +1107,50 @@ __device__ __forceinline__ void proposals_body(Chain<T>* chains) {
 
 // Gamma^{-1} in global memory (large k_max, large batches): registers held
 // to what lets several CTAs share an SM.
-template <typename T>
+template <typename T, bool LU>
 __global__ void __launch_bounds__(256) k_proposals(Chain<T>* chains) {
-  proposals_body<T, false>(chains);
+  proposals_body<T, false, LU>(chains);
 }
 
 // Gamma^{-1} in shared memory, whose size already limits the CTAs per SM:
 // registers unrationed (4-6 % faster per block than at 64 registers).
-template <typename T>
+template <typename T, bool LU>
 __global__ void __launch_bounds__(256, 1) k_proposals_smem(Chain<T>* chains) {
-  proposals_body<T, true>(chains);
+  proposals_body<T, true, LU>(chains);
+}
+
+// LU form: Gamma^{-1} = U^{-1} L^{-1} from the block's factors, for the flush
+// (which uses Gamma^{-1} in either form).  One thread per column c: a = L^{-1}
+// e_c by forward substitution (a_r = 0 above c), then b = U^{-1} a by backward
+// substitution, in shared memory [row][lane]; 32 columns per CTA, grid
+// (column blocks, spin, chain).  2 j^3 / 3 multiply-adds per spin, against the
+// flush's n j^2.
+template <typename T>
+__global__ void __launch_bounds__(32) k_lu_inverse(Chain<T>* chains) {
+  const Chain<T>& c = chains[blockIdx.z];
+  const Dyn& d = *c.dyn;
+  const int j = d.k_acc, c0 = blockIdx.x * 32;
+  if (d.status || c0 >= j) return;
+  extern __shared__ __align__(16) unsigned char lu_raw[];
+  T* a = reinterpret_cast<T*>(lu_raw);
+  const int spin = blockIdx.y, lane = threadIdx.x, col = c0 + lane, LG = c.k_max + 1;
+  const T* F = c.Glu[spin];
+  for (int r = 0; r < c0; ++r) a[r * 32 + lane] = (T)0;
+  for (int r = c0; r < j; ++r) {
+    const T* Lr = F + (size_t)r * LG;
+    T acc = (r == col) ? (T)1 : (T)0;
+    for (int l = c0; l < r; ++l) acc -= Lr[l] * a[l * 32 + lane];
+    a[r * 32 + lane] = acc;
+  }
+  T* Gi = c.Ginv[spin];
+  for (int r = j - 1; r >= 0; --r) {
+    const T* Ur = F + (size_t)r * LG;
+    T acc = a[r * 32 + lane];
+    for (int l = r + 1; l < j; ++l) acc -= Ur[l] * a[l * 32 + lane];
+    acc = acc / Ur[r];
+    a[r * 32 + lane] = acc;
+    if (col < j) Gi[(size_t)r * LG + col] = acc;
+  }
 }
 
 template <typename T>
@@ -1104,6 +1328,11 @@ void launch_philox_test(uint64_t seed, uint32_t chain, int64_t t0, int count, in
 
 // ----------------------------------------------------------- launchers
 template <typename T>
+int lu_inverse_smem(const LaunchShape& ls) {
+  return (int)(sizeof(T) * 32 * (size_t)ls.max_k);
+}
+
+template <typename T>
 void launch_block(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t st, PhaseTimer* pt,
                   const TcMaps* maps) {
   const int nch = ls.n_chains;
@@ -1116,7 +1345,7 @@ void launch_block(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t st, Pha
   if constexpr (std::is_same<T, float>::value) prep_tc = ls.prep_tc != 0;
   if (prep_tc) {
     if constexpr (std::is_same<T, float>::value) launch_prep_tc(dchains, maps, ls, st);
-    pt->end(1, st, 2);
+    pt->end(1, st, 1 + launch_gemm<T>(dchains, ls, PH_GCOL_NEW, st));
   } else {
     int nk = launch_gemm<T>(dchains, ls, PH_RTILDE, st);
     nk += launch_gemm<T>(dchains, ls, PH_GCOL_OLD, st);
@@ -1124,9 +1353,16 @@ void launch_block(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t st, Pha
     pt->end(1, st, nk);
   }
   pt->begin(2, st);
-  if (ls.gamma_in_smem) k_proposals_smem<T><<<nch, 256, ls.prop_smem, st>>>(dchains);
-  else k_proposals<T><<<nch, 256, ls.prop_smem, st>>>(dchains);
-  pt->end(2, st, 1);
+  if (ls.gamma_lu) {
+    if (ls.gamma_in_smem) k_proposals_smem<T, true><<<nch, 256, ls.prop_smem, st>>>(dchains);
+    else k_proposals<T, true><<<nch, 256, ls.prop_smem, st>>>(dchains);
+  } else {
+    if (ls.gamma_in_smem) k_proposals_smem<T, false><<<nch, 256, ls.prop_smem, st>>>(dchains);
+    else k_proposals<T, false><<<nch, 256, ls.prop_smem, st>>>(dchains);
+  }
+  if (ls.gamma_lu)
+    k_lu_inverse<T><<<dim3((ls.max_k + 31) / 32, 2, nch), 32, lu_inverse_smem<T>(ls), st>>>(dchains);
+  pt->end(2, st, ls.gamma_lu ? 2 : 1);
   bool tc = false;
   if constexpr (std::is_same<T, float>::value) tc = ls.use_tc != 0;
   pt->begin(4, st);
@@ -1156,11 +1392,13 @@ void launch_block(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t st, Pha
 
 template <typename T>
 cudaError_t configure_block_kernels(const LaunchShape& ls) {
-  cudaError_t e = cudaFuncSetAttribute(k_proposals_smem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       ls.prop_smem);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_proposals<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              ls.prop_smem);
+  const cudaFuncAttribute dyn = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e = cudaFuncSetAttribute(k_proposals_smem<T, false>, dyn, ls.prop_smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_proposals<T, false>, dyn, ls.prop_smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_proposals_smem<T, true>, dyn, ls.prop_smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_proposals<T, true>, dyn, ls.prop_smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_lu_inverse<T>, dyn, lu_inverse_smem<T>(ls));
+  return e;
 }
 
 template int launch_gemm<double>(Chain<double>*, const LaunchShape&, int, cudaStream_t);

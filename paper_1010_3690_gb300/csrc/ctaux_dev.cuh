@@ -119,7 +119,9 @@ struct Chain {
   T* Cpan[2];
   T* Bpan[2];
   T* Gcol[2];
-  T* Ginv[2];
+  T* Ginv[2];                // Gamma^{-1}, row-major, row stride k_max + 1 (inverse form)
+  T* Glu[2];                 // L (strictly lower) and U (upper) of Gamma, same layout (LU form)
+  int gamma_lu;              // 1: Gamma kept as L U
   double* lam[2];
   int* P;
   int* S;

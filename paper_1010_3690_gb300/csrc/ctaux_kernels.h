@@ -102,6 +102,8 @@ struct LaunchShape {
   int mats;              // Matsubara-frequency measurement on (n_matsubara > 0)
   int tc_wait_limit;     // polls of a tensor-core flush pipeline wait (0: 2^24)
   int prep_tc;           // mixed form: prep products on the tensor cores
+  int gamma_lu;          // Gamma kept as L U (CTAUX_GAMMA_LU)
+  int max_k;             // largest k_max of the context's chains
   int tile_mask[PH_COUNT];  // tile variants in the context's table, per product (bit v)
 };
 

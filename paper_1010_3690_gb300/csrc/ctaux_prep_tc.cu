@@ -4,6 +4,8 @@
 //   product 0: R~[a][j]     = sum_{l<n} C[a][l] N[l][j]            -> N_ext[n + a][j]
 //   product 1: G[i][a]      = sum_{l<n} N[i][l] B[l][a]             -> Gcol[a][i], i < n
 //   product 2: G[n + a][b] += sum_{l<n} C[a][l] G[l][b]             (onto G0(new_a, new_b))
+// (launch_prep_tc runs products 0 and 1; the block runs product 2, a few
+// k x k tiles with the long inner dimension n, on the CUDA cores split over K)
 // with C = G0(new, old)(e^{V_old} - 1) and B = G0(old, new) (the gathered
 // panels), as 128 x 128 output tiles of a tcgen05 GEMM with the split 3xTF32
 // product of Ootomo & Yokota (2022): hi*hi in one float32 TMEM accumulator,
@@ -403,15 +405,16 @@ cudaError_t configure_prep_tc() {
                               prep_tc_smem_bytes());
 }
 
+// Products 0 and 1 (independent of each other) on the tensor cores.  Product
+// 2 (k_ins x k_ins, reading product 1's columns) has a handful of tiles with a
+// long inner dimension, which the tensor-core pipeline runs one K chunk at a
+// time on a few SMs; the caller runs it on the CUDA cores (split over K).
 void launch_prep_tc(Chain<float>* dchains, const TcMaps* maps, const LaunchShape& ls,
                     cudaStream_t st) {
   const int lim = ls.tc_wait_limit;
   const uint32_t wl = lim > 0 ? (uint32_t)lim : lim < 0 ? (uint32_t)(-(int64_t)lim) : kWaitLimit;
-  // products 0 and 1 are independent; product 2 reads product 1's columns
   k_prep_tc<<<ls.tc_ctas, kPrepThreads, prep_tc_smem_bytes(), st>>>(dchains, ls.n_chains, maps, 0,
                                                                     2, wl);
-  k_prep_tc<<<ls.tc_ctas, kPrepThreads, prep_tc_smem_bytes(), st>>>(dchains, ls.n_chains, maps, 2,
-                                                                    3, wl);
 }
 
 }  // namespace ctaux

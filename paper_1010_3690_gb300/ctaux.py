@@ -16,6 +16,8 @@ _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_ctaux.so"
 
 CTAUX_FP64 = 0
 CTAUX_MIXED = 1
+CTAUX_GAMMA_INVERSE = 0
+CTAUX_GAMMA_LU = 1
 STATUS = {0: "CTAUX_OK", 1: "CTAUX_EINVAL", 2: "CTAUX_ENOMEM", 3: "CTAUX_ECUDA",
           4: "CTAUX_ECAPACITY", 5: "CTAUX_ESINGULAR", 6: "CTAUX_EDRIFT", 7: "CTAUX_ETIMEOUT",
           8: "CTAUX_ENUMERIC"}
@@ -39,7 +41,8 @@ class Params(C.Structure):
                 ("tie_refine_iters", C.c_int), ("use_graph", C.c_int),
                 ("refresh_df64", C.c_int), ("meas_bin_size", C.c_int),
                 ("n_matsubara", C.c_int), ("drift_limit", C.c_double),
-                ("mixed_prep_tc", C.c_int), ("tc_wait_limit", C.c_int)]
+                ("mixed_prep_tc", C.c_int), ("tc_wait_limit", C.c_int),
+                ("gamma_form", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -178,7 +181,7 @@ class Context:
                  n_tau_bins=32, n_anchors=4, trace_capacity=0, device=0, mixed_flush_tc=1,
                  tie_guard=1e-4, tie_refine_iters=0, refresh_df64=0, use_graph=0,
                  meas_bin_size=0, n_matsubara=0, drift_limit=0.0, mixed_prep_tc=1,
-                 tc_wait_limit=0):
+                 tc_wait_limit=0, gamma_form=0):
         self._keep = []
         cps = (ChainParams * len(chains))()
         self.chain_inputs = list(chains)
@@ -194,7 +197,7 @@ class Context:
                              n_tau_bins, n_anchors, trace_capacity, device, mixed_flush_tc,
                              tie_guard, tie_refine_iters, int(use_graph), int(refresh_df64),
                              int(meas_bin_size), int(n_matsubara), float(drift_limit),
-                             int(mixed_prep_tc), int(tc_wait_limit))
+                             int(mixed_prep_tc), int(tc_wait_limit), int(gamma_form))
         self.n_tau_bins = n_tau_bins
         self.n_matsubara = n_matsubara
         self.trace_capacity = trace_capacity
