@@ -187,7 +187,7 @@ ctaux_status build_chains(ctaux_ctx* ctx) {
   // panel): then its ~35 grid barriers per panel, not its work, set its time,
   // and one CTA per SM makes each barrier shorter (measured: 0.081 -> 0.059 ms
   // per block for one 2x2x2 chain at n ~ 400; 22 % slower at n ~ 2100)
-  int nb = refresh_blocks_per_sm<T>();
+  int nb = refresh_blocks_per_sm<T>(ls.refresh_df64 != 0);
   long long cap_tiles = 0;
   for (const auto& cp : ctx->chains) {
     const long long tb = (cp.capacity + cp.k_max + 31) / 32;

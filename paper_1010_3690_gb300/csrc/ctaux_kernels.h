@@ -162,7 +162,7 @@ cudaError_t configure_block_kernels(const LaunchShape& ls);
 template <typename T>
 int launch_gemm(Chain<T>* dchains, const LaunchShape& ls, int phase, cudaStream_t st);
 template <typename T>
-int refresh_blocks_per_sm();
+int refresh_blocks_per_sm(bool df);
 size_t refresh_work_doubles(int ld);
 template <typename T>
 void launch_measure(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t st, PhaseTimer* pt);

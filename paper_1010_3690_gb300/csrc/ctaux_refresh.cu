@@ -31,9 +31,13 @@ cudaError_t launch_refresh(Chain<T>* dchains, const LaunchShape& ls, int only_ch
   // double-float elimination only for the float32 form's own refreshes; the
   // near-tie fallback (filter 1) keeps float64, whose N it also stores
   const void* fn = (const void*)k_refresh<T, double>;
+  size_t dyn = 0;
   if constexpr (std::is_same<T, float>::value)
-    if (ls.refresh_df64 && filter == 0) fn = (const void*)k_refresh<T, df64>;
-  e = cudaLaunchCooperativeKernel(fn, dim3(ls.refresh_grid), dim3(256), args, 0, st);
+    if (ls.refresh_df64 && filter == 0) {
+      fn = (const void*)k_refresh<T, df64>;
+      dyn = refresh_dyn_smem<df64>();
+    }
+  e = cudaLaunchCooperativeKernel(fn, dim3(ls.refresh_grid), dim3(256), args, dyn, st);
   if (e == cudaSuccess) {
     if (only_chain >= 0)
       k_refresh_finish<T><<<1, 1, 0, st>>>(dchains, nch, only_chain, filter);
@@ -46,14 +50,20 @@ cudaError_t launch_refresh(Chain<T>* dchains, const LaunchShape& ls, int only_ch
 }
 
 template <typename T>
-int refresh_blocks_per_sm() {
-  // the grid must be co-resident for either element type
+int refresh_blocks_per_sm(bool df) {
+  // with the double-float option the grid must be co-resident for either
+  // element type (the near-tie fallback keeps float64)
   int nb = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_refresh<T, double>, 256, 0);
   if constexpr (std::is_same<T, float>::value) {
-    int nb2 = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb2, k_refresh<T, df64>, 256, 0);
-    nb = nb < nb2 ? nb : nb2;
+    if (df) {
+      int nb2 = 0;
+      cudaFuncSetAttribute(k_refresh<T, df64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           refresh_dyn_smem<df64>());
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb2, k_refresh<T, df64>, 256,
+                                                    refresh_dyn_smem<df64>());
+      nb = nb < nb2 ? nb : nb2;
+    }
   }
   return nb;
 }
@@ -64,7 +74,7 @@ template cudaError_t launch_refresh<float>(Chain<float>*, const LaunchShape&, in
                                            PhaseTimer*, int);
 size_t refresh_work_doubles(int ld) { return 2 * refresh_work_per_spin(ld); }
 
-template int refresh_blocks_per_sm<double>();
-template int refresh_blocks_per_sm<float>();
+template int refresh_blocks_per_sm<double>(bool);
+template int refresh_blocks_per_sm<float>(bool);
 
 }  // namespace ctaux

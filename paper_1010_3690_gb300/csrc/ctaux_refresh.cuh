@@ -23,6 +23,8 @@
 
 #include <cooperative_groups.h>
 
+#include <type_traits>
+
 #include "ctaux_df64.cuh"
 #include "ctaux_dev.cuh"
 #include "ctaux_kernels.h"
@@ -82,11 +84,50 @@ struct ElDotDf {
 };
 __device__ __forceinline__ ElDot64 el_dot(double init) { return ElDot64(init); }
 __device__ __forceinline__ ElDotDf el_dot(df64 init) { return ElDotDf(init); }
+
+// Trailing-update tile edge: 32 for float64 (the FP64 pipe bounds it), 64 for
+// double-float, where each thread keeps a 4 x 4 block of compensated sums so
+// that the float32 pipe, not shared-memory loads or latency, bounds it.
+template <typename E>
+__host__ __device__ constexpr int trail_tile() {
+  return std::is_same<E, df64>::value ? 64 : 32;
+}
+
+// Compensated sum started from a double-float value: s carries the high
+// part and the error-free running sum of the high products, c the low part,
+// the rounding errors and the cross terms (Dot2 with the initial value split
+// between the two).
+struct DfAcc {
+  float s, c;
+  __device__ __forceinline__ void init(df64 x) {
+    s = x.hi;
+    c = x.lo;
+  }
+  __device__ __forceinline__ void add(df64 x, df64 y) {
+    float pe, se;
+    const float p = two_prod(x.hi, y.hi, pe);
+    const float cross = __fmaf_rn(x.hi, y.lo, __fmaf_rn(x.lo, y.hi, pe));
+    s = two_sum(s, p, se);
+    c = __fadd_rn(c, __fadd_rn(se, cross));
+  }
+  __device__ __forceinline__ df64 value() const {
+    df64 r;
+    r.hi = two_sum(s, c, r.lo);
+    return r;
+  }
+};
 __device__ __forceinline__ int key_row(unsigned long long k) {
   return (int)(0xffffffffu - (unsigned)(k & 0xffffffffull));
 }
 
 constexpr int kPB = 32;  // panel width
+
+// Dynamic shared memory of the refresh kernel for element type E.
+template <typename E>
+__host__ __device__ constexpr int refresh_dyn_smem() {
+  return trail_tile<E>() == 32 ? 0
+                              : 2 * (int)sizeof(E) * (trail_tile<E>() * (kPB + 1) + kPB * (trail_tile<E>() + 1));
+}
 
 // per-spin work area: X (ld x ld), two panel buffers (ld x kPB), pivot rows (ld x kPB)
 __host__ __device__ inline size_t refresh_work_per_spin(int ld) {
@@ -119,6 +160,146 @@ __device__ __forceinline__ RowUnit row_unit(const int* offr, int n_chains, int u
   return r;
 }
 
+// Trailing update of one panel in double-float, 64 x 64 tiles: each CTA walks
+// its tiles (grid stride over the tile units), with the next tile's panel and
+// pivot-row values copied into the other shared-memory buffer by cp.async
+// while the current tile is computed, and the current tile's X values loaded
+// into registers before its products.  Thread (tr, tc) of 16 x 16 owns rows
+// tr + 16a and columns tc + 16b (a, b = 0..3): 16 compensated sums, each
+// started at zero and added to X at the end.
+struct DfTile {
+  int ci, spin, m, i0, j0;
+};
+
+template <typename T>
+__device__ __forceinline__ bool df_tile(Chain<T>* chains, int n_chains, const int* offr,
+                                        const int* offt, int c0, int u, DfTile& t) {
+  t.ci = find_chain(offt, n_chains, u);
+  t.m = (offr[t.ci + 1] - offr[t.ci]) >> 1;
+  if (c0 >= t.m) return false;
+  const int tb = (t.m + 63) / 64, l = u - offt[t.ci];
+  t.spin = l / (tb * tb);
+  const int tile = l - t.spin * tb * tb;
+  t.i0 = (tile % tb) * 64;
+  t.j0 = (tile / tb) * 64;
+  return true;
+}
+
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, bool ok) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(ok ? 8 : 0)
+               : "memory");
+}
+
+template <typename T>
+__device__ void trail_update_df64(Chain<T>* chains, int n_chains, const int* offr, const int* offt,
+                                  int tot_t, int c0, unsigned char* dyn) {
+  constexpr int TB = 64;
+  using Prow = df64[kPB + 1];
+  using Rrow = df64[TB + 1];
+  const size_t buf_bytes = sizeof(df64) * (TB * (kPB + 1) + kPB * (TB + 1));
+  auto Pbuf = [&](int b) { return reinterpret_cast<Prow*>(dyn + b * buf_bytes); };
+  auto Rbuf = [&](int b) {
+    return reinterpret_cast<Rrow*>(dyn + b * buf_bytes + sizeof(df64) * TB * (kPB + 1));
+  };
+  // cp.async of tile t's panel rows and pivot-row columns into buffer b
+  auto prefetch = [&](const DfTile& t, int b) {
+    const Chain<T>& c = chains[t.ci];
+    const int ld = c.ld, bw = min(kPB, t.m - c0);
+    const df64* X = reinterpret_cast<const df64*>(c.work + (size_t)t.spin * refresh_work_per_spin(ld));
+    const df64* Pa = X + (size_t)ld * ld;
+    const df64* Pf = (bw & 1) ? Pa + (size_t)kPB * ld : Pa;  // panel after bw steps
+    const df64* Rr = Pa + (size_t)2 * kPB * ld;
+    Prow* Ps = Pbuf(b);
+    Rrow* Rs = Rbuf(b);
+    for (int e = threadIdx.x; e < TB * kPB; e += blockDim.x) {
+      const int r = e % TB, k = e / TB;
+      const bool okp = t.i0 + r < t.m && k < bw;
+      cp_async8(&Ps[r][k], okp ? Pf + (size_t)k * ld + t.i0 + r : Pf, okp);
+      const int kk = e % kPB, jj = e / kPB;   // Rr rows are contiguous in k
+      const bool okr = t.j0 + jj < t.m;
+      cp_async8(&Rs[kk][jj], okr ? Rr + (size_t)(t.j0 + jj) * kPB + kk : Rr, okr);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+
+  const int stride = gridDim.x;
+  int u = blockIdx.x;
+  DfTile cur;
+  while (u < tot_t && !df_tile(chains, n_chains, offr, offt, c0, u, cur)) u += stride;
+  if (u >= tot_t) return;
+  prefetch(cur, 0);
+  const int tr = threadIdx.x & 15, tc = threadIdx.x >> 4;
+  int b = 0;
+  while (u < tot_t) {
+    // the next tile of this CTA
+    int un = u + stride;
+    DfTile nxt;
+    while (un < tot_t && !df_tile(chains, n_chains, offr, offt, c0, un, nxt)) un += stride;
+
+    const Chain<T>& c = chains[cur.ci];
+    const int ld = c.ld, m = cur.m, spin = cur.spin, bw = min(kPB, m - c0), cn = c0 + bw;
+    df64* X = reinterpret_cast<df64*>(c.work + (size_t)spin * refresh_work_per_spin(ld));
+    unsigned long long* keys = c.pkeys + (size_t)spin * ld;
+    const int8_t* used = c.used + spin * ld;
+    const int* pcol = c.pcol + spin * ld;
+    // X values of this tile (zero for pivot rows, panel columns and padding)
+    df64 xin[4][4];
+    bool row_ok[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const int i = cur.i0 + tr + 16 * a;
+      row_ok[a] = i < m;
+      const int pci = row_ok[a] ? pcol[i] : -1;
+      const bool in_R = pci >= c0 && pci < cn;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int j = cur.j0 + tc + 16 * q;
+        const bool keep = row_ok[a] && !in_R && j < m && !(j >= c0 && j < cn);
+        xin[a][q] = keep ? X[(size_t)j * ld + i] : df_zero();
+      }
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();   // this tile's buffer is complete; the other one is free
+    if (un < tot_t) prefetch(nxt, b ^ 1);
+    const Prow* Ps = Pbuf(b);
+    const Rrow* Rs = Rbuf(b);
+    DfAcc acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[a][q].init(df_zero());
+#pragma unroll 1
+    for (int k = 0; k < kPB; ++k) {
+      df64 pv[4], qv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) pv[a] = Ps[tr + 16 * a][k];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) qv[q] = Rs[k][tc + 16 * q];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[a][q].add(pv[a], qv[q]);
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      if (!row_ok[a]) continue;
+      const int r = tr + 16 * a, i = cur.i0 + r;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int j = cur.j0 + tc + 16 * q;
+        if (j >= m) continue;
+        const df64 v = (j >= c0 && j < cn) ? Ps[r][j - c0] : df_add(xin[a][q], acc[a][q].value());
+        X[(size_t)j * ld + i] = v;
+        if (j == cn && !used[i]) atomicMax(keys + cn, pivot_key(v, i));
+      }
+    }
+    cur = nxt;
+    u = un;
+    b ^= 1;
+  }
+}
+
 template <typename T, typename E>
 __device__ void refresh_body(Chain<T>* chains, int n_chains, int only_chain, int filter) {
   cg::grid_group grid = cg::this_grid();
@@ -129,15 +310,19 @@ __device__ void refresh_body(Chain<T>* chains, int n_chains, int only_chain, int
   __shared__ int offr[kMaxChains + 1];
   __shared__ int offt[kMaxChains + 1];
   __shared__ int max_m_s;
-  __shared__ E Ps[32][kPB + 1];
-  __shared__ E Rs[kPB][33];
+  constexpr int TB = trail_tile<E>();
+  // panel and pivot-row tiles: static for 32 x 32; the 64 x 64 double-float
+  // tiles are double-buffered in dynamic shared memory (refresh_dyn_smem bytes)
+  __shared__ E Ps[TB == 32 ? 32 : 1][kPB + 1];
+  __shared__ E Rs[TB == 32 ? kPB : 1][33];
+  extern __shared__ __align__(16) unsigned char refresh_dyn[];
   __shared__ double red[3][8];
 
   if (threadIdx.x == 0) max_m_s = 0;
   __syncthreads();
   for (int ci = threadIdx.x; ci < n_chains; ci += blockDim.x) {
     const int m = refresh_order(chains[ci], ci, c_lo, c_hi, filter);
-    const int tb = (m + 31) / 32;
+    const int tb = (m + TB - 1) / TB;
     offr[ci] = 2 * m;
     offt[ci] = 2 * tb * tb;
     atomicMax(&max_m_s, m);
@@ -184,39 +369,72 @@ __device__ void refresh_body(Chain<T>* chains, int n_chains, int only_chain, int
       Pa[(size_t)k * ld + ru.i] = X[(size_t)(c0 + k) * ld + ru.i];
     }
     grid.sync();
-    // A1: the column steps, on the panel only ((row unit, panel column) pairs)
+    // A1: the column steps, on the panel only: one thread per row unit, the
+    // row's panel values transformed column by column; the pivot key of the
+    // next column is reduced per warp before its atomic
     for (int k = 0; k < kPB; ++k) {
-      for (int u = gtid; u < tot_r * kPB; u += gthreads) {
-        const int kk = u / tot_r;
-        const RowUnit ru = row_unit(offr, n_chains, u - kk * tot_r);
-        if (c0 + k >= ru.m || c0 + kk >= ru.m) continue;
-        const Chain<T>& c = chains[ru.ci];
-        const int ld = c.ld, col = c0 + k, i = ru.i, spin = ru.spin;
-        E* X = reinterpret_cast<E*>(c.work + (size_t)spin * refresh_work_per_spin(ld));
-        E* Pa = X + (size_t)ld * ld;
-        E* Pb = Pa + (size_t)kPB * ld;
-        const E* src = (k & 1) ? Pb : Pa;
-        E* dst = (k & 1) ? Pa : Pb;
-        unsigned long long* keys = c.pkeys + (size_t)spin * ld;
-        int8_t* used = c.used + spin * ld;
-        const int pr = key_row(keys[col]);
-        const E piv = src[(size_t)k * ld + pr];
-        if (i == 0 && kk == 0) {
-          const double pd = el_to(piv);
-          c.perm[spin * ld + col] = pr;
-          used[pr] = 1;  // read below only for rows other than pr
-          c.pcol[spin * ld + pr] = col;
-          if (!(fabs(pd) > 0.0) || !isfinite(pd)) atomicOr(&c.dyn->status, DS_SINGULAR);
-          c.work_logdet[spin] += log(fabs(pd));
+      for (int ub = gtid - (int)(threadIdx.x & 31); ub < tot_r; ub += gthreads) {
+        const int u = ub + (int)(threadIdx.x & 31);
+        unsigned long long* kaddr = nullptr;
+        unsigned long long cand = 0ull;
+        if (u < tot_r) {
+          const RowUnit ru = row_unit(offr, n_chains, u);
+          if (c0 + k < ru.m) {
+            const Chain<T>& c = chains[ru.ci];
+            const int ld = c.ld, col = c0 + k, i = ru.i, spin = ru.spin;
+            const int nkk = min(kPB, ru.m - c0);
+            E* X = reinterpret_cast<E*>(c.work + (size_t)spin * refresh_work_per_spin(ld));
+            E* Pa = X + (size_t)ld * ld;
+            E* Pb = Pa + (size_t)kPB * ld;
+            const E* src = (k & 1) ? Pb : Pa;
+            E* dst = (k & 1) ? Pa : Pb;
+            unsigned long long* keys = c.pkeys + (size_t)spin * ld;
+            int8_t* used = c.used + spin * ld;
+            const int pr = key_row(keys[col]);
+            const E piv = src[(size_t)k * ld + pr];
+            if (i == 0) {
+              const double pd = el_to(piv);
+              c.perm[spin * ld + col] = pr;
+              used[pr] = 1;  // read below only for rows other than pr
+              c.pcol[spin * ld + pr] = col;
+              if (!(fabs(pd) > 0.0) || !isfinite(pd)) atomicOr(&c.dyn->status, DS_SINGULAR);
+              c.work_logdet[spin] += log(fabs(pd));
+            }
+            const E ipiv = el_recip(piv);
+            const E xic = src[(size_t)k * ld + i];
+            E vnext = el_zero<E>();
+            for (int kk = 0; kk < nkk; ++kk) {
+              E v;
+              if (i == pr) v = (kk == k) ? ipiv : el_mul(src[(size_t)kk * ld + pr], ipiv);
+              else if (kk == k) v = el_neg(el_mul(xic, ipiv));
+              else v = el_sub(src[(size_t)kk * ld + i], el_mul(xic, el_mul(src[(size_t)kk * ld + pr], ipiv)));
+              dst[(size_t)kk * ld + i] = v;
+              if (kk == k + 1) vnext = v;
+            }
+            if (k + 1 < nkk && i != pr && !used[i]) {
+              kaddr = keys + col + 1;
+              cand = pivot_key(vnext, i);
+            }
+          }
         }
-        const E ipiv = el_recip(piv);
-        const E xic = src[(size_t)k * ld + i];
-        E v;
-        if (i == pr) v = (kk == k) ? ipiv : el_mul(src[(size_t)kk * ld + pr], ipiv);
-        else if (kk == k) v = el_neg(el_mul(xic, ipiv));
-        else v = el_sub(src[(size_t)kk * ld + i], el_mul(xic, el_mul(src[(size_t)kk * ld + pr], ipiv)));
-        dst[(size_t)kk * ld + i] = v;
-        if (kk == k + 1 && i != pr && !used[i]) atomicMax(keys + col + 1, pivot_key(v, i));
+        // one atomic per warp where every lane with a candidate shares the key
+        const unsigned want = __ballot_sync(0xffffffffu, kaddr != nullptr);
+        if (want) {
+          const int lead = __ffs(want) - 1;
+          const unsigned long long* a0 = reinterpret_cast<const unsigned long long*>(
+              __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(kaddr), lead));
+          if (__all_sync(0xffffffffu, kaddr == nullptr || kaddr == a0)) {
+            unsigned long long mx = cand;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+              const unsigned long long y = __shfl_xor_sync(0xffffffffu, mx, o);
+              mx = y > mx ? y : mx;
+            }
+            if ((int)(threadIdx.x & 31) == lead) atomicMax(kaddr, mx);
+          } else if (kaddr) {
+            atomicMax(kaddr, cand);
+          }
+        }
       }
       grid.sync();
     }
@@ -234,14 +452,17 @@ __device__ void refresh_body(Chain<T>* chains, int n_chains, int only_chain, int
       Rr[(size_t)j * kPB + k] = (c0 + k < ru.m) ? X[(size_t)j * ld + perm[c0 + k]] : el_zero<E>();
     }
     grid.sync();
-    // B1: trailing rank-bw update in 32 x 32 tiles (tile units), panel written
+    // B1: trailing rank-bw update in TB x TB tiles (tile units), panel written
     // back, pivot key of the next panel's first column
+    if constexpr (TB == 64) {
+      trail_update_df64<T>(chains, n_chains, offr, offt, tot_t, c0, refresh_dyn);
+    } else {
     for (int u = blockIdx.x; u < tot_t; u += gridDim.x) {
       const int ci = find_chain(offt, n_chains, u);
       const int m = (offr[ci + 1] - offr[ci]) >> 1;
       if (c0 >= m) continue;  // uniform over the CTA
       const Chain<T>& c = chains[ci];
-      const int tb = (m + 31) / 32, l = u - offt[ci];
+      const int tb = (m + TB - 1) / TB, l = u - offt[ci];
       const int spin = l / (tb * tb), tile = l - spin * tb * tb;
       const int ld = c.ld, bw = min(kPB, m - c0), cn = c0 + bw;
       E* X = reinterpret_cast<E*>(c.work + (size_t)spin * refresh_work_per_spin(ld));
@@ -251,19 +472,20 @@ __device__ void refresh_body(Chain<T>* chains, int n_chains, int only_chain, int
       unsigned long long* keys = c.pkeys + (size_t)spin * ld;
       const int8_t* used = c.used + spin * ld;
       const int* pcol = c.pcol + spin * ld;
-      const int i0 = (tile % tb) * 32, j0 = (tile / tb) * 32;
+      const int i0 = (tile % tb) * TB, j0 = (tile / tb) * TB;
       __syncthreads();
-      for (int e = threadIdx.x; e < 32 * kPB; e += blockDim.x) {
-        const int r = e % 32, k = e / 32;
+      for (int e = threadIdx.x; e < TB * kPB; e += blockDim.x) {
+        const int r = e % TB, k = e / TB;
         Ps[r][k] = (i0 + r < m && k < bw) ? Pf[(size_t)k * ld + i0 + r] : el_zero<E>();
-        const int jj = e % 32, kk = e / 32;
+        const int kk = e % kPB, jj = e / kPB;   // Rr rows are contiguous in k
         Rs[kk][jj] = (j0 + jj < m) ? Rr[(size_t)(j0 + jj) * kPB + kk] : el_zero<E>();
       }
       __syncthreads();
+      {
       // thread (row r, column group g): columns q = g + 8c, c = 0..3, so that
       // each panel value Ps[r][k] is loaded once for four products
       const int r = threadIdx.x % 32, i = i0 + r, g = threadIdx.x / 32;
-      static_assert(kPB == 32, "a 32 x 32 tile per 256 threads");
+      static_assert(kPB == 32 && TB == 32, "a 32 x 32 tile per 256 threads");
       if (i < m) {
         const int pci = pcol[i];
         const bool in_R = pci >= c0 && pci < cn;
@@ -289,6 +511,8 @@ __device__ void refresh_body(Chain<T>* chains, int n_chains, int only_chain, int
           if (j == cn && !used[i]) atomicMax(keys + cn, pivot_key(v, i));
         }
       }
+      }
+    }
     }
     grid.sync();
   }

@@ -313,16 +313,17 @@ def test_mixed_tensor_core_flush_matches_cuda_core_flush(n0, k):
         assert err_tc <= 1e-4 and err_cc <= 1e-4
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-@pytest.mark.parametrize("n", [1, 31, 32, 33, 100, 430])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_df64"])
+@pytest.mark.parametrize("n", [1, 31, 32, 33, 63, 64, 65, 100, 129, 430])
 def test_refresh_inverse_at_panel_edges(n, precision):
-    """The blocked FP64 recomputation (32-column panels) at orders around panel edges."""
+    """The blocked recomputation (32-column panels; trailing tiles of 32, or 64 in
+    double-float) at orders around panel and tile edges."""
     ch = configs.cube8(K=256.0, k_max=32, capacity=512)
     cfg = configs.synthetic_configuration(ch, n, seed=n)
     oc = oracle_for(ch)
     oc.set_config(cfg["tau"], cfg["site"], cfg["s"], cfg["birth"], cfg["t"])
     prec = pk.CTAUX_FP64 if precision == "fp64" else pk.CTAUX_MIXED
-    with pk.Context([ch], precision=prec) as ctx:
+    with pk.Context([ch], precision=prec, refresh_df64=int(precision == "mixed_df64")) as ctx:
         ctx.set_config(0, cfg["tau"], cfg["site"], cfg["s"], cfg["birth"], cfg["t"])
         st = ctx.stats(0)
         for spin in (0, 1):
