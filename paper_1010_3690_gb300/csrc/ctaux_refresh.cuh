@@ -369,16 +369,23 @@ __device__ void refresh_body(Chain<T>* chains, int n_chains, int only_chain, int
       Pa[(size_t)k * ld + ru.i] = X[(size_t)(c0 + k) * ld + ru.i];
     }
     grid.sync();
-    // A1: the column steps, on the panel only: one thread per row unit, the
-    // row's panel values transformed column by column; the pivot key of the
-    // next column is reduced per warp before its atomic
+    // A1: the column steps, on the panel only.  Work unit = (row unit, group
+    // of W = 32 / G panel columns), G the largest power of two <= 32 with
+    // rows x G <= threads: few rows spread their columns over more threads,
+    // many rows take whole panel rows.  A unit's panel values are loaded in
+    // batches of 4 before they are transformed; the next column's pivot key
+    // is reduced per warp before its atomic.
+    int G = 1;
+    while (G < kPB && tot_r * (2 * G) <= gthreads) G *= 2;
+    const int W = kPB / G;
     for (int k = 0; k < kPB; ++k) {
-      for (int ub = gtid - (int)(threadIdx.x & 31); ub < tot_r; ub += gthreads) {
+      for (int ub = gtid - (int)(threadIdx.x & 31); ub < tot_r * G; ub += gthreads) {
         const int u = ub + (int)(threadIdx.x & 31);
         unsigned long long* kaddr = nullptr;
         unsigned long long cand = 0ull;
-        if (u < tot_r) {
-          const RowUnit ru = row_unit(offr, n_chains, u);
+        if (u < tot_r * G) {
+          const int grp = u / tot_r;
+          const RowUnit ru = row_unit(offr, n_chains, u - grp * tot_r);
           if (c0 + k < ru.m) {
             const Chain<T>& c = chains[ru.ci];
             const int ld = c.ld, col = c0 + k, i = ru.i, spin = ru.spin;
@@ -392,7 +399,7 @@ __device__ void refresh_body(Chain<T>* chains, int n_chains, int only_chain, int
             int8_t* used = c.used + spin * ld;
             const int pr = key_row(keys[col]);
             const E piv = src[(size_t)k * ld + pr];
-            if (i == 0) {
+            if (i == 0 && grp == 0) {
               const double pd = el_to(piv);
               c.perm[spin * ld + col] = pr;
               used[pr] = 1;  // read below only for rows other than pr
@@ -403,15 +410,28 @@ __device__ void refresh_body(Chain<T>* chains, int n_chains, int only_chain, int
             const E ipiv = el_recip(piv);
             const E xic = src[(size_t)k * ld + i];
             E vnext = el_zero<E>();
-            for (int kk = 0; kk < nkk; ++kk) {
-              E v;
-              if (i == pr) v = (kk == k) ? ipiv : el_mul(src[(size_t)kk * ld + pr], ipiv);
-              else if (kk == k) v = el_neg(el_mul(xic, ipiv));
-              else v = el_sub(src[(size_t)kk * ld + i], el_mul(xic, el_mul(src[(size_t)kk * ld + pr], ipiv)));
-              dst[(size_t)kk * ld + i] = v;
-              if (kk == k + 1) vnext = v;
+            for (int kb = grp * W; kb < grp * W + W; kb += 4) {
+              E xs[4], xp[4];
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                const int kk = kb + q;
+                const bool in = q < W && kk < nkk;
+                xs[q] = in ? src[(size_t)kk * ld + i] : el_zero<E>();
+                xp[q] = in ? src[(size_t)kk * ld + pr] : el_zero<E>();
+              }
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                const int kk = kb + q;
+                if (q >= W || kk >= nkk) continue;
+                E v;
+                if (i == pr) v = (kk == k) ? ipiv : el_mul(xp[q], ipiv);
+                else if (kk == k) v = el_neg(el_mul(xic, ipiv));
+                else v = el_sub(xs[q], el_mul(xic, el_mul(xp[q], ipiv)));
+                dst[(size_t)kk * ld + i] = v;
+                if (kk == k + 1) vnext = v;
+              }
             }
-            if (k + 1 < nkk && i != pr && !used[i]) {
+            if (k + 1 < nkk && (k + 1) / W == grp && i != pr && !used[i]) {
               kaddr = keys + col + 1;
               cand = pivot_key(vnext, i);
             }
