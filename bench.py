@@ -62,11 +62,18 @@ WORKLOADS = {
                   refresh_every=128, autotune="16,32,64,128", autotune_tiles=True),
 }
 
-# DRAM bytes per timed step of the dominant phase's kernels (dram__bytes_read.sum
-# + dram__bytes_write.sum, summed over the phase's launches of one block) from
-# one ncu capture of the same workload in the state the timed blocks run in
-# (summaries under profiles/); an entry is removed when its kernels change
-DRAM_TRAFFIC = {}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the
+# dominant kernel, per unit of work, from an ncu capture of the same kernel on a
+# smaller case (profiles/k_refresh_cube100_traffic.md).  The refresh reads and
+# writes its float64 work matrix X (8 m^2 bytes per spin, far above L2 at these
+# orders) once per 32-column panel, so its traffic grows as m^3: the capture at
+# m = 4000 (one chain, both spins, 66.1 GB) gives bytes per m^3, scaled to a
+# launch by the sum of m^3 over the chains it refreshes.  An entry is removed
+# when its kernel changes.
+DRAM_TRAFFIC = {
+    ("cube100", "fp64", "refresh"): (32925212672 + 33162264064) / 4000.0 ** 3,
+    ("cube100", "mixed_df64", "refresh"): (32591805952 + 33272619776) / 4000.0 ** 3,
+}
 
 
 def workload(name, K=None, k_max=None, chain_id=0, n_chains=None):
@@ -715,9 +722,16 @@ def measure_form(args, pk, torch, dist, chains, meta, refresh, form, local, worl
             # N is read by the R~ and the G_{old,new} products: one read per spin is
             # the algorithmic minimum
             n_mean = meta_order_mean[0]
-            return dict(bound="alu", achieved=dw["prep_flop"] / sec / 1e12, peak=alu_peak,
-                        unit="TFLOP/s", peak_source=alu_src,
-                        alg_bytes_per_step=2.0 * elem * n_mean * n_mean * len(chains))
+            r = dict(achieved=dw["prep_flop"] / sec / 1e12, unit="TFLOP/s",
+                     alg_bytes_per_step=2.0 * elem * n_mean * n_mean * len(chains))
+            if precision == pk.CTAUX_MIXED:
+                # products 0 and 1 on the tensor cores (3xTF32), the small k x k
+                # product on the CUDA cores
+                r.update(bound="tensor", peak=tf32x3_peak,
+                         peak_source=f"3xTF32 = bf16 {peak_kind} x 1100/2250 / 3 products")
+            else:
+                r.update(bound="alu", peak=alu_peak, peak_source=alu_src)
+            return r
         if nm == "proposals":
             a = dw["gamma_flop"] / sec / 1e12
             return dict(bound="alu", achieved=a, peak=alu_peak, unit="TFLOP/s",
@@ -749,7 +763,8 @@ def measure_form(args, pk, torch, dist, chains, meta, refresh, form, local, worl
     # construction) is reported in phase_ms_per_step only
     dom = int(phase_ms[:names.index("tie_refine")].argmax())
     r = roof(dom)
-    traffic = DRAM_TRAFFIC.get((args.workload, form, names[dom]))
+    coef = DRAM_TRAFFIC.get((args.workload, form, names[dom]))
+    traffic = coef * sum(float(m) ** 3 for m in orders) if coef else None
     roofline = {"kernel": names[dom], "bound": r["bound"], "achieved": r["achieved"],
                 "peak": r["peak"], "unit": r["unit"],
                 "frac": r["achieved"] / r["peak"] if r["peak"] else None,
