@@ -490,7 +490,8 @@ def main():
         sec = results[form]
         line[form] = {k: sec["line"][k] for k in ("value", "ms_per_step", "dtype", "roofline",
                                                  "flush_roofline", "phase_ms_per_step",
-                                                 "drift_max_last_refresh", "order_n",
+                                                 "drift_max_last_refresh",
+                                                 "drift_rel_max_last_refresh", "order_n",
                                                  "near_ties", "tie_refreshes", "gpu_launches",
                                                  "refreshes_in_timed_region", "clocks")}
         line[f"{form}_vs_fp64"] = sec["line"]["value"] / prim["line"]["value"]
@@ -819,6 +820,9 @@ def measure_form(args, pk, torch, dist, chains, meta, refresh, form, local, worl
             "gpu_launches": kernels,
             "accept_rate": acc / max(1, steps * sum(c.k_max for c in chains) * world),
             "drift_max_last_refresh": max(ctx.stats(i)["last_drift_max"] for i in range(len(chains))),
+            # the same relative to max |N| of each chain's fresh N
+            "drift_rel_max_last_refresh": max(ctx.stats(i)["last_drift_rel"]
+                                              for i in range(len(chains))),
             "near_ties": ties, "tie_refreshes": tie_refreshes,
             "clocks": clk}
     if measurement is not None:

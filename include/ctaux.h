@@ -135,11 +135,12 @@ typedef struct {
                                          max |N_run - N_fresh| / max |N_fresh| exceeds it makes
                                          the next synchronous call return CTAUX_EDRIFT once (the
                                          chain continues from the fresh N); 0 = off */
-  int mixed_prep_tc;                  /* mixed form with mixed_flush_tc: 1 = the prep products
-                                         (rows of the extended N and G columns of the new
-                                         vertices, Sec. IV A) on the tensor cores, split 3xTF32;
-                                         the flush and the refresh then also keep N^T; 0 =
-                                         float32 CUDA-core products.  Needs capacity + k_max > 96 */
+  int mixed_prep_tc;                  /* mixed form with mixed_flush_tc: 1 = the two large prep
+                                         products (rows of the extended N and G columns of the
+                                         new vertices over the old ones, Sec. IV A) on the tensor
+                                         cores, split 3xTF32; the flush step and the refresh then
+                                         also keep N^T; 0 = float32 CUDA-core products.  Needs
+                                         capacity + k_max > 96 */
   int tc_wait_limit;                  /* mixed form, tensor-core flush: most polls of one
                                          pipeline wait before the kernel stops with
                                          CTAUX_ETIMEOUT; 0 = 2^24 (seconds).  A negative value
