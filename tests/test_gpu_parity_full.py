@@ -53,11 +53,13 @@ def _forms():
     return [("fp64", pk.CTAUX_FP64, RTOL64, 1e-8), ("mixed", pk.CTAUX_MIXED, RTOL_MIXED, 1e-4)]
 
 
-def test_cube100_full_size_k256_prefix_and_flush():
+@pytest.mark.parametrize("gamma", ["inverse", "lu"])
+def test_cube100_full_size_k256_prefix_and_flush(gamma):
     """The 100-site cluster as the benchmark runs it: K=5700, k_max=256, 8 chains
-    started at order 7000, one block.  Chain 0's first proposals against the
-    oracle (about a second each at this order), and every chain's N after the
-    rank-k_acc flush (k_acc ~ 220) against the inverse of its configuration."""
+    started at order 7000, one block, Gamma as its inverse or as L U.  Chain 0's
+    first proposals against the oracle (about a second each at this order), and
+    every chain's N after the rank-k_acc flush (k_acc ~ 220) against the inverse
+    of its configuration."""
     n_chains, order, n_replay = 8, 7000, 10
     chains = [configs.cube100(K=5700.0, k_max=256, capacity=9216, seed=i, chain_id=i)
               for i in range(n_chains)]
@@ -67,7 +69,7 @@ def test_cube100_full_size_k256_prefix_and_flush():
     recs = oc.run(n_replay)
     for name, prec, rtol, ntol in _forms():
         with pk.Context(chains, precision=prec, trace_capacity=256, refresh_every=0,
-                        use_graph=1) as ctx:
+                        use_graph=1, gamma_form=1 if gamma == "lu" else 0) as ctx:
             _start(ctx, chains, order)
             ctx.sweep(1, measure=True)
             ctx.synchronize()
@@ -79,7 +81,7 @@ def test_cube100_full_size_k256_prefix_and_flush():
             st = ctx.stats(0)
             k_acc = int(sum(st["accepted"]))
             errs = [_check_N_is_inverse(ctx, c, oc, ntol) for c in (0, n_chains - 1)]
-            print(f"cube100 {name}: worst ratio error {worst:.2e} over {k} proposals, "
+            print(f"cube100 {name} {gamma}: worst ratio error {worst:.2e} over {k} proposals, "
                   f"{k_acc} accepted in the block, N error {max(errs):.2e}")
 
 
@@ -110,17 +112,19 @@ def test_sq36_full_size_block_parity(name, prec, rtol):
               f"near ties {st['near_ties']}, N error {nerr:.2e}, sign {st['sign']}")
 
 
+@pytest.mark.parametrize("gamma", [0, 1])
 @pytest.mark.parametrize("prec", [0, 1])
-def test_k256_whole_blocks_against_oracle(prec):
-    """k_max = 256 (Gamma^{-1} of 2 x 256 x 257 entries, kept in global memory)
-    over three blocks of the 2x2x2 cluster at order 430.  In the mixed form a
-    block ends early at a near tie (decided in FP64 and applied by the next
-    block), so its trace holds at most 3 x 256 records."""
+def test_k256_whole_blocks_against_oracle(prec, gamma):
+    """k_max = 256 (Gamma^{-1}, or L U, of 2 x 256 x 257 entries, kept in global
+    memory) over three blocks of the 2x2x2 cluster at order 430.  In the mixed
+    form a block ends early at a near tie (decided in FP64 and applied by the
+    next block), so its trace holds at most 3 x 256 records."""
     ch = configs.cube8(K=256.0, k_max=256, capacity=1024)
     cfg = configs.synthetic_configuration(ch, 430, seed=5)
     oc = oracle_for(ch)
     oc.set_config(cfg["tau"], cfg["site"], cfg["s"], cfg["birth"], cfg["t"])
-    with pk.Context([ch], precision=prec, trace_capacity=768, refresh_every=0) as ctx:
+    with pk.Context([ch], precision=prec, trace_capacity=768, refresh_every=0,
+                    gamma_form=gamma) as ctx:
         ctx.set_config(0, cfg["tau"], cfg["site"], cfg["s"], cfg["birth"], cfg["t"])
         ctx.sweep(3)
         ctx.synchronize()
@@ -130,7 +134,8 @@ def test_k256_whole_blocks_against_oracle(prec):
         worst = compare_traces(tr, oc.run(len(tr)), RTOL64 if prec == 0 else RTOL_MIXED)
         assert st["t"] == oc.t
         compare_config(ctx, 0, oc)
-        print(f"cube8 k=256 precision {prec}: {len(tr)} proposals, worst ratio error {worst:.2e}, "
+        print(f"cube8 k=256 precision {prec} gamma {gamma}: {len(tr)} proposals, "
+              f"worst ratio error {worst:.2e}, "
               f"near ties {st['near_ties']}")
 
 
