@@ -33,12 +33,20 @@ struct ctaux_ctx {
   int blocks_since_refresh = 0;
   std::string err;
   int max_ld = 0;
-  // CUDA graphs of one block (with its near-tie launch) and of one measurement,
-  // captured on first use on a private stream, with their kernel counts per phase
+  // CUDA graphs of one block (with its near-tie launch), of one measurement,
+  // and of one block with the previous block's measurement beside it (on the
+  // side stream), captured on first use on a private stream, with their
+  // kernel counts per phase
   cudaStream_t capture_stream = nullptr;
-  cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
-  long long graph_kernels[2][PhaseTimer::kPhases] = {};
+  cudaStream_t side_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaGraphExec_t graph_exec[3] = {nullptr, nullptr, nullptr};
+  long long graph_kernels[3][PhaseTimer::kPhases] = {};
   bool graph_failed = false;
+  // graph mode: the measurement of the last block swept, not yet launched (it
+  // runs beside the next block, or alone before any other call reads or
+  // changes the state)
+  bool meas_pending = false;
   // tile-variant table of the products (the autotuner's cache), host copy
   std::vector<int8_t> tile_table = std::vector<int8_t>(kTileTable, 0);
   int8_t* tile_table_dev = nullptr;
@@ -115,7 +123,7 @@ ctaux_status build_chains(ctaux_ctx* ctx) {
   ls.kchunk = (sizeof(T) == 8) ? 32 : 128;
   // split-K partial tiles per (chain, spin): the most any product of the chain
   // can use at its capacity, at most kMaxPartials (device rule in gemm_items)
-  std::vector<size_t> kpart_of(ctx->chains.size(), 1);
+  std::vector<size_t> kpart_of(ctx->chains.size(), 1), kpart_meas_of(ctx->chains.size(), 1);
   for (size_t ci = 0; ci < ctx->chains.size(); ++ci) {
     const ctaux_chain_params& cp = ctx->chains[ci];
     const long cap_m = cp.capacity + cp.k_max, k = cp.k_max;
@@ -129,8 +137,11 @@ ctaux_status build_chains(ctaux_ctx* ctx) {
         const long tiles = ((rows[ph] + tl.bm - 1) / tl.bm) * ((cols[ph] + tl.bn - 1) / tl.bn);
         const long k_inner = ph == PH_FLUSH ? k : cap_m;
         const long ks = std::max<long>(1, (k_inner + ls.kchunk - 1) / ls.kchunk);
-        if (ks > 1)
-          need = std::max(need, (size_t)std::min<long>(kMaxPartials, tiles * ks) * tl.bm * tl.bn);
+        if (ks > 1) {
+          const size_t el = (size_t)std::min<long>(kMaxPartials, tiles * ks) * tl.bm * tl.bn;
+          need = std::max(need, el);
+          if (ph == PH_MEAS) kpart_meas_of[ci] = std::max(kpart_meas_of[ci], el);
+        }
       }
     kpart_of[ci] = need;
   }
@@ -250,6 +261,7 @@ ctaux_status build_chains(ctaux_ctx* ctx) {
       c.birth[b] = dalloc<int64_t>(ctx, ld, &err);
     }
     c.s0 = dalloc<int8_t>(ctx, ld, &err);
+    c.s_meas = dalloc<int8_t>(ctx, ld, &err);
     // panel rows: k_max, or whole 128-row TMA boxes for the tensor-core prep
     const size_t KR = prep_tc ? (size_t)round_up(std::max(cp.k_max, 128), 128) : K;
     for (int spin = 0; spin < 2; ++spin) {
@@ -265,6 +277,8 @@ ctaux_status build_chains(ctaux_ctx* ctx) {
       c.Mpts[spin] = dalloc<double>(ctx, (size_t)ls.meas_lchunks * P.n_anchors * cp.n_c * P.n_tau_bins, &err);
       c.kpart[spin] = dalloc<T>(ctx, kpart_of[ci], &err);
       c.ticket[spin] = dalloc<int>(ctx, kMaxPartials, &err);
+      c.kpart_meas[spin] = dalloc<T>(ctx, kpart_meas_of[ci], &err);
+      c.ticket_meas[spin] = dalloc<int>(ctx, kMaxPartials, &err);
     }
     c.gamma_lu = P.gamma_form == CTAUX_GAMMA_LU ? 1 : 0;
     c.kp = round_up(cp.k_max, 32);
@@ -436,6 +450,29 @@ ctaux_status do_sweeps(ctaux_ctx* ctx, int n_sweeps, int measure, cudaStream_t s
     launch_measure<T>(dc, ctx->ls, s, p);
     return cudaSuccess;
   };
+  // a block with the previous block's measurement beside it: the measurement's
+  // head first, its tail on the side stream from the block's proposals to its end
+  struct Tail {
+    Chain<T>* dc;
+    const LaunchShape* ls;
+    int kernels;
+  } tail{dc, &ctx->ls, 0};
+  auto block_meas = [&](cudaStream_t s, PhaseTimer* p) -> cudaError_t {
+    int nk = launch_measure_head<T>(dc, ctx->ls, s);
+    BlockFork fk{ctx->side_stream, ctx->ev_fork, ctx->ev_join,
+                 [](void* a, cudaStream_t side) {
+                   Tail* t = static_cast<Tail*>(a);
+                   t->kernels = launch_measure_tail<T>(t->dc, *t->ls, side);
+                 },
+                 &tail};
+    launch_block<T>(dc, ctx->ls, s, p, ctx->tc_maps_dev, &fk);
+    p->kernels[5] += nk + tail.kernels;
+    if (!ties) return cudaSuccess;
+    p->begin(7, s);
+    cudaError_t e = launch_tie_refine(reinterpret_cast<Chain<float>*>(dc), ctx->ls, s);
+    p->end(7, s, 1);
+    return e;
+  };
   // graph mode (not while profiling: the phase events would be frozen into the graph)
   const bool graphs = ctx->params.use_graph && !pt->on && !ctx->graph_failed;
   auto run = [&](int which, auto&& body) -> cudaError_t {
@@ -465,8 +502,21 @@ ctaux_status do_sweeps(ctaux_ctx* ctx, int n_sweeps, int measure, cudaStream_t s
     }
     return body(st, pt);
   };
+  // with graphs, the measurement of block s (after its refresh, if one is due)
+  // runs beside block s + 1, also across calls; it is left pending after the
+  // last block, and launched alone (n_sweeps = 0) before any other entry point
+  // reads or changes the state
+  const bool can_fold = graphs && ctx->side_stream != nullptr;
+  bool pend = ctx->meas_pending;
+  ctx->meas_pending = false;
+  if (pend && (n_sweeps == 0 || !can_fold)) {
+    cudaError_t e = run(1, meas);
+    if (e != cudaSuccess) return set_err(ctx, CTAUX_ECUDA, "measurement launch: %s", cudaGetErrorString(e));
+    pend = false;
+  }
   for (int s = 0; s < n_sweeps; ++s) {
-    cudaError_t e = run(0, block);
+    cudaError_t e = pend ? run(2, block_meas) : run(0, block);
+    pend = false;
     if (e != cudaSuccess) return set_err(ctx, CTAUX_ECUDA, "block launch: %s", cudaGetErrorString(e));
     ctx->blocks_since_refresh += 1;
     if (ctx->params.refresh_every > 0 && ctx->blocks_since_refresh >= ctx->params.refresh_every) {
@@ -475,14 +525,33 @@ ctaux_status do_sweeps(ctaux_ctx* ctx, int n_sweeps, int measure, cudaStream_t s
       ctx->blocks_since_refresh = 0;
     }
     if (measure) {
-      e = run(1, meas);
-      if (e != cudaSuccess) return set_err(ctx, CTAUX_ECUDA, "measurement launch: %s", cudaGetErrorString(e));
+      if (can_fold) {
+        pend = true;
+      } else {
+        e = run(1, meas);
+        if (e != cudaSuccess) return set_err(ctx, CTAUX_ECUDA, "measurement launch: %s", cudaGetErrorString(e));
+      }
     }
   }
+  ctx->meas_pending = pend;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return set_err(ctx, CTAUX_ECUDA, "sweep launch: %s", cudaGetErrorString(e));
   return CTAUX_OK;
 }
+
+// Launch the pending measurement (graph mode) on the sweeps' stream.
+ctaux_status flush_pending(ctaux_ctx* ctx) {
+  if (!ctx->meas_pending) return CTAUX_OK;
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  return is_mixed(ctx) ? do_sweeps<float>(ctx, 0, 0, ctx->last_stream)
+                       : do_sweeps<double>(ctx, 0, 0, ctx->last_stream);
+}
+
+#define FLUSH_PENDING(ctx)                          \
+  do {                                              \
+    const ctaux_status _fp = flush_pending(ctx);    \
+    if (_fp != CTAUX_OK) return _fp;                \
+  } while (0)
 
 }  // namespace
 
@@ -539,6 +608,11 @@ ctaux_status ctaux_init(const ctaux_params* params, ctaux_ctx** out) {
     if (ge != cudaSuccess) {
       cudaGetLastError();
       ctx->graph_failed = true;
+    } else if (cudaStreamCreateWithFlags(&ctx->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
+               cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+               cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      ctx->side_stream = nullptr;   // measurements then run after their blocks
     }
   }
   *out = ctx;
@@ -557,6 +631,7 @@ ctaux_status ctaux_sweep(ctaux_ctx* ctx, int n_sweeps, int measure, void* cuda_s
 
 ctaux_status ctaux_synchronize(ctaux_ctx* ctx) {
   if (!ctx) return CTAUX_EINVAL;
+  FLUSH_PENDING(ctx);
   CUDA_TRY(ctx, cudaStreamSynchronize(ctx->last_stream));
   CUDA_TRY(ctx, cudaGetLastError());
   return check_device_status(ctx);
@@ -565,6 +640,7 @@ ctaux_status ctaux_synchronize(ctaux_ctx* ctx) {
 ctaux_status ctaux_get_accumulators(ctaux_ctx* ctx, int chain, double* sum_out, double* sumsq_out,
                                     double* bin_sum_out, double* bin_sumsq_out, int64_t* counts_out) {
   if (!ctx || chain < 0 || chain >= (int)ctx->chains.size()) return CTAUX_EINVAL;
+  FLUSH_PENDING(ctx);
   CUDA_TRY(ctx, cudaStreamSynchronize(ctx->last_stream));
   const ctaux_chain_params& cp = ctx->chains[chain];
   const size_t nb = (size_t)2 * cp.n_classes * ctx->params.n_tau_bins;
@@ -590,6 +666,7 @@ ctaux_status ctaux_get_accumulators(ctaux_ctx* ctx, int chain, double* sum_out, 
 ctaux_status ctaux_measure_G(ctaux_ctx* ctx, int chain, double* G_out, double* err_out,
                              int64_t* n_meas_out) {
   if (!ctx || chain < 0 || chain >= (int)ctx->chains.size() || !G_out) return CTAUX_EINVAL;
+  FLUSH_PENDING(ctx);
   const ctaux_chain_params& cp = ctx->chains[chain];
   const size_t nb = (size_t)2 * cp.n_classes * ctx->params.n_tau_bins;
   std::vector<double> sum(nb), sq(nb), bs(nb), bq(nb);
@@ -619,6 +696,7 @@ ctaux_status ctaux_measure_G(ctaux_ctx* ctx, int chain, double* G_out, double* e
 ctaux_status ctaux_measure_G_matsubara(ctaux_ctx* ctx, int chain, double* G_out, double* err_out,
                                        int64_t* n_meas_out) {
   if (!ctx || chain < 0 || chain >= (int)ctx->chains.size() || !G_out) return CTAUX_EINVAL;
+  FLUSH_PENDING(ctx);
   if (ctx->params.n_matsubara <= 0)
     return set_err(ctx, CTAUX_EINVAL, "the context measures no Matsubara frequencies (n_matsubara = 0)");
   CUDA_TRY(ctx, cudaStreamSynchronize(ctx->last_stream));
@@ -648,6 +726,7 @@ ctaux_status ctaux_measure_G_matsubara(ctaux_ctx* ctx, int chain, double* G_out,
 
 ctaux_status ctaux_reset_measurements(ctaux_ctx* ctx) {
   if (!ctx) return CTAUX_EINVAL;
+  FLUSH_PENDING(ctx);
   if (is_mixed(ctx))
     launch_reset_measure<float>(reinterpret_cast<Chain<float>*>(ctx->chains_dev), ctx->ls, ctx->last_stream);
   else
@@ -658,6 +737,7 @@ ctaux_status ctaux_reset_measurements(ctaux_ctx* ctx) {
 
 ctaux_status ctaux_recompute(ctaux_ctx* ctx, double* drift_max_out) {
   if (!ctx) return CTAUX_EINVAL;
+  FLUSH_PENDING(ctx);
   ctaux_status r = is_mixed(ctx) ? do_refresh<float>(ctx, -1, ctx->last_stream)
                                  : do_refresh<double>(ctx, -1, ctx->last_stream);
   if (r != CTAUX_OK) return r;
@@ -677,6 +757,7 @@ ctaux_status ctaux_recompute(ctaux_ctx* ctx, double* drift_max_out) {
 
 ctaux_status ctaux_get_stats(ctaux_ctx* ctx, int chain, ctaux_stats* out) {
   if (!ctx || !out || chain < 0 || chain >= (int)ctx->chains.size()) return CTAUX_EINVAL;
+  FLUSH_PENDING(ctx);
   Dyn d;
   ctaux_status r = read_dyn(ctx, chain, &d);
   if (r != CTAUX_OK) return r;
@@ -710,6 +791,7 @@ ctaux_status ctaux_get_stats(ctaux_ctx* ctx, int chain, ctaux_stats* out) {
 ctaux_status ctaux_get_trace(ctaux_ctx* ctx, int chain, ctaux_trace_rec* buf, int cap, int* n_out) {
   if (!ctx || chain < 0 || chain >= (int)ctx->chains.size() || (!buf && cap > 0) || !n_out)
     return CTAUX_EINVAL;
+  FLUSH_PENDING(ctx);
   *n_out = 0;
   const int tc = ctx->params.trace_capacity;
   if (tc <= 0) return CTAUX_OK;
@@ -734,6 +816,7 @@ ctaux_status ctaux_get_trace(ctaux_ctx* ctx, int chain, ctaux_trace_rec* buf, in
 ctaux_status ctaux_get_config(ctaux_ctx* ctx, int chain, double* tau, int* site, int* s,
                               int64_t* birth, int cap, int* n_out, int64_t* t_out) {
   if (!ctx || chain < 0 || chain >= (int)ctx->chains.size() || !n_out) return CTAUX_EINVAL;
+  FLUSH_PENDING(ctx);
   Dyn d;
   ctaux_status r = read_dyn(ctx, chain, &d);
   if (r != CTAUX_OK) return r;
@@ -760,6 +843,7 @@ ctaux_status ctaux_get_config(ctaux_ctx* ctx, int chain, double* tau, int* site,
 ctaux_status ctaux_set_config(ctaux_ctx* ctx, int chain, const double* tau, const int* site,
                               const int* s, const int64_t* birth, int n, int64_t t) {
   if (!ctx || chain < 0 || chain >= (int)ctx->chains.size() || n < 0 || t < 0) return CTAUX_EINVAL;
+  FLUSH_PENDING(ctx);
   const ctaux_chain_params& cp = ctx->chains[chain];
   if (n > cp.capacity) return set_err(ctx, CTAUX_ECAPACITY, "order %d above capacity %d", n, cp.capacity);
   if (n > 0 && (!tau || !site || !s || !birth)) return CTAUX_EINVAL;
@@ -815,6 +899,7 @@ ctaux_status ctaux_set_config(ctaux_ctx* ctx, int chain, const double* tau, cons
 ctaux_status ctaux_get_N(ctaux_ctx* ctx, int chain, int spin, double* out, int ld_out, int* m_out) {
   if (!ctx || chain < 0 || chain >= (int)ctx->chains.size() || spin < 0 || spin > 1 || !m_out)
     return CTAUX_EINVAL;
+  FLUSH_PENDING(ctx);
   Dyn d;
   ctaux_status r = read_dyn(ctx, chain, &d);
   if (r != CTAUX_OK) return r;
@@ -841,6 +926,7 @@ ctaux_status ctaux_get_N(ctaux_ctx* ctx, int chain, int spin, double* out, int l
 
 ctaux_status ctaux_set_profiling(ctaux_ctx* ctx, int on) {
   if (!ctx) return CTAUX_EINVAL;
+  FLUSH_PENDING(ctx);
   if (ctx->profiling && !on) ctx->timer->collect();
   ctx->profiling = on != 0;
   ctx->timer->on = ctx->profiling;
@@ -849,6 +935,7 @@ ctaux_status ctaux_set_profiling(ctaux_ctx* ctx, int on) {
 
 ctaux_status ctaux_get_phase_times(ctaux_ctx* ctx, double* ms_out, int64_t* kernels_out) {
   if (!ctx) return CTAUX_EINVAL;
+  FLUSH_PENDING(ctx);
   ctx->timer->collect();
   for (int p = 0; p < PhaseTimer::kPhases; ++p) {
     if (ms_out) ms_out[p] = ctx->timer->ms[p];
@@ -861,6 +948,7 @@ ctaux_status ctaux_get_work(ctaux_ctx* ctx, double* prep_flop, double* flush_flo
                             double* gamma_flop, double* meas_flop, double* refresh_flop,
                             double* mats_flop) {
   if (!ctx) return CTAUX_EINVAL;
+  FLUSH_PENDING(ctx);
   double a = 0.0, b = 0.0, c = 0.0, g = 0.0, me = 0.0, rf = 0.0, mw = 0.0;
   for (size_t ci = 0; ci < ctx->chains.size(); ++ci) {
     Dyn d;
@@ -886,6 +974,7 @@ ctaux_status ctaux_get_work(ctaux_ctx* ctx, double* prep_flop, double* flush_flo
 
 ctaux_status ctaux_set_kmax(ctaux_ctx* ctx, int chain, int k_max) {
   if (!ctx || chain < 0 || chain >= (int)ctx->chains.size()) return CTAUX_EINVAL;
+  FLUSH_PENDING(ctx);
   if (k_max < 1 || k_max > ctx->chains[chain].k_max) return CTAUX_EINVAL;  // buffers sized at init
   CUDA_TRY(ctx, cudaStreamSynchronize(ctx->last_stream));
   if (is_mixed(ctx)) {
@@ -909,6 +998,7 @@ int current_kmax(ctaux_ctx* ctx, int chain) {
 ctaux_status ctaux_autotune_k(ctaux_ctx* ctx, const int* candidates, int n_candidates, int n_blocks,
                               int* k_out, double* rate_out) {
   if (!ctx || !candidates || n_candidates < 1 || n_blocks < 1) return CTAUX_EINVAL;
+  FLUSH_PENDING(ctx);
   for (int i = 0; i < n_candidates; ++i)
     if (candidates[i] < 1 || candidates[i] > kMaxK) return CTAUX_EINVAL;
   const int nch = (int)ctx->chains.size();
@@ -1022,6 +1112,7 @@ ctaux_status ctaux_autotune_k(ctaux_ctx* ctx, const int* candidates, int n_candi
 
 ctaux_status ctaux_set_tile_table(ctaux_ctx* ctx, const int8_t* table) {
   if (!ctx || !table) return CTAUX_EINVAL;
+  FLUSH_PENDING(ctx);
   for (int i = 0; i < kTileTable; ++i)
     if (table[i] < 0 || table[i] >= kTileVariants) return CTAUX_EINVAL;
   CUDA_TRY(ctx, cudaStreamSynchronize(ctx->last_stream));
@@ -1033,7 +1124,7 @@ ctaux_status ctaux_set_tile_table(ctaux_ctx* ctx, const int8_t* table) {
     ctx->ls.tile_mask[ph] = mask;
   }
   // captured graphs hold the old set of launches
-  for (int w = 0; w < 2; ++w)
+  for (int w = 0; w < 3; ++w)
     if (ctx->graph_exec[w]) {
       cudaGraphExecDestroy(ctx->graph_exec[w]);
       ctx->graph_exec[w] = nullptr;
@@ -1049,6 +1140,7 @@ ctaux_status ctaux_get_tile_table(ctaux_ctx* ctx, int8_t* table_out) {
 
 ctaux_status ctaux_autotune_tiles(ctaux_ctx* ctx, int n_blocks, int8_t* table_out, double* gain_out) {
   if (!ctx || n_blocks < 1) return CTAUX_EINVAL;
+  FLUSH_PENDING(ctx);
   const int nch = (int)ctx->chains.size();
   const bool mixed = is_mixed(ctx);
   // products this context launches on the CUDA cores, with the phase timer and
@@ -1162,9 +1254,12 @@ void ctaux_destroy(ctaux_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->last_stream);
-  for (int w = 0; w < 2; ++w)
+  for (int w = 0; w < 3; ++w)
     if (ctx->graph_exec[w]) cudaGraphExecDestroy(ctx->graph_exec[w]);
   if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
+  if (ctx->side_stream) cudaStreamDestroy(ctx->side_stream);
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   for (void* p : ctx->allocations) cudaFree(p);
   if (ctx->timer) {
     if (ctx->timer->created)

@@ -293,7 +293,10 @@ __device__ __forceinline__ void gemm_item(const Chain<T>& c, const Dyn& d, int l
     __syncthreads();
   }
   if (nslices > 1) {
-    T* part = c.kpart[spin] + (size_t)tile * nslices * GBM * GBN;
+    // the measurement product has partial tiles and tickets of its own: it
+    // may run beside a block's products
+    T* part = (PHASE == PH_MEAS ? c.kpart_meas[spin] : c.kpart[spin]) + (size_t)tile * nslices * GBM * GBN;
+    int* tickets = PHASE == PH_MEAS ? c.ticket_meas[spin] : c.ticket[spin];
 #pragma unroll
     for (int a = 0; a < TM; ++a)
 #pragma unroll
@@ -301,7 +304,7 @@ __device__ __forceinline__ void gemm_item(const Chain<T>& c, const Dyn& d, int l
         part[(size_t)ks * GBM * GBN + (ty + NTY * a) * GBN + tx + NTX * b] = acc[a][b];
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) *s_last = (atomicAdd(c.ticket[spin] + tile, 1) == nslices - 1);
+    if (threadIdx.x == 0) *s_last = (atomicAdd(tickets + tile, 1) == nslices - 1);
     __syncthreads();
     if (!*s_last) return;
     __threadfence();
@@ -314,7 +317,7 @@ __device__ __forceinline__ void gemm_item(const Chain<T>& c, const Dyn& d, int l
           v += __ldcg(part + (size_t)q * GBM * GBN + (ty + NTY * a) * GBN + tx + NTX * b);
         acc[a][b] = v;
       }
-    if (threadIdx.x == 0) c.ticket[spin][tile] = 0;
+    if (threadIdx.x == 0) tickets[tile] = 0;
   }
 #pragma unroll
   for (int a = 0; a < TM; ++a) {
@@ -1334,7 +1337,7 @@ int lu_inverse_smem(const LaunchShape& ls) {
 
 template <typename T>
 void launch_block(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t st, PhaseTimer* pt,
-                  const TcMaps* maps) {
+                  const TcMaps* maps, const BlockFork* fork) {
   const int nch = ls.n_chains;
   pt->begin(0, st);
   k_plan<T><<<nch, 256, 0, st>>>(dchains);
@@ -1351,6 +1354,14 @@ void launch_block(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t st, Pha
     nk += launch_gemm<T>(dchains, ls, PH_GCOL_OLD, st);
     nk += launch_gemm<T>(dchains, ls, PH_GCOL_NEW, st);
     pt->end(1, st, nk);
+  }
+  if (fork) {
+    // side work from here on (the proposals change the spins, the flush writes
+    // the other buffer of N and of the configuration)
+    cudaEventRecord(fork->ev_fork, st);
+    cudaStreamWaitEvent(fork->side, fork->ev_fork, 0);
+    fork->fn(fork->arg, fork->side);
+    cudaEventRecord(fork->ev_join, fork->side);
   }
   pt->begin(2, st);
   if (ls.gamma_lu) {
@@ -1386,6 +1397,7 @@ void launch_block(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t st, Pha
   } else {
     pt->end(3, st, launch_gemm<T>(dchains, ls, PH_FLUSH, st));
   }
+  if (fork) cudaStreamWaitEvent(st, fork->ev_join, 0);   // the side work ends before the block does
   k_finish_block<T><<<(nch + 127) / 128, 128, 0, st>>>(dchains, nch);
   pt->kernels[4] += 1;
 }
@@ -1404,9 +1416,9 @@ cudaError_t configure_block_kernels(const LaunchShape& ls) {
 template int launch_gemm<double>(Chain<double>*, const LaunchShape&, int, cudaStream_t);
 template int launch_gemm<float>(Chain<float>*, const LaunchShape&, int, cudaStream_t);
 template void launch_block<double>(Chain<double>*, const LaunchShape&, cudaStream_t, PhaseTimer*,
-                                   const TcMaps*);
+                                   const TcMaps*, const BlockFork*);
 template void launch_block<float>(Chain<float>*, const LaunchShape&, cudaStream_t, PhaseTimer*,
-                                  const TcMaps*);
+                                  const TcMaps*, const BlockFork*);
 template cudaError_t configure_block_kernels<double>(const LaunchShape&);
 template cudaError_t configure_block_kernels<float>(const LaunchShape&);
 

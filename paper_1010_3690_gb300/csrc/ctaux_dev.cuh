@@ -137,6 +137,9 @@ struct Chain {
   const int8_t* tile_var;    // tile-variant table of the products (tile_table_index)
   T* kpart[2];               // split-K partial tiles
   int* ticket[2];            // split-K arrival counters per output tile
+  T* kpart_meas[2];          // the same for the measurement product, which may run beside a block
+  int* ticket_meas[2];
+  int8_t* s_meas;            // spins of the measured configuration, copied when a measurement starts
   double* work;              // refresh: per spin X (ld x ld), two panels, pivot rows (float64)
   int* perm;                 // refresh pivot rows [spin][ld]
   int8_t* used;              // refresh pivot flags [spin][ld]

@@ -154,9 +154,18 @@ struct PhaseTimer {
   }
 };
 
+// Work run beside a block on a second stream: forked before the block's
+// proposals, joined before its end (k_finish_block).
+struct BlockFork {
+  cudaStream_t side;
+  cudaEvent_t ev_fork, ev_join;
+  void (*fn)(void* arg, cudaStream_t side);
+  void* arg;
+};
+
 template <typename T>
 void launch_block(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t st, PhaseTimer* pt,
-                  const TcMaps* maps);
+                  const TcMaps* maps, const BlockFork* fork = nullptr);
 template <typename T>
 cudaError_t configure_block_kernels(const LaunchShape& ls);
 template <typename T>
@@ -166,6 +175,13 @@ int refresh_blocks_per_sm(bool df);
 size_t refresh_work_doubles(int ld);
 template <typename T>
 void launch_measure(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t st, PhaseTimer* pt);
+// The measurement in two parts: the head (counters, G0 panels and the copy of
+// the spins) must run before the next block's proposals change the spins; the
+// tail reads only what the next block leaves alone until its end.
+template <typename T>
+int launch_measure_head(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t st);
+template <typename T>
+int launch_measure_tail(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t st);
 template <typename T>
 cudaError_t launch_refresh(Chain<T>* dchains, const LaunchShape& ls, int only_chain,
                            cudaStream_t st, PhaseTimer* pt, int filter = 0);

@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(256) k_mats_phase(Chain<T>* chains) {
     const int l = c.vorder[p];
     double sn, cs;
     sincos(mats_w(f, c.beta) * c.tau[buf][l], &sn, &cs);
-    const int si = c.s[buf][l] + 2;
+    const int si = c.s_meas[l] + 2;
     static_cast<C2*>(c.PhR)[e] = C2{(T)cs, (T)(-sn)};
     const double e0 = c.ev[0][si] - 1.0, e1 = c.ev[1][si] - 1.0;
     static_cast<C2*>(c.PhL[0])[e] = C2{(T)(e0 * cs), (T)(e0 * sn)};

@@ -32,6 +32,11 @@ __global__ void __launch_bounds__(256) k_meas_gather(Chain<T>* chains) {
     const double nd = (double)n;
     d.work_meas += 2.0 * (2.0 * nd * nd * A + 2.0 * A * (double)c.n_c * c.n_bins * nd);
   }
+  // the spins of the measured configuration: the next block's proposals may
+  // change them while the rest of the measurement runs
+  if (spin == 0)
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+      c.s_meas[v] = c.s[buf][v];
   const long total = (long)n * A;
   for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (long)gridDim.x * blockDim.x) {
@@ -158,7 +163,7 @@ __global__ void __launch_bounds__(256) k_meas_eval(Chain<T>* chains, int n_chain
           st.tau[q] = c.tau[buf][v];
           st.site[q] = c.site[buf][v];
         } else {
-          const double em1 = c.ev[spin][c.s[buf][v] + 2] - 1.0;
+          const double em1 = c.ev[spin][c.s_meas[v] + 2] - 1.0;
           st.w[b][q] = (T)(em1 * (double)c.Mv[spin][(long)b * c.ld + v]);
         }
       }
@@ -182,7 +187,7 @@ __global__ void __launch_bounds__(256) k_meas_eval(Chain<T>* chains, int n_chain
     }
     const double* tau = c.tau[buf];
     const int* site = c.site[buf];
-    const int8_t* s = c.s[buf];
+    const int8_t* s = c.s_meas;
     const int bin = pt % B, xa = (pt / B) % c.n_c, b = pt / (B * c.n_c);
     const double tb = (double)b * c.beta / (double)A;
     const double tc = ((double)bin + 0.5) * c.beta / (double)B;
@@ -285,15 +290,26 @@ __global__ void k_meas_reset(Chain<T>* chains) {
 }
 
 template <typename T>
-void launch_measure(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t st, PhaseTimer* pt) {
+int launch_measure_head(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t st) {
+  k_meas_gather<T><<<dim3(ls.gather_slices, 2, ls.n_chains), 256, 0, st>>>(dchains);
+  return 1;
+}
+
+template <typename T>
+int launch_measure_tail(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t st) {
   const int nch = ls.n_chains;
-  pt->begin(5, st);
-  k_meas_gather<T><<<dim3(ls.gather_slices, 2, nch), 256, 0, st>>>(dchains);
   const int ng = launch_gemm<T>(dchains, ls, PH_MEAS, st);
   k_meas_eval<T><<<ls.persist_ctas, 256, 0, st>>>(dchains, nch);
   k_meas_accumulate<T><<<dim3(ls.meas_acc_blocks, 2, nch), 256, 0, st>>>(dchains);
   if (ls.mats) launch_matsubara<T>(dchains, ls, st);
-  pt->end(5, st, 3 + ng + (ls.mats ? 5 : 0));
+  return 2 + ng + (ls.mats ? 5 : 0);
+}
+
+template <typename T>
+void launch_measure(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t st, PhaseTimer* pt) {
+  pt->begin(5, st);
+  const int nk = launch_measure_head<T>(dchains, ls, st);
+  pt->end(5, st, nk + launch_measure_tail<T>(dchains, ls, st));
 }
 
 template <typename T>
@@ -302,6 +318,10 @@ void launch_reset_measure(Chain<T>* dchains, const LaunchShape& ls, cudaStream_t
 }
 
 template void launch_measure<double>(Chain<double>*, const LaunchShape&, cudaStream_t, PhaseTimer*);
+template int launch_measure_head<double>(Chain<double>*, const LaunchShape&, cudaStream_t);
+template int launch_measure_head<float>(Chain<float>*, const LaunchShape&, cudaStream_t);
+template int launch_measure_tail<double>(Chain<double>*, const LaunchShape&, cudaStream_t);
+template int launch_measure_tail<float>(Chain<float>*, const LaunchShape&, cudaStream_t);
 template void launch_measure<float>(Chain<float>*, const LaunchShape&, cudaStream_t, PhaseTimer*);
 template void launch_reset_measure<double>(Chain<double>*, const LaunchShape&, cudaStream_t);
 template void launch_reset_measure<float>(Chain<float>*, const LaunchShape&, cudaStream_t);

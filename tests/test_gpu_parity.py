@@ -522,6 +522,42 @@ def test_graph_launches_equal_direct_launches(precision):
     assert s0["t"] == s1["t"] and s0["refreshes"] == s1["refreshes"]
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_measurement_beside_the_next_block_equals_serial_order(precision):
+    """In graph mode the measurement of a block runs beside the next block (its
+    spins copied before that block's proposals, its split-K partial tiles apart
+    from the block's).  Four chains of uneven order, the Matsubara measurement
+    on, two refreshes on the way: the accumulated G(tau), G(i omega), traces and
+    configurations equal direct launches (measurement after each block) bit
+    for bit."""
+    chs = configs.batch(n_chains=4, k_max=32, n_tau=512)
+    prec = pk.CTAUX_MIXED if precision == "mixed" else pk.CTAUX_FP64
+    out = []
+    for graph in (0, 1):
+        with pk.Context(chs, precision=prec, refresh_every=4, trace_capacity=2048,
+                        use_graph=graph, n_matsubara=8) as ctx:
+            for i, ch in enumerate(chs):
+                n0 = min(300 + 100 * i, ch.capacity - 2 * ch.k_max)
+                cfg = configs.synthetic_configuration(ch, n0, seed=40 + i)
+                ctx.set_config(i, cfg["tau"], cfg["site"], cfg["s"], cfg["birth"], cfg["t"])
+            ctx.sweep(2, measure=False)
+            for _ in range(2):
+                ctx.sweep(5, measure=True)
+            ctx.synchronize()
+            res = []
+            for i in range(len(chs)):
+                res.append((ctx.trace(i), ctx.get_config(i), ctx.measure_G(i)[0],
+                            ctx.measure_G_matsubara(i)[0], ctx.stats(i)["measurements"]))
+            out.append(res)
+    for a, b in zip(*out):
+        np.testing.assert_array_equal(a[0], b[0])
+        for key in ("tau", "site", "s", "birth"):
+            np.testing.assert_array_equal(a[1][key], b[1][key])
+        np.testing.assert_array_equal(a[2], b[2])
+        np.testing.assert_array_equal(a[3], b[3])
+        assert a[4] == b[4] == 10
+
+
 @pytest.mark.parametrize("n0,k", [(430, 64), (1000, 128), (60, 32), (300, 256)])
 def test_mixed_tensor_core_prep_matches_oracle_and_cuda_core_prep(n0, k):
     """The prep products on the tensor cores (split 3xTF32 with separate main and
