@@ -50,9 +50,8 @@ N_TAU_BINS, N_ANCHORS = 32, 4
 # the chains start from (0 = empty), the order the CPU oracle samples at,
 # chains per GPU and the refresh cadence.
 WORKLOADS = {
-    # Gamma as L U at k = 256 (measured faster there; the inverse elsewhere)
     "cube100": dict(K=5700.0, k_max=256, thermalize=5, start_order=7000, n_target=7000,
-                    chains=8, refresh_every=32, gamma="lu"),
+                    chains=8, refresh_every=32),
     "cube8": dict(K=256.0, k_max=64, thermalize=300, start_order=0, n_target=430, chains=1,
                   refresh_every=32),
     "sq36": dict(K=1400.0, k_max=128, thermalize=200, start_order=0, n_target=2000, chains=1,
@@ -443,8 +442,7 @@ def main():
                          "host core (the paper's CPU comparison, Sec. V A) at --cpu-orders")
     ap.add_argument("--cpu-orders", dest="cpu_orders", default="512,1024,2048")
     ap.add_argument("--gamma", choices=["inverse", "lu"], default=None,
-                    help="how a block keeps Gamma: partitioned inverse or L U (Sec. III D); "
-                         "default: the workload's (L U for cube100, else the inverse)")
+                    help="how a block keeps Gamma: partitioned inverse (default) or L U (Sec. III D)")
     ap.add_argument("--k-sweep", dest="k_sweep", default=None,
                     help="comma-separated k_max values: print proposals/s per k instead")
     args = ap.parse_args()

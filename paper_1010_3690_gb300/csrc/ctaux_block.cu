@@ -463,34 +463,61 @@ __device__ __forceinline__ void lu_solve_pair(const T* G, int LG, const A* iu, A
                                               int j, int ht, int hw, int lane) {
   for (int r0 = r_start & ~31; r0 < j; r0 += 32) {
     const int r1 = min(j, r0 + 32), nb = r1 - r0, r = r0 + lane;
-    if (hw == 0) {
-      A v = (r < r1) ? y[r] : (A)0;
-      for (int t = 0; t < nb - 1; ++t) {
-        const A yt = __shfl_sync(0xffffffffu, v, t);
-        if (lane > t && r < r1) v -= (A)G[(size_t)r * LG + r0 + t] * yt;
+    if (hw < 2) {
+      // the diagonal block first, in registers (one memory latency instead of
+      // one per step): warp 0 lane i holds L[r0 + i][r0 + t], warp 1 lane i
+      // holds U[r0 + t][r0 + i], for t < i
+      A m[32];
+#pragma unroll
+      for (int t = 0; t < 32; ++t) {
+        const bool in = t < lane && r < r1;
+        m[t] = in ? (A)(hw == 0 ? G[(size_t)r * LG + r0 + t] : G[(size_t)(r0 + t) * LG + r]) : (A)0;
       }
-      if (r < r1) y[r] = v;
-    } else if (hw == 1) {
-      A v = (r < r1) ? x[r] : (A)0;
-      for (int t = 0; t < nb - 1; ++t) {
-        const A xt = __shfl_sync(0xffffffffu, v, t) * iu[r0 + t];
-        if (lane > t && r < r1) v -= (A)G[(size_t)(r0 + t) * LG + r] * xt;
+      if (hw == 0) {
+        A v = (r < r1) ? y[r] : (A)0;
+#pragma unroll
+        for (int t = 0; t < 31; ++t) {
+          const A yt = __shfl_sync(0xffffffffu, v, t);
+          if (t < lane) v -= m[t] * yt;
+        }
+        if (r < r1) y[r] = v;
+      } else {
+        const A iur = (r < r1) ? iu[r] : (A)0;
+        A v = (r < r1) ? x[r] : (A)0;
+#pragma unroll
+        for (int t = 0; t < 31; ++t) {
+          const A xt = __shfl_sync(0xffffffffu, v, t) * __shfl_sync(0xffffffffu, iur, t);
+          if (t < lane) v -= m[t] * xt;
+        }
+        if (r < r1) x[r] = v * iur;
       }
-      if (r < r1) x[r] = v * iu[r];
     }
     __syncthreads();
     if (r1 < j) {
-      // rows below the block: y_r -= L[r, blk] y_blk, x_r -= U[blk, r]^T x_blk
-      for (int e = ht; e < 2 * (j - r1); e += 128) {
-        const int rr = r1 + (e >> 1);
-        A acc = (A)0;
-        if (e & 1) {
-          for (int t = r0; t < r1; ++t) acc += (A)G[(size_t)t * LG + rr] * x[t];
-          x[rr] -= acc;
+      // rows below the block: y_r -= L[r, blk] y_blk (threads [0, j - r1)),
+      // x_r -= U[blk, r]^T x_blk (the next j - r1 threads: U's rows are read
+      // along r, coalesced); several loads in flight per thread
+      const int below = j - r1;
+      for (int e = ht; e < 2 * below; e += 128) {
+        const bool isx = e >= below;
+        const int rr = r1 + (isx ? e - below : e);
+        A a0 = (A)0, a1 = (A)0;
+        if (isx) {
+          const T* Uc = G + (size_t)r0 * LG + rr;
+#pragma unroll 8
+          for (int t = 0; t < nb; t += 2) {
+            a0 += (A)Uc[(size_t)t * LG] * x[r0 + t];
+            if (t + 1 < nb) a1 += (A)Uc[(size_t)(t + 1) * LG] * x[r0 + t + 1];
+          }
+          x[rr] -= a0 + a1;
         } else {
-          const T* Lr = G + (size_t)rr * LG;
-          for (int t = r0; t < r1; ++t) acc += (A)Lr[t] * y[t];
-          y[rr] -= acc;
+          const T* Lr = G + (size_t)rr * LG + r0;
+#pragma unroll 8
+          for (int t = 0; t < nb; t += 2) {
+            a0 += (A)Lr[t] * y[r0 + t];
+            if (t + 1 < nb) a1 += (A)Lr[t + 1] * y[r0 + t + 1];
+          }
+          y[rr] -= a0 + a1;
         }
       }
       __syncthreads();
@@ -756,7 +783,7 @@ __device__ __forceinline__ void proposals_body(Chain<T>* chains) {
               part += wv[r] * acc;
             }
           }
-        } else {
+        } else if constexpr (GS) {
           for (int r = ht; r < j; r += 128) {
             A a0 = (A)0, a1 = (A)0;
             const T* Gr = G + (size_t)r * LG;
@@ -767,6 +794,23 @@ __device__ __forceinline__ void proposals_body(Chain<T>* chains) {
             }
             if (cc < j) a0 += (A)Gr[cc] * sv[cc];
             const A y = a0 + a1;
+            yv[r] = y;
+            part += wv[r] * y;
+          }
+        } else {
+          // Gamma^{-1} in global memory: four accumulators, several loads in flight
+          for (int r = ht; r < j; r += 128) {
+            A a0 = (A)0, a1 = (A)0, a2 = (A)0, a3 = (A)0;
+            const T* Gr = G + (size_t)r * LG;
+            int cc = 0;
+            for (; cc + 3 < j; cc += 4) {
+              a0 += (A)Gr[cc] * sv[cc];
+              a1 += (A)Gr[cc + 1] * sv[cc + 1];
+              a2 += (A)Gr[cc + 2] * sv[cc + 2];
+              a3 += (A)Gr[cc + 3] * sv[cc + 3];
+            }
+            for (; cc < j; ++cc) a0 += (A)Gr[cc] * sv[cc];
+            const A y = (a0 + a1) + (a2 + a3);
             yv[r] = y;
             part += wv[r] * y;
           }
@@ -986,28 +1030,57 @@ __device__ __forceinline__ void proposals_body(Chain<T>* chains) {
           }
         } else {
           for (int cc = ht; cc < j; cc += 128) {
-            A a0 = (A)0, a1 = (A)0;
+            A a0 = (A)0, a1 = (A)0, a2 = (A)0, a3 = (A)0;
             int r = 0;
-            for (; r + 1 < j; r += 2) {
+            for (; r + 3 < j; r += 4) {
               a0 += wv[r] * (A)G[(size_t)r * LG + cc];
               a1 += wv[r + 1] * (A)G[(size_t)(r + 1) * LG + cc];
+              a2 += wv[r + 2] * (A)G[(size_t)(r + 2) * LG + cc];
+              a3 += wv[r + 3] * (A)G[(size_t)(r + 3) * LG + cc];
             }
-            if (r < j) a0 += wv[r] * (A)G[(size_t)r * LG + cc];
-            zv[cc] = (a0 + a1) * sc;
+            for (; r < j; ++r) a0 += wv[r] * (A)G[(size_t)r * LG + cc];
+            zv[cc] = ((a0 + a1) + (a2 + a3)) * sc;
           }
         }
         __syncthreads();
-        // (j+1) x (j+1) update: rows from ht / 16, columns from ht % 16 (no division)
         const int j1 = j + 1;
-        for (int r = ht >> 4; r < j1; r += 8) {
-          const A yr = (r < j) ? yv[r] : (A)0;
-          for (int cc = ht & 15; cc < j1; cc += 16) {
-            A v;
-            if (r < j && cc < j) v = (A)G[(size_t)r * LG + cc] + yr * zv[cc];
-            else if (r < j) v = -yr * sc;
-            else if (cc < j) v = -zv[cc];
-            else v = sc;
-            G[(size_t)r * LG + cc] = (T)v;
+        if constexpr (GS) {
+          // (j+1) x (j+1) update: rows from ht / 16, columns from ht % 16 (no division)
+          for (int r = ht >> 4; r < j1; r += 8) {
+            const A yr = (r < j) ? yv[r] : (A)0;
+            for (int cc = ht & 15; cc < j1; cc += 16) {
+              A v;
+              if (r < j && cc < j) v = (A)G[(size_t)r * LG + cc] + yr * zv[cc];
+              else if (r < j) v = -yr * sc;
+              else if (cc < j) v = -zv[cc];
+              else v = sc;
+              G[(size_t)r * LG + cc] = (T)v;
+            }
+          }
+        } else {
+          // global memory: items of (column, chunk of 8 rows), consecutive
+          // items on consecutive columns (a warp reads a row segment
+          // coalesced), spread evenly over the threads
+          const int nrc = (j1 + 7) >> 3;
+          for (int e = ht; e < j1 * nrc; e += 128) {
+            const int cc = e % j1, rb = (e / j1) * 8, re = min(j1, rb + 8);
+            const bool old_col = cc < j;
+            const A zc = old_col ? zv[cc] : (A)0;
+            A g8[8];   // the chunk's old values, loaded before any store
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              const int r = rb + u;
+              g8[u] = (r < re && r < j && old_col) ? (A)G[(size_t)r * LG + cc] : (A)0;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              const int r = rb + u;
+              if (r >= re) break;
+              A v;
+              if (r < j) v = old_col ? g8[u] + yv[r] * zc : -yv[r] * sc;
+              else v = old_col ? -zc : sc;
+              G[(size_t)r * LG + cc] = (T)v;
+            }
           }
         }
         if (ht == 0) {
