@@ -9,22 +9,24 @@
 // with C = G0(new, old)(e^{V_old} - 1) and B = G0(old, new) (the gathered
 // panels), as 128 x 128 output tiles of a tcgen05 GEMM with the split 3xTF32
 // product of Ootomo & Yokota (2022): hi*hi in one float32 TMEM accumulator,
-// hi*lo + lo*hi in a second one, added in the epilogue.
+// hi*lo + lo*hi in a second one, added in the epilogue.  The split truncates
+// (bit masks, no conversion instructions): the converter warps set the
+// kernel's pace.
 //
 // Both operands are read by TMA as K-major float32 rows (K = the old-vertex
 // index l): C and B are the panels' rows, the columns of N (column-major) are
 // the K-major rows of product 0's B operand, and product 1's A operand is
 // N^T (rows of N), a copy that the flush and the refresh keep beside N.
-// Converter warps split every staged float32 tile into tf32 hi = rna(x) and
-// lo = rna(x - hi) and zero the elements with l >= n (so rows of N_ext being
-// written, and stale panel entries, never enter a product).
+// Converter warps split every staged float32 tile into tf32 hi (x truncated)
+// and lo (x - hi truncated) and zero the elements with l >= n (so rows of
+// N_ext being written, and stale panel entries, never enter a product).
 //
 // One persistent CTA per SM, warp-specialised like the tensor-core flush:
 //   warp 0 (one thread): TMA producer into a ring of raw float32 stages;
 //   warp 1 (one thread): MMA issuer, 6 tcgen05.mma per 16-wide K chunk into
 //     one of two TMEM accumulator pairs (main hi*hi, correction hi*lo + lo*hi);
-//   warp 2: TMEM allocation;
-//   warps 4-7: converters, raw stage -> split stage;
+//   warps 2-7: converters, raw stage -> split stage (warp 2 allocates the
+//     TMEM first);
 //   warps 8-11: epilogue, TMEM lane quarter w % 4, all 128 columns: adds each
 //     segment's partial tile to the float32 tile accumulator in shared memory
 //     and writes the tile after the last segment.
@@ -43,6 +45,7 @@ namespace {
 
 using namespace tc;
 constexpr int kRawStages = 3, kSplitStages = 3;
+constexpr int kConvWarps = 6;   // warps 2..7 (warp 2 allocates the TMEM first)
 // K chunks accumulated in TMEM before the epilogue adds the partial tile to a
 // float32 accumulator in shared memory (round to nearest): the tensor cores'
 // own additions truncate, so long inner dimensions are summed in segments
@@ -125,7 +128,7 @@ __device__ __forceinline__ void split_group(const float4 x, int off_in_tile, int
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
     if (k0 + e < K) {
-      split_tf32(xs[e], h[e], l[e]);
+      split_tf32_trunc(xs[e], h[e], l[e]);
     } else {
       h[e] = 0.f;
       l[e] = 0.f;
@@ -178,10 +181,10 @@ __global__ void __launch_bounds__(kPrepThreads, 1) k_prep_tc(Chain<float>* chain
   if (threadIdx.x == 0) {
     for (int s = 0; s < kRawStages; ++s) {
       mbar_init(smem_u32(rfull + s), 1);
-      mbar_init(smem_u32(rempty + s), 4);   // one arrival per converter warp
+      mbar_init(smem_u32(rempty + s), kConvWarps);   // one arrival per converter warp
     }
     for (int s = 0; s < kSplitStages; ++s) {
-      mbar_init(smem_u32(sfull + s), 4);    // one arrival per converter warp
+      mbar_init(smem_u32(sfull + s), kConvWarps);    // one arrival per converter warp
       mbar_init(smem_u32(sempty + s), 1);   // tcgen05.commit
     }
     for (int b = 0; b < 2; ++b) {
@@ -229,9 +232,9 @@ __global__ void __launch_bounds__(kPrepThreads, 1) k_prep_tc(Chain<float>* chain
         break;
       }
     }
-  } else if (warp >= 4 && warp < 8) {
+  } else if (warp >= 8 - kConvWarps && warp < 8) {
     // ---- converters: raw float32 stage -> hi / lo split stage
-    const int ct = threadIdx.x - 128;  // 0..127
+    const int ct = threadIdx.x - 32 * (8 - kConvWarps);  // 0 .. 32 kConvWarps - 1
     uint32_t taken = 0;
     for (int w = blockIdx.x; w < total; w += gridDim.x) {
       if (__any_sync(0xffffffffu, *err_s != 0)) break;
@@ -248,8 +251,7 @@ __global__ void __launch_bounds__(kPrepThreads, 1) k_prep_tc(Chain<float>* chain
         unsigned char* sb = split + ss * kSplitStageBytes;
         // 2 tiles x 512 groups of 16 bytes, 8 per thread
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const int g = ct + 128 * q;               // 0..1023
+        for (int g = ct; g < 1024; g += 32 * kConvWarps) {   // 2 tiles x 512 groups
           const int tile = g >> 9, o = (g & 511) * 16;
           const float4 x = *reinterpret_cast<const float4*>(rb + tile * kTileBytes + o);
           float4 hi, lo;
@@ -275,7 +277,7 @@ __global__ void __launch_bounds__(kPrepThreads, 1) k_prep_tc(Chain<float>* chain
         break;
       }
     }
-    if (threadIdx.x == 128) *conv_taken = taken;
+    if (threadIdx.x == 32 * (8 - kConvWarps)) *conv_taken = taken;
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer: each segment of kSegChunks K chunks into the next free
     // accumulator pair

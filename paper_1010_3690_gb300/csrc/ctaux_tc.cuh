@@ -108,5 +108,13 @@ __device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
   lo = __uint_as_float(l);
 }
 
+// The same split by truncation, without conversions: hi = x with its low 13
+// significand bits cleared (a tf32 value), lo = (x - hi) (exact in float32)
+// likewise truncated.  hi + lo keeps 22 of x's 24 significand bits.
+__device__ __forceinline__ void split_tf32_trunc(float x, float& hi, float& lo) {
+  hi = __uint_as_float(__float_as_uint(x) & 0xffffe000u);
+  lo = __uint_as_float(__float_as_uint(x - hi) & 0xffffe000u);
+}
+
 }  // namespace tc
 }  // namespace ctaux
