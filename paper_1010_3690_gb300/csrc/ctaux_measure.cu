@@ -237,11 +237,13 @@ __global__ void k_meas_accumulate(Chain<T>* chains) {
     const int cls = e / B, bin = e % B;
     const double* Mp = c.Mpts[spin];
     double acc = 0.0;
-    const int terms = A * nc * nchunks;
-    for (int u = lane; u < terms; u += 32) {
-      const int q = u % nchunks, r = u / nchunks, xa = r % nc, b = r / nc;
+    // only the sites of this class (a warp-uniform test), lanes over the chunks
+    for (int xa = 0; xa < nc; ++xa) {
       if (c.dx_class[xa * nc] != cls) continue;
-      acc += Mp[(size_t)q * npts + (b * nc + xa) * B + bin];
+      for (int b = 0; b < A; ++b) {
+        const double* src = Mp + (size_t)(b * nc + xa) * B + bin;
+        for (int q = lane; q < nchunks; q += 32) acc += src[(size_t)q * npts];
+      }
     }
     acc = warp_sum(acc);
     if (lane == 0) {
