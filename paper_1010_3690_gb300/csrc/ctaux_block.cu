@@ -1339,28 +1339,48 @@ __global__ void __launch_bounds__(256) k_flush_y(Chain<T>* chains, int n_chains)
     }
     __syncthreads();
     const T* Gi = c.Ginv[spin];
+    const int LGi = KM + 1;
     if constexpr (!SPLIT) {
+      // float64: one (row, column) per thread (the FP64 pipe bounds it)
       for (int e = threadIdx.x; e < kYRows * kacc; e += blockDim.x) {
         const int aa = e % kYRows, r = e / kYRows;
         if (Si[aa] < 0) continue;
         A acc = (A)0;
-        for (int q = 0; q < kacc; ++q) acc += gh[q * kYRows + aa] * (A)Gi[(size_t)q * (KM + 1) + r];
+        for (int q = 0; q < kacc; ++q) acc += gh[q * kYRows + aa] * (A)Gi[(size_t)q * LGi + r];
         c.Y[spin][(size_t)r * c.ld + a0 + aa] = (T)acc;
       }
-    } else {
-      const int KP = c.kp;
-      for (int e = threadIdx.x; e < kYRows * KP; e += blockDim.x) {
-        const int r = e % KP, aa = e / KP;
-        if (Si[aa] < 0) continue;
-        float hi = 0.f, lo = 0.f;
-        if (r < kacc) {
-          float acc = 0.f;
-          for (int q = 0; q < kacc; ++q)
-            acc += (float)gh[q * kYRows + aa] * (float)Gi[(size_t)q * (KM + 1) + r];
-          split_tf32_y(acc, hi, lo);
+      continue;
+    }
+    // float32: a thread per column r of Y; the 16 rows' sums share each
+    // Gamma^{-1} load (a column of Gamma^{-1}, read coalesced across the
+    // threads), sums in q order
+    const int ncol = SPLIT ? c.kp : kacc;
+    for (int r = threadIdx.x; r < ncol; r += blockDim.x) {
+      A acc[kYRows];
+#pragma unroll
+      for (int aa = 0; aa < kYRows; ++aa) acc[aa] = (A)0;
+      if (r < kacc) {
+        for (int q = 0; q < kacc; ++q) {
+          const A g = (A)Gi[(size_t)q * LGi + r];
+          const A* gq = gh + q * kYRows;
+#pragma unroll
+          for (int aa = 0; aa < kYRows; ++aa) acc[aa] += gq[aa] * g;
         }
-        c.Yh[spin][(size_t)(a0 + aa) * KP + r] = hi;
-        c.Yl[spin][(size_t)(a0 + aa) * KP + r] = lo;
+      }
+      if constexpr (!SPLIT) {
+#pragma unroll
+        for (int aa = 0; aa < kYRows; ++aa)
+          if (Si[aa] >= 0) c.Y[spin][(size_t)r * c.ld + a0 + aa] = (T)acc[aa];
+      } else {
+        const int KP = c.kp;
+#pragma unroll
+        for (int aa = 0; aa < kYRows; ++aa) {
+          if (Si[aa] < 0) continue;
+          float hi = 0.f, lo = 0.f;
+          if (r < kacc) split_tf32_y((float)acc[aa], hi, lo);
+          c.Yh[spin][(size_t)(a0 + aa) * KP + r] = hi;
+          c.Yl[spin][(size_t)(a0 + aa) * KP + r] = lo;
+        }
       }
     }
   }

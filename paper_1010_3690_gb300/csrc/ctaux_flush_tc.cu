@@ -384,38 +384,44 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_flush_tc(Chain<float>* chains
 }
 
 // N'^T for the tensor-core prep (its G_{old,new} = N B reads rows of N as
-// K-major rows): 32 x 32 tiles of the flushed N' through shared memory, all
-// chains, both spins; nothing to do for a block that left N unchanged.
+// K-major rows): 64 x 64 tiles of the flushed N' through shared memory (16
+// loads in flight per thread), all chains, both spins; nothing to do for a
+// block that left N unchanged.
 __global__ void __launch_bounds__(256) k_transpose_n(Chain<float>* chains, int n_chains) {
-  __shared__ float tile[32][33];
+  __shared__ float tile[64][65];
   __shared__ int off[kMaxChains + 1];
   for (int ci = threadIdx.x; ci < n_chains; ci += blockDim.x) {
     const Dyn& d = *chains[ci].dyn;
-    const int tb = (d.n_new + 31) / 32;
+    const int tb = (d.n_new + 63) / 64;
     off[ci] = (d.status || d.flush_noop || !chains[ci].NT[0][0]) ? 0 : 2 * tb * tb;
   }
   __syncthreads();
   block_exclusive_scan(off, n_chains);
   const int total = off[n_chains];
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;  // 64 x 4
   for (int w = blockIdx.x; w < total; w += gridDim.x) {
     const int ci = find_chain(off, n_chains, w);
     const Chain<float>& c = chains[ci];
     const Dyn& d = *c.dyn;
-    const int nn = d.n_new, tb = (nn + 31) / 32, l = w - off[ci];
+    const int nn = d.n_new, tb = (nn + 63) / 64, l = w - off[ci];
     const int spin = l / (tb * tb), t = l % (tb * tb);
-    const int i0 = (t % tb) * 32, j0 = (t / tb) * 32, ld = c.ld;
+    const int i0 = (t % tb) * 64, j0 = (t / tb) * 64, ld = c.ld;
     const float* src = c.N[1 - d.buf][spin];   // the flush wrote the other buffer
     float* dst = c.NT[1 - d.buf][spin];
     __syncthreads();
-    for (int r = ty; r < 32; r += 8) {
-      const int i = i0 + tx, j = j0 + r;
-      tile[r][tx] = (i < nn && j < nn) ? src[(long)j * ld + i] : 0.f;   // N'[i][j]
+    float v[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int i = i0 + tx, j = j0 + ty + 4 * u;
+      v[u] = (i < nn && j < nn) ? src[(long)j * ld + i] : 0.f;   // N'[i][j]
     }
+#pragma unroll
+    for (int u = 0; u < 16; ++u) tile[ty + 4 * u][tx] = v[u];
     __syncthreads();
-    for (int r = ty; r < 32; r += 8) {
-      const int i = i0 + r, j = j0 + tx;
-      if (i < nn && j < nn) dst[(long)i * ld + j] = tile[tx][r];      // N'^T[j][i] = N'[i][j]
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int i = i0 + ty + 4 * u, j = j0 + tx;
+      if (i < nn && j < nn) dst[(long)i * ld + j] = tile[tx][ty + 4 * u];   // N'^T[j][i] = N'[i][j]
     }
   }
 }
