@@ -863,10 +863,26 @@ __device__ __forceinline__ void proposals_body(Chain<T>* chains) {
     }
     __syncthreads();
     if (tid == 0) {
-      double R = f_s * ratio_s[0] * ratio_s[1];
-      const double pacc = fmin(1.0, fabs(R));
-      bool accept = dr.u_acc < pacc;
-      bool finite = isfinite(R);
+      double R;
+      bool accept, finite, near;
+      // float32 form: the product and the comparisons in float32 (the ratios
+      // are float32 already; a decision that the rounding of the product or of
+      // u could change lies inside the guard band, which is decided in FP64),
+      // unless the float32 product overflows
+      const float Rf = (sizeof(T) == 4) ? (float)f_s * (float)ratio_s[0] * (float)ratio_s[1] : 0.f;
+      if (sizeof(T) == 4 && isfinite(Rf)) {
+        const float uf = (float)dr.u_acc, aR = fabsf(Rf);
+        R = (double)Rf;
+        finite = true;
+        accept = uf < fminf(1.f, aR);
+        near = fabsf(uf - aR) < (float)(tie_guard > 0.0 ? tie_guard : kTieGuard) * fmaxf(uf, aR);
+      } else {
+        R = f_s * ratio_s[0] * ratio_s[1];
+        accept = dr.u_acc < fmin(1.0, fabs(R));
+        finite = isfinite(R);
+        near = (sizeof(T) == 4) && finite &&
+               fabs(dr.u_acc - fabs(R)) < (tie_guard > 0.0 ? tie_guard : kTieGuard) * fmax(dr.u_acc, fabs(R));
+      }
       if (!finite) accept = false;
       const bool forced = (sizeof(T) == 4) && forced_t == t;
       int dec;
@@ -876,8 +892,7 @@ __device__ __forceinline__ void proposals_body(Chain<T>* chains) {
         R = d.forced_R;
         finite = true;
         dec = accept ? 1 : 0;
-      } else if (sizeof(T) == 4 && tie_guard > 0.0 && finite &&
-                 fabs(dr.u_acc - fabs(R)) < tie_guard * fmax(dr.u_acc, fabs(R))) {
+      } else if (sizeof(T) == 4 && tie_guard > 0.0 && finite && near) {
         // near tie in the float32 form: the block ends before this proposal,
         // which is decided in FP64 after the flush
         d.tie_pending = 1;
@@ -887,8 +902,7 @@ __device__ __forceinline__ void proposals_body(Chain<T>* chains) {
         dec = 2;
       } else {
         dec = accept ? 1 : 0;
-        if (sizeof(T) == 4 && tie_guard == 0.0 && finite &&
-            fabs(dr.u_acc - fabs(R)) < kTieGuard * fmax(dr.u_acc, fabs(R)))
+        if (sizeof(T) == 4 && tie_guard == 0.0 && finite && near)
           ties++;  // detection only (FP64 re-evaluation off)
       }
       if (dec != 2) {
