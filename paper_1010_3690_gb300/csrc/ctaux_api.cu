@@ -304,8 +304,7 @@ ctaux_status build_chains(ctaux_ctx* ctx) {
           if (err != cudaSuccess)
             return set_err(ctx, CTAUX_ENOMEM, "device allocation failed: %s", cudaGetErrorString(err));
           me = encode_prep_maps(&host_maps[2 * ci + spin], reinterpret_cast<float*>(c.Cpan[spin]),
-                                reinterpret_cast<float*>(c.Bpan[spin]), reinterpret_cast<float*>(c.Gcol[spin]),
-                                (int)KR, reinterpret_cast<float*>(c.N[0][spin]),
+                                reinterpret_cast<float*>(c.Bpan[spin]), (int)KR, reinterpret_cast<float*>(c.N[0][spin]),
                                 reinterpret_cast<float*>(c.N[1][spin]), c.NT[0][spin], c.NT[1][spin], c.ld);
           if (me != cudaSuccess)
             return set_err(ctx, CTAUX_ECUDA, "prep tensor map encoding failed (%s)", cudaGetErrorString(me));

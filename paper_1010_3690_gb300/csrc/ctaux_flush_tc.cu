@@ -462,20 +462,19 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 }  // namespace
 
 // Host: the prep's TMA descriptors of one (chain, spin): rows of ld float32
-// (the panels C, B and the G columns with panel_rows rows; both buffers of N
+// (the panels C and B with panel_rows rows; both buffers of N
 // and of N^T with ld rows), boxes of 128 rows x kTcBK float32, 64-byte swizzle.
-cudaError_t encode_prep_maps(TcMaps* out, float* cpan, float* bpan, float* gcol, int panel_rows,
+cudaError_t encode_prep_maps(TcMaps* out, float* cpan, float* bpan, int panel_rows,
                              float* n0, float* n1, float* nt0, float* nt1, int ld) {
   PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
   if (!encode) return cudaErrorNotSupported;
   const cuuint32_t estr[2] = {1, 1};
   const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(float)};
   const cuuint32_t box[2] = {(cuuint32_t)kTcBK, 128u};
-  float* ptrs[7] = {cpan, bpan, gcol, n0, n1, nt0, nt1};
-  CUtensorMap* maps[7] = {&out->cpan, &out->bpan, &out->gcol, &out->nb[0], &out->nb[1],
-                          &out->nt[0], &out->nt[1]};
-  for (int i = 0; i < 7; ++i) {
-    const cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)(i < 3 ? panel_rows : ld)};
+  float* ptrs[6] = {cpan, bpan, n0, n1, nt0, nt1};
+  CUtensorMap* maps[6] = {&out->cpan, &out->bpan, &out->nb[0], &out->nb[1], &out->nt[0], &out->nt[1]};
+  for (int i = 0; i < 6; ++i) {
+    const cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)(i < 2 ? panel_rows : ld)};
     const CUresult r = encode(maps[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, ptrs[i], dims, strides,
                               box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);

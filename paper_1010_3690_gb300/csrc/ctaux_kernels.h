@@ -32,7 +32,7 @@ struct TcMaps {
   CUtensorMap nb1[2], nbg[2];
   // tensor-core prep: the panels' rows and N, N^T as K-major rows (boxes of
   // 128 rows x kTcBK float32, 64-byte swizzle)
-  CUtensorMap cpan, bpan, gcol, nb[2], nt[2];
+  CUtensorMap cpan, bpan, nb[2], nt[2];
 };
 
 enum { PH_RTILDE = 0, PH_GCOL_OLD = 1, PH_GCOL_NEW = 2, PH_FLUSH = 3, PH_MEAS = 4, PH_COUNT = 5 };
@@ -197,7 +197,7 @@ int tc_smem_bytes();
 cudaError_t configure_prep_tc();
 void launch_prep_tc(Chain<float>* dchains, const TcMaps* maps, const LaunchShape& ls,
                     cudaStream_t st);
-cudaError_t encode_prep_maps(TcMaps* out, float* cpan, float* bpan, float* gcol, int panel_rows,
+cudaError_t encode_prep_maps(TcMaps* out, float* cpan, float* bpan, int panel_rows,
                              float* n0, float* n1, float* nt0, float* nt1, int ld);
 cudaError_t configure_flush_tc();
 void launch_flush_tc(Chain<float>* dchains, const TcMaps* maps, const LaunchShape& ls,

@@ -3,10 +3,9 @@
 // vertices, and the columns of G = N_ext G0 for them):
 //   product 0: R~[a][j]     = sum_{l<n} C[a][l] N[l][j]            -> N_ext[n + a][j]
 //   product 1: G[i][a]      = sum_{l<n} N[i][l] B[l][a]             -> Gcol[a][i], i < n
-//   product 2: G[n + a][b] += sum_{l<n} C[a][l] G[l][b]             (onto G0(new_a, new_b))
-// (launch_prep_tc runs products 0 and 1; the block runs product 2, a few
-// k x k tiles with the long inner dimension n, on the CUDA cores split over K)
-// with C = G0(new, old)(e^{V_old} - 1) and B = G0(old, new) (the gathered
+// (the third prep product, G[n + a][b] += sum_{l<n} C[a][l] G[l][b], is a few
+// k x k tiles over the long inner dimension n: the block runs it on the CUDA
+// cores, split over K) with C = G0(new, old)(e^{V_old} - 1) and B = G0(old, new) (the gathered
 // panels), as 128 x 128 output tiles of a tcgen05 GEMM with the split 3xTF32
 // product of Ootomo & Yokota (2022): hi*hi in one float32 TMEM accumulator,
 // hi*lo + lo*hi in a second one, added in the epilogue.  The split truncates
@@ -77,35 +76,29 @@ __device__ __forceinline__ int prep_items_of(const Dyn& d, int prod) {
   if (d.status) return 0;
   int M, N, K;
   prep_dims(d, prod, M, N, K);
-  if (M == 0 || N == 0 || K == 0) return 0;   // K = 0: product 2's output is its input
+  if (M == 0 || N == 0 || K == 0) return 0;   // no old vertices or no insertions
   return 2 * ((M + 127) / 128) * ((N + 127) / 128);
 }
 
-__device__ __forceinline__ int prep_items(const Dyn& d, int p_lo, int p_hi) {
-  int t = 0;
-  for (int p = p_lo; p < p_hi; ++p) t += prep_items_of(d, p);
-  return t;
+__device__ __forceinline__ int prep_items(const Dyn& d) {
+  return prep_items_of(d, 0) + prep_items_of(d, 1);
 }
 
 __device__ __forceinline__ PrepItem prep_item(Chain<float>* chains, const int* off, int n_chains,
-                                              int p_lo, int p_hi, int w) {
+                                              int w) {
   PrepItem it;
   it.ci = find_chain(off, n_chains, w);
   const Dyn& d = *chains[it.ci].dyn;
   int l = w - off[it.ci];
-  it.prod = p_lo;
-  for (int p = p_lo; p < p_hi; ++p) {
-    const int k = prep_items_of(d, p);
-    it.prod = p;
-    if (l < k) break;
-    l -= k;
-  }
+  const int k0 = prep_items_of(d, 0);
+  it.prod = l < k0 ? 0 : 1;
+  if (it.prod == 1) l -= k0;
   prep_dims(d, it.prod, it.M, it.N, it.K);
   const int tm = (it.M + 127) / 128, tn = (it.N + 127) / 128;
   it.spin = l / (tm * tn);
   const int tile = l % (tm * tn);
   // consecutive items share the operand that is the same for a whole row
-  // (product 0, 2: C) or column (product 1: B) of tiles
+  // (product 0: C) or column (product 1: B) of tiles
   if (it.prod == 1) {
     it.m0 = (tile % tm) * 128;
     it.n0 = (tile / tm) * 128;
@@ -140,14 +133,13 @@ __device__ __forceinline__ void split_group(const float4 x, int off_in_tile, int
 
 }  // namespace
 
-// Products p_lo .. p_hi - 1 of every chain.  Barrier completion c of an
+// Products 0 and 1 of every chain.  Barrier completion c of an
 // mbarrier has parity c & 1.
 __global__ void __launch_bounds__(kPrepThreads, 1) k_prep_tc(Chain<float>* chains, int n_chains,
-                                                             const TcMaps* maps, int p_lo, int p_hi,
-                                                             uint32_t wl) {
+                                                             const TcMaps* maps, uint32_t wl) {
   __shared__ int off[kMaxChains + 1];
   for (int ci = threadIdx.x; ci < n_chains; ci += blockDim.x)
-    off[ci] = prep_items(*chains[ci].dyn, p_lo, p_hi);
+    off[ci] = prep_items(*chains[ci].dyn);
   __syncthreads();
   block_exclusive_scan(off, n_chains);
   const int total = off[n_chains];
@@ -206,11 +198,11 @@ __global__ void __launch_bounds__(kPrepThreads, 1) k_prep_tc(Chain<float>* chain
   if (warp == 0 && lane == 0) {
     // ---- TMA producer
     for (int w = blockIdx.x; w < total && !*err_s; w += gridDim.x) {
-      const PrepItem t = prep_item(chains, off, n_chains, p_lo, p_hi, w);
+      const PrepItem t = prep_item(chains, off, n_chains, w);
       const TcMaps& mp = maps[t.ci * 2 + t.spin];
       const int buf = chains[t.ci].dyn->buf;
       const CUtensorMap* ma = (t.prod == 1) ? &mp.nt[buf] : &mp.cpan;
-      const CUtensorMap* mb = (t.prod == 0) ? &mp.nb[buf] : (t.prod == 1 ? &mp.bpan : &mp.gcol);
+      const CUtensorMap* mb = (t.prod == 0) ? &mp.nb[buf] : &mp.bpan;
       const int nk = (t.K + kBK - 1) / kBK;
       bool ok = true;
       for (int kc = 0; kc < nk; ++kc) {
@@ -238,7 +230,7 @@ __global__ void __launch_bounds__(kPrepThreads, 1) k_prep_tc(Chain<float>* chain
     uint32_t taken = 0;
     for (int w = blockIdx.x; w < total; w += gridDim.x) {
       if (__any_sync(0xffffffffu, *err_s != 0)) break;
-      const PrepItem t = prep_item(chains, off, n_chains, p_lo, p_hi, w);
+      const PrepItem t = prep_item(chains, off, n_chains, w);
       const int nk = (t.K + kBK - 1) / kBK;
       bool ok = true;
       for (int kc = 0; kc < nk; ++kc) {
@@ -284,7 +276,7 @@ __global__ void __launch_bounds__(kPrepThreads, 1) k_prep_tc(Chain<float>* chain
     uint32_t taken = 0, q = 0;
     bool ok = true;
     for (int w = blockIdx.x; w < total && ok && !*err_s; w += gridDim.x) {
-      const PrepItem t = prep_item(chains, off, n_chains, p_lo, p_hi, w);
+      const PrepItem t = prep_item(chains, off, n_chains, w);
       const int nk = (t.K + kBK - 1) / kBK;
       for (int k0 = 0; k0 < nk && ok; k0 += kSegChunks) {
         const uint32_t b = q & 1, ub = q >> 1;
@@ -328,7 +320,7 @@ __global__ void __launch_bounds__(kPrepThreads, 1) k_prep_tc(Chain<float>* chain
     uint32_t q = 0;
     for (int w = blockIdx.x; w < total; w += gridDim.x) {
       if (__any_sync(0xffffffffu, *err_s != 0)) break;
-      const PrepItem t = prep_item(chains, off, n_chains, p_lo, p_hi, w);
+      const PrepItem t = prep_item(chains, off, n_chains, w);
       const Chain<float>& c = chains[t.ci];
       const Dyn& d = *c.dyn;
       const int ld = c.ld, n = d.n;
@@ -376,8 +368,7 @@ __global__ void __launch_bounds__(kPrepThreads, 1) k_prep_tc(Chain<float>* chain
           if (col >= t.N) break;
           const float v = acc_s[j * 128 + rl];
           if (t.prod == 0) Nb[(long)col * ld + n + row] = v;
-          else if (t.prod == 1) Gc[(long)col * ld + row] = v;
-          else Gc[(long)col * ld + n + row] += v;
+          else Gc[(long)col * ld + row] = v;
         }
       }
       __syncwarp();
@@ -415,8 +406,7 @@ void launch_prep_tc(Chain<float>* dchains, const TcMaps* maps, const LaunchShape
                     cudaStream_t st) {
   const int lim = ls.tc_wait_limit;
   const uint32_t wl = lim > 0 ? (uint32_t)lim : lim < 0 ? (uint32_t)(-(int64_t)lim) : kWaitLimit;
-  k_prep_tc<<<ls.tc_ctas, kPrepThreads, prep_tc_smem_bytes(), st>>>(dchains, ls.n_chains, maps, 0,
-                                                                    2, wl);
+  k_prep_tc<<<ls.tc_ctas, kPrepThreads, prep_tc_smem_bytes(), st>>>(dchains, ls.n_chains, maps, wl);
 }
 
 }  // namespace ctaux
