@@ -653,6 +653,9 @@ def measure_form(args, pk, torch, dist, chains, meta, refresh, form, local, worl
     def accepted_total():
         return sum(sum(ctx.stats(i)["accepted"]) for i in range(len(chains)))
 
+    def proposals_total():
+        return sum(sum(ctx.stats(i)["proposals"]) for i in range(len(chains)))
+
     def refreshes_total():
         return sum(ctx.stats(i)["refreshes"] for i in range(len(chains)))
 
@@ -660,6 +663,7 @@ def measure_form(args, pk, torch, dist, chains, meta, refresh, form, local, worl
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     acc0 = accepted_total()
+    prop0 = proposals_total()
     ref0 = refreshes_total()
     _, kern0 = ctx.phase_times()
     ties0 = sum(ctx.stats(i)["near_ties"] for i in range(len(chains)))
@@ -680,6 +684,8 @@ def measure_form(args, pk, torch, dist, chains, meta, refresh, form, local, worl
     clk = clocks.stop()
     total_ms = sum(s_.elapsed_time(e_) for s_, e_ in zip(starts, ends))
     acc = accepted_total() - acc0
+    props = proposals_total() - prop0
+    accept_rate = acc / max(1, props)    # this rank's chains
     n_refreshes = (refreshes_total() - ref0) // max(1, len(chains))
     _, kern1 = ctx.phase_times()
     kernels = int((kern1 - kern0).sum())
@@ -778,6 +784,12 @@ def measure_form(args, pk, torch, dist, chains, meta, refresh, form, local, worl
             roofline[key] = r[key]
     if traffic and r.get("alg_bytes_per_step"):
         roofline["traffic_over_alg_bytes"] = traffic / r["alg_bytes_per_step"]
+    # fraction of its roofline for every phase that has one
+    phase_fracs = {}
+    for i in range(names.index("tie_refine")):
+        ri = roof(i)
+        if ri.get("peak") and ri.get("achieved") is not None:
+            phase_fracs[names[i]] = ri["achieved"] / ri["peak"]
     fr = roof(names.index("flush_gemm"))
     flush_roof = {"bound": fr["bound"], "achieved": fr["achieved"], "peak": fr["peak"],
                   "unit": fr["unit"], "frac": fr["achieved"] / fr["peak"],
@@ -820,7 +832,11 @@ def measure_form(args, pk, torch, dist, chains, meta, refresh, form, local, worl
             "phase_pass_steps": prof_steps,
             "refreshes_in_timed_region": int(n_refreshes),
             "gpu_launches": kernels,
-            "accept_rate": acc / max(1, steps * sum(c.k_max for c in chains) * world),
+            "accept_rate": accept_rate,
+            # per GPU; a sweep is one block (k_max proposals) of every chain
+            "proposals_per_s": props / (total_ms / 1e3),
+            "sweeps_per_s": steps * len(chains) / (total_ms / 1e3),
+            "phase_roofline_frac": phase_fracs,
             "drift_max_last_refresh": max(ctx.stats(i)["last_drift_max"] for i in range(len(chains))),
             # the same relative to max |N| of each chain's fresh N
             "drift_rel_max_last_refresh": max(ctx.stats(i)["last_drift_rel"]
