@@ -55,3 +55,32 @@ def test_init_rejects_bad_arguments_without_a_gpu():
     assert ei.value.code == 1
     with pytest.raises(ctaux.CtauxError):
         ctaux.Context([ch], p_insert=0.9, p_flip=0.3)
+
+
+def test_struct_layouts_match_the_c_compiler(tmp_path):
+    """Every field of the ctypes mirrors sits at the offset the C compiler gives
+    it in include/ctaux.h, and the structs have the same sizes (host C, no GPU)."""
+    import shutil
+    import subprocess
+    from paper_1010_3690_gb300 import ctaux
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    pairs = [("ctaux_chain_params", ctaux.ChainParams), ("ctaux_params", ctaux.Params),
+             ("ctaux_stats", ctaux.Stats), ("ctaux_trace_rec", ctaux.TraceRec)]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ctaux.h"', "int main(void) {"]
+    expect = []
+    for cname, cls in pairs:
+        lines.append(f'  printf("%zu\\n", sizeof({cname}));')
+        expect.append(ctypes.sizeof(cls))
+        for fname, _ in cls._fields_:
+            lines.append(f'  printf("%zu\\n", offsetof({cname}, {fname}));')
+            expect.append(getattr(cls, fname).offset)
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True,
+                                          text=True).stdout.split()]
+    assert got == expect
