@@ -203,7 +203,11 @@ ctaux_status ctaux_init(const ctaux_params *params, ctaux_ctx **out);
  * products (Sec. IV A), k_max proposals with Gamma growth (Secs. III D, IV B),
  * the Woodbury flush with compaction (Sec. IV C), then, if `measure` is
  * non-zero, one G(tau) measurement (Sec. IV D), and every refresh_every
- * blocks a from-scratch FP64 recomputation of N. */
+ * blocks a from-scratch FP64 recomputation of N.  With use_graph, a block's
+ * measurement runs on a second stream beside the next block, and the last
+ * block's measurement is launched by the next call that reads or changes the
+ * context (another ctaux_sweep, ctaux_synchronize, ctaux_measure_G, ...), on
+ * the stream of this call; the results equal the serial order bit for bit. */
 ctaux_status ctaux_sweep(ctaux_ctx *ctx, int n_sweeps, int measure, void *cuda_stream);
 
 /* G(tau) measurement of one chain (Sec. IV D; the estimator is the row of an
